@@ -1,0 +1,701 @@
+/*
+ * FP64 CPU oracle of the Probe-Particle Model hot path (LJ + point charges).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the package smoke check and
+ * the CPU-baseline leg of the benchmark load this library.  The product path
+ * (the CUDA library and its Python binding) never calls it, and the two share
+ * no code, header, table or constant.
+ *
+ * Everything here is the plain definition of the discrete model, written as
+ * loops in double precision:
+ *   - force-field grid by direct pair sum over all sample atoms (Sec. 5.1.1,
+ *     step 1), pair terms from Eq. (LJ) with the mixing rules R_iPP = R_i+R_PP,
+ *     e_iPP = sqrt(e_i e_PP) and Eq. (point-charge electrostatics), F = -grad E
+ *     (Sec. 2.2);
+ *   - trilinear interpolation of the force grid (Sec. 5.1.1, step 2);
+ *   - tip springs of Eq. (F_tip), total PP force of Eq. (F_PP), FIRE
+ *     relaxation (Sec. 5.1.1, step 2; Bitzek et al. 2006), warm-started from
+ *     the previous height, followed by a Newton polish with the exact 3x3
+ *     Jacobian to |G| < 1e-11 eV/A;
+ *   - tip force Fz = -F^T_{R,z} at the relaxed PP (Sec. 2.1);
+ *   - frequency shift of Eq. (df) by product integration of a piecewise
+ *     linear Fz against the kernel u / sqrt(a^2 - u^2), a = A/2;
+ *   - the implicit-function adjoint of all of the above (the paper has no
+ *     gradients; this is the derivative of the same discrete model).
+ *
+ * Readings of the paper that the code fixes (all units: A, eV, e):
+ *   d0 = (d0x, d0y, -sqrt(R0^2 - d0x^2 - d0y^2)): the PP hangs below the tip;
+ *   per-pair r^2 floor (core_frac * R_iPP)^2, displacement left unscaled;
+ *   grid nodes x_i = x0 + i*dx, periodic in x,y when periodic_xy, clamped in z
+ *   (cell index in [0, nz-2], fraction in [0,1]);
+ *   spring constants are given in N/m and converted with 1 eV/A^2 = 16.02176634
+ *   N/m; Coulomb constant 14.3996454784 eV*A/e^2.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_KE 14.3996454784          /* Coulomb constant, eV*A/e^2 */
+#define OR_EVA2_TO_NM 16.02176634    /* 1 eV/A^2 in N/m (SI: 1 eV = 1.602176634e-19 J) */
+#define OR_NM_TO_EVA2 (1.0 / OR_EVA2_TO_NM) /* 1 N/m in eV/A^2 */
+#define OR_PI 3.14159265358979323846
+
+typedef struct { int n; const double *x, *y, *z, *R, *eps, *q; } or_atoms;
+typedef struct { double R_pp, eps_pp, Q, coul_rc; int min_image; double core_frac; } or_probe;
+typedef struct { int nx, ny, nz; double x0, y0, z0, dx, dy, dz; int periodic_xy; } or_grid;
+typedef struct { double kx, ky, kR, R0, d0x, d0y; } or_tip; /* springs in N/m */
+typedef struct { int nx, ny, nz; double x0, y0, px, py, z_top, dz; } or_scan;
+typedef struct {
+    int max_iter; double ftol, dt0, dt_max, f_inc, f_dec, alpha0, f_alpha, mass; int n_min;
+} or_fire;
+typedef struct { double A_pp, k, f0; } or_df; /* A (peak-to-peak), N/m, Hz */
+
+static void set_threads(int nthreads) {
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+}
+
+int or_max_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* ------------------------------------------------------------------ pairs */
+
+/* One sample atom seen from point r.  The pair force is S * delta. */
+typedef struct {
+    double d[3];        /* delta = r - r_i (minimum image when enabled) */
+    double r;           /* distance after the core floor */
+    int clamped;        /* the floor replaced |delta| */
+    double S, E;        /* force factor and energy */
+    double dSdr;        /* dS/dr at fixed R_iPP */
+    double dSdR;        /* total dS/dR_iPP, including the floor's R-dependence */
+    double S_lj_e;      /* LJ part of S per unit e_iPP */
+    double S_el_qq;     /* Coulomb part of S per unit k_e Q q_i */
+    double e_ij;        /* e_iPP */
+} or_pair;
+
+static void pair_eval(const or_atoms* A, int i, const or_probe* P, double Lx, double Ly,
+                      const double pt[3], or_pair* o) {
+    double dx = pt[0] - A->x[i], dy = pt[1] - A->y[i], dz = pt[2] - A->z[i];
+    if (P->min_image) {
+        dx -= Lx * nearbyint(dx / Lx);
+        dy -= Ly * nearbyint(dy / Ly);
+    }
+    o->d[0] = dx; o->d[1] = dy; o->d[2] = dz;
+    const double Rij = A->R[i] + P->R_pp;              /* mixing rule, Eq. (LJ) */
+    const double eij = sqrt(A->eps[i] * P->eps_pp);    /* mixing rule, Eq. (LJ) */
+    const double qq = OR_KE * P->Q * A->q[i];          /* Eq. (point charges) */
+    const double r2 = dx * dx + dy * dy + dz * dz;
+    const double rmin = P->core_frac * Rij;
+    double r;
+    if (r2 < rmin * rmin) { r = rmin; o->clamped = 1; }
+    else { r = sqrt(r2); o->clamped = 0; }
+    o->r = r;
+    o->e_ij = eij;
+    /* E_LJ = e [(R/r)^12 - 2 (R/r)^6];  F = -dE/dr rhat = 12 e [(R/r)^12 - (R/r)^6] / r^2 * delta */
+    const double s6 = pow(Rij / r, 6.0);
+    const double s12 = s6 * s6;
+    o->S_lj_e = 12.0 * (s12 - s6) / (r * r);
+    const double E_lj = eij * (s12 - 2.0 * s6);
+    const double dSlj_dr = 12.0 * eij * (-14.0 * s12 + 8.0 * s6) / (r * r * r);
+    const double dSlj_dR = 12.0 * eij * (12.0 * s12 - 6.0 * s6) / (Rij * r * r);
+    /* E_el = qq / r (optionally shifted-force truncated at rc) */
+    double c, e_el, dc_dr;
+    if (P->coul_rc > 0.0) {
+        const double rc = P->coul_rc;
+        if (r < rc) {
+            c = 1.0 / (r * r * r) - 1.0 / (rc * rc * r);
+            e_el = 1.0 / r - 1.0 / rc + (r - rc) / (rc * rc);
+            dc_dr = -3.0 / (r * r * r * r) + 1.0 / (rc * rc * r * r);
+        } else {
+            c = 0.0; e_el = 0.0; dc_dr = 0.0;
+        }
+    } else {
+        c = 1.0 / (r * r * r);
+        e_el = 1.0 / r;
+        dc_dr = -3.0 / (r * r * r * r);
+    }
+    o->S_el_qq = c;
+    o->S = eij * o->S_lj_e + qq * c;
+    o->E = E_lj + qq * e_el;
+    o->dSdr = dSlj_dr + qq * dc_dr;
+    o->dSdR = dSlj_dR + (o->clamped ? o->dSdr * P->core_frac : 0.0);
+}
+
+/* Sample force and energy at r by direct sum (the definition of a grid node value). */
+static int sample_point(const or_atoms* A, const or_probe* P, double Lx, double Ly,
+                        const double r[3], double out[4], double Js[9]) {
+    double F[3] = {0, 0, 0}, E = 0.0;
+    int core = 0;
+    if (Js) memset(Js, 0, 9 * sizeof(double));
+    for (int i = 0; i < A->n; ++i) {
+        or_pair p;
+        pair_eval(A, i, P, Lx, Ly, r, &p);
+        for (int a = 0; a < 3; ++a) F[a] += p.S * p.d[a];
+        E += p.E;
+        core |= p.clamped;
+        if (Js) {
+            for (int a = 0; a < 3; ++a) {
+                Js[a * 3 + a] += p.S;
+                if (!p.clamped && p.r > 0.0)
+                    for (int b = 0; b < 3; ++b) Js[a * 3 + b] += p.dSdr * p.d[a] * p.d[b] / p.r;
+            }
+        }
+    }
+    out[0] = F[0]; out[1] = F[1]; out[2] = F[2]; out[3] = E;
+    return core;
+}
+
+static void grid_period(const or_grid* G, double* Lx, double* Ly) {
+    *Lx = G->nx * G->dx;
+    *Ly = G->ny * G->dy;
+}
+
+/* Force-field grid, layout [nz][ny][nx][4] = (Fx, Fy, Fz, E); core[node] = 1 where a pair hit the floor. */
+int or_make_ff(const or_atoms* A, const or_probe* P, const or_grid* G, double* ff,
+               unsigned char* core, int nthreads) {
+    if (!A || !P || !G || !ff || G->nx < 2 || G->ny < 2 || G->nz < 2) return 1;
+    set_threads(nthreads);
+    double Lx, Ly;
+    grid_period(G, &Lx, &Ly);
+    const long nxy = (long)G->nx * G->ny;
+    const long total = nxy * G->nz;
+#pragma omp parallel for schedule(static)
+    for (long g = 0; g < total; ++g) {
+        const long k = g / nxy, rem = g % nxy, j = rem / G->nx, i = rem % G->nx;
+        double r[3] = {G->x0 + i * G->dx, G->y0 + j * G->dy, G->z0 + k * G->dz};
+        int c = sample_point(A, P, Lx, Ly, r, ff + 4 * g, NULL);
+        if (core) core[g] = (unsigned char)c;
+    }
+    return 0;
+}
+
+/* Sample force/energy at arbitrary points pts[npts][3] (grid-free). */
+int or_ff_points(const or_atoms* A, const or_probe* P, const or_grid* G, int npts,
+                 const double* pts, double* out, unsigned char* core, int nthreads) {
+    if (!A || !P || !G || npts < 0) return 1;
+    set_threads(nthreads);
+    double Lx, Ly;
+    grid_period(G, &Lx, &Ly);
+#pragma omp parallel for schedule(static)
+    for (int t = 0; t < npts; ++t) {
+        int c = sample_point(A, P, Lx, Ly, pts + 3 * t, out + 4 * t, NULL);
+        if (core) core[t] = (unsigned char)c;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------ interpolation */
+
+static void axis_locate(double p, double o, double h, int n, int periodic,
+                        long* i0, long* i1, double* t, double* dtdp) {
+    const double f = (p - o) / h;
+    const double fl = floor(f);
+    long i = (long)fl;
+    double tt = f - fl, d = 1.0 / h;
+    if (periodic) {
+        long m = i % n;
+        if (m < 0) m += n;
+        *i0 = m;
+        *i1 = (m + 1) % n;
+    } else {
+        if (i < 0) i = 0;
+        if (i > n - 2) i = n - 2;
+        tt = f - (double)i;
+        if (tt < 0.0) { tt = 0.0; d = 0.0; }
+        else if (tt > 1.0) { tt = 1.0; d = 0.0; }
+        *i0 = i;
+        *i1 = i + 1;
+    }
+    *t = tt;
+    *dtdp = d;
+}
+
+/* Trilinear interpolant of (Fx,Fy,Fz) at p and, optionally, its exact Jacobian
+ * J[a*3+b] = dF_a/dp_b and the 8 corner node indices and weights. */
+static void interp(const double* ff, const or_grid* G, const double p[3], double F[3], double* J,
+                   long node[8], double w8[8]) {
+    long ix[2], iy[2], iz[2];
+    double tx, ty, tz, gx, gy, gz;
+    axis_locate(p[0], G->x0, G->dx, G->nx, G->periodic_xy, &ix[0], &ix[1], &tx, &gx);
+    axis_locate(p[1], G->y0, G->dy, G->ny, G->periodic_xy, &iy[0], &iy[1], &ty, &gy);
+    axis_locate(p[2], G->z0, G->dz, G->nz, 0, &iz[0], &iz[1], &tz, &gz);
+    const double wx[2] = {1.0 - tx, tx}, wy[2] = {1.0 - ty, ty}, wz[2] = {1.0 - tz, tz};
+    const double sx[2] = {-gx, gx}, sy[2] = {-gy, gy}, sz[2] = {-gz, gz};
+    F[0] = F[1] = F[2] = 0.0;
+    if (J) memset(J, 0, 9 * sizeof(double));
+    int c = 0;
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b)
+            for (int e = 0; e < 2; ++e, ++c) {
+                const long g = (iz[a] * G->ny + iy[b]) * G->nx + ix[e];
+                const double* v = ff + 4 * g;
+                const double w = wz[a] * wy[b] * wx[e];
+                for (int m = 0; m < 3; ++m) F[m] += w * v[m];
+                if (J) {
+                    const double dw[3] = {wz[a] * wy[b] * sx[e], wz[a] * sy[b] * wx[e], sz[a] * wy[b] * wx[e]};
+                    for (int m = 0; m < 3; ++m)
+                        for (int n = 0; n < 3; ++n) J[m * 3 + n] += dw[n] * v[m];
+                }
+                if (node) { node[c] = g; w8[c] = w; }
+            }
+}
+
+int or_interp_points(const double* ff, const or_grid* G, int npts, const double* pts,
+                     double* F, double* J) {
+    for (int t = 0; t < npts; ++t) interp(ff, G, pts + 3 * t, F + 3 * t, J ? J + 9 * t : NULL, NULL, NULL);
+    return 0;
+}
+
+/* --------------------------------------------------------------- tip model */
+
+typedef struct { double kx, ky, kR, R0, d0x, d0y, d0z; } tip_si; /* eV/A^2 */
+
+static tip_si tip_units(const or_tip* T) {
+    tip_si t;
+    t.kx = T->kx * OR_NM_TO_EVA2;
+    t.ky = T->ky * OR_NM_TO_EVA2;
+    t.kR = T->kR * OR_NM_TO_EVA2;
+    t.R0 = T->R0;
+    t.d0x = T->d0x;
+    t.d0y = T->d0y;
+    t.d0z = -sqrt(fmax(T->R0 * T->R0 - T->d0x * T->d0x - T->d0y * T->d0y, 0.0));
+    return t;
+}
+
+/* Eq. (F_tip): F^T = -k_R (|d| - R0) d/|d| - k_xy (.) (d - d0), k_xy = (kx, ky, 0). */
+static void tip_force(const tip_si* t, const double d[3], double F[3], double* J) {
+    const double dn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    const double s = -t->kR * (dn - t->R0) / dn;
+    F[0] = s * d[0] - t->kx * (d[0] - t->d0x);
+    F[1] = s * d[1] - t->ky * (d[1] - t->d0y);
+    F[2] = s * d[2];
+    if (J) {
+        /* dF/dd = -kR [(1 - R0/|d|) I + R0 d d^T / |d|^3] - diag(kx, ky, 0) */
+        const double a = -t->kR * (1.0 - t->R0 / dn);
+        const double b = -t->kR * t->R0 / (dn * dn * dn);
+        for (int m = 0; m < 3; ++m)
+            for (int n = 0; n < 3; ++n) J[m * 3 + n] = (m == n ? a : 0.0) + b * d[m] * d[n];
+        J[0] -= t->kx;
+        J[4] -= t->ky;
+    }
+}
+
+/* Tip force on the cantilever, Fz = -F^T_{R,z} = kR (|d| - R0) d_z / |d| (Sec. 2.1). */
+static double tip_fz(const tip_si* t, const double d[3]) {
+    const double dn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    return t->kR * (dn - t->R0) * d[2] / dn;
+}
+
+/* ---------------------------------------------------------- PP relaxation */
+
+typedef struct {
+    const double* ff;   /* grid mode when non-NULL */
+    const or_grid* G;
+    const or_atoms* A;  /* direct (grid-free) mode when ff == NULL */
+    const or_probe* P;
+    double Lx, Ly;
+    tip_si tip;
+} or_model;
+
+/* Total PP force G(p) = F^T + F^S of Eq. (F_PP) and optionally its Jacobian. */
+static void total_force(const or_model* M, const double anchor[3], const double p[3],
+                        double Gv[3], double* J) {
+    double d[3] = {p[0] - anchor[0], p[1] - anchor[1], p[2] - anchor[2]};
+    double Ft[3], Fs[3], Jt[9], Js[9];
+    tip_force(&M->tip, d, Ft, J ? Jt : NULL);
+    if (M->ff) {
+        interp(M->ff, M->G, p, Fs, J ? Js : NULL, NULL, NULL);
+    } else {
+        double o[4];
+        sample_point(M->A, M->P, M->Lx, M->Ly, p, o, J ? Js : NULL);
+        Fs[0] = o[0]; Fs[1] = o[1]; Fs[2] = o[2];
+    }
+    for (int m = 0; m < 3; ++m) Gv[m] = Ft[m] + Fs[m];
+    if (J)
+        for (int m = 0; m < 9; ++m) J[m] = Jt[m] + Js[m];
+}
+
+static double norm3(const double v[3]) { return sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]); }
+
+/* FIRE (Bitzek et al. 2006) with semi-implicit Euler steps.  Each iteration:
+ * evaluate G; stop if |G| < ftol; from the second iteration on, if G.v > 0 mix
+ * v <- (1-alpha) v + alpha |v| G/|G| and, after more than n_min such steps in a
+ * row, grow dt (capped at dt_max) and shrink alpha; if G.v <= 0 zero v, halve
+ * dt and reset alpha; then v += dt G / m, p += dt v.  Returns the number of
+ * position updates; *res gets the last evaluated |G|. */
+static int fire_relax(const or_model* M, const or_fire* Fp, const double anchor[3], double p[3],
+                      double* res) {
+    double v[3] = {0, 0, 0}, Gv[3];
+    double dt = Fp->dt0, alpha = Fp->alpha0;
+    int npos = 0, it = 0;
+    double g = 0.0;
+    for (it = 0; it < Fp->max_iter; ++it) {
+        total_force(M, anchor, p, Gv, NULL);
+        g = norm3(Gv);
+        if (g < Fp->ftol) break;
+        if (it > 0) {
+            const double P = Gv[0] * v[0] + Gv[1] * v[1] + Gv[2] * v[2];
+            if (P > 0.0) {
+                const double vn = norm3(v);
+                for (int m = 0; m < 3; ++m) v[m] = (1.0 - alpha) * v[m] + alpha * vn * Gv[m] / g;
+                if (npos > Fp->n_min) {
+                    dt = fmin(dt * Fp->f_inc, Fp->dt_max);
+                    alpha *= Fp->f_alpha;
+                }
+                ++npos;
+            } else {
+                v[0] = v[1] = v[2] = 0.0;
+                dt *= Fp->f_dec;
+                alpha = Fp->alpha0;
+                npos = 0;
+            }
+        }
+        for (int m = 0; m < 3; ++m) {
+            v[m] += dt * Gv[m] / Fp->mass;
+            p[m] += dt * v[m];
+        }
+    }
+    if (it == Fp->max_iter) {
+        total_force(M, anchor, p, Gv, NULL);
+        g = norm3(Gv);
+    }
+    *res = g;
+    return it;
+}
+
+/* Solve the 3x3 system A x = b by Gaussian elimination with partial pivoting. */
+static int solve3(const double* Ain, const double* b, double* x) {
+    double A[3][4];
+    for (int m = 0; m < 3; ++m) {
+        for (int n = 0; n < 3; ++n) A[m][n] = Ain[m * 3 + n];
+        A[m][3] = b[m];
+    }
+    for (int c = 0; c < 3; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < 3; ++r)
+            if (fabs(A[r][c]) > fabs(A[piv][c])) piv = r;
+        if (A[piv][c] == 0.0) return 1;
+        if (piv != c)
+            for (int n = 0; n < 4; ++n) { double t = A[c][n]; A[c][n] = A[piv][n]; A[piv][n] = t; }
+        for (int r = c + 1; r < 3; ++r) {
+            const double f = A[r][c] / A[c][c];
+            for (int n = c; n < 4; ++n) A[r][n] -= f * A[c][n];
+        }
+    }
+    for (int m = 2; m >= 0; --m) {
+        double s = A[m][3];
+        for (int n = m + 1; n < 3; ++n) s -= A[m][n] * x[n];
+        x[m] = s / A[m][m];
+    }
+    return 0;
+}
+
+/* Newton iterations p <- p - J^{-1} G with backtracking on |G|, to |G| < tol. */
+static int newton_polish(const or_model* M, const double anchor[3], double p[3], double tol,
+                         double* res) {
+    double Gv[3], J[9], dp[3], q[3], Gq[3];
+    for (int it = 0; it < 200; ++it) {
+        total_force(M, anchor, p, Gv, J);
+        const double g = norm3(Gv);
+        *res = g;
+        if (g < tol) return 1;
+        const double rhs[3] = {-Gv[0], -Gv[1], -Gv[2]};
+        if (solve3(J, rhs, dp)) return 0;
+        double step = 1.0;
+        int moved = 0;
+        while (step > 1e-10) {
+            for (int m = 0; m < 3; ++m) q[m] = p[m] + step * dp[m];
+            total_force(M, anchor, q, Gq, NULL);
+            if (norm3(Gq) < g) { moved = 1; break; }
+            step *= 0.5;
+        }
+        if (!moved) return 0;
+        p[0] = q[0]; p[1] = q[1]; p[2] = q[2];
+    }
+    total_force(M, anchor, p, Gv, NULL);
+    *res = norm3(Gv);
+    return *res < tol;
+}
+
+/* Eigenvalues of a symmetric 3x3 matrix by cyclic Jacobi rotations; returns the smallest. */
+static double sym3_min_eig(const double* S) {
+    double a[3][3];
+    for (int m = 0; m < 3; ++m)
+        for (int n = 0; n < 3; ++n) a[m][n] = S[m * 3 + n];
+    for (int sweep = 0; sweep < 50; ++sweep) {
+        const double off = a[0][1] * a[0][1] + a[0][2] * a[0][2] + a[1][2] * a[1][2];
+        if (off < 1e-30) break;
+        for (int pq = 0; pq < 3; ++pq) {
+            const int P = pq == 2 ? 1 : 0, Q = pq == 0 ? 1 : 2;
+            if (fabs(a[P][Q]) < 1e-300) continue;
+            const double th = 0.5 * atan2(2.0 * a[P][Q], a[Q][Q] - a[P][P]);
+            const double c = cos(th), s = sin(th);
+            for (int k = 0; k < 3; ++k) {
+                const double akp = a[k][P], akq = a[k][Q];
+                a[k][P] = c * akp - s * akq;
+                a[k][Q] = s * akp + c * akq;
+            }
+            for (int k = 0; k < 3; ++k) {
+                const double apk = a[P][k], aqk = a[Q][k];
+                a[P][k] = c * apk - s * aqk;
+                a[Q][k] = s * apk + c * aqk;
+            }
+        }
+    }
+    double e = a[0][0];
+    if (a[1][1] < e) e = a[1][1];
+    if (a[2][2] < e) e = a[2][2];
+    return e;
+}
+
+/* Relax the listed pixel columns over all scan heights.
+ *   ff == NULL selects the grid-free model (F^S by direct pair sum at p).
+ *   cols[c] = j*scan.nx + i.  Outputs per column c and height k (index c*nz+k):
+ *   pos[3], fz, iters (FIRE updates), res (|G| after FIRE), lam (smallest
+ *   eigenvalue of the symmetrised stiffness -J at the final p), ok (Newton
+ *   reached |G| < polish_tol; 1 when polishing is off).
+ *   Warm start: p(0) = anchor + d0, p(k) = p(k-1) - dz z_hat.  With
+ *   polish_tol > 0 the polished p(k-1) seeds height k. */
+int or_relax_columns(const double* ff, const or_grid* G, const or_atoms* A, const or_probe* P,
+                     const or_scan* S, const or_tip* T, const or_fire* Fp, int ncols,
+                     const int* cols, double polish_tol, double* pos, double* fz, int* iters,
+                     double* res, double* lam, int* ok, int nthreads) {
+    if (!G || !S || !T || !Fp || !cols || ncols < 0) return 1;
+    if (!ff && (!A || !P)) return 1;
+    set_threads(nthreads);
+    or_model M;
+    M.ff = ff; M.G = G; M.A = A; M.P = P;
+    grid_period(G, &M.Lx, &M.Ly);
+    M.tip = tip_units(T);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int c = 0; c < ncols; ++c) {
+        const int i = cols[c] % S->nx, j = cols[c] / S->nx;
+        double p[3];
+        for (int k = 0; k < S->nz; ++k) {
+            const double anchor[3] = {S->x0 + i * S->px, S->y0 + j * S->py, S->z_top - k * S->dz};
+            if (k == 0) {
+                p[0] = anchor[0] + M.tip.d0x;
+                p[1] = anchor[1] + M.tip.d0y;
+                p[2] = anchor[2] + M.tip.d0z;
+            } else {
+                p[2] -= S->dz;
+            }
+            double r = 0.0;
+            const int it = fire_relax(&M, Fp, anchor, p, &r);
+            int good = 1;
+            if (polish_tol > 0.0) {
+                double r2;
+                good = newton_polish(&M, anchor, p, polish_tol, &r2);
+            }
+            double Gv[3], J[9], Ks[9];
+            total_force(&M, anchor, p, Gv, J);
+            for (int m = 0; m < 3; ++m)
+                for (int n = 0; n < 3; ++n) Ks[m * 3 + n] = -0.5 * (J[m * 3 + n] + J[n * 3 + m]);
+            const double d[3] = {p[0] - anchor[0], p[1] - anchor[1], p[2] - anchor[2]};
+            const long o = (long)c * S->nz + k;
+            if (pos) { pos[3 * o] = p[0]; pos[3 * o + 1] = p[1]; pos[3 * o + 2] = p[2]; }
+            if (fz) fz[o] = tip_fz(&M.tip, d);
+            if (iters) iters[o] = it;
+            if (res) res[o] = r;
+            if (lam) lam[o] = sym3_min_eig(Ks);
+            if (ok) ok[o] = good;
+        }
+    }
+    return 0;
+}
+
+/* ---------------------------------------------------------- frequency shift */
+
+static double prim1(double u, double a) { return -sqrt(fmax(a * a - u * u, 0.0)); }
+static double prim2(double u, double a) {
+    double s = u / a;
+    if (s > 1.0) s = 1.0;
+    if (s < -1.0) s = -1.0;
+    return 0.5 * a * a * asin(s) - 0.5 * u * sqrt(fmax(a * a - u * u, 0.0));
+}
+
+/* Weights W_j (j = -m..m, stored at W[j+m]) with
+ *   integral_{-a}^{a} u f(u) / sqrt(a^2 - u^2) du = sum_j W_j f(j h)
+ * exactly for every f that is linear between the nodes u_j = j h; m = ceil(a/h).
+ * Uses the primitives of u/sqrt(a^2-u^2) and u^2/sqrt(a^2-u^2). Returns m. */
+int or_df_weights(double a, double h, double* W) {
+    const int m = (int)ceil(a / h - 1e-9);
+    if (!W) return m;
+    for (int j = 0; j <= 2 * m; ++j) W[j] = 0.0;
+    for (int j = -m; j < m; ++j) {
+        const double uj = j * h, uj1 = (j + 1) * h;
+        const double lo = fmax(uj, -a), hi = fmin(uj1, a);
+        if (!(lo < hi)) continue;
+        const double I1 = prim1(hi, a) - prim1(lo, a);
+        const double I2 = prim2(hi, a) - prim2(lo, a);
+        W[j + m] += (uj1 * I1 - I2) / h;
+        W[j + 1 + m] += (I2 - uj * I1) / h;
+    }
+    return m;
+}
+
+/* Eq. (df): df(z_c) = -(f0/2k) (8/(pi A^2)) integral_{-A/2}^{A/2} u Fz(z_c+u)/sqrt(A^2/4-u^2) du.
+ * fz[nz][npix] at tip heights z_k = z_top - k dz (k grows downward), df[nz-2m][npix]
+ * labelled by the centre index c = m..nz-1-m.  Fz in eV/A, k in N/m, f0 in Hz. */
+int or_fz_to_df(const double* fz, int nz, int npix, double dz, const or_df* D, double* df) {
+    const double a = 0.5 * D->A_pp;
+    const int m = or_df_weights(a, dz, NULL);
+    if (nz < 2 * m + 1 || npix < 0) return 1;
+    double* W = (double*)malloc((2 * m + 1) * sizeof(double));
+    or_df_weights(a, dz, W);
+    const double pref = -(D->f0 / (2.0 * D->k)) * (2.0 / (OR_PI * a * a)) * OR_EVA2_TO_NM;
+    for (int c = m; c <= nz - 1 - m; ++c)
+        for (int px = 0; px < npix; ++px) {
+            double s = 0.0;
+            for (int j = -m; j <= m; ++j) s += W[j + m] * fz[(long)(c - j) * npix + px];
+            df[(long)(c - m) * npix + px] = pref * s;
+        }
+    free(W);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ adjoint */
+
+/* Accumulate a . dF/d(theta_i) for one pair into the per-atom gradients
+ * g[0..2] (position), g[3] (R_i), g[4] (eps_i), g[5] (q_i), and *gQ. */
+static void pair_grad(const or_pair* p, const or_atoms* A, int i, const or_probe* P,
+                      const double a[3], double* g, double* gQ) {
+    const double ad = a[0] * p->d[0] + a[1] * p->d[1] + a[2] * p->d[2];
+    for (int m = 0; m < 3; ++m) {
+        double v = p->S * a[m];
+        if (!p->clamped && p->r > 0.0) v += p->dSdr * ad * p->d[m] / p->r;
+        g[m] -= v;  /* delta = r - r_i, d delta / d r_i = -I */
+    }
+    g[3] += ad * p->dSdR;
+    if (p->e_ij > 0.0) g[4] += ad * p->S_lj_e * P->eps_pp / (2.0 * p->e_ij);
+    g[5] += ad * OR_KE * P->Q * p->S_el_qq;
+    *gQ += ad * OR_KE * A->q[i] * p->S_el_qq;
+}
+
+/* Gradient of L = sum_c sum_pix g_df[c][pix] * df[c][pix] with respect to the
+ * atoms (x, y, z, q, R, eps) and the tip (kx, ky, kR in per N/m, Q), by the
+ * implicit function theorem at the relaxed positions pos[nz][ny][nx][3]:
+ *   g_Fz = K^T g_df;  J^T lambda = g_Fz grad_p Fz;
+ *   dL/dtheta = g_Fz dFz/dtheta - lambda . dG/dtheta.
+ * Grid mode (ff != NULL): the grid adjoint Gbar_g = -sum lambda w_g(p*) is
+ * contracted with the pair derivatives of every node value.  Direct mode:
+ * the pair derivatives are taken at p* itself.
+ * gtip = {dL/dkx, dL/dky, dL/dkR, dL/dQ}.  grid_adj (optional) gets Gbar [nz][ny][nx][3]. */
+int or_backward(const double* ff, const or_grid* G, const or_atoms* A, const or_probe* P,
+                const or_scan* S, const or_tip* T, const or_df* D, const double* pos,
+                const double* g_df, double* grads /*[n][6]*/, double* gtip, double* grid_adj,
+                int nthreads) {
+    if (!G || !A || !P || !S || !T || !D || !pos || !g_df || !grads || !gtip) return 1;
+    set_threads(nthreads);
+    or_model M;
+    M.ff = ff; M.G = G; M.A = A; M.P = P;
+    grid_period(G, &M.Lx, &M.Ly);
+    M.tip = tip_units(T);
+    const tip_si* t = &M.tip;
+    const int nz = S->nz;
+    const long npix = (long)S->nx * S->ny;
+    const double a = 0.5 * D->A_pp;
+    const int m = or_df_weights(a, S->dz, NULL);
+    if (nz < 2 * m + 1) return 1;
+    double* W = (double*)malloc((2 * m + 1) * sizeof(double));
+    or_df_weights(a, S->dz, W);
+    const double pref = -(D->f0 / (2.0 * D->k)) * (2.0 / (OR_PI * a * a)) * OR_EVA2_TO_NM;
+    /* g_Fz = K^T g_df */
+    double* gfz = (double*)calloc((size_t)nz * npix, sizeof(double));
+    for (int c = m; c <= nz - 1 - m; ++c)
+        for (long px = 0; px < npix; ++px) {
+            const double gd = g_df[(long)(c - m) * npix + px];
+            for (int j = -m; j <= m; ++j) gfz[(long)(c - j) * npix + px] += pref * W[j + m] * gd;
+        }
+    free(W);
+    const long nnode = (long)G->nx * G->ny * G->nz;
+    double* gbar = ff ? (double*)calloc((size_t)nnode * 3, sizeof(double)) : NULL;
+    double* lam = (double*)calloc((size_t)nz * npix * 3, sizeof(double));
+    double gkx = 0, gky = 0, gkR = 0;
+    for (int k = 0; k < nz; ++k)
+        for (long px = 0; px < npix; ++px) {
+            const long o = (long)k * npix + px;
+            const double gf = gfz[o];
+            if (gf == 0.0) continue;
+            const int i = (int)(px % S->nx), j = (int)(px / S->nx);
+            const double anchor[3] = {S->x0 + i * S->px, S->y0 + j * S->py, S->z_top - k * S->dz};
+            const double* p = pos + 3 * o;
+            const double d[3] = {p[0] - anchor[0], p[1] - anchor[1], p[2] - anchor[2]};
+            const double dn = norm3(d);
+            double Gv[3], J[9], JT[9];
+            total_force(&M, anchor, p, Gv, J);
+            for (int r = 0; r < 3; ++r)
+                for (int s = 0; s < 3; ++s) JT[r * 3 + s] = J[s * 3 + r];
+            /* grad_p Fz = kR [(1 - R0/|d|) z_hat + R0 d_z d / |d|^3] */
+            double gphi[3];
+            for (int r = 0; r < 3; ++r) gphi[r] = t->kR * t->R0 * d[2] * d[r] / (dn * dn * dn);
+            gphi[2] += t->kR * (1.0 - t->R0 / dn);
+            double rhs[3] = {gf * gphi[0], gf * gphi[1], gf * gphi[2]}, l[3];
+            if (solve3(JT, rhs, l)) continue;
+            lam[3 * o] = l[0]; lam[3 * o + 1] = l[1]; lam[3 * o + 2] = l[2];
+            /* tip parameters: dG/dkx = -(d_x - d0x) x_hat, ... (internal units) */
+            gkx += l[0] * (d[0] - t->d0x);
+            gky += l[1] * (d[1] - t->d0y);
+            gkR += gf * (dn - t->R0) * d[2] / dn + (l[0] * d[0] + l[1] * d[1] + l[2] * d[2]) * (dn - t->R0) / dn;
+            if (gbar) {
+                long node[8];
+                double w8[8], F[3];
+                interp(ff, G, p, F, NULL, node, w8);
+                for (int c8 = 0; c8 < 8; ++c8)
+                    for (int r = 0; r < 3; ++r) gbar[3 * node[c8] + r] -= l[r] * w8[c8];
+            }
+        }
+    gtip[0] = gkx * OR_NM_TO_EVA2;
+    gtip[1] = gky * OR_NM_TO_EVA2;
+    gtip[2] = gkR * OR_NM_TO_EVA2;
+    double gQ_total = 0.0;
+    const int n = A->n;
+    double* gQ_atom = (double*)calloc((size_t)n, sizeof(double));
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int ia = 0; ia < n; ++ia) {
+        double g[6] = {0, 0, 0, 0, 0, 0}, gQ = 0.0;
+        if (gbar) {
+            const long nxy = (long)G->nx * G->ny;
+            for (long gi = 0; gi < nnode; ++gi) {
+                const double* av = gbar + 3 * gi;
+                if (av[0] == 0.0 && av[1] == 0.0 && av[2] == 0.0) continue;
+                const long kk = gi / nxy, rem = gi % nxy, jj = rem / G->nx, ii = rem % G->nx;
+                const double r[3] = {G->x0 + ii * G->dx, G->y0 + jj * G->dy, G->z0 + kk * G->dz};
+                or_pair pr;
+                pair_eval(A, ia, P, M.Lx, M.Ly, r, &pr);
+                pair_grad(&pr, A, ia, P, av, g, &gQ);
+            }
+        } else {
+            for (long o = 0; o < (long)nz * npix; ++o) {
+                const double* l = lam + 3 * o;
+                if (l[0] == 0.0 && l[1] == 0.0 && l[2] == 0.0) continue;
+                const double av[3] = {-l[0], -l[1], -l[2]};
+                or_pair pr;
+                pair_eval(A, ia, P, M.Lx, M.Ly, pos + 3 * o, &pr);
+                pair_grad(&pr, A, ia, P, av, g, &gQ);
+            }
+        }
+        for (int r = 0; r < 6; ++r) grads[6 * ia + r] = g[r];
+        gQ_atom[ia] = gQ;
+    }
+    for (int ia = 0; ia < n; ++ia) gQ_total += gQ_atom[ia];
+    gtip[3] = gQ_total;
+    if (grid_adj && gbar) memcpy(grid_adj, gbar, (size_t)nnode * 3 * sizeof(double));
+    free(gQ_atom);
+    free(gbar);
+    free(lam);
+    free(gfz);
+    return 0;
+}
