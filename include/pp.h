@@ -1,0 +1,196 @@
+/*
+ * pp.h -- C ABI of the GB300 (sm_103a) Probe-Particle Model hot path.
+ *
+ * Three stages of the paper's two-step scheme (Sec. 5.1.1) plus its tip
+ * readout and frequency shift (Sec. 2.1), each a CUDA kernel:
+ *
+ *   pp_make_ff     force-field grid from Lennard-Jones (Eq. LJ, mixing rules
+ *                  R_iPP = R_i + R_PP, e_iPP = sqrt(e_i e_PP)) and point-charge
+ *                  Coulomb (Eq. point charges) pair sums, F = -grad E (Sec. 2.2);
+ *   pp_relax_scan  relaxed tip scan: per pixel, heights from the top down, FIRE
+ *                  on F_PP = F_T + F_S (Eq. F_PP, Eq. F_tip) with F_S trilinearly
+ *                  interpolated from the grid (Sec. 5.1.1 step 2), warm-started
+ *                  from the previous height; output Fz = -F^T_{R,z} (Sec. 2.1);
+ *   pp_fz_to_df    Fz(z) -> frequency shift df by Eq. df (Giessibl kernel).
+ *
+ * Conventions shared by every entry point
+ *   Units      Angstrom, eV, elementary charge; spring constants and the
+ *              cantilever stiffness in N/m; f0 in Hz; df in Hz.
+ *   Memory     Every array argument is DEVICE memory owned by the caller,
+ *              unless its comment says host.  The library allocates nothing
+ *              and keeps no pointer after the call returns (its kernels may
+ *              still be running on `stream`).
+ *   Execution  All work is enqueued on `stream` (a cudaStream_t; NULL = the
+ *              legacy default stream).  No call synchronises the host except
+ *              pp_backward when it is given a NULL workspace size query.
+ *   Errors     Every call returns a pp_status; nothing throws across the ABI.
+ *              Shapes, sizes and NULL pointers are checked on the host before
+ *              any launch; a failed check launches nothing.  PP_ERR_CUDA means
+ *              a launch failed (the CUDA error string is in pp_last_error()).
+ *              Device data is not scanned.
+ *   Threads    Calls are thread-safe; pp_last_error() is per host thread.
+ *   Device     The current CUDA device of the calling thread is used.
+ */
+#ifndef PP_H_
+#define PP_H_
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define PP_API __attribute__((visibility("default")))
+#else
+#define PP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PP_OK = 0,
+    PP_ERR_ARG = 1,         /* NULL pointer or a parameter out of range      */
+    PP_ERR_SHAPE = 2,       /* inconsistent or unsupported sizes             */
+    PP_ERR_CUDA = 3,        /* a CUDA launch or call failed                  */
+    PP_ERR_CAPACITY = 4,    /* a caller buffer (workspace) is too small      */
+    PP_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up            */
+    PP_ERR_UNSUPPORTED = 6  /* a valid request this build does not implement */
+} pp_status;
+
+typedef void* pp_stream; /* cudaStream_t */
+
+/* Sample atoms, structure of arrays, n >= 0.  Device pointers to n floats. */
+typedef struct {
+    int n;
+    const float *x, *y, *z; /* positions, A                                  */
+    const float *R;         /* LJ radius R_i, A (mixing: R_iPP = R_i + R_PP)  */
+    const float *eps;       /* LJ well depth e_i >= 0, eV (e_iPP = sqrt(e_i e_PP)) */
+    const float *q;         /* point charge q_i, e                           */
+} pp_atoms;
+
+/* Probe particle.  The pair force is floored per pair at
+ * r^2 >= (core_frac * R_iPP)^2 (displacement unscaled) so that no value is
+ * infinite; coul_rc > 0 selects a shifted-force Coulomb truncated at coul_rc
+ * (F = k_e Q q (1/r^2 - 1/rc^2) r_hat for r < rc, 0 beyond); min_image = 1
+ * sums each atom's nearest lateral periodic image, period = grid extent
+ * (nx*dx, ny*dy). */
+typedef struct {
+    float R_pp, eps_pp; /* A, eV                       */
+    float Q;            /* probe charge, e             */
+    float coul_rc;      /* A; 0 = plain Coulomb        */
+    int min_image;      /* 0 or 1                      */
+    float core_frac;    /* floor radius / R_iPP, in (0, 1) */
+} pp_probe;
+
+/* Regular force-field grid: node (i,j,k) sits at (x0+i*dx, y0+j*dy, z0+k*dz).
+ * Interpolation wraps i,j periodically when periodic_xy = 1, else clamps; it
+ * always clamps in z (cell index in [0, nz-2], fraction in [0,1]).
+ * layout 0: node (i,j,k) at float4 index (k*ny + j)*nx + i.
+ * layout 1: bricks of bx*by*bz nodes (each a power of two, 1..16), bricks in
+ *           x-fastest order, nodes x-fastest inside a brick; dimensions are
+ *           padded up to whole bricks.  pp_ff_floats() gives the size.
+ * Every node holds 4 floats (Fx, Fy, Fz, E) in eV/A and eV; the buffer must be
+ * 16-byte aligned. */
+typedef struct {
+    int nx, ny, nz;
+    float x0, y0, z0;
+    float dx, dy, dz;
+    int periodic_xy;
+    int layout;
+    int bx, by, bz;
+} pp_grid;
+
+/* Tip springs of Eq. F_tip, with d = r_PP - r_TIP and
+ * d0 = (d0x, d0y, -sqrt(R0^2 - d0x^2 - d0y^2)) (the PP hangs below the tip):
+ *   F_T = -kR (|d| - R0) d/|d| - (kx (d_x - d0x), ky (d_y - d0y), 0). */
+typedef struct {
+    float kx, ky, kR; /* N/m */
+    float R0;         /* A   */
+    float d0x, d0y;   /* A   */
+} pp_tip;
+
+/* Tip anchors: pixel (i,j) at height index k is at
+ * (x0 + i*px, y0 + j*py, z_top - k*dz), k = 0..nz-1 (approaching the sample). */
+typedef struct {
+    int nx, ny, nz;
+    float x0, y0, px, py;
+    float z_top, dz;
+} pp_scan;
+
+/* FIRE (Bitzek et al. 2006), semi-implicit Euler.  Per height: v = 0,
+ * dt = dt0, alpha = alpha0.  Each iteration evaluates G = F_PP and stops when
+ * |G| < ftol (eV/A) or after max_iter position updates; from the second
+ * iteration on, G.v > 0 mixes v <- (1-alpha) v + alpha |v| G/|G| and, after
+ * more than n_min such steps in a row, sets dt <- min(dt*f_inc, dt_max),
+ * alpha <- alpha*f_alpha; G.v <= 0 sets v = 0, dt <- dt*f_dec,
+ * alpha <- alpha0.  Then v += dt G/mass, p += dt v. */
+typedef struct {
+    int max_iter;
+    float ftol, dt0, dt_max, f_inc, f_dec, alpha0, f_alpha, mass;
+    int n_min;
+} pp_fire;
+
+/* Cantilever of Eq. df: A_pp is the PEAK-TO-PEAK amplitude (A), k the
+ * stiffness (N/m), f0 the base frequency (Hz). */
+typedef struct {
+    float A_pp, k, f0;
+} pp_df;
+
+/* Number of floats of a force-field buffer for `grid` (4 per stored node,
+ * brick padding included); 0 if the grid is invalid. */
+PP_API size_t pp_ff_floats(const pp_grid* grid);
+
+/* Half-width in samples of the df stencil: m = ceil(A_pp/2 / dz).  A scan of
+ * nz heights yields nz - 2m df values per pixel (centre labelling); -1 if the
+ * arguments are invalid. */
+PP_API int pp_df_margin(float A_pp, float dz);
+
+/* FF grid assembly (Sec. 5.1.1 step 1; Eqs. LJ and point charges; Sec. 2.2).
+ * Writes all nodes of `ff` (pp_ff_floats(grid) floats, padding nodes
+ * included) with (Fx, Fy, Fz, E) = sum over atoms of the pair force and
+ * energy at the node.  atoms->n may be 0 (all zeros).  Errors: PP_ERR_ARG
+ * (NULL, core_frac outside (0,1), negative eps), PP_ERR_SHAPE (nx, ny, nz < 2,
+ * spacing <= 0, brick not a power of two), PP_ERR_CUDA. */
+PP_API pp_status pp_make_ff(const pp_atoms* atoms, const pp_probe* probe, const pp_grid* grid,
+                     float* ff, pp_stream stream);
+
+/* Relaxed tip scan (Sec. 5.1.1 step 2; Eqs. F_PP, F_tip; Sec. 2.1 readout).
+ * One thread per pixel walks the heights k = 0..nz-1: start p = anchor + d0
+ * at k = 0 and p = p*(k-1) - dz z_hat after that, relax by FIRE, write
+ *   pos[((k*ny + j)*nx + i)*3 + c]  relaxed PP position (nullable),
+ *   fz[(k*ny + j)*nx + i]           Fz = kR (|d| - R0) d_z/|d|, eV/A,
+ *   iters[(k*ny + j)*nx + i]        FIRE position updates; == max_iter when
+ *                                   |G| < ftol was not reached (nullable).
+ * Non-convergence is reported through iters only.  When fused_df and df are
+ * both non-NULL the same launch also writes df[(c*ny + j)*nx + i],
+ * c = 0..nz-2m-1, exactly as pp_fz_to_df would.  Errors: PP_ERR_ARG,
+ * PP_ERR_SHAPE (grid invalid, scan sizes < 1, nz < 2m+1 with fused df),
+ * PP_ERR_UNSUPPORTED (m > 31), PP_ERR_CUDA. */
+PP_API pp_status pp_relax_scan(const float* ff, const pp_grid* grid, const pp_scan* scan,
+                        const pp_tip* tip, const pp_fire* fire,
+                        float* pos, float* fz, int* iters,
+                        const pp_df* fused_df, float* df, pp_stream stream);
+
+/* Frequency shift of Eq. df.  fz[k*npix + p] holds Fz (eV/A) at tip heights
+ * z_k = z_top - k*dz; df[c*npix + p] (Hz), c = 0..nz-2m-1, is centred at
+ * z_{c+m}.  Fz is taken piecewise linear between the heights and integrated
+ * exactly against u/sqrt(a^2 - u^2), a = A_pp/2.  npix = 0 is a no-op (fz and df
+ * may then be NULL).  Errors: PP_ERR_ARG,
+ * PP_ERR_SHAPE (nz < 2m+1), PP_ERR_UNSUPPORTED (m > 31), PP_ERR_CUDA. */
+PP_API pp_status pp_fz_to_df(const float* fz, int nz, int npix, float dz, const pp_df* df_params,
+                      float* df, pp_stream stream);
+
+/* Layout conversion of a force-field buffer: src laid out as `src_grid`,
+ * dst as `dst_grid`; the two must describe the same nodes (nx, ny, nz) and
+ * may differ in layout and brick shape.  Padding nodes of dst are zeroed.
+ * Errors: PP_ERR_ARG, PP_ERR_SHAPE, PP_ERR_CUDA. */
+PP_API pp_status pp_ff_convert(const float* src, const pp_grid* src_grid, float* dst,
+                        const pp_grid* dst_grid, pp_stream stream);
+
+/* Message of the last failed call on this host thread ("" if none). */
+PP_API const char* pp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PP_H_ */

@@ -1,0 +1,117 @@
+"""User-level API: one molecule, force field -> relaxed scan -> df image.
+
+`Simulator` owns the device buffers of one workload shape (grid and scan) and
+runs the three C-ABI stages on the current torch stream; `run_host` is the
+end-to-end call that starts from host atom arrays and returns the df image
+in host memory.  Nothing here computes: it allocates with torch and calls
+libpp through `pp.py`.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import pp
+
+ATOM_KEYS = ("x", "y", "z", "R", "eps", "q")
+
+
+def atoms_to_device(atoms, device="cuda"):
+    """Host atom dict (numpy) -> dict of float32 CUDA tensors."""
+    return {k: torch.as_tensor(np.asarray(atoms[k], dtype=np.float32), device=device) for k in ATOM_KEYS}
+
+
+class Simulator:
+    """Preallocated FF grid, positions, Fz, iteration counts and df for one case shape."""
+
+    def __init__(self, case, layout=0, brick=(4, 4, 4), fire=None, device="cuda", fused_df=True,
+                 want_pos=True, want_iters=True):
+        self.case = case
+        self.device = torch.device(device)
+        self.grid = pp.make_grid(case["grid"], layout=layout, brick=brick)
+        self.probe = pp.make_probe(case["probe"])
+        self.scan = pp.make_scan(case["scan"])
+        self.tip = pp.make_tip(case["tip"])
+        self.fire = pp.make_fire(fire or case["fire"])
+        self.dfp = pp.make_df(case["df"])
+        self.fused_df = fused_df
+        s = case["scan"]
+        self.m = pp.pp_df_margin(self.dfp.A_pp, self.scan.dz)
+        if self.m < 0 or s["nz"] < 2 * self.m + 1:
+            raise ValueError("scan has fewer heights than the df stencil needs")
+        nz, ny, nx = s["nz"], s["ny"], s["nx"]
+        self.ff = torch.empty(pp.pp_ff_floats(self.grid), dtype=torch.float32, device=self.device)
+        self.pos = torch.empty((nz, ny, nx, 3), dtype=torch.float32, device=self.device) if want_pos else None
+        self.fz = torch.empty((nz, ny, nx), dtype=torch.float32, device=self.device)
+        self.iters = torch.empty((nz, ny, nx), dtype=torch.int32, device=self.device) if want_iters else None
+        self.df = torch.empty((nz - 2 * self.m, ny, nx), dtype=torch.float32, device=self.device)
+        self._host = None
+
+    def make_ff(self, atoms_dev, stream=None):
+        pp.pp_make_ff(pp.make_atoms(atoms_dev), self.probe, self.grid, self.ff, stream)
+
+    def relax(self, stream=None):
+        if self.fused_df:
+            pp.pp_relax_scan(self.ff, self.grid, self.scan, self.tip, self.fire, self.pos, self.fz, self.iters,
+                             self.dfp, self.df, stream)
+        else:
+            pp.pp_relax_scan(self.ff, self.grid, self.scan, self.tip, self.fire, self.pos, self.fz, self.iters,
+                             None, None, stream)
+            pp.pp_fz_to_df(self.fz, self.scan.nz, self.scan.nx * self.scan.ny, self.scan.dz, self.dfp, self.df,
+                           stream)
+
+    def run(self, atoms_dev, stream=None):
+        """Device-resident forward pass; returns the df tensor (device)."""
+        self.make_ff(atoms_dev, stream)
+        self.relax(stream)
+        return self.df
+
+    # ---- end to end from host memory
+    def _host_buffers(self, n_atoms):
+        if self._host is None or self._host["n"] != n_atoms:
+            pin = torch.cuda.is_available()
+            self._host = {
+                "n": n_atoms,
+                "atoms_h": torch.empty((6, n_atoms), dtype=torch.float32, pin_memory=pin),
+                "atoms_d": torch.empty((6, n_atoms), dtype=torch.float32, device=self.device),
+                "df_h": torch.empty(tuple(self.df.shape), dtype=torch.float32, pin_memory=pin),
+            }
+        return self._host
+
+    def run_host(self, atoms_host, out=None, stream=None):
+        """Host atoms (numpy dict) -> host df image: H2D copy, FF, relax, df, D2H copy.
+
+        Returns the host (pinned) df tensor after synchronising the stream.
+        Bytes moved: 24 per atom host->device, 4 per df value device->host.
+        """
+        n = int(len(atoms_host["x"]))
+        hb = self._host_buffers(n)
+        for r, k in enumerate(ATOM_KEYS):
+            hb["atoms_h"][r].copy_(torch.from_numpy(np.asarray(atoms_host[k], dtype=np.float32)))
+        st = stream or torch.cuda.current_stream()
+        with torch.cuda.stream(st):
+            hb["atoms_d"].copy_(hb["atoms_h"], non_blocking=True)
+            dev = {k: hb["atoms_d"][r] for r, k in enumerate(ATOM_KEYS)}
+            self.run(dev, st)
+            hb["df_h"].copy_(self.df, non_blocking=True)
+        st.synchronize()
+        if out is not None:
+            out.copy_(hb["df_h"])
+            return out
+        return hb["df_h"]
+
+    def h2d_bytes(self, n_atoms):
+        return 6 * 4 * n_atoms
+
+    def d2h_bytes(self):
+        return self.df.numel() * 4
+
+
+def afm(case, atoms=None, layout=0, fire=None, device="cuda"):
+    """One-shot simulation of a case dict; returns host numpy arrays (df, fz, pos, iters, ff)."""
+    sim = Simulator(case, layout=layout, fire=fire, device=device)
+    dev = atoms_to_device(atoms if atoms is not None else case["atoms"], device)
+    sim.run(dev)
+    torch.cuda.synchronize()
+    return {"df": sim.df.cpu().numpy(), "fz": sim.fz.cpu().numpy(), "pos": sim.pos.cpu().numpy(),
+            "iters": sim.iters.cpu().numpy(), "ff": sim.ff, "sim": sim}

@@ -1,0 +1,280 @@
+// C ABI of libpp: argument checks, unit conversion, launch.
+#include <math.h>
+
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "pp_internal.cuh"
+
+namespace pp {
+
+static thread_local std::string g_error;
+
+void set_error(const std::string& msg) { g_error = msg; }
+
+pp_status cuda_status(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return PP_OK;
+    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return PP_ERR_CUDA;
+}
+
+static bool pow2_in(int v, int lo, int hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; }
+static int ilog2(int v) {
+    int l = 0;
+    while ((1 << l) < v) ++l;
+    return l;
+}
+static bool finite_pos(float v) { return isfinite(v) && v > 0.f; }
+
+bool make_grid_map(const pp_grid* g, GridMap* out, std::string* why) {
+    if (!g) { *why = "grid is NULL"; return false; }
+    if (g->nx < 2 || g->ny < 2 || g->nz < 2) { *why = "grid needs nx, ny, nz >= 2"; return false; }
+    if (!finite_pos(g->dx) || !finite_pos(g->dy) || !finite_pos(g->dz)) { *why = "grid spacing must be > 0"; return false; }
+    if (!isfinite(g->x0) || !isfinite(g->y0) || !isfinite(g->z0)) { *why = "grid origin must be finite"; return false; }
+    if (g->periodic_xy != 0 && g->periodic_xy != 1) { *why = "periodic_xy must be 0 or 1"; return false; }
+    GridMap m;
+    m.nx = g->nx; m.ny = g->ny; m.nz = g->nz;
+    if (g->layout == 0) {
+        const int64_t n = (int64_t)g->nx * g->ny * g->nz;
+        if (n >= (int64_t(1) << 31)) { *why = "grid has 2^31 or more nodes"; return false; }
+        m.ax = {0, 1, 0, 0};
+        m.ay = {0, g->nx, 0, 0};
+        m.az = {0, g->nx * g->ny, 0, 0};
+        m.stored_nodes = n;
+    } else if (g->layout == 1) {
+        if (!pow2_in(g->bx, 1, 16) || !pow2_in(g->by, 1, 16) || !pow2_in(g->bz, 1, 16)) {
+            *why = "brick sides must be powers of two in [1, 16]";
+            return false;
+        }
+        const int lx = ilog2(g->bx), ly = ilog2(g->by), lz = ilog2(g->bz), lb = lx + ly + lz;
+        const int64_t nbx = (g->nx + g->bx - 1) / g->bx, nby = (g->ny + g->by - 1) / g->by;
+        const int64_t nbz = (g->nz + g->bz - 1) / g->bz;
+        const int64_t n = (nbx * nby * nbz) << lb;
+        if (n >= (int64_t(1) << 31)) { *why = "bricked grid has 2^31 or more slots"; return false; }
+        m.ax = {lx, 1 << lb, g->bx - 1, 0};
+        m.ay = {ly, (int)(nbx << lb), g->by - 1, lx};
+        m.az = {lz, (int)((nbx * nby) << lb), g->bz - 1, lx + ly};
+        m.stored_nodes = n;
+    } else {
+        *why = "layout must be 0 (linear) or 1 (bricked)";
+        return false;
+    }
+    *out = m;
+    return true;
+}
+
+int df_half_width(double A_pp, double dz) {
+    if (!(A_pp > 0.0) || !(dz > 0.0) || !isfinite(A_pp) || !isfinite(dz)) return -1;
+    const double m = ceil(0.5 * A_pp / dz - 1e-9);
+    return m > 1e6 ? -1 : (int)m;
+}
+
+// W(u_j), u_j = j*dz (j = -m..m): exact quadrature weights of
+// integral_{-a}^{a} u f(u) / sqrt(a^2 - u^2) du for f linear between nodes.
+// On [u_j, u_j+1] the hat functions are (u_{j+1} - u)/h and (u - u_j)/h, so
+// each interval needs the two moments of the kernel, integral u/sqrt and
+// integral u^2/sqrt, taken from their antiderivatives -sqrt(a^2-u^2) and
+// (a^2/2) asin(u/a) - (u/2) sqrt(a^2-u^2).
+static void giessibl_weights(double a, double h, int m, std::vector<double>& W) {
+    W.assign(2 * m + 1, 0.0);
+    auto root = [a](double u) { return sqrt(fmax(a * a - u * u, 0.0)); };
+    auto m1 = [&](double u) { return -root(u); };
+    auto m2 = [&](double u) {
+        const double s = fmin(fmax(u / a, -1.0), 1.0);
+        return 0.5 * a * a * asin(s) - 0.5 * u * root(u);
+    };
+    for (int j = -m; j < m; ++j) {
+        const double ul = j * h, ur = (j + 1) * h;
+        const double lo = fmax(ul, -a), hi = fmin(ur, a);
+        if (hi <= lo) continue;
+        const double k1 = m1(hi) - m1(lo), k2 = m2(hi) - m2(lo);
+        W[j + m] += (ur * k1 - k2) / h;      // left node's hat
+        W[j + 1 + m] += (k2 - ul * k1) / h;  // right node's hat
+    }
+}
+
+void df_stencil(double A_pp, double dz, double k, double f0, int m, float* coef) {
+    const double a = 0.5 * A_pp;
+    std::vector<double> W;
+    giessibl_weights(a, dz, m, W);
+    const double pref = -(f0 / (2.0 * k)) * (2.0 / (kPi * a * a)) * kEvA2ToNm;
+    // Fz at height index c+s sits at u = -s*dz from the centre: heights fall as the index grows
+    for (int s = -m; s <= m; ++s) coef[s + m] = (float)(pref * W[-s + m]);
+}
+
+}  // namespace pp
+
+using namespace pp;
+
+extern "C" {
+
+const char* pp_last_error(void) { return g_error.c_str(); }
+
+size_t pp_ff_floats(const pp_grid* grid) {
+    GridMap m;
+    std::string why;
+    if (!make_grid_map(grid, &m, &why)) return 0;
+    return (size_t)m.stored_nodes * 4;
+}
+
+int pp_df_margin(float A_pp, float dz) { return df_half_width(A_pp, dz); }
+
+static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+pp_status pp_make_ff(const pp_atoms* atoms, const pp_probe* probe, const pp_grid* grid, float* ff,
+                     pp_stream stream) {
+    g_error.clear();
+    if (!atoms || !probe || !grid || !ff) { set_error("pp_make_ff: NULL argument"); return PP_ERR_ARG; }
+    if (atoms->n < 0) { set_error("pp_make_ff: atoms->n < 0"); return PP_ERR_ARG; }
+    if (atoms->n > 0 && (!atoms->x || !atoms->y || !atoms->z || !atoms->R || !atoms->eps || !atoms->q)) {
+        set_error("pp_make_ff: NULL atom array");
+        return PP_ERR_ARG;
+    }
+    if (!(probe->core_frac > 0.f && probe->core_frac < 1.f)) { set_error("pp_make_ff: core_frac must be in (0,1)"); return PP_ERR_ARG; }
+    if (!(probe->eps_pp >= 0.f) || !isfinite(probe->R_pp) || !isfinite(probe->Q) || !(probe->coul_rc >= 0.f)) {
+        set_error("pp_make_ff: invalid probe parameters");
+        return PP_ERR_ARG;
+    }
+    if (probe->min_image != 0 && probe->min_image != 1) { set_error("pp_make_ff: min_image must be 0 or 1"); return PP_ERR_ARG; }
+    if (!aligned16(ff)) { set_error("pp_make_ff: ff must be 16-byte aligned"); return PP_ERR_ARG; }
+    GridMap map;
+    std::string why;
+    if (!make_grid_map(grid, &map, &why)) { set_error("pp_make_ff: " + why); return PP_ERR_SHAPE; }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (map.stored_nodes > (int64_t)grid->nx * grid->ny * grid->nz) {
+        pp_status st = cuda_status(cudaMemsetAsync(ff, 0, (size_t)map.stored_nodes * 16, s), "pp_make_ff memset");
+        if (st != PP_OK) return st;
+    }
+    FFLaunch L;
+    L.x = atoms->x; L.y = atoms->y; L.z = atoms->z; L.R = atoms->R; L.eps = atoms->eps; L.q = atoms->q;
+    L.n = atoms->n;
+    L.R_pp = probe->R_pp;
+    L.eps_pp = probe->eps_pp;
+    L.kQ = (float)(kCoulomb * (double)probe->Q);
+    L.core_frac = probe->core_frac;
+    L.coul_rc = probe->coul_rc;
+    L.min_image = probe->min_image;
+    L.Lx = grid->nx * grid->dx;
+    L.Ly = grid->ny * grid->dy;
+    L.x0 = grid->x0; L.y0 = grid->y0; L.z0 = grid->z0;
+    L.dx = grid->dx; L.dy = grid->dy; L.dz = grid->dz;
+    L.map = map;
+    L.ff = reinterpret_cast<float4*>(ff);
+    return cuda_status(launch_ff_assemble(L, s), "pp_make_ff launch");
+}
+
+static bool check_tip_fire(const pp_tip* tip, const pp_fire* fire, std::string* why) {
+    if (!(tip->kR > 0.f) || !(tip->R0 > 0.f) || !(tip->kx >= 0.f) || !(tip->ky >= 0.f) ||
+        !isfinite(tip->kR) || !isfinite(tip->kx) || !isfinite(tip->ky) || !isfinite(tip->d0x) || !isfinite(tip->d0y)) {
+        *why = "invalid tip springs";
+        return false;
+    }
+    if (!(tip->d0x * tip->d0x + tip->d0y * tip->d0y < tip->R0 * tip->R0)) { *why = "|(d0x, d0y)| must be < R0"; return false; }
+    if (fire->max_iter < 0 || !(fire->ftol > 0.f) || !(fire->dt0 > 0.f) || !(fire->dt_max > 0.f) ||
+        !(fire->f_inc >= 1.f) || !(fire->f_dec > 0.f && fire->f_dec <= 1.f) || !(fire->alpha0 >= 0.f && fire->alpha0 <= 1.f) ||
+        !(fire->f_alpha > 0.f && fire->f_alpha <= 1.f) || !(fire->mass > 0.f) || fire->n_min < 0) {
+        *why = "invalid FIRE parameters";
+        return false;
+    }
+    return true;
+}
+
+pp_status pp_relax_scan(const float* ff, const pp_grid* grid, const pp_scan* scan, const pp_tip* tip,
+                        const pp_fire* fire, float* pos, float* fz, int* iters, const pp_df* fused_df, float* df,
+                        pp_stream stream) {
+    g_error.clear();
+    if (!ff || !grid || !scan || !tip || !fire || !fz) { set_error("pp_relax_scan: NULL argument"); return PP_ERR_ARG; }
+    if (!aligned16(ff)) { set_error("pp_relax_scan: ff must be 16-byte aligned"); return PP_ERR_ARG; }
+    GridMap map;
+    std::string why;
+    if (!make_grid_map(grid, &map, &why)) { set_error("pp_relax_scan: " + why); return PP_ERR_SHAPE; }
+    if (scan->nx < 1 || scan->ny < 1 || scan->nz < 1) { set_error("pp_relax_scan: scan sizes must be >= 1"); return PP_ERR_SHAPE; }
+    if ((int64_t)scan->nx * scan->ny * scan->nz * 3 >= (int64_t(1) << 31)) {
+        set_error("pp_relax_scan: scan too large for one call");
+        return PP_ERR_SHAPE;
+    }
+    if (!isfinite(scan->x0) || !isfinite(scan->y0) || !isfinite(scan->px) || !isfinite(scan->py) ||
+        !isfinite(scan->z_top) || !finite_pos(scan->dz)) {
+        set_error("pp_relax_scan: invalid scan geometry");
+        return PP_ERR_ARG;
+    }
+    if (!check_tip_fire(tip, fire, &why)) { set_error("pp_relax_scan: " + why); return PP_ERR_ARG; }
+    RelaxLaunch L;
+    std::memset(&L, 0, sizeof(L));
+    L.ff = reinterpret_cast<const float4*>(ff);
+    L.map = map;
+    L.gx0 = grid->x0; L.gy0 = grid->y0; L.gz0 = grid->z0;
+    L.inv_dx = 1.f / grid->dx; L.inv_dy = 1.f / grid->dy; L.inv_dz = 1.f / grid->dz;
+    L.periodic_xy = grid->periodic_xy;
+    L.snx = scan->nx; L.sny = scan->ny; L.snz = scan->nz;
+    L.sx0 = scan->x0; L.sy0 = scan->y0; L.spx = scan->px; L.spy = scan->py;
+    L.z_top = scan->z_top; L.sdz = scan->dz;
+    L.kx = (float)(tip->kx * kNmToEvA2);
+    L.ky = (float)(tip->ky * kNmToEvA2);
+    L.kR = (float)(tip->kR * kNmToEvA2);
+    L.R0 = tip->R0;
+    L.d0x = tip->d0x;
+    L.d0y = tip->d0y;
+    L.d0z = (float)(-sqrt((double)tip->R0 * tip->R0 - (double)tip->d0x * tip->d0x - (double)tip->d0y * tip->d0y));
+    L.max_iter = fire->max_iter;
+    L.n_min = fire->n_min;
+    L.ftol2 = fire->ftol * fire->ftol;
+    L.dt0 = fire->dt0; L.dt_max = fire->dt_max; L.f_inc = fire->f_inc; L.f_dec = fire->f_dec;
+    L.alpha0 = fire->alpha0; L.f_alpha = fire->f_alpha; L.inv_mass = 1.f / fire->mass;
+    L.pos = pos; L.fz = fz; L.iters = iters;
+    L.df_m = -1;
+    L.df = nullptr;
+    if (fused_df && df) {
+        if (!finite_pos(fused_df->k) || !isfinite(fused_df->f0)) { set_error("pp_relax_scan: invalid df parameters"); return PP_ERR_ARG; }
+        const int m = df_half_width(fused_df->A_pp, scan->dz);
+        if (m < 0) { set_error("pp_relax_scan: invalid df amplitude"); return PP_ERR_ARG; }
+        if (m > kMaxDfHalfWidth) { set_error("pp_relax_scan: df stencil wider than 63 taps"); return PP_ERR_UNSUPPORTED; }
+        if (scan->nz < 2 * m + 1) { set_error("pp_relax_scan: fewer heights than the df stencil"); return PP_ERR_SHAPE; }
+        L.df_m = m;
+        L.df = df;
+        df_stencil(fused_df->A_pp, scan->dz, fused_df->k, fused_df->f0, m, L.coef);
+    }
+    return cuda_status(launch_relax_scan(L, (cudaStream_t)stream), "pp_relax_scan launch");
+}
+
+pp_status pp_fz_to_df(const float* fz, int nz, int npix, float dz, const pp_df* dfp, float* df, pp_stream stream) {
+    g_error.clear();
+    if (!dfp) { set_error("pp_fz_to_df: NULL argument"); return PP_ERR_ARG; }
+    if (nz < 1 || npix < 0) { set_error("pp_fz_to_df: nz >= 1 and npix >= 0 required"); return PP_ERR_SHAPE; }
+    if (npix > 0 && (!fz || !df)) { set_error("pp_fz_to_df: NULL argument"); return PP_ERR_ARG; }
+    if (!finite_pos(dz) || !finite_pos(dfp->k) || !isfinite(dfp->f0)) { set_error("pp_fz_to_df: invalid parameters"); return PP_ERR_ARG; }
+    const int m = df_half_width(dfp->A_pp, dz);
+    if (m < 0) { set_error("pp_fz_to_df: invalid amplitude"); return PP_ERR_ARG; }
+    if (m > kMaxDfHalfWidth) { set_error("pp_fz_to_df: df stencil wider than 63 taps"); return PP_ERR_UNSUPPORTED; }
+    if (nz < 2 * m + 1) { set_error("pp_fz_to_df: fewer heights than the df stencil"); return PP_ERR_SHAPE; }
+    DfLaunch L;
+    std::memset(&L, 0, sizeof(L));
+    L.fz = fz; L.df = df; L.nz = nz; L.npix = npix; L.m = m;
+    if (npix == 0) return PP_OK;
+    df_stencil(dfp->A_pp, dz, dfp->k, dfp->f0, m, L.coef);
+    return cuda_status(launch_fz_to_df(L, (cudaStream_t)stream), "pp_fz_to_df launch");
+}
+
+pp_status pp_ff_convert(const float* src, const pp_grid* src_grid, float* dst, const pp_grid* dst_grid,
+                        pp_stream stream) {
+    g_error.clear();
+    if (!src || !dst || !src_grid || !dst_grid) { set_error("pp_ff_convert: NULL argument"); return PP_ERR_ARG; }
+    if (!aligned16(src) || !aligned16(dst)) { set_error("pp_ff_convert: buffers must be 16-byte aligned"); return PP_ERR_ARG; }
+    GridMap sm, dm;
+    std::string why;
+    if (!make_grid_map(src_grid, &sm, &why) || !make_grid_map(dst_grid, &dm, &why)) {
+        set_error("pp_ff_convert: " + why);
+        return PP_ERR_SHAPE;
+    }
+    if (sm.nx != dm.nx || sm.ny != dm.ny || sm.nz != dm.nz) { set_error("pp_ff_convert: node counts differ"); return PP_ERR_SHAPE; }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (dm.stored_nodes > (int64_t)dm.nx * dm.ny * dm.nz) {
+        pp_status st = cuda_status(cudaMemsetAsync(dst, 0, (size_t)dm.stored_nodes * 16, s), "pp_ff_convert memset");
+        if (st != PP_OK) return st;
+    }
+    return cuda_status(launch_ff_convert(reinterpret_cast<const float4*>(src), sm, reinterpret_cast<float4*>(dst), dm, s),
+                       "pp_ff_convert launch");
+}
+
+}  // extern "C"

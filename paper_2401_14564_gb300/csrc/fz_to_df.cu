@@ -1,0 +1,68 @@
+// K3: Fz(z) -> df (Eq. df), and K8: force-field layout conversion.
+//
+// df at the centre height c is a (2m+1)-tap stencil over the Fz column,
+//   df[c - m] = sum_{s=-m..m} coef[s+m] Fz[c+s],
+// whose weights come from integrating a piecewise-linear Fz exactly against
+// the Giessibl kernel u / sqrt(a^2 - u^2) over one peak-to-peak amplitude.
+// The stencil is HBM-bound streaming work: lanes run along the pixel axis
+// (contiguous), each thread produces one output, the 2m+1 taps of a column
+// are re-read from L1/L2 rather than from DRAM.
+#include "pp_internal.cuh"
+
+namespace pp {
+namespace {
+
+constexpr int kThreads = 256;
+
+__global__ void __launch_bounds__(kThreads) fz_to_df_kernel(const DfLaunch P) {
+    const int nout = P.nz - 2 * P.m;
+    const int64_t total = (int64_t)nout * P.npix;
+    for (int64_t o = blockIdx.x * (int64_t)kThreads + threadIdx.x; o < total;
+         o += (int64_t)gridDim.x * kThreads) {
+        const int c = (int)(o / P.npix) + P.m;
+        const int64_t px = o - (int64_t)(c - P.m) * P.npix;
+        float s = 0.f;
+        const float* col = P.fz + px;
+        for (int t = -P.m; t <= P.m; ++t) s = fmaf(P.coef[t + P.m], __ldg(col + (int64_t)(c + t) * P.npix), s);
+        P.df[o] = s;
+    }
+}
+
+__global__ void ff_convert_kernel(const float4* __restrict__ src, const GridMap sm, float4* __restrict__ dst,
+                                  const GridMap dm) {
+    const int64_t n = (int64_t)dm.nx * dm.ny * dm.nz;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(g % dm.nx);
+        const int64_t r = g / dm.nx;
+        const int j = (int)(r % dm.ny);
+        const int k = (int)(r / dm.ny);
+        dst[node_index(dm, i, j, k)] = __ldg(src + node_index(sm, i, j, k));
+    }
+}
+
+int grid_blocks(int64_t work, int threads) {
+    int dev = 0, sms = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t need = (work + threads - 1) / threads;
+    const int64_t cap = (int64_t)sms * 16;
+    return (int)(need < cap ? (need > 0 ? need : 1) : cap);
+}
+
+}  // namespace
+
+cudaError_t launch_fz_to_df(const DfLaunch& L, cudaStream_t s) {
+    const int64_t total = (int64_t)(L.nz - 2 * L.m) * L.npix;
+    if (total <= 0) return cudaSuccess;
+    fz_to_df_kernel<<<grid_blocks(total, kThreads), kThreads, 0, s>>>(L);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ff_convert(const float4* src, const GridMap& sm, float4* dst, const GridMap& dm,
+                              cudaStream_t s) {
+    const int64_t n = (int64_t)dm.nx * dm.ny * dm.nz;
+    if (n <= 0) return cudaSuccess;
+    ff_convert_kernel<<<grid_blocks(n, 256), 256, 0, s>>>(src, sm, dst, dm);
+    return cudaGetLastError();
+}
+
+}  // namespace pp

@@ -1,0 +1,95 @@
+// Internal definitions shared by the CUDA translation units of libpp.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "pp.h"
+
+namespace pp {
+
+// Physical constants (own copies; SI-exact electron-volt).
+constexpr double kCoulomb = 14.3996454784;          // k_e, eV*A/e^2
+constexpr double kEvA2ToNm = 16.02176634;           // 1 eV/A^2 in N/m
+constexpr double kNmToEvA2 = 1.0 / 16.02176634;     // 1 N/m in eV/A^2
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kMaxDfHalfWidth = 31;                 // df stencil of at most 63 taps
+
+// Separable node addressing: the float4 index of node (i,j,k) is
+// X(i) + Y(j) + Z(k), each term ((v >> sh) * mul) + ((v & mask) << lsh).
+// Linear layout: sh = mask = lsh = 0 and mul = 1, nx, nx*ny.  Bricked
+// layout: sh = log2(brick side), mul = brick volume times the number of
+// bricks before it along that axis, the remainder placed x-fastest inside.
+struct AxisMap {
+    int sh, mul, mask, lsh;
+};
+
+struct GridMap {
+    AxisMap ax, ay, az;
+    int nx, ny, nz;
+    int64_t stored_nodes;  // float4 slots including brick padding
+};
+
+__host__ __device__ __forceinline__ int axis_off(const AxisMap& a, int v) {
+    return ((v >> a.sh) * a.mul) + ((v & a.mask) << a.lsh);
+}
+
+__host__ __device__ __forceinline__ int node_index(const GridMap& g, int i, int j, int k) {
+    return axis_off(g.ax, i) + axis_off(g.ay, j) + axis_off(g.az, k);
+}
+
+// Host-side helpers (api.cu).
+bool make_grid_map(const pp_grid* g, GridMap* out, std::string* why);
+void set_error(const std::string& msg);
+pp_status cuda_status(cudaError_t e, const char* what);
+int df_half_width(double A_pp, double dz);
+// coef[s + m] (s = -m..m) multiplies Fz at height index c + s for the output
+// centred at c; includes the -(f0/2k) * 2/(pi a^2) prefactor and eV/A^2 -> N/m.
+void df_stencil(double A_pp, double dz, double k, double f0, int m, float* coef);
+
+// Launchers (one per kernel translation unit).
+struct FFLaunch {
+    const float *x, *y, *z, *R, *eps, *q;
+    int n;
+    float R_pp, eps_pp, kQ, core_frac, coul_rc;
+    int min_image;
+    float Lx, Ly;
+    float x0, y0, z0, dx, dy, dz;
+    GridMap map;
+    float4* ff;
+};
+cudaError_t launch_ff_assemble(const FFLaunch& L, cudaStream_t s);
+
+struct RelaxLaunch {
+    const float4* ff;
+    GridMap map;
+    float gx0, gy0, gz0, inv_dx, inv_dy, inv_dz;
+    int periodic_xy;
+    int snx, sny, snz;
+    float sx0, sy0, spx, spy, z_top, sdz;
+    float kx, ky, kR, R0, d0x, d0y, d0z;  // eV/A^2, A
+    int max_iter, n_min;
+    float ftol2, dt0, dt_max, f_inc, f_dec, alpha0, f_alpha, inv_mass;
+    float* pos;
+    float* fz;
+    int* iters;
+    int df_m;      // -1: no fused df
+    float* df;
+    float coef[2 * kMaxDfHalfWidth + 1];
+};
+cudaError_t launch_relax_scan(const RelaxLaunch& L, cudaStream_t s);
+
+struct DfLaunch {
+    const float* fz;
+    float* df;
+    int nz, npix, m;
+    float coef[2 * kMaxDfHalfWidth + 1];
+};
+cudaError_t launch_fz_to_df(const DfLaunch& L, cudaStream_t s);
+
+cudaError_t launch_ff_convert(const float4* src, const GridMap& sm, float4* dst, const GridMap& dm,
+                              cudaStream_t s);
+
+}  // namespace pp

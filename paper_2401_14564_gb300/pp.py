@@ -1,0 +1,220 @@
+"""ctypes binding of libpp (include/pp.h): same entry points, argument marshalling only.
+
+Every function takes torch CUDA tensors (device memory) and plain dicts of
+parameters, turns them into the C structs of pp.h, and calls the library on
+the current torch stream.  All arithmetic happens in the CUDA kernels; there is
+no CPU path.  A missing or unloadable libpp.so raises at first use.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+import threading
+
+import torch
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+HEADER = os.path.join(os.path.dirname(PKG), "include", "pp.h")
+LIB_PATH = os.path.join(PKG, "libpp.so")
+
+STATUS = {0: "PP_OK", 1: "PP_ERR_ARG", 2: "PP_ERR_SHAPE", 3: "PP_ERR_CUDA", 4: "PP_ERR_CAPACITY",
+          5: "PP_ERR_TIMEOUT", 6: "PP_ERR_UNSUPPORTED"}
+
+
+class PPError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+fp = C.POINTER(C.c_float)
+
+
+class Atoms(C.Structure):
+    _fields_ = [("n", C.c_int)] + [(k, C.c_void_p) for k in ("x", "y", "z", "R", "eps", "q")]
+
+
+class Probe(C.Structure):
+    _fields_ = [("R_pp", C.c_float), ("eps_pp", C.c_float), ("Q", C.c_float), ("coul_rc", C.c_float),
+                ("min_image", C.c_int), ("core_frac", C.c_float)]
+
+
+class Grid(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int)] + \
+               [(k, C.c_float) for k in ("x0", "y0", "z0", "dx", "dy", "dz")] + \
+               [(k, C.c_int) for k in ("periodic_xy", "layout", "bx", "by", "bz")]
+
+
+class Tip(C.Structure):
+    _fields_ = [(k, C.c_float) for k in ("kx", "ky", "kR", "R0", "d0x", "d0y")]
+
+
+class Scan(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int)] + \
+               [(k, C.c_float) for k in ("x0", "y0", "px", "py", "z_top", "dz")]
+
+
+class Fire(C.Structure):
+    _fields_ = [("max_iter", C.c_int)] + \
+               [(k, C.c_float) for k in ("ftol", "dt0", "dt_max", "f_inc", "f_dec", "alpha0", "f_alpha", "mass")] + \
+               [("n_min", C.c_int)]
+
+
+class DF(C.Structure):
+    _fields_ = [("A_pp", C.c_float), ("k", C.c_float), ("f0", C.c_float)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def declared_symbols(header=HEADER):
+    """Names of the entry points declared in include/pp.h."""
+    text = open(header).read()
+    return re.findall(r"^PP_API\s+[\w\s\*]+?\b(pp_\w+)\s*\(", text, flags=re.M)
+
+
+def lib():
+    """Load libpp.so (raises if it was not built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                                   "or python -m paper_2401_14564_gb300.build")
+            L = C.CDLL(LIB_PATH)
+            vp, st = C.c_void_p, C.c_int
+            L.pp_ff_floats.argtypes = [C.POINTER(Grid)]
+            L.pp_ff_floats.restype = C.c_size_t
+            L.pp_df_margin.argtypes = [C.c_float, C.c_float]
+            L.pp_df_margin.restype = C.c_int
+            L.pp_make_ff.argtypes = [C.POINTER(Atoms), C.POINTER(Probe), C.POINTER(Grid), vp, vp]
+            L.pp_make_ff.restype = st
+            L.pp_relax_scan.argtypes = [vp, C.POINTER(Grid), C.POINTER(Scan), C.POINTER(Tip), C.POINTER(Fire),
+                                        vp, vp, vp, C.POINTER(DF), vp, vp]
+            L.pp_relax_scan.restype = st
+            L.pp_fz_to_df.argtypes = [vp, C.c_int, C.c_int, C.c_float, C.POINTER(DF), vp, vp]
+            L.pp_fz_to_df.restype = st
+            L.pp_ff_convert.argtypes = [vp, C.POINTER(Grid), vp, C.POINTER(Grid), vp]
+            L.pp_ff_convert.restype = st
+            L.pp_last_error.argtypes = []
+            L.pp_last_error.restype = C.c_char_p
+            _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != 0:
+        raise PPError(status, lib().pp_last_error().decode())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _dev(t, name, dtype=torch.float32, allow_none=False):
+    if t is None:
+        if allow_none:
+            return None
+        raise ValueError(f"{name} is required")
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t.data_ptr()
+
+
+# ----------------------------------------------------------------- structs
+
+def make_grid(g, layout=0, brick=(4, 4, 4)):
+    return Grid(int(g["nx"]), int(g["ny"]), int(g["nz"]), g["x0"], g["y0"], g["z0"], g["dx"], g["dy"], g["dz"],
+                int(g["periodic_xy"]), int(g.get("layout", layout)), *[int(b) for b in g.get("brick", brick)])
+
+
+def make_probe(p):
+    return Probe(p["R_pp"], p["eps_pp"], p["Q"], p["coul_rc"], int(p["min_image"]), p["core_frac"])
+
+
+def make_tip(t):
+    return Tip(t["kx"], t["ky"], t["kR"], t["R0"], t["d0x"], t["d0y"])
+
+
+def make_scan(s):
+    return Scan(int(s["nx"]), int(s["ny"]), int(s["nz"]), s["x0"], s["y0"], s["px"], s["py"], s["z_top"], s["dz"])
+
+
+def make_fire(f):
+    return Fire(int(f["max_iter"]), f["ftol"], f["dt0"], f["dt_max"], f["f_inc"], f["f_dec"], f["alpha0"],
+                f["f_alpha"], f["mass"], int(f["n_min"]))
+
+
+def make_df(d):
+    return DF(d["A_pp"], d["k"], d["f0"])
+
+
+def make_atoms(t):
+    """t: dict of six float32 CUDA tensors x, y, z, R, eps, q (length n)."""
+    n = int(t["x"].numel())
+    ptrs = [_dev(t[k], k) if n > 0 else 0 for k in ("x", "y", "z", "R", "eps", "q")]
+    for k in ("x", "y", "z", "R", "eps", "q"):
+        if t[k].numel() != n:
+            raise ValueError("atom arrays differ in length")
+    return Atoms(n, *ptrs)
+
+
+# ----------------------------------------------------------------- entry points
+
+def pp_ff_floats(grid: Grid) -> int:
+    return int(lib().pp_ff_floats(C.byref(grid)))
+
+
+def pp_df_margin(A_pp: float, dz: float) -> int:
+    return int(lib().pp_df_margin(A_pp, dz))
+
+
+def pp_make_ff(atoms: Atoms, probe: Probe, grid: Grid, ff: torch.Tensor, stream=None):
+    if ff.numel() < pp_ff_floats(grid):
+        raise ValueError("ff buffer smaller than pp_ff_floats(grid)")
+    _check(lib().pp_make_ff(C.byref(atoms), C.byref(probe), C.byref(grid), _dev(ff, "ff"), _stream(stream)))
+
+
+def pp_relax_scan(ff, grid: Grid, scan: Scan, tip: Tip, fire: Fire, pos, fz, iters, fused_df=None, df=None,
+                  stream=None):
+    npx = scan.nx * scan.ny * scan.nz
+    if fz.numel() < npx or (pos is not None and pos.numel() < 3 * npx) or (iters is not None and iters.numel() < npx):
+        raise ValueError("output buffer too small for the scan")
+    if ff.numel() < pp_ff_floats(grid):
+        raise ValueError("ff buffer smaller than pp_ff_floats(grid)")
+    if df is not None and fused_df is not None:
+        m = pp_df_margin(fused_df.A_pp, scan.dz)
+        if m >= 0 and df.numel() < (scan.nz - 2 * m) * scan.nx * scan.ny:
+            raise ValueError("df buffer too small")
+    _check(lib().pp_relax_scan(_dev(ff, "ff"), C.byref(grid), C.byref(scan), C.byref(tip), C.byref(fire),
+                               _dev(pos, "pos", allow_none=True), _dev(fz, "fz"),
+                               _dev(iters, "iters", torch.int32, allow_none=True),
+                               C.byref(fused_df) if fused_df is not None else None,
+                               _dev(df, "df", allow_none=True), _stream(stream)))
+
+
+def pp_fz_to_df(fz, nz: int, npix: int, dz: float, df_params: DF, df, stream=None):
+    m = pp_df_margin(df_params.A_pp, dz)
+    if fz.numel() < nz * npix or (m >= 0 and df.numel() < max(nz - 2 * m, 0) * npix):
+        raise ValueError("buffer too small")
+    _check(lib().pp_fz_to_df(_dev(fz, "fz"), int(nz), int(npix), float(dz), C.byref(df_params), _dev(df, "df"),
+                             _stream(stream)))
+
+
+def pp_ff_convert(src, src_grid: Grid, dst, dst_grid: Grid, stream=None):
+    if src.numel() < pp_ff_floats(src_grid) or dst.numel() < pp_ff_floats(dst_grid):
+        raise ValueError("buffer too small")
+    _check(lib().pp_ff_convert(_dev(src, "src"), C.byref(src_grid), _dev(dst, "dst"), C.byref(dst_grid),
+                               _stream(stream)))
+
+
+def pp_last_error() -> str:
+    return lib().pp_last_error().decode()

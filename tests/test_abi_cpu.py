@@ -1,0 +1,67 @@
+"""The C-ABI library loads without a GPU, exports every entry point that
+include/pp.h declares, and rejects bad arguments on the host before any launch."""
+import ctypes as C
+
+import pytest
+
+from paper_2401_14564_gb300 import build, pp
+
+
+@pytest.fixture(scope="module")
+def L():
+    build.build()
+    return pp.lib()
+
+
+def test_exports_every_declared_symbol(L):
+    names = pp.declared_symbols()
+    assert {"pp_make_ff", "pp_relax_scan", "pp_fz_to_df", "pp_last_error"} <= set(names)
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_ff_floats_and_layouts(L):
+    g = pp.make_grid({"nx": 10, "ny": 6, "nz": 5, "x0": 0, "y0": 0, "z0": 0, "dx": 0.1, "dy": 0.1, "dz": 0.1,
+                      "periodic_xy": 1})
+    assert pp.pp_ff_floats(g) == 10 * 6 * 5 * 4
+    g.layout = 1
+    g.bx, g.by, g.bz = 4, 4, 2
+    assert pp.pp_ff_floats(g) == (3 * 4) * (2 * 4) * (3 * 2) * 4
+    g.bx = 3
+    assert pp.pp_ff_floats(g) == 0
+    g.layout = 0
+    g.nz = 1
+    assert pp.pp_ff_floats(g) == 0
+
+
+def test_df_margin(L):
+    assert pp.pp_df_margin(1.0, 0.1) == 5
+    assert pp.pp_df_margin(1.0, 0.3) == 2
+    assert pp.pp_df_margin(0.0, 0.1) == -1
+    assert pp.pp_df_margin(1.0, -0.1) == -1
+
+
+def test_null_arguments_rejected_on_host(L):
+    assert L.pp_make_ff(None, None, None, None, None) == 1
+    assert b"NULL" in L.pp_last_error()
+    assert L.pp_relax_scan(None, None, None, None, None, None, None, None, None, None, None) == 1
+    assert L.pp_fz_to_df(None, 10, 10, C.c_float(0.1), None, None, None) == 1
+
+
+def test_bad_shapes_rejected_on_host(L):
+    grid = pp.make_grid({"nx": 1, "ny": 6, "nz": 5, "x0": 0, "y0": 0, "z0": 0, "dx": 0.1, "dy": 0.1, "dz": 0.1,
+                         "periodic_xy": 1})
+    probe = pp.make_probe({"R_pp": 1.66, "eps_pp": 0.0091, "Q": -0.1, "coul_rc": 0.0, "min_image": 0,
+                           "core_frac": 0.5})
+    atoms = pp.Atoms(0, None, None, None, None, None, None)
+    fake = C.c_void_p(16)  # never dereferenced: the shape check fails first
+    assert L.pp_make_ff(C.byref(atoms), C.byref(probe), C.byref(grid), fake, None) == 2
+    assert b"nz >= 2" in L.pp_last_error() or b"nx, ny, nz" in L.pp_last_error()
+    probe.core_frac = 1.5
+    grid.nx = 4
+    assert L.pp_make_ff(C.byref(atoms), C.byref(probe), C.byref(grid), fake, None) == 1
+    dfp = pp.DF(1.0, 1800.0, 30300.0)
+    # 5 heights cannot hold an 11-tap stencil
+    assert L.pp_fz_to_df(fake, 5, 7, C.c_float(0.1), C.byref(dfp), fake, None) == 2
+    dfp.A_pp = 10.0  # 101 taps
+    assert L.pp_fz_to_df(fake, 200, 7, C.c_float(0.1), C.byref(dfp), fake, None) == 6
