@@ -48,6 +48,19 @@ def relax_compare(r_gpu, r_orc, basin_tol=0.05, lam_min=0.01):
             int((~well).sum()), int((well & ~same).sum()))
 
 
+def ill_conditioned_within_bound(pos_gpu, r_orc, ftol, lam_min=0.01, basin_tol=0.05, slack=1e-4):
+    """Entries with 0 < lambda < lam_min in the same basin obey |dp| <= 1.1 ftol / lambda + slack.
+
+    FIRE stops at |G| < ftol, so the GPU position can sit ftol/lambda from the fixed
+    point (plus FP32 rounding of the grid, ~1e-6 relative); returns (checked, ok) counts.
+    """
+    dp = np.linalg.norm(pos_gpu - r_orc["pos"], axis=-1)
+    lam = r_orc["lam"]
+    sel = (lam > 0) & (lam < lam_min) & (dp < basin_tol)
+    ok = dp[sel] <= 1.1 * ftol / lam[sel] + slack
+    return int(sel.sum()), int(ok.sum())
+
+
 def df_keep(keep, m):
     """A df output centred at c is compared when all heights c-m..c+m are kept."""
     nz = keep.shape[0]
