@@ -168,6 +168,50 @@ def workload_config(case):
             "parallelism": "replicas", "l2": "flushed (256 MiB write) before every timed step; FF grid 210 MB > L2"}
 
 
+def measure_bwd_fwd(case, steps, warmup, flush, tag):
+    """CUDA-event times of the forward (FF + relaxed scan + df) and of pp_backward on one workload."""
+    import torch
+
+    from paper_2401_14564_gb300 import afm, pp
+
+    sim = afm.Simulator(case)
+    atoms_t = afm.atoms_to_device(case["atoms"])
+    n = len(case["atoms"]["x"])
+    grads = {k: torch.empty(n, device="cuda") for k in ("x", "y", "z", "q", "R", "eps")}
+    grads["tip"] = torch.empty(4, device="cuda")
+    ws = torch.empty(pp.pp_backward_workspace(sim.grid) // 4 + 1, dtype=torch.float32, device="cuda")
+    w = torch.randn(tuple(sim.df.shape), generator=torch.Generator().manual_seed(7)).to("cuda")
+    atoms = pp.make_atoms(atoms_t)
+    g = pp.make_grads(grads)
+
+    def bwd():
+        pp.pp_backward(atoms, sim.probe, sim.grid, sim.ff, sim.scan, sim.tip, sim.dfp, sim.pos, w, g, ws)
+
+    for _ in range(max(warmup, 3)):
+        sim.run(atoms_t)
+        bwd()
+    stream = torch.cuda.current_stream()
+    tf, tb = [], []
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        sim.run(atoms_t)
+        e1.record(stream)
+        flush.zero_()
+        e2a = torch.cuda.Event(enable_timing=True)
+        e2a.record(stream)
+        bwd()
+        e2.record(stream)
+        torch.cuda.synchronize()
+        tf.append(e0.elapsed_time(e1))
+        tb.append(e2a.elapsed_time(e2))
+    f, b = statistics.mean(tf), statistics.mean(tb)
+    return {"workload": tag, "fwd_ms": f, "bwd_ms": b, "ratio": b / f,
+            "note": "forward = FF + relaxed scan + fused df; backward = pp_backward (df adjoint, 3x3 implicit solves, "
+                    "grid-adjoint scatter, per-atom pair-derivative sums); L2 flushed before each"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -286,6 +330,13 @@ def main():
             "e2e": {"value": world * units / (e2e_ms * 1e-3), "unit": UNIT,
                     "h2d_bytes_per_step": sim.h2d_bytes(len(case["atoms"]["x"])), "d2h_bytes_per_step": sim.d2h_bytes()},
             "gpu_launches": 2 * args.steps, "clocks": clk, "wall_s_timed": t_wall}
+    g4 = synth.gradient_case()
+    line["bwd_fwd"] = [
+        measure_bwd_fwd(g4, max(3, args.steps // 2), args.warmup, flush,
+                        "mol40 seed 4040: 40 atoms, grid %dx%dx%d, scan 128x128x20" % (
+                            g4["grid"]["nx"], g4["grid"]["ny"], g4["grid"]["nz"])),
+        measure_bwd_fwd(case, max(3, args.steps // 2), args.warmup, flush, "flake60 (this line's workload)"),
+    ]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(case)
     if rank == 0:

@@ -21,8 +21,7 @@
  *              and keeps no pointer after the call returns (its kernels may
  *              still be running on `stream`).
  *   Execution  All work is enqueued on `stream` (a cudaStream_t; NULL = the
- *              legacy default stream).  No call synchronises the host except
- *              pp_backward when it is given a NULL workspace size query.
+ *              legacy default stream).  No call synchronises the host.
  *   Errors     Every call returns a pp_status; nothing throws across the ABI.
  *              Shapes, sizes and NULL pointers are checked on the host before
  *              any launch; a failed check launches nothing.  PP_ERR_CUDA means
@@ -185,6 +184,40 @@ PP_API pp_status pp_fz_to_df(const float* fz, int nz, int npix, float dz, const 
  * Errors: PP_ERR_ARG, PP_ERR_SHAPE, PP_ERR_CUDA. */
 PP_API pp_status pp_ff_convert(const float* src, const pp_grid* src_grid, float* dst,
                         const pp_grid* dst_grid, pp_stream stream);
+
+/* Gradients of pp_backward, device arrays owned by the caller: x, y, z, q, R,
+ * eps hold n floats each (dL/dx_i in 1/A, dL/dq_i per e, dL/dR_i per A,
+ * dL/deps_i per eV); tip holds 4 floats {dL/dkx, dL/dky, dL/dkR (per N/m),
+ * dL/dQ (per e)}.  pp_backward overwrites all of them. */
+typedef struct {
+    float *x, *y, *z, *q, *R, *eps;
+    float* tip;
+} pp_grads;
+
+/* Bytes of scratch pp_backward needs for `grid`: a 256-byte header plus one
+ * float4 per stored grid node (the grid adjoint); 0 if the grid is invalid. */
+PP_API size_t pp_backward_workspace(const pp_grid* grid);
+
+/* Gradient of L = sum_{c,pix} g_df[c][pix] * df[c][pix] with respect to the
+ * atoms (x, y, z, q, R, eps) and the tip (kx, ky, kR, Q).  The paper has no
+ * gradients: this is the implicit-function adjoint of the same discrete
+ * model at the relaxed positions of a forward pass -- for every relaxed point
+ * J^T lambda = (dFz/dp)^T g_Fz with J the exact 3x3 Jacobian of F_T + F_S
+ * (trilinear interpolant included), g_Fz the transpose of the df stencil
+ * (Eq. df) applied to g_df, then a grid adjoint -lambda (x) trilinear weights
+ * contracted with the pair derivatives of Eqs. LJ and point charges on the
+ * nodes it touches.  Inputs: the forward's atoms, probe, grid, force field
+ * `ff`, scan, tip and df parameters, and its relaxed positions
+ * pos[nz][ny][nx][3]; g_df[nz-2m][ny][nx].  Points where FIRE stopped at
+ * max_iter are differentiated as if converged.  Scratch `ws` (16-byte
+ * aligned, >= pp_backward_workspace(grid) bytes) is overwritten; FP32
+ * atomics make the sums order-dependent at rounding level.  Errors:
+ * PP_ERR_ARG, PP_ERR_SHAPE, PP_ERR_CAPACITY (ws too small), PP_ERR_UNSUPPORTED
+ * (df stencil wider than 63 taps), PP_ERR_CUDA. */
+PP_API pp_status pp_backward(const pp_atoms* atoms, const pp_probe* probe, const pp_grid* grid,
+                             const float* ff, const pp_scan* scan, const pp_tip* tip,
+                             const pp_df* df_params, const float* pos, const float* g_df,
+                             const pp_grads* grads, void* ws, size_t ws_bytes, pp_stream stream);
 
 /* Message of the last failed call on this host thread ("" if none). */
 PP_API const char* pp_last_error(void);

@@ -204,8 +204,10 @@ pp_status pp_relax_scan(const float* ff, const pp_grid* grid, const pp_scan* sca
     std::memset(&L, 0, sizeof(L));
     L.ff = reinterpret_cast<const float4*>(ff);
     L.map = map;
-    L.gx0 = grid->x0; L.gy0 = grid->y0; L.gz0 = grid->z0;
     L.inv_dx = 1.f / grid->dx; L.inv_dy = 1.f / grid->dy; L.inv_dz = 1.f / grid->dz;
+    L.gx0s = (float)(-(double)grid->x0 / grid->dx);
+    L.gy0s = (float)(-(double)grid->y0 / grid->dy);
+    L.gz0s = (float)(-(double)grid->z0 / grid->dz);
     L.periodic_xy = grid->periodic_xy;
     L.snx = scan->nx; L.sny = scan->ny; L.snz = scan->nz;
     L.sx0 = scan->x0; L.sy0 = scan->y0; L.spx = scan->px; L.spy = scan->py;
@@ -217,6 +219,9 @@ pp_status pp_relax_scan(const float* ff, const pp_grid* grid, const pp_scan* sca
     L.d0x = tip->d0x;
     L.d0y = tip->d0y;
     L.d0z = (float)(-sqrt((double)tip->R0 * tip->R0 - (double)tip->d0x * tip->d0x - (double)tip->d0y * tip->d0y));
+    L.R0sq = (float)((double)tip->R0 * tip->R0);
+    L.c0 = (float)((double)L.d0x * L.d0x + (double)L.d0y * L.d0y + (double)L.d0z * L.d0z - (double)tip->R0 * tip->R0);
+    L.layout = grid->layout;
     L.max_iter = fire->max_iter;
     L.n_min = fire->n_min;
     L.ftol2 = fire->ftol * fire->ftol;
@@ -254,6 +259,97 @@ pp_status pp_fz_to_df(const float* fz, int nz, int npix, float dz, const pp_df* 
     if (npix == 0) return PP_OK;
     df_stencil(dfp->A_pp, dz, dfp->k, dfp->f0, m, L.coef);
     return cuda_status(launch_fz_to_df(L, (cudaStream_t)stream), "pp_fz_to_df launch");
+}
+
+size_t pp_backward_workspace(const pp_grid* grid) {
+    GridMap m;
+    std::string why;
+    if (!make_grid_map(grid, &m, &why)) return 0;
+    return kBwdHeader + (size_t)m.stored_nodes * 16;
+}
+
+pp_status pp_backward(const pp_atoms* atoms, const pp_probe* probe, const pp_grid* grid, const float* ff,
+                      const pp_scan* scan, const pp_tip* tip, const pp_df* dfp, const float* pos, const float* g_df,
+                      const pp_grads* grads, void* ws, size_t ws_bytes, pp_stream stream) {
+    g_error.clear();
+    if (!atoms || !probe || !grid || !ff || !scan || !tip || !dfp || !pos || !g_df || !grads || !ws) {
+        set_error("pp_backward: NULL argument");
+        return PP_ERR_ARG;
+    }
+    if (atoms->n < 0) { set_error("pp_backward: atoms->n < 0"); return PP_ERR_ARG; }
+    if (atoms->n > 0 && (!atoms->x || !atoms->y || !atoms->z || !atoms->R || !atoms->eps || !atoms->q ||
+                         !grads->x || !grads->y || !grads->z || !grads->q || !grads->R || !grads->eps)) {
+        set_error("pp_backward: NULL atom or gradient array");
+        return PP_ERR_ARG;
+    }
+    if (!grads->tip) { set_error("pp_backward: NULL tip gradient"); return PP_ERR_ARG; }
+    if (!aligned16(ff) || !aligned16(ws)) { set_error("pp_backward: ff and ws must be 16-byte aligned"); return PP_ERR_ARG; }
+    if (!(probe->core_frac > 0.f && probe->core_frac < 1.f) || !(probe->eps_pp >= 0.f) || !(probe->coul_rc >= 0.f) ||
+        (probe->min_image != 0 && probe->min_image != 1)) {
+        set_error("pp_backward: invalid probe parameters");
+        return PP_ERR_ARG;
+    }
+    GridMap map;
+    std::string why;
+    if (!make_grid_map(grid, &map, &why)) { set_error("pp_backward: " + why); return PP_ERR_SHAPE; }
+    if (scan->nx < 1 || scan->ny < 1 || scan->nz < 1 ||
+        (int64_t)scan->nx * scan->ny * scan->nz * 3 >= (int64_t(1) << 31)) {
+        set_error("pp_backward: invalid scan size");
+        return PP_ERR_SHAPE;
+    }
+    if (!finite_pos(scan->dz)) { set_error("pp_backward: invalid scan geometry"); return PP_ERR_ARG; }
+    pp_fire dummy = {1, 1.f, 1.f, 1.f, 1.f, 1.f, 0.f, 1.f, 1.f, 0};
+    if (!check_tip_fire(tip, &dummy, &why)) { set_error("pp_backward: " + why); return PP_ERR_ARG; }
+    if (!finite_pos(dfp->k) || !isfinite(dfp->f0)) { set_error("pp_backward: invalid df parameters"); return PP_ERR_ARG; }
+    const int m = df_half_width(dfp->A_pp, scan->dz);
+    if (m < 0) { set_error("pp_backward: invalid df amplitude"); return PP_ERR_ARG; }
+    if (m > kMaxDfHalfWidth) { set_error("pp_backward: df stencil wider than 63 taps"); return PP_ERR_UNSUPPORTED; }
+    if (scan->nz < 2 * m + 1) { set_error("pp_backward: fewer heights than the df stencil"); return PP_ERR_SHAPE; }
+    const size_t need = kBwdHeader + (size_t)map.stored_nodes * 16;
+    if (ws_bytes < need) {
+        set_error("pp_backward: workspace too small (need " + std::to_string(need) + " bytes)");
+        return PP_ERR_CAPACITY;
+    }
+    BwdLaunch L;
+    std::memset(&L, 0, sizeof(L));
+    L.ax = atoms->x; L.ay = atoms->y; L.az = atoms->z; L.aR = atoms->R; L.aeps = atoms->eps; L.aq = atoms->q;
+    L.n = atoms->n;
+    L.R_pp = probe->R_pp; L.eps_pp = probe->eps_pp;
+    L.kQ = (float)(kCoulomb * (double)probe->Q);
+    L.ke = (float)kCoulomb;
+    L.Q = probe->Q;
+    L.core_frac = probe->core_frac; L.coul_rc = probe->coul_rc; L.min_image = probe->min_image;
+    L.Lx = grid->nx * grid->dx; L.Ly = grid->ny * grid->dy;
+    L.ff = reinterpret_cast<const float4*>(ff);
+    L.map = map;
+    L.layout = grid->layout;
+    L.x0 = grid->x0; L.y0 = grid->y0; L.z0 = grid->z0; L.dx = grid->dx; L.dy = grid->dy; L.dz = grid->dz;
+    L.inv_dx = 1.f / grid->dx; L.inv_dy = 1.f / grid->dy; L.inv_dz = 1.f / grid->dz;
+    L.gx0s = (float)(-(double)grid->x0 / grid->dx);
+    L.gy0s = (float)(-(double)grid->y0 / grid->dy);
+    L.gz0s = (float)(-(double)grid->z0 / grid->dz);
+    L.periodic_xy = grid->periodic_xy;
+    L.snx = scan->nx; L.sny = scan->ny; L.snz = scan->nz;
+    L.sx0 = scan->x0; L.sy0 = scan->y0; L.spx = scan->px; L.spy = scan->py; L.z_top = scan->z_top; L.sdz = scan->dz;
+    L.kx = (float)(tip->kx * kNmToEvA2); L.ky = (float)(tip->ky * kNmToEvA2); L.kR = (float)(tip->kR * kNmToEvA2);
+    L.R0 = tip->R0; L.d0x = tip->d0x; L.d0y = tip->d0y;
+    L.d0z = (float)(-sqrt((double)tip->R0 * tip->R0 - (double)tip->d0x * tip->d0x - (double)tip->d0y * tip->d0y));
+    L.R0sq = (float)((double)tip->R0 * tip->R0);
+    L.c0 = (float)((double)L.d0x * L.d0x + (double)L.d0y * L.d0y + (double)L.d0z * L.d0z - (double)tip->R0 * tip->R0);
+    L.nm = (float)kNmToEvA2;
+    L.m = m;
+    L.nzo = scan->nz - 2 * m;
+    df_stencil(dfp->A_pp, scan->dz, dfp->k, dfp->f0, m, L.coef);
+    L.pos = pos;
+    L.g_df = g_df;
+    L.gx = grads->x; L.gy = grads->y; L.gz = grads->z; L.gq = grads->q; L.gR = grads->R; L.geps = grads->eps;
+    L.gtip = grads->tip;
+    L.slab = reinterpret_cast<int*>(ws);
+    L.gbar = reinterpret_cast<float4*>(reinterpret_cast<char*>(ws) + kBwdHeader);
+    cudaStream_t s = (cudaStream_t)stream;
+    pp_status st = cuda_status(cudaMemsetAsync(L.gbar, 0, (size_t)map.stored_nodes * 16, s), "pp_backward memset");
+    if (st != PP_OK) return st;
+    return cuda_status(launch_backward(L, s), "pp_backward launch");
 }
 
 pp_status pp_ff_convert(const float* src, const pp_grid* src_grid, float* dst, const pp_grid* dst_grid,

@@ -1,0 +1,287 @@
+// Adjoint of the df image with respect to atoms and tip parameters.
+//
+// The paper has no gradients; this differentiates the same discrete model.
+// For L = sum g_df * df:
+//   K3^T  g_Fz = transpose of the df stencil applied to g_df (fused into K4);
+//   K4    per relaxed point (pixel, height), at equilibrium G(p*) = 0 the
+//         implicit function theorem gives dp*/dtheta = -J^{-1} dG/dtheta with
+//         J = dG/dp (tip-spring Jacobian + exact Jacobian of the trilinear
+//         interpolant), so with lambda = J^{-T} (dFz/dp)^T g_Fz:
+//           dL/dtheta = g_Fz dFz/dtheta - lambda . dG/dtheta.
+//         The grid values enter G through the trilinear weights, so the grid
+//         adjoint is Gbar_g = -sum lambda w_g(p*) (float4 atomics); the tip
+//         springs give dL/dkx = lambda_x e_x, dL/dky = lambda_y e_y, and
+//         dL/dkR = g_Fz (|d|-R0) d_z/|d| + lambda.d (|d|-R0)/|d|;
+//   K5    dL/dtheta_i = sum_g Gbar_g . dF_g/dtheta_i for every atom, by
+//         recomputing the pair terms of the force-field grid (Eqs. LJ and
+//         point charges) on the grid nodes with a nonzero adjoint, restricted
+//         to the z-slab K4 touched;
+//   fin   charges: dL/dq_i = Q C_i, dL/dQ = sum_i q_i C_i with
+//         C_i = sum_g (Gbar_g . delta) k_e c(r); eps via e_iPP = sqrt(e_i e_PP).
+// No relaxation iterate is stored or replayed: only the saved p*.
+#include "interp.cuh"
+
+namespace pp {
+namespace {
+
+constexpr int kAdjThreads = 128;
+constexpr int kFFBThreads = 64;
+constexpr int kFFBNodes = 512;  // grid nodes staged per K5 CTA
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__global__ void init_kernel(const BwdLaunch P) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t == 0) {
+        P.slab[0] = 0x7fffffff;
+        P.slab[1] = -1;
+        P.gtip[0] = P.gtip[1] = P.gtip[2] = P.gtip[3] = 0.f;
+    }
+    for (int a = t; a < P.n; a += gridDim.x * blockDim.x) {
+        P.gx[a] = 0.f; P.gy[a] = 0.f; P.gz[a] = 0.f;
+        P.gq[a] = 0.f; P.gR[a] = 0.f; P.geps[a] = 0.f;
+    }
+}
+
+template <int LAYOUT>
+__global__ void __launch_bounds__(kAdjThreads) relax_adjoint_kernel(const BwdLaunch P) {
+    const int npix = P.snx * P.sny;
+    const int64_t total = (int64_t)npix * P.snz;
+    const int64_t o = (int64_t)blockIdx.x * kAdjThreads + threadIdx.x;
+    float gkx = 0.f, gky = 0.f, gkR = 0.f;
+    int kmin = 0x7fffffff, kmax = -1;
+    if (o < total) {
+        const int k = (int)(o / npix), pix = (int)(o - (int64_t)k * npix);
+        // g_Fz = (df stencil)^T g_df: df[c] = sum_s coef[s+m] Fz[c+m+s]
+        float gf = 0.f;
+        for (int s = -P.m; s <= P.m; ++s) {
+            const int c = k - P.m - s;
+            if (c >= 0 && c < P.nzo) gf = fmaf(P.coef[s + P.m], __ldg(P.g_df + (int64_t)c * npix + pix), gf);
+        }
+        if (gf != 0.f) {
+            const int i = pix % P.snx, j = pix / P.snx;
+            const float px = __ldg(P.pos + 3 * o), py = __ldg(P.pos + 3 * o + 1), pz = __ldg(P.pos + 3 * o + 2);
+            const float ax = fmaf((float)i, P.spx, P.sx0), ay = fmaf((float)j, P.spy, P.sy0);
+            const float az = P.z_top - k * P.sdz;
+            const float dx = px - ax, dy = py - ay, dz = pz - az;
+            const float ex = dx - P.d0x, ey = dy - P.d0y, ez = dz - P.d0z;
+            // q = |d|^2 - R0^2 without cancellation, as in the forward kernel
+            const float q = fmaf(2.f * P.d0x + ex, ex, fmaf(2.f * P.d0y + ey, ey, fmaf(2.f * P.d0z + ez, ez, P.c0)));
+            const float d2 = P.R0sq + q;
+            const float rs = rsqrtf(d2);
+            const float dn = d2 * rs;
+            const float ext = __fdividef(q, fmaf(P.R0, dn, d2));  // (|d| - R0) / |d|
+            const float ar = -P.kR * ext;                          // -kR (1 - R0/|d|)
+            const float br = -P.kR * P.R0 * rs * rs * rs;          // -kR R0 / |d|^3
+            // J = dF_T/dd + dF_S/dp
+            const Cells cl = locate(P, px, py, pz);
+            float4 v[8];
+            load_corners<LAYOUT>(P.ff, P.map, cl, v);
+            float J[3][3];
+            trilinear_jacobian(v, cl, P.inv_dx, P.inv_dy, P.inv_dz, J);
+            const float dd[3] = {dx, dy, dz};
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int b = 0; b < 3; ++b) J[a][b] += (a == b ? ar : 0.f) + br * dd[a] * dd[b];
+            J[0][0] -= P.kx;
+            J[1][1] -= P.ky;
+            // dFz/dp = kR [(1 - R0/|d|) z_hat + R0 d_z d / |d|^3]
+            const float r0 = -br * dz * dx * gf, r1 = -br * dz * dy * gf, r2 = (-ar - br * dz * dz) * gf;
+            // solve J^T lambda = r by the adjugate
+            const float a00 = J[0][0], a01 = J[1][0], a02 = J[2][0];
+            const float a10 = J[0][1], a11 = J[1][1], a12 = J[2][1];
+            const float a20 = J[0][2], a21 = J[1][2], a22 = J[2][2];
+            const float c00 = a11 * a22 - a12 * a21, c01 = a02 * a21 - a01 * a22, c02 = a01 * a12 - a02 * a11;
+            const float c10 = a12 * a20 - a10 * a22, c11 = a00 * a22 - a02 * a20, c12 = a02 * a10 - a00 * a12;
+            const float c20 = a10 * a21 - a11 * a20, c21 = a01 * a20 - a00 * a21, c22 = a00 * a11 - a01 * a10;
+            const float det = a00 * c00 + a01 * c10 + a02 * c20;
+            if (det != 0.f && isfinite(det)) {
+                const float id = 1.f / det;
+                const float lx = (c00 * r0 + c01 * r1 + c02 * r2) * id;
+                const float ly = (c10 * r0 + c11 * r1 + c12 * r2) * id;
+                const float lz = (c20 * r0 + c21 * r1 + c22 * r2) * id;
+                gkx = lx * ex;
+                gky = ly * ey;
+                gkR = gf * ext * dz + (lx * dx + ly * dy + lz * dz) * ext;
+                // grid adjoint: Gbar += -lambda w_g at the 8 corners
+                int idx[8];
+                corner_index<LAYOUT>(P.map, cl, idx);
+                float w[8];
+                corner_weights(cl, w);
+#pragma unroll
+                for (int c = 0; c < 8; ++c)
+                    if (w[c] != 0.f) atomicAdd(P.gbar + idx[c], make_float4(-lx * w[c], -ly * w[c], -lz * w[c], 0.f));
+                kmin = cl.z.i0;
+                kmax = cl.z.i1;
+            }
+        }
+    }
+    gkx = warp_sum(gkx);
+    gky = warp_sum(gky);
+    gkR = warp_sum(gkR);
+    kmin = __reduce_min_sync(0xffffffffu, kmin);
+    kmax = __reduce_max_sync(0xffffffffu, kmax);
+    if ((threadIdx.x & 31) == 0) {
+        if (gkx != 0.f) atomicAdd(P.gtip + 0, gkx * P.nm);
+        if (gky != 0.f) atomicAdd(P.gtip + 1, gky * P.nm);
+        if (gkR != 0.f) atomicAdd(P.gtip + 2, gkR * P.nm);
+        if (kmax >= 0) {
+            atomicMin(P.slab + 0, kmin);
+            atomicMax(P.slab + 1, kmax);
+        }
+    }
+}
+
+// K5: per-atom contraction of the grid adjoint with the pair derivatives.
+// A CTA stages kFFBNodes consecutive nodes (logical x-fastest order), keeps
+// those with a nonzero adjoint, and each thread then sweeps them for one atom,
+// accumulating (dx, dy, dz, dR, de_iPP, C) in registers.
+template <bool kMinImage, bool kCutoff>
+__global__ void __launch_bounds__(kFFBThreads) ff_backward_kernel(const BwdLaunch P) {
+    __shared__ float4 sp[kFFBNodes];  // node position (x, y, z, -)
+    __shared__ float4 sg[kFFBNodes];  // adjoint (gx, gy, gz, -)
+    __shared__ int scount;
+    const int nx = P.map.nx, ny = P.map.ny;
+    const int64_t nxy = (int64_t)nx * ny;
+    const int64_t first = (int64_t)blockIdx.x * kFFBNodes;
+    const int klo = P.slab[0], khi = P.slab[1];
+    if (khi < 0) return;
+    const int kfirst = (int)(first / nxy), klast = (int)((first + kFFBNodes - 1) / nxy);
+    if (klast < klo || kfirst > khi) return;
+    if (threadIdx.x == 0) scount = 0;
+    __syncthreads();
+    const int64_t total = nxy * P.map.nz;
+    for (int t = threadIdx.x; t < kFFBNodes; t += kFFBThreads) {
+        const int64_t g = first + t;
+        bool keep = false;
+        float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+        int i = 0, j = 0, k = 0;
+        if (g < total) {
+            k = (int)(g / nxy);
+            const int64_t r = g - (int64_t)k * nxy;
+            j = (int)(r / nx);
+            i = (int)(r - (int64_t)j * nx);
+            a = P.gbar[node_index(P.map, i, j, k)];
+            keep = (a.x != 0.f) || (a.y != 0.f) || (a.z != 0.f);
+        }
+        const unsigned mask = __ballot_sync(0xffffffffu, keep);
+        int base = 0;
+        if ((threadIdx.x & 31) == 0 && mask) base = atomicAdd(&scount, __popc(mask));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (keep) {
+            const int slot = base + __popc(mask & ((1u << (threadIdx.x & 31)) - 1u));
+            sp[slot] = make_float4(P.x0 + i * P.dx, P.y0 + j * P.dy, P.z0 + k * P.dz, 0.f);
+            sg[slot] = a;
+        }
+    }
+    __syncthreads();
+    const int cnt = scount;
+    if (cnt == 0) return;
+    const float rc2 = kCutoff ? P.coul_rc * P.coul_rc : 0.f;
+    const float irc2 = kCutoff ? 1.f / rc2 : 0.f;
+    const float invLx = kMinImage ? 1.f / P.Lx : 0.f, invLy = kMinImage ? 1.f / P.Ly : 0.f;
+    for (int a0 = 0; a0 < P.n; a0 += kFFBThreads) {
+        const int ia = a0 + threadIdx.x;
+        if (ia >= P.n) break;
+        const float ax = P.ax[ia], ay = P.ay[ia], azz = P.az[ia];
+        const float Rij = P.aR[ia] + P.R_pp;
+        const float eij = sqrtf(P.aeps[ia] * P.eps_pp);
+        const float qq = P.kQ * P.aq[ia];
+        const float rmin2 = (P.core_frac * Rij) * (P.core_frac * Rij);
+        const float R2 = Rij * Rij, iR = 1.f / Rij;
+        float gpx = 0.f, gpy = 0.f, gpz = 0.f, gRr = 0.f, ge = 0.f, C = 0.f;
+        for (int s = 0; s < cnt; ++s) {
+            const float4 np = sp[s], gb = sg[s];
+            float dx = np.x - ax, dy = np.y - ay;
+            const float dz = np.z - azz;
+            if (kMinImage) {
+                dx = fmaf(-P.Lx, rintf(dx * invLx), dx);
+                dy = fmaf(-P.Ly, rintf(dy * invLy), dy);
+            }
+            const float r2raw = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const bool clamped = r2raw < rmin2;
+            const float r2 = clamped ? rmin2 : r2raw;
+            const float rs = rsqrtf(r2);
+            const float ir2 = rs * rs;
+            const float s6 = R2 * ir2 * (R2 * ir2) * (R2 * ir2);
+            const float s12 = s6 * s6;
+            const float Slj_e = 12.f * (s12 - s6) * ir2;                 // LJ S per unit e_iPP
+            const float dSlj_dr = 12.f * eij * (8.f * s6 - 14.f * s12) * ir2 * rs;
+            const float dSlj_dR = 12.f * eij * (12.f * s12 - 6.f * s6) * ir2 * iR;
+            float c, dc_dr;
+            if (kCutoff) {
+                const bool in = r2 < rc2;
+                c = in ? rs * (ir2 - irc2) : 0.f;                        // 1/r^3 - 1/(r rc^2)
+                dc_dr = in ? ir2 * (irc2 - 3.f * ir2) : 0.f;             // -3/r^4 + 1/(r^2 rc^2)
+            } else {
+                c = rs * ir2;
+                dc_dr = -3.f * ir2 * ir2;
+            }
+            const float S = fmaf(eij, Slj_e, qq * c);
+            const float dSdr = fmaf(qq, dc_dr, dSlj_dr);
+            const float ad = fmaf(gb.x, dx, fmaf(gb.y, dy, gb.z * dz));
+            const float rad = clamped ? 0.f : dSdr * ad * rs;            // dS/dr (a.delta) / r
+            gpx -= fmaf(S, gb.x, rad * dx);
+            gpy -= fmaf(S, gb.y, rad * dy);
+            gpz -= fmaf(S, gb.z, rad * dz);
+            gRr = fmaf(ad, clamped ? fmaf(dSdr, P.core_frac, dSlj_dR) : dSlj_dR, gRr);
+            ge = fmaf(ad, Slj_e, ge);
+            C = fmaf(ad, c, C);
+        }
+        atomicAdd(P.gx + ia, gpx);
+        atomicAdd(P.gy + ia, gpy);
+        atomicAdd(P.gz + ia, gpz);
+        atomicAdd(P.gR + ia, gRr);
+        atomicAdd(P.geps + ia, ge);
+        atomicAdd(P.gq + ia, C);
+    }
+}
+
+// Charges and well depths from the accumulated sums; dL/dQ by a block reduction.
+__global__ void finalize_kernel(const BwdLaunch P) {
+    __shared__ float red[32];
+    float acc = 0.f;
+    for (int a = threadIdx.x; a < P.n; a += blockDim.x) {
+        const float C = P.gq[a] * P.ke;  // sum (a.delta) k_e c
+        acc = fmaf(P.aq[a], C, acc);
+        P.gq[a] = P.Q * C;
+        const float eij = sqrtf(P.aeps[a] * P.eps_pp);
+        P.geps[a] = eij > 0.f ? P.geps[a] * P.eps_pp / (2.f * eij) : 0.f;
+    }
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        float v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
+        v = warp_sum(v);
+        if (threadIdx.x == 0) P.gtip[3] = v;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_backward(const BwdLaunch& L, cudaStream_t s) {
+    init_kernel<<<(L.n + 255) / 256 + 1, 256, 0, s>>>(L);
+    const int64_t total = (int64_t)L.snx * L.sny * L.snz;
+    const int blocks = (int)((total + kAdjThreads - 1) / kAdjThreads);
+    if (L.layout == 0) relax_adjoint_kernel<0><<<blocks, kAdjThreads, 0, s>>>(L);
+    else relax_adjoint_kernel<1><<<blocks, kAdjThreads, 0, s>>>(L);
+    if (L.n > 0) {
+        const int64_t nodes = (int64_t)L.map.nx * L.map.ny * L.map.nz;
+        const int fb = (int)((nodes + kFFBNodes - 1) / kFFBNodes);
+        const bool cut = L.coul_rc > 0.f;
+        if (L.min_image && cut) ff_backward_kernel<true, true><<<fb, kFFBThreads, 0, s>>>(L);
+        else if (L.min_image) ff_backward_kernel<true, false><<<fb, kFFBThreads, 0, s>>>(L);
+        else if (cut) ff_backward_kernel<false, true><<<fb, kFFBThreads, 0, s>>>(L);
+        else ff_backward_kernel<false, false><<<fb, kFFBThreads, 0, s>>>(L);
+    }
+    finalize_kernel<<<1, 256, 0, s>>>(L);
+    return cudaGetLastError();
+}
+
+}  // namespace pp

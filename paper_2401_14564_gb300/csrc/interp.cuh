@@ -1,0 +1,181 @@
+// Device helpers shared by the relaxation (K2) and its adjoint (K4): packed
+// FP32 pairs, grid-cell location, corner loads and the trilinear force
+// interpolant (Sec. 5.1.1 step 2) with its exact Jacobian.
+#pragma once
+
+#include "pp_internal.cuh"
+
+namespace pp {
+
+// ---- packed FP32 pairs (PTX f32x2, sm_100 and later)
+__device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+        "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+__device__ __forceinline__ float2 f2sub(float2 a, float2 b) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "sub.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 lerp2(float2 a, float2 b, float t) {
+    return f2fma(make_float2(t, t), f2sub(b, a), a);
+}
+__device__ __forceinline__ float lerpf(float a, float b, float t) { return fmaf(t, b - a, a); }
+
+struct Cell {
+    int i0, i1;
+    float t;     // fraction in [0, 1]
+    float dtdf;  // d t / d f: 1 inside, 0 where the fraction is clamped
+};
+
+// Cell along one axis from the scaled coordinate f = (p - o) / h.  In-range
+// cells (0 <= i <= n-2, the usual case) take a few instructions; the rest
+// wrap (periodic) or clamp (index in [0, n-2], fraction in [0, 1]).  The
+// conversion saturates, so any input (NaN included) ends up in range.
+__device__ __forceinline__ Cell axis_cell(float f, int n, int periodic) {
+    Cell c;
+    c.i0 = __float2int_rd(f);  // floor, saturating (NaN -> 0)
+    c.i1 = c.i0 + 1;
+    c.t = f - (float)c.i0;
+    c.dtdf = 1.f;
+    if ((unsigned)c.i0 > (unsigned)(n - 2)) {
+        if (periodic) {
+            const float nf = (float)n;
+            float g = fminf(fmaxf(f, -1.0e7f), 1.0e7f);
+            g = fmaf(-nf, floorf(g / nf), g);  // [0, n] up to rounding
+            c.i0 = min(max(__float2int_rd(g), 0), n - 1);
+            c.i1 = (c.i0 + 1 == n) ? 0 : c.i0 + 1;
+            c.t = fminf(fmaxf(g - (float)c.i0, 0.f), 1.f);
+        } else {
+            const int i = min(max(c.i0, 0), n - 2);
+            const float t = f - (float)i;
+            c.dtdf = (t > 0.f && t < 1.f) ? 1.f : 0.f;
+            c.t = fminf(fmaxf(t, 0.f), 1.f);
+            c.i0 = i;
+            c.i1 = i + 1;
+        }
+    }
+    return c;
+}
+
+struct Cells {
+    Cell x, y, z;
+};
+
+template <class L>
+__device__ __forceinline__ Cells locate(const L& P, float px, float py, float pz) {
+    Cells c;
+    c.x = axis_cell(fmaf(px, P.inv_dx, P.gx0s), P.map.nx, P.periodic_xy);
+    c.y = axis_cell(fmaf(py, P.inv_dy, P.gy0s), P.map.ny, P.periodic_xy);
+    c.z = axis_cell(fmaf(pz, P.inv_dz, P.gz0s), P.map.nz, 0);
+    return c;
+}
+
+template <int LAYOUT>
+__device__ __forceinline__ int off_x(const GridMap& m, int i) { return LAYOUT == 0 ? i : axis_off(m.ax, i); }
+template <int LAYOUT>
+__device__ __forceinline__ int off_y(const GridMap& m, int j) { return LAYOUT == 0 ? j * m.ay.mul : axis_off(m.ay, j); }
+template <int LAYOUT>
+__device__ __forceinline__ int off_z(const GridMap& m, int k) { return LAYOUT == 0 ? k * m.az.mul : axis_off(m.az, k); }
+
+// Storage indices of the 8 corners, ordered c[(dz*2 + dy)*2 + dx].
+template <int LAYOUT>
+__device__ __forceinline__ void corner_index(const GridMap& m, const Cells& c, int idx[8]) {
+    const int x0 = off_x<LAYOUT>(m, c.x.i0), x1 = off_x<LAYOUT>(m, c.x.i1);
+    const int y0 = off_y<LAYOUT>(m, c.y.i0), y1 = off_y<LAYOUT>(m, c.y.i1);
+    const int z0 = off_z<LAYOUT>(m, c.z.i0), z1 = off_z<LAYOUT>(m, c.z.i1);
+    const int r00 = y0 + z0, r10 = y1 + z0, r01 = y0 + z1, r11 = y1 + z1;
+    idx[0] = r00 + x0; idx[1] = r00 + x1; idx[2] = r10 + x0; idx[3] = r10 + x1;
+    idx[4] = r01 + x0; idx[5] = r01 + x1; idx[6] = r11 + x0; idx[7] = r11 + x1;
+}
+
+template <int LAYOUT>
+__device__ __forceinline__ void load_corners(const float4* __restrict__ ff, const GridMap& m, const Cells& c,
+                                             float4 v[8]) {
+    int idx[8];
+    corner_index<LAYOUT>(m, c, idx);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = __ldg(ff + idx[q]);
+}
+
+// Trilinear interpolant of (Fx, Fy, Fz); (Fx, Fy) as packed pairs.
+__device__ __forceinline__ float3 trilinear(const float4 v[8], const Cells& c) {
+    const float tx = c.x.t, ty = c.y.t, tz = c.z.t;
+    const float2 a00 = lerp2(make_float2(v[0].x, v[0].y), make_float2(v[1].x, v[1].y), tx);
+    const float2 a10 = lerp2(make_float2(v[2].x, v[2].y), make_float2(v[3].x, v[3].y), tx);
+    const float2 a01 = lerp2(make_float2(v[4].x, v[4].y), make_float2(v[5].x, v[5].y), tx);
+    const float2 a11 = lerp2(make_float2(v[6].x, v[6].y), make_float2(v[7].x, v[7].y), tx);
+    const float2 fxy = lerp2(lerp2(a00, a10, ty), lerp2(a01, a11, ty), tz);
+    const float fz = lerpf(lerpf(lerpf(v[0].z, v[1].z, tx), lerpf(v[2].z, v[3].z, tx), ty),
+                           lerpf(lerpf(v[4].z, v[5].z, tx), lerpf(v[6].z, v[7].z, tx), ty), tz);
+    return make_float3(fxy.x, fxy.y, fz);
+}
+
+template <int LAYOUT, class L>
+__device__ __forceinline__ float3 sample_force(const L& P, float px, float py, float pz) {
+    const Cells c = locate(P, px, py, pz);
+    float4 v[8];
+    load_corners<LAYOUT>(P.ff, P.map, c, v);
+    return trilinear(v, c);
+}
+
+// Trilinear weights of the 8 corners (same order as corner_index).
+__device__ __forceinline__ void corner_weights(const Cells& c, float w[8]) {
+    const float wx[2] = {1.f - c.x.t, c.x.t}, wy[2] = {1.f - c.y.t, c.y.t}, wz[2] = {1.f - c.z.t, c.z.t};
+#pragma unroll
+    for (int q = 0; q < 8; ++q) w[q] = wz[q >> 2] * wy[(q >> 1) & 1] * wx[q & 1];
+}
+
+// Exact Jacobian J[a][b] = dF_a / dp_b of the trilinear interpolant: the
+// x-derivative is the (y,z)-bilinear blend of the x-differences times dt/dx,
+// and likewise for y and z.
+__device__ __forceinline__ void trilinear_jacobian(const float4 v[8], const Cells& c, float inv_dx, float inv_dy,
+                                                   float inv_dz, float J[3][3]) {
+    const float wx[2] = {1.f - c.x.t, c.x.t}, wy[2] = {1.f - c.y.t, c.y.t}, wz[2] = {1.f - c.z.t, c.z.t};
+    const float sx = c.x.dtdf * inv_dx, sy = c.y.dtdf * inv_dy, sz = c.z.dtdf * inv_dz;
+    float3 gx = make_float3(0.f, 0.f, 0.f), gy = gx, gz = gx;
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int cz = 0; cz < 2; ++cz) {
+            const float4 hi = v[(cz * 2 + b) * 2 + 1], lo = v[(cz * 2 + b) * 2];
+            const float w = wy[b] * wz[cz];
+            gx.x = fmaf(w, hi.x - lo.x, gx.x);
+            gx.y = fmaf(w, hi.y - lo.y, gx.y);
+            gx.z = fmaf(w, hi.z - lo.z, gx.z);
+        }
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int cz = 0; cz < 2; ++cz) {
+            const float4 hi = v[(cz * 2 + 1) * 2 + a], lo = v[(cz * 2) * 2 + a];
+            const float w = wx[a] * wz[cz];
+            gy.x = fmaf(w, hi.x - lo.x, gy.x);
+            gy.y = fmaf(w, hi.y - lo.y, gy.y);
+            gy.z = fmaf(w, hi.z - lo.z, gy.z);
+        }
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const float4 hi = v[(2 + b) * 2 + a], lo = v[b * 2 + a];
+            const float w = wx[a] * wy[b];
+            gz.x = fmaf(w, hi.x - lo.x, gz.x);
+            gz.y = fmaf(w, hi.y - lo.y, gz.y);
+            gz.z = fmaf(w, hi.z - lo.z, gz.z);
+        }
+    J[0][0] = gx.x * sx; J[0][1] = gy.x * sy; J[0][2] = gz.x * sz;
+    J[1][0] = gx.y * sx; J[1][1] = gy.y * sy; J[1][2] = gz.y * sz;
+    J[2][0] = gx.z * sx; J[2][1] = gy.z * sy; J[2][2] = gz.z * sz;
+}
+
+}  // namespace pp

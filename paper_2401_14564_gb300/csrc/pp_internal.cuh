@@ -65,11 +65,13 @@ cudaError_t launch_ff_assemble(const FFLaunch& L, cudaStream_t s);
 struct RelaxLaunch {
     const float4* ff;
     GridMap map;
-    float gx0, gy0, gz0, inv_dx, inv_dy, inv_dz;
+    float gx0s, gy0s, gz0s, inv_dx, inv_dy, inv_dz;  // cell coordinate f = p * inv_d + g0s, g0s = -origin/d
     int periodic_xy;
     int snx, sny, snz;
     float sx0, sy0, spx, spy, z_top, sdz;
+    int layout;                           // 0 linear, 1 bricked
     float kx, ky, kR, R0, d0x, d0y, d0z;  // eV/A^2, A
+    float R0sq, c0;                       // R0^2 and |d0|^2 - R0^2 (rounding residue of d0)
     int max_iter, n_min;
     float ftol2, dt0, dt_max, f_inc, f_dec, alpha0, f_alpha, inv_mass;
     float* pos;
@@ -88,6 +90,39 @@ struct DfLaunch {
     float coef[2 * kMaxDfHalfWidth + 1];
 };
 cudaError_t launch_fz_to_df(const DfLaunch& L, cudaStream_t s);
+
+struct BwdLaunch {
+    // atoms and probe
+    const float *ax, *ay, *az, *aR, *aeps, *aq;
+    int n;
+    float R_pp, eps_pp, kQ, ke, Q, core_frac, coul_rc;
+    int min_image;
+    float Lx, Ly;
+    // grid (node positions x0 + i*dx ..., cell coordinate p * inv_d + g0s)
+    const float4* ff;
+    GridMap map;
+    int layout;
+    float x0, y0, z0, dx, dy, dz;
+    float gx0s, gy0s, gz0s, inv_dx, inv_dy, inv_dz;
+    int periodic_xy;
+    // scan and tip springs (eV/A^2); nm converts a gradient per eV/A^2 into per N/m
+    int snx, sny, snz;
+    float sx0, sy0, spx, spy, z_top, sdz;
+    float kx, ky, kR, R0, d0x, d0y, d0z, R0sq, c0, nm;
+    // df stencil and the forward's saved state
+    int m, nzo;
+    float coef[2 * kMaxDfHalfWidth + 1];
+    const float* pos;
+    const float* g_df;
+    // outputs (accumulated) and caller scratch
+    float *gx, *gy, *gz, *gq, *gR, *geps, *gtip;
+    float4* gbar;
+    int* slab;
+};
+cudaError_t launch_backward(const BwdLaunch& L, cudaStream_t s);
+
+// Workspace of pp_backward: a 256-byte header (z-slab bounds) then the grid adjoint.
+constexpr size_t kBwdHeader = 256;
 
 cudaError_t launch_ff_convert(const float4* src, const GridMap& sm, float4* dst, const GridMap& dm,
                               cudaStream_t s);

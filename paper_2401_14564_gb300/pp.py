@@ -65,6 +65,10 @@ class DF(C.Structure):
     _fields_ = [("A_pp", C.c_float), ("k", C.c_float), ("f0", C.c_float)]
 
 
+class Grads(C.Structure):
+    _fields_ = [(k, C.c_void_p) for k in ("x", "y", "z", "q", "R", "eps", "tip")]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -98,6 +102,11 @@ def lib():
             L.pp_fz_to_df.restype = st
             L.pp_ff_convert.argtypes = [vp, C.POINTER(Grid), vp, C.POINTER(Grid), vp]
             L.pp_ff_convert.restype = st
+            L.pp_backward_workspace.argtypes = [C.POINTER(Grid)]
+            L.pp_backward_workspace.restype = C.c_size_t
+            L.pp_backward.argtypes = [C.POINTER(Atoms), C.POINTER(Probe), C.POINTER(Grid), vp, C.POINTER(Scan),
+                                      C.POINTER(Tip), C.POINTER(DF), vp, vp, C.POINTER(Grads), vp, C.c_size_t, vp]
+            L.pp_backward.restype = st
             L.pp_last_error.argtypes = []
             L.pp_last_error.restype = C.c_char_p
             _lib = L
@@ -214,6 +223,31 @@ def pp_ff_convert(src, src_grid: Grid, dst, dst_grid: Grid, stream=None):
         raise ValueError("buffer too small")
     _check(lib().pp_ff_convert(_dev(src, "src"), C.byref(src_grid), _dev(dst, "dst"), C.byref(dst_grid),
                                _stream(stream)))
+
+
+def pp_backward_workspace(grid: Grid) -> int:
+    return int(lib().pp_backward_workspace(C.byref(grid)))
+
+
+def make_grads(g):
+    """g: dict of float32 CUDA tensors x, y, z, q, R, eps (n each) and tip (4)."""
+    n = int(g["x"].numel())
+    if g["tip"].numel() < 4:
+        raise ValueError("tip gradient needs 4 floats")
+    return Grads(*[_dev(g[k], k) if n > 0 else 0 for k in ("x", "y", "z", "q", "R", "eps")], _dev(g["tip"], "tip"))
+
+
+def pp_backward(atoms: Atoms, probe: Probe, grid: Grid, ff, scan: Scan, tip: Tip, df_params: DF, pos, g_df,
+                grads: Grads, ws, stream=None):
+    npx = scan.nx * scan.ny * scan.nz
+    m = pp_df_margin(df_params.A_pp, scan.dz)
+    if pos.numel() < 3 * npx or (m >= 0 and g_df.numel() < max(scan.nz - 2 * m, 0) * scan.nx * scan.ny):
+        raise ValueError("pos or g_df smaller than the scan")
+    if ff.numel() < pp_ff_floats(grid):
+        raise ValueError("ff buffer smaller than pp_ff_floats(grid)")
+    _check(lib().pp_backward(C.byref(atoms), C.byref(probe), C.byref(grid), _dev(ff, "ff"), C.byref(scan),
+                             C.byref(tip), C.byref(df_params), _dev(pos, "pos"), _dev(g_df, "g_df"), C.byref(grads),
+                             _dev(ws, "ws", ws.dtype), ws.numel() * ws.element_size(), _stream(stream)))
 
 
 def pp_last_error() -> str:

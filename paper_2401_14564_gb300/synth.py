@@ -69,7 +69,7 @@ def default_fire(**kw):
 
 def parity_fire(**kw):
     """Tighter FIRE settings used when positions are compared to 1e-3 Angstrom."""
-    return default_fire(max_iter=2000, ftol=1e-5, **kw)
+    return default_fire(**{"max_iter": 2000, "ftol": 1e-5, **kw})
 
 
 def default_df(**kw):

@@ -1,0 +1,165 @@
+"""GPU parity of the implicit adjoint (K3^T, K4, K5) against the FP64 oracle adjoint.
+
+The oracle adjoint is pinned to central finite differences of the oracle's
+forward pass (tests/test_oracle_adjoint.py).  Bars:
+  - isolated: the CUDA adjoint evaluated at the oracle's relaxed positions
+    agrees with the oracle to relative L2 <= 1e-4 per gradient vector;
+  - end to end (each side relaxes on its own grid, ftol 1e-6 eV/A; 2e-7 on the
+    40-atom workload): relative L2 <= 1e-3 per gradient vector (atom x, y, z,
+    q, R, eps; tip kx, ky, kR, Q).
+"""
+import copy
+
+import numpy as np
+import pytest
+import torch
+
+from helpers import case32, df_keep
+from paper_2401_14564_gb300 import afm, autograd, pp, synth
+
+pytestmark = pytest.mark.gpu
+
+KEYS = ("x", "y", "z", "q", "R", "eps")
+TIP = ("kx", "ky", "kR", "Q")
+
+
+def weights(c, seed=7):
+    s = c["scan"]
+    m = pp.pp_df_margin(c["df"]["A_pp"], s["dz"])
+    return np.random.default_rng(seed).standard_normal((s["nz"] - 2 * m, s["ny"], s["nx"]))
+
+
+def gpu_backward(c, pos, w, layout=0):
+    """CUDA adjoint at the given relaxed positions, on the CUDA FF grid."""
+    grid = pp.make_grid(c["grid"], layout)
+    atoms_t = afm.atoms_to_device(c["atoms"])
+    atoms = pp.make_atoms(atoms_t)
+    ff = torch.empty(pp.pp_ff_floats(grid), dtype=torch.float32, device="cuda")
+    pp.pp_make_ff(atoms, pp.make_probe(c["probe"]), grid, ff)
+    n = len(c["atoms"]["x"])
+    g = {k: torch.full((n,), float("nan"), device="cuda") for k in KEYS}
+    g["tip"] = torch.full((4,), float("nan"), device="cuda")
+    ws = torch.empty(pp.pp_backward_workspace(grid) // 4 + 1, dtype=torch.float32, device="cuda")
+    pos_t = torch.as_tensor(np.asarray(pos, dtype=np.float32), device="cuda").contiguous()
+    w_t = torch.as_tensor(np.asarray(w, dtype=np.float32), device="cuda").contiguous()
+    pp.pp_backward(atoms, pp.make_probe(c["probe"]), grid, ff, pp.make_scan(c["scan"]), pp.make_tip(c["tip"]),
+                   pp.make_df(c["df"]), pos_t, w_t, pp.make_grads(g), ws)
+    torch.cuda.synchronize()
+    out = {k: g[k].cpu().numpy().astype(np.float64) for k in KEYS}
+    t = g["tip"].cpu().numpy().astype(np.float64)
+    out.update({k: t[i] for i, k in enumerate(TIP)})
+    return out
+
+
+def rel(a, b):
+    a, b = np.atleast_1d(a), np.atleast_1d(b)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+def check(got, ref, tol):
+    errs = {k: rel(got[k], ref[k]) for k in KEYS + TIP}
+    bad = {k: v for k, v in errs.items() if not v <= tol}
+    assert not bad, (bad, errs)
+    return errs
+
+
+def small():
+    return case32(synth.small_case(seed=9, n_atoms=8, nxy=40, nz=36, scan_px=9, nz_scan=14, d=0.15))
+
+
+@pytest.mark.parametrize("layout", [0, 1])
+def test_isolated_adjoint_matches_oracle(orc, layout):
+    c = small()
+    w = weights(c)
+    o = orc.forward(c)
+    ref = orc.backward(o["ff"], c["grid"], c["atoms"], c["probe"], c["scan"], c["tip"], c["df"], o["pos"], w)
+    got = gpu_backward(c, o["pos"], w, layout)
+    check(got, ref, 1e-4)
+
+
+def test_isolated_adjoint_min_image_cutoff(orc):
+    c = small()
+    c["probe"] = dict(c["probe"], coul_rc=3.0, min_image=1)
+    w = weights(c, 3)
+    o = orc.forward(c)
+    ref = orc.backward(o["ff"], c["grid"], c["atoms"], c["probe"], c["scan"], c["tip"], c["df"], o["pos"], w)
+    got = gpu_backward(c, o["pos"], w)
+    check(got, ref, 1e-4)
+
+
+def end_to_end(orc, c, w, tol, ftol=1e-6):
+    """Each side relaxes on its own grid.  As in the relaxation parity, df outputs whose
+    stencil touches an ill-conditioned point (lambda_min < 0.01 eV/A^2) or a point where the
+    two sides settled in different basins get zero loss weight: near a bifurcation the
+    gradient is dominated by 1/lambda and by which side of the saddle FP32 rounding lands on."""
+    fire = synth.parity_fire(ftol=ftol, max_iter=20000)
+    g = afm.afm(c, fire=fire)
+    assert (g["iters"] < fire["max_iter"]).mean() > 0.999
+    o = orc.forward(c, fire=fire)
+    keep = (o["lam"] >= 0.01) & (np.linalg.norm(g["pos"] - o["pos"], axis=-1) < 0.05)
+    m = (keep.shape[0] - np.asarray(w).shape[0]) // 2
+    w = np.where(df_keep(keep, m), w, 0.0)
+    assert (w != 0).mean() > 0.8
+    got = gpu_backward(c, g["pos"], w)
+    ref = orc.backward(o["ff"], c["grid"], c["atoms"], c["probe"], c["scan"], c["tip"], c["df"], o["pos"], w)
+    return check(got, ref, tol)
+
+
+def test_end_to_end_small(orc):
+    c = small()
+    end_to_end(orc, c, weights(c), 1e-3)
+
+
+def test_gradient_workload_end_to_end(orc):
+    # 40-atom nonplanar molecule, 128 x 128 px x 20 heights, loss sum(w * df), w ~ N(0,1) seed 7
+    # the tip scalars are signed sums over all 327k relaxed points, so the forward is
+    # converged further (|G| < 2e-7 eV/A, still 20x above the FP32 noise of G)
+    c = case32(synth.gradient_case())
+    end_to_end(orc, c, c["w"], 1e-3, ftol=2e-7)
+
+
+def test_charge_scaling_identity_on_gpu(orc):
+    c = small()
+    o = orc.forward(c)
+    got = gpu_backward(c, o["pos"], weights(c))
+    lhs = float((c["atoms"]["q"] * got["q"]).sum())
+    assert lhs == pytest.approx(c["probe"]["Q"] * got["Q"], rel=1e-4)
+
+
+def test_autograd_function_matches_direct_call(orc):
+    c = small()
+    fire = synth.parity_fire()
+    at = afm.atoms_to_device(c["atoms"])
+    leaves = {k: at[k].clone().requires_grad_(True) for k in KEYS}
+    tips = {k: torch.tensor(float(c["tip"][k] if k != "Q" else c["probe"]["Q"]), requires_grad=True) for k in TIP}
+    df = autograd.afm_df(leaves, tips["kx"], tips["ky"], tips["kR"], tips["Q"], c, fire=fire)
+    w = weights(c)
+    loss = (df * torch.as_tensor(w, dtype=torch.float32, device="cuda")).sum()
+    loss.backward()
+    g = afm.afm(c, fire=fire)
+    direct = gpu_backward(c, g["pos"], w)
+    # the two runs differ only in the order of FP32 atomic additions (and dL/dQ = sum q_i C_i
+    # cancels across a neutral molecule), hence 1e-4 rather than bit equality
+    for k in KEYS:
+        assert rel(leaves[k].grad.cpu().numpy(), direct[k]) < 1e-4, k
+    for k in TIP:
+        assert rel(tips[k].grad.item(), direct[k]) < 1e-4, k
+
+
+def test_workspace_too_small_is_rejected():
+    c = small()
+    grid = pp.make_grid(c["grid"])
+    need = pp.pp_backward_workspace(grid)
+    ws = torch.empty(need // 4 - 4, dtype=torch.float32, device="cuda")
+    n = len(c["atoms"]["x"])
+    g = {k: torch.empty(n, device="cuda") for k in KEYS}
+    g["tip"] = torch.empty(4, device="cuda")
+    at = afm.atoms_to_device(c["atoms"])
+    ff = torch.zeros(pp.pp_ff_floats(grid), device="cuda")
+    s = c["scan"]
+    pos = torch.zeros((s["nz"], s["ny"], s["nx"], 3), device="cuda")
+    w = torch.zeros((s["nz"] - 10, s["ny"], s["nx"]), device="cuda")
+    with pytest.raises(pp.PPError) as e:
+        pp.pp_backward(pp.make_atoms(at), pp.make_probe(c["probe"]), grid, ff, pp.make_scan(s), pp.make_tip(c["tip"]),
+                       pp.make_df(c["df"]), pos, w, pp.make_grads(g), ws)
+    assert e.value.status == 4
