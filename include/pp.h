@@ -219,6 +219,30 @@ PP_API pp_status pp_backward(const pp_atoms* atoms, const pp_probe* probe, const
                              const pp_df* df_params, const float* pos, const float* g_df,
                              const pp_grads* grads, void* ws, size_t ws_bytes, pp_stream stream);
 
+/* pp_backward without a caller workspace.  The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc -- code in
+ * a real-time acquisition or control loop, or a plugin whose host forbids
+ * device allocations after start-up (cudaMalloc may block and synchronise
+ * the device), and C or Fortran callers without a device allocator.  It
+ * computes exactly what pp_backward computes, taking its scratch from a
+ * 32 MiB array that every GPU loading this library holds until the process
+ * exits; it allocates nothing itself.  Grids whose pp_backward_workspace()
+ * exceeds pp_backward_noalloc_capacity() bytes (about 2.1 million stored
+ * nodes) are rejected with PP_ERR_CAPACITY.  The first call on each device
+ * looks up the array's device address (make that call before any stream
+ * capture).  All calls share the one array and it keeps the last call's
+ * contents (each call clears what must start at zero): calls that overlap on
+ * the GPU -- on different streams, or from different threads -- race and
+ * must be serialised by the caller.  Inputs, outputs and errors as
+ * pp_backward. */
+PP_API pp_status pp_backward_noalloc(const pp_atoms* atoms, const pp_probe* probe, const pp_grid* grid,
+                                     const float* ff, const pp_scan* scan, const pp_tip* tip,
+                                     const pp_df* df_params, const float* pos, const float* g_df,
+                                     const pp_grads* grads, pp_stream stream);
+
+/* Bytes of the static scratch behind pp_backward_noalloc. */
+PP_API size_t pp_backward_noalloc_capacity(void);
+
 /* Message of the last failed call on this host thread ("" if none). */
 PP_API const char* pp_last_error(void);
 

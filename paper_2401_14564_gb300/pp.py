@@ -107,6 +107,12 @@ def lib():
             L.pp_backward.argtypes = [C.POINTER(Atoms), C.POINTER(Probe), C.POINTER(Grid), vp, C.POINTER(Scan),
                                       C.POINTER(Tip), C.POINTER(DF), vp, vp, C.POINTER(Grads), vp, C.c_size_t, vp]
             L.pp_backward.restype = st
+            L.pp_backward_noalloc.argtypes = [C.POINTER(Atoms), C.POINTER(Probe), C.POINTER(Grid), vp,
+                                              C.POINTER(Scan), C.POINTER(Tip), C.POINTER(DF), vp, vp,
+                                              C.POINTER(Grads), vp]
+            L.pp_backward_noalloc.restype = st
+            L.pp_backward_noalloc_capacity.argtypes = []
+            L.pp_backward_noalloc_capacity.restype = C.c_size_t
             L.pp_last_error.argtypes = []
             L.pp_last_error.restype = C.c_char_p
             _lib = L
@@ -248,6 +254,24 @@ def pp_backward(atoms: Atoms, probe: Probe, grid: Grid, ff, scan: Scan, tip: Tip
     _check(lib().pp_backward(C.byref(atoms), C.byref(probe), C.byref(grid), _dev(ff, "ff"), C.byref(scan),
                              C.byref(tip), C.byref(df_params), _dev(pos, "pos"), _dev(g_df, "g_df"), C.byref(grads),
                              _dev(ws, "ws", ws.dtype), ws.numel() * ws.element_size(), _stream(stream)))
+
+
+def pp_backward_noalloc_capacity() -> int:
+    return int(lib().pp_backward_noalloc_capacity())
+
+
+def pp_backward_noalloc(atoms: Atoms, probe: Probe, grid: Grid, ff, scan: Scan, tip: Tip, df_params: DF, pos, g_df,
+                        grads: Grads, stream=None):
+    """pp_backward with the library's static scratch (no workspace argument, nothing allocated)."""
+    npx = scan.nx * scan.ny * scan.nz
+    m = pp_df_margin(df_params.A_pp, scan.dz)
+    if pos.numel() < 3 * npx or (m >= 0 and g_df.numel() < max(scan.nz - 2 * m, 0) * scan.nx * scan.ny):
+        raise ValueError("pos or g_df smaller than the scan")
+    if ff.numel() < pp_ff_floats(grid):
+        raise ValueError("ff buffer smaller than pp_ff_floats(grid)")
+    _check(lib().pp_backward_noalloc(C.byref(atoms), C.byref(probe), C.byref(grid), _dev(ff, "ff"), C.byref(scan),
+                                     C.byref(tip), C.byref(df_params), _dev(pos, "pos"), _dev(g_df, "g_df"),
+                                     C.byref(grads), _stream(stream)))
 
 
 def pp_last_error() -> str:
