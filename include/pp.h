@@ -21,7 +21,8 @@
  *              and keeps no pointer after the call returns (its kernels may
  *              still be running on `stream`).
  *   Execution  All work is enqueued on `stream` (a cudaStream_t; NULL = the
- *              legacy default stream).  No call synchronises the host.
+ *              legacy default stream).  No call synchronises the host except
+ *              pp_batch_status, which reads a status word back.
  *   Errors     Every call returns a pp_status; nothing throws across the ABI.
  *              Shapes, sizes and NULL pointers are checked on the host before
  *              any launch; a failed check launches nothing.  PP_ERR_CUDA means
@@ -184,6 +185,75 @@ PP_API pp_status pp_fz_to_df(const float* fz, int nz, int npix, float dz, const 
  * Errors: PP_ERR_ARG, PP_ERR_SHAPE, PP_ERR_CUDA. */
 PP_API pp_status pp_ff_convert(const float* src, const pp_grid* src_grid, float* dst,
                         const pp_grid* dst_grid, pp_stream stream);
+
+/* ---------------------------------------------------------------- batches
+ * Many molecules of uneven size in one persistent launch (a7; the paper's
+ * batch generator for ML datasets, Sec. 4.4, motivates it; the method per
+ * molecule is exactly pp_make_ff + pp_relax_scan with fused df).  Grids are
+ * linear layout; all molecules share the probe, tip, FIRE, df parameters,
+ * the scan height step and the periodic_xy flag. */
+typedef struct {
+    long long ff_offset;  /* float4 index of this molecule's grid in the packed ff buffer  */
+    long long out_offset; /* index of its [snz][sny][snx] block in fz and iters (x3 in pos) */
+    long long df_offset;  /* index of its [snz-2m][sny][snx] block in df                    */
+    int atom_offset;      /* first atom in the packed atom arrays                           */
+    int n_atoms;          /* >= 0                                                           */
+    int nx, ny, nz;       /* grid nodes (>= 2 each)                                         */
+    float x0, y0, z0, dx, dy, dz;
+    int snx, sny, snz;    /* scan pixels and heights                                        */
+    float sx0, sy0, spx, spy, z_top;
+} pp_mol_desc;
+
+typedef struct {
+    pp_probe probe;
+    pp_tip tip;
+    pp_fire fire;
+    pp_df df;
+    float scan_dz;          /* height step of every scan, A                                  */
+    int periodic_xy;        /* interpolation wrap of every grid (0 or 1)                      */
+    long long ff_capacity;  /* float4 slots in ff                                             */
+    long long out_capacity; /* entries in fz and iters (pos holds 3x)                         */
+    long long df_capacity;  /* entries in df                                                  */
+    int n_atoms_total;      /* length of the packed atom arrays                               */
+    int ctas;               /* persistent CTAs of 128 threads; 0 = fill the GPU               */
+    long long spin_limit;   /* polls (~128 ns apart) before a relax item stops waiting for its
+                               molecule's force field; 0 = 1<<23 (about one second)           */
+    int wait_extra;         /* test hook, 0 in normal use: relax items wait for this many more
+                               force-field tiles than exist, so every wait runs out            */
+} pp_batch_params;
+
+/* Status bits reported by pp_batch_status. */
+#define PP_BATCH_BAD_DESC 1 /* a descriptor was invalid or overran a buffer: that molecule was skipped */
+#define PP_BATCH_TIMEOUT 2  /* a bounded wait ran out: some relax tiles were not computed            */
+
+/* Scratch bytes of pp_batch_run for nmol molecules (0 if nmol < 1). */
+PP_API size_t pp_batch_workspace(int nmol);
+
+/* One launch over all molecules: a planning kernel validates every device
+ * descriptor (bad ones are skipped and flagged) and lays out a work list of
+ * force-field tiles (8x4 columns x 8 z-nodes) and relax tiles (8x4 pixels,
+ * all heights) ordered FF(0), FF(1), R(0), FF(2), R(1), ...; then a
+ * persistent kernel whose warps pull items from a device counter.  A relax
+ * tile waits (bounded, see spin_limit) until every force-field tile of its
+ * molecule is done; items are handed out in list order, so the force field
+ * it waits for is always being computed by running warps.  Writes, per
+ * molecule, the force field, fz, df and (nullable) pos and iters exactly as
+ * pp_make_ff + pp_relax_scan (fused df) on that molecule alone.  descs is a
+ * DEVICE array of nmol descriptors; atoms are packed device arrays; ws is
+ * 16-byte aligned scratch of pp_batch_workspace(nmol) bytes.  Nothing is
+ * synchronised: the launch can be captured in a CUDA graph and replayed.
+ * Errors detected on the host: PP_ERR_ARG, PP_ERR_SHAPE, PP_ERR_CAPACITY,
+ * PP_ERR_UNSUPPORTED, PP_ERR_CUDA; errors found on the device are reported
+ * by pp_batch_status. */
+PP_API pp_status pp_batch_run(const pp_mol_desc* descs, int nmol, const pp_batch_params* params,
+                              const pp_atoms* atoms, float* ff, float* pos, float* fz, int* iters,
+                              float* df, void* ws, size_t ws_bytes, pp_stream stream);
+
+/* Device-side status of the last pp_batch_run on `ws`: waits for `stream`,
+ * then stores the PP_BATCH_* bits in *flags (host int).  Returns
+ * PP_ERR_TIMEOUT if a wait ran out, PP_ERR_CAPACITY if a descriptor was bad,
+ * else PP_OK.  This call synchronises the host with the stream. */
+PP_API pp_status pp_batch_status(const void* ws, int* flags, pp_stream stream);
 
 /* Gradients of pp_backward, device arrays owned by the caller: x, y, z, q, R,
  * eps hold n floats each (dL/dx_i in 1/A, dL/dq_i per e, dL/dR_i per A,

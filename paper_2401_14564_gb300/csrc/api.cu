@@ -352,6 +352,70 @@ pp_status pp_backward(const pp_atoms* atoms, const pp_probe* probe, const pp_gri
     return cuda_status(launch_backward(L, s), "pp_backward launch");
 }
 
+size_t pp_batch_workspace(int nmol) { return batch_workspace_bytes(nmol); }
+
+pp_status pp_batch_run(const pp_mol_desc* descs, int nmol, const pp_batch_params* bp, const pp_atoms* atoms,
+                       float* ff, float* pos, float* fz, int* iters, float* df, void* ws, size_t ws_bytes,
+                       pp_stream stream) {
+    g_error.clear();
+    if (!descs || !bp || !atoms || !ff || !fz || !df || !ws) { set_error("pp_batch_run: NULL argument"); return PP_ERR_ARG; }
+    if (nmol < 1 || nmol > (1 << 24)) { set_error("pp_batch_run: nmol must be in [1, 2^24]"); return PP_ERR_SHAPE; }
+    if (atoms->n < 0 || (atoms->n > 0 && (!atoms->x || !atoms->y || !atoms->z || !atoms->R || !atoms->eps || !atoms->q))) {
+        set_error("pp_batch_run: invalid packed atoms");
+        return PP_ERR_ARG;
+    }
+    if (!aligned16(ff) || !aligned16(ws)) { set_error("pp_batch_run: ff and ws must be 16-byte aligned"); return PP_ERR_ARG; }
+    const pp_probe* probe = &bp->probe;
+    if (!(probe->core_frac > 0.f && probe->core_frac < 1.f) || !(probe->eps_pp >= 0.f) || !(probe->coul_rc >= 0.f) ||
+        !isfinite(probe->R_pp) || !isfinite(probe->Q) || (probe->min_image != 0 && probe->min_image != 1)) {
+        set_error("pp_batch_run: invalid probe parameters");
+        return PP_ERR_ARG;
+    }
+    std::string why;
+    if (!check_tip_fire(&bp->tip, &bp->fire, &why)) { set_error("pp_batch_run: " + why); return PP_ERR_ARG; }
+    if (!finite_pos(bp->scan_dz) || (bp->periodic_xy != 0 && bp->periodic_xy != 1)) {
+        set_error("pp_batch_run: invalid scan_dz or periodic_xy");
+        return PP_ERR_ARG;
+    }
+    if (bp->ff_capacity < 0 || bp->out_capacity < 0 || bp->df_capacity < 0 || bp->n_atoms_total < 0 ||
+        bp->n_atoms_total > atoms->n || bp->ctas < 0 || bp->spin_limit < 0 || bp->wait_extra < 0) {
+        set_error("pp_batch_run: invalid capacities or launch settings");
+        return PP_ERR_ARG;
+    }
+    if (!finite_pos(bp->df.k) || !isfinite(bp->df.f0)) { set_error("pp_batch_run: invalid df parameters"); return PP_ERR_ARG; }
+    const int m = df_half_width(bp->df.A_pp, bp->scan_dz);
+    if (m < 0) { set_error("pp_batch_run: invalid df amplitude"); return PP_ERR_ARG; }
+    if (m > kMaxDfHalfWidth) { set_error("pp_batch_run: df stencil wider than 63 taps"); return PP_ERR_UNSUPPORTED; }
+    const size_t need = batch_workspace_bytes(nmol);
+    if (ws_bytes < need) {
+        set_error("pp_batch_run: workspace too small (need " + std::to_string(need) + " bytes)");
+        return PP_ERR_CAPACITY;
+    }
+    BatchArgs A;
+    std::memset(&A, 0, sizeof(A));
+    A.descs = descs; A.nmol = nmol; A.params = *bp; A.atoms = *atoms;
+    A.ff = ff; A.pos = pos; A.fz = fz; A.df = df; A.iters = iters; A.ws = ws;
+    A.df_m = m;
+    df_stencil(bp->df.A_pp, bp->scan_dz, bp->df.k, bp->df.f0, m, A.coef);
+    return cuda_status(launch_batch(A, (cudaStream_t)stream), "pp_batch_run launch");
+}
+
+pp_status pp_batch_status(const void* ws, int* flags, pp_stream stream) {
+    g_error.clear();
+    if (!ws || !flags) { set_error("pp_batch_status: NULL argument"); return PP_ERR_ARG; }
+    int st = 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    pp_status r = cuda_status(cudaMemcpyAsync(&st, reinterpret_cast<const char*>(ws) + 8, sizeof(int),
+                                              cudaMemcpyDeviceToHost, s), "pp_batch_status copy");
+    if (r != PP_OK) return r;
+    r = cuda_status(cudaStreamSynchronize(s), "pp_batch_status sync");
+    if (r != PP_OK) return r;
+    *flags = st;
+    if (st & PP_BATCH_TIMEOUT) { set_error("pp_batch_run: a bounded wait ran out"); return PP_ERR_TIMEOUT; }
+    if (st & PP_BATCH_BAD_DESC) { set_error("pp_batch_run: invalid descriptor(s) skipped"); return PP_ERR_CAPACITY; }
+    return PP_OK;
+}
+
 pp_status pp_ff_convert(const float* src, const pp_grid* src_grid, float* dst, const pp_grid* dst_grid,
                         pp_stream stream) {
     g_error.clear();

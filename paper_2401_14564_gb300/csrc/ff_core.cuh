@@ -1,0 +1,106 @@
+// Pair-sum core of the force-field grid assembly (Sec. 5.1.1 step 1;
+// Eqs. LJ and point charges; F = -grad E, Sec. 2.2), shared by K1 and the
+// batched kernel K6.
+//
+// Atoms are staged as 64-byte records in shared memory, each per-atom
+// constant stored twice so that one 16-byte broadcast load yields a ready
+// packed f32x2 operand:
+//   s0 = (x, y, rmin^2, 0)     s1 = (-z, -z, R_iPP^2, R_iPP^2)
+//   s2 = (12 e, 12 e, kq, kq)  s3 = (e, e, 0, 0)
+// with R_iPP = R_i + R_PP, e = e_iPP = sqrt(e_i e_PP), kq = k_e Q q_i and
+// rmin = core_frac R_iPP.  A thread accumulates ZP packed pairs of z-nodes
+// of one grid column: per node and atom, u3 = (R_iPP^2 / r^2)^3,
+//   F += [12 e (u3^2 - u3) / r^2 + kq / r^3] (r_node - r_atom),
+//   E += e (u3^2 - 2 u3) + kq / r,
+// with r^2 floored at rmin^2 (shifted-force Coulomb when kCutoff).
+#pragma once
+
+#include "interp.cuh"
+
+namespace pp {
+
+struct FFConst {
+    float R_pp, eps_pp, kQ, core_frac;
+    float Lx, Ly, invLx, invLy;  // minimum-image period
+    float rc2, irc2, two_irc;    // shifted-force cutoff
+};
+
+__device__ __forceinline__ FFConst ff_const(float R_pp, float eps_pp, float kQ, float core_frac, float Lx, float Ly,
+                                            float coul_rc) {
+    FFConst c;
+    c.R_pp = R_pp; c.eps_pp = eps_pp; c.kQ = kQ; c.core_frac = core_frac;
+    c.Lx = Lx; c.Ly = Ly;
+    c.invLx = 1.f / Lx; c.invLy = 1.f / Ly;
+    c.rc2 = coul_rc * coul_rc;
+    c.irc2 = coul_rc > 0.f ? 1.f / c.rc2 : 0.f;
+    c.two_irc = coul_rc > 0.f ? 2.f / coul_rc : 0.f;
+    return c;
+}
+
+// Mixing rules and the staged record of one atom.
+__device__ __forceinline__ void ff_stage_atom(const FFConst& c, float x, float y, float z, float R, float eps, float q,
+                                              float4& s0, float4& s1, float4& s2, float4& s3) {
+    const float Rij = R + c.R_pp;
+    const float eij = sqrtf(eps * c.eps_pp);
+    const float rmin = c.core_frac * Rij;
+    const float kq = c.kQ * q;
+    s0 = make_float4(x, y, rmin * rmin, 0.f);
+    s1 = make_float4(-z, -z, Rij * Rij, Rij * Rij);
+    s2 = make_float4(12.f * eij, 12.f * eij, kq, kq);
+    s3 = make_float4(eij, eij, 0.f, 0.f);
+}
+
+template <int ZP, bool kMinImage, bool kCutoff>
+__device__ __forceinline__ void ff_accumulate(const float4* s0, const float4* s1, const float4* s2, const float4* s3,
+                                              int cnt, const FFConst& c, float gx, float gy, const float2 (&gz)[ZP],
+                                              float2 (&fx)[ZP], float2 (&fy)[ZP], float2 (&fz)[ZP], float2 (&en)[ZP]) {
+    const float2 minus1 = make_float2(-1.f, -1.f);
+#pragma unroll 1
+    for (int a = 0; a < cnt; ++a) {
+        const float4 A0 = s0[a], A1 = s1[a], A2 = s2[a], A3 = s3[a];
+        float rx = gx - A0.x;
+        float ry = gy - A0.y;
+        if (kMinImage) {
+            rx = fmaf(-c.Lx, rintf(rx * c.invLx), rx);
+            ry = fmaf(-c.Ly, rintf(ry * c.invLy), ry);
+        }
+        const float rxy2 = fmaf(rx, rx, ry * ry);
+        const float2 RX = make_float2(rx, rx), RY = make_float2(ry, ry), RXY = make_float2(rxy2, rxy2);
+        const float2 NZ = make_float2(A1.x, A1.y), R2 = make_float2(A1.z, A1.w);
+        const float2 E12 = make_float2(A2.x, A2.y), KQ = make_float2(A2.z, A2.w);
+        const float2 EE = make_float2(A3.x, A3.y);
+#pragma unroll
+        for (int t = 0; t < ZP; ++t) {
+            const float2 rz = f2add(gz[t], NZ);
+            float2 r2 = f2fma(rz, rz, RXY);
+            r2.x = fmaxf(r2.x, A0.z);
+            r2.y = fmaxf(r2.y, A0.z);
+            const float2 rs = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+            const float2 ir2 = f2mul(rs, rs);
+            const float2 u = f2mul(R2, ir2);
+            const float2 u3 = f2mul(f2mul(u, u), u);
+            const float2 lj = f2mul(u3, f2add(u3, minus1));  // u6 - u3
+            float2 eel = f2mul(KQ, rs);                         // kq / r
+            float2 f;
+            if (kCutoff) {
+                eel.x = (r2.x < c.rc2) ? eel.x : 0.f;
+                eel.y = (r2.y < c.rc2) ? eel.y : 0.f;
+                // kq (1/r^3 - 1/(r rc^2)) + 12 e (u6 - u3) / r^2
+                f = f2fma(eel, make_float2(-c.irc2, -c.irc2), f2mul(f2fma(E12, lj, eel), ir2));
+                // shifted-force energy kq (1/r + r/rc^2 - 2/rc)
+                float2 ee = f2fma(eel, f2mul(r2, make_float2(c.irc2, c.irc2)), eel);
+                ee.x -= (r2.x < c.rc2) ? KQ.x * c.two_irc : 0.f;
+                ee.y -= (r2.y < c.rc2) ? KQ.y * c.two_irc : 0.f;
+                eel = ee;
+            } else {
+                f = f2mul(f2fma(E12, lj, eel), ir2);  // (12 e (u6 - u3) + kq / r) / r^2
+            }
+            fx[t] = f2fma(f, RX, fx[t]);
+            fy[t] = f2fma(f, RY, fy[t]);
+            fz[t] = f2fma(f, rz, fz[t]);
+            en[t] = f2add(f2fma(EE, f2sub(lj, u3), en[t]), eel);  // e (u6 - 2 u3) + E_el
+        }
+    }
+}
+
+}  // namespace pp

@@ -17,6 +17,24 @@ __device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) {
         : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
     return d;
 }
+__device__ __forceinline__ float2 f2mul(float2 a, float2 b) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 f2add(float2 a, float2 b) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "add.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
 __device__ __forceinline__ float2 f2sub(float2 a, float2 b) {
     float2 d;
     asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
@@ -98,13 +116,15 @@ __device__ __forceinline__ void corner_index(const GridMap& m, const Cells& c, i
     idx[4] = r01 + x0; idx[5] = r01 + x1; idx[6] = r11 + x0; idx[7] = r11 + x1;
 }
 
-template <int LAYOUT>
+// kCoherent = false: read-only path (grids not written during the kernel);
+// true: plain L1-cached loads, for grids another warp wrote in this kernel.
+template <int LAYOUT, bool kCoherent = false>
 __device__ __forceinline__ void load_corners(const float4* __restrict__ ff, const GridMap& m, const Cells& c,
                                              float4 v[8]) {
     int idx[8];
     corner_index<LAYOUT>(m, c, idx);
 #pragma unroll
-    for (int q = 0; q < 8; ++q) v[q] = __ldg(ff + idx[q]);
+    for (int q = 0; q < 8; ++q) v[q] = kCoherent ? __ldca(ff + idx[q]) : __ldg(ff + idx[q]);
 }
 
 // Trilinear interpolant of (Fx, Fy, Fz); (Fx, Fy) as packed pairs.

@@ -121,6 +121,21 @@ struct BwdLaunch {
 };
 cudaError_t launch_backward(const BwdLaunch& L, cudaStream_t s);
 
+struct BatchArgs {
+    const pp_mol_desc* descs;
+    int nmol;
+    pp_batch_params params;
+    pp_atoms atoms;
+    float* ff;
+    float *pos, *fz, *df;
+    int* iters;
+    void* ws;
+    int df_m;
+    float coef[2 * kMaxDfHalfWidth + 1];
+};
+size_t batch_workspace_bytes(int nmol);
+cudaError_t launch_batch(const BatchArgs& A, cudaStream_t s);
+
 // Workspace of pp_backward: a 256-byte header (z-slab bounds) then the grid adjoint.
 constexpr size_t kBwdHeader = 256;
 

@@ -65,6 +65,21 @@ class DF(C.Structure):
     _fields_ = [("A_pp", C.c_float), ("k", C.c_float), ("f0", C.c_float)]
 
 
+class MolDesc(C.Structure):
+    _fields_ = [("ff_offset", C.c_longlong), ("out_offset", C.c_longlong), ("df_offset", C.c_longlong),
+                ("atom_offset", C.c_int), ("n_atoms", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int)] + \
+               [(k, C.c_float) for k in ("x0", "y0", "z0", "dx", "dy", "dz")] + \
+               [("snx", C.c_int), ("sny", C.c_int), ("snz", C.c_int)] + \
+               [(k, C.c_float) for k in ("sx0", "sy0", "spx", "spy", "z_top")]
+
+
+class BatchParams(C.Structure):
+    _fields_ = [("probe", Probe), ("tip", Tip), ("fire", Fire), ("df", DF), ("scan_dz", C.c_float),
+                ("periodic_xy", C.c_int), ("ff_capacity", C.c_longlong), ("out_capacity", C.c_longlong),
+                ("df_capacity", C.c_longlong), ("n_atoms_total", C.c_int), ("ctas", C.c_int),
+                ("spin_limit", C.c_longlong), ("wait_extra", C.c_int)]
+
+
 class Grads(C.Structure):
     _fields_ = [(k, C.c_void_p) for k in ("x", "y", "z", "q", "R", "eps", "tip")]
 
@@ -113,6 +128,13 @@ def lib():
             L.pp_backward_noalloc.restype = st
             L.pp_backward_noalloc_capacity.argtypes = []
             L.pp_backward_noalloc_capacity.restype = C.c_size_t
+            L.pp_batch_workspace.argtypes = [C.c_int]
+            L.pp_batch_workspace.restype = C.c_size_t
+            L.pp_batch_run.argtypes = [vp, C.c_int, C.POINTER(BatchParams), C.POINTER(Atoms), vp, vp, vp, vp, vp,
+                                       vp, C.c_size_t, vp]
+            L.pp_batch_run.restype = st
+            L.pp_batch_status.argtypes = [vp, C.POINTER(C.c_int), vp]
+            L.pp_batch_status.restype = st
             L.pp_last_error.argtypes = []
             L.pp_last_error.restype = C.c_char_p
             _lib = L
@@ -272,6 +294,27 @@ def pp_backward_noalloc(atoms: Atoms, probe: Probe, grid: Grid, ff, scan: Scan, 
     _check(lib().pp_backward_noalloc(C.byref(atoms), C.byref(probe), C.byref(grid), _dev(ff, "ff"), C.byref(scan),
                                      C.byref(tip), C.byref(df_params), _dev(pos, "pos"), _dev(g_df, "g_df"),
                                      C.byref(grads), _stream(stream)))
+
+
+def pp_batch_workspace(nmol: int) -> int:
+    return int(lib().pp_batch_workspace(int(nmol)))
+
+
+def pp_batch_run(descs, nmol: int, params: BatchParams, atoms: Atoms, ff, pos, fz, iters, df, ws, stream=None):
+    """descs: uint8 CUDA tensor holding nmol pp_mol_desc records."""
+    if descs.numel() < nmol * C.sizeof(MolDesc):
+        raise ValueError("descriptor buffer too small")
+    _check(lib().pp_batch_run(_dev(descs, "descs", torch.uint8), int(nmol), C.byref(params), C.byref(atoms),
+                              _dev(ff, "ff"), _dev(pos, "pos", allow_none=True), _dev(fz, "fz"),
+                              _dev(iters, "iters", torch.int32, allow_none=True), _dev(df, "df"),
+                              _dev(ws, "ws", ws.dtype), ws.numel() * ws.element_size(), _stream(stream)))
+
+
+def pp_batch_status(ws, stream=None):
+    """(pp_status, flags) of the last batch run on ws; synchronises the stream."""
+    flags = C.c_int(0)
+    st = lib().pp_batch_status(_dev(ws, "ws", ws.dtype), C.byref(flags), _stream(stream))
+    return int(st), int(flags.value)
 
 
 def pp_last_error() -> str:

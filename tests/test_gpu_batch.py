@@ -1,0 +1,105 @@
+"""The batched persistent launch (pp_batch_run) against the single-molecule path.
+
+Each molecule of a batch must come out bit-identical to pp_make_ff +
+pp_relax_scan (fused df) run on that molecule alone: the batch runs the same
+FF pair-sum core and the same FIRE core, only scheduled differently.  The
+single-molecule path is itself parity-tested against the FP64 oracle.
+Also: CUDA-graph replay, a forced timeout of the bounded wait (reported as a
+status, the context stays usable), and invalid descriptors being skipped.
+"""
+import copy
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from helpers import case32
+from paper_2401_14564_gb300 import afm, batch, pp, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def cases(n=10, first_seed=1000):
+    cs = [case32(c) for c in synth.batch_cases(n, first_seed)]
+    # ragged extras: a scan that is not a multiple of the 8x4 tile, and a molecule without atoms
+    r = copy.deepcopy(cs[0])
+    r["scan"] = dict(r["scan"], nx=13, ny=7)
+    cs.append(r)
+    e = copy.deepcopy(cs[1])
+    for k in ("x", "y", "z", "R", "eps", "q"):
+        e["atoms"][k] = e["atoms"][k][:0]
+    cs.append(e)
+    return cs
+
+
+def single(c):
+    sim = afm.Simulator(c)
+    sim.run(afm.atoms_to_device(c["atoms"]))
+    torch.cuda.synchronize()
+    g = c["grid"]
+    return {"fz": sim.fz.cpu().numpy(), "df": sim.df.cpu().numpy(), "iters": sim.iters.cpu().numpy(),
+            "pos": sim.pos.cpu().numpy(), "ff": sim.ff.view(g["nz"], g["ny"], g["nx"], 4).cpu().numpy()}
+
+
+def test_batch_matches_single_molecule_path_bit_for_bit():
+    cs = cases()
+    b = batch.Batch(cs, want_pos=True)
+    b.run()
+    st, flags = b.status()
+    assert st == 0 and flags == 0
+    for n, c in enumerate(cs):
+        got = {k: v.cpu().numpy() for k, v in b.molecule(n).items()}
+        ref = single(c)
+        for k in ("ff", "fz", "df", "iters", "pos"):
+            assert np.array_equal(got[k], ref[k]), (n, k)
+
+
+def test_graph_replay_reproduces_the_eager_run():
+    cs = cases(6, 2000)
+    b = batch.Batch(cs)
+    b.run()
+    torch.cuda.synchronize()
+    eager = (b.fz.clone(), b.df.clone(), b.iters.clone())
+    b.fz.fill_(float("nan"))
+    b.df.fill_(float("nan"))
+    b.capture()
+    b.fz.fill_(float("nan"))
+    b.df.fill_(float("nan"))
+    b.replay()
+    b.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(b.fz, eager[0]) and torch.equal(b.df, eager[1]) and torch.equal(b.iters, eager[2])
+    assert b.status() == (0, 0)
+
+
+def test_bounded_wait_times_out_with_a_status():
+    # relax tiles wait for one force-field tile more than exists: every wait runs out
+    # after ~1000 polls; the kernel returns, the status says so, the context stays usable
+    cs = cases(3, 3000)
+    b = batch.Batch(cs, spin_limit=1000, wait_extra=1)
+    b.run()
+    st, flags = b.status()
+    assert st == 5 and (flags & 2)
+    ok = batch.Batch(cs)
+    ok.run()
+    assert ok.status() == (0, 0)
+    got = ok.molecule(0)["df"].cpu().numpy()
+    assert np.array_equal(got, single(cs[0])["df"])
+
+
+def test_invalid_descriptor_is_skipped_and_flagged():
+    cs = cases(4, 4000)
+    b = batch.Batch(cs)
+    raw = b.descs.cpu().numpy().copy()
+    d = pp.MolDesc.from_buffer_copy(raw[ctypes.sizeof(pp.MolDesc) * 2: ctypes.sizeof(pp.MolDesc) * 3].tobytes())
+    d.ff_offset = b.params.ff_capacity  # grid would run past the end of ff
+    raw[ctypes.sizeof(pp.MolDesc) * 2: ctypes.sizeof(pp.MolDesc) * 3] = np.frombuffer(bytes(d), dtype=np.uint8)
+    b.descs.copy_(torch.as_tensor(raw))
+    b.df.fill_(7.0)
+    b.run()
+    st, flags = b.status()
+    assert st == 4 and (flags & 1)
+    for n in (0, 1, 3):
+        assert np.array_equal(b.molecule(n)["df"].cpu().numpy(), single(cs[n])["df"]), n
+    assert (b.molecule(2)["df"].cpu().numpy() == 7.0).all()
