@@ -212,6 +212,23 @@ def measure_bwd_fwd(case, steps, warmup, flush, tag):
                     "grid-adjoint scatter, per-atom pair-derivative sums); L2 flushed before each"}
 
 
+def measure_slab(steps, warmup, flush):
+    """2516-atom periodic slab: 512x512x250 grid with minimum image and an 8 A shifted-force
+    Coulomb cut, 512x512 px x 60 heights; forward and adjoint times."""
+    import torch
+
+    from paper_2401_14564_gb300 import synth
+
+    case = synth.slab_case()
+    r = measure_bwd_fwd(case, steps, warmup, flush, "slab2016+mol500: 2516 atoms, grid 512x512x250, scan 512x512x60")
+    g, s = case["grid"], case["scan"]
+    pairs = g["nx"] * g["ny"] * g["nz"] * len(case["atoms"]["x"])
+    r["pixel_z_per_s_fwd"] = s["nx"] * s["ny"] * s["nz"] / (r["fwd_ms"] * 1e-3)
+    r["pairs"] = pairs
+    torch.cuda.empty_cache()
+    return r
+
+
 def measure_batch(n_mol, steps, warmup, flush, seq_sample=64):
     """Batched molecules/s: pp_batch_run over n_mol seeded molecules replayed from a CUDA graph,
     beside the same molecules run one by one through pp_make_ff + pp_relax_scan."""
@@ -272,6 +289,7 @@ def main():
     ap.add_argument("--layout", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-slab", action="store_true")
     ap.add_argument("--batch-mol", type=int, default=1024)
     args = ap.parse_args()
     rank, world, local = dist_env()
@@ -390,6 +408,8 @@ def main():
                             g4["grid"]["nx"], g4["grid"]["ny"], g4["grid"]["nz"])),
         measure_bwd_fwd(case, max(3, args.steps // 2), args.warmup, flush, "flake60 (this line's workload)"),
     ]
+    if not args.no_slab:
+        line["slab"] = measure_slab(3, 1, flush)
     if not args.no_batch:
         line["batched"] = measure_batch(args.batch_mol, max(3, args.steps // 4), args.warmup, flush)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -48,7 +48,8 @@ class Probe(C.Structure):
 
 class Grid(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int)] + \
-               [(k, C.c_double) for k in ("x0", "y0", "z0", "dx", "dy", "dz")] + [("periodic_xy", C.c_int)]
+               [(k, C.c_double) for k in ("x0", "y0", "z0", "dx", "dy", "dz")] + [("periodic_xy", C.c_int)] + \
+               [("Lx", C.c_double), ("Ly", C.c_double)]
 
 
 class Tip(C.Structure):
@@ -121,7 +122,9 @@ def _probe(p):
 
 
 def _grid(g):
-    return Grid(g["nx"], g["ny"], g["nz"], g["x0"], g["y0"], g["z0"], g["dx"], g["dy"], g["dz"], int(g["periodic_xy"]))
+    """Grid dict -> struct; optional "Lx", "Ly" set the minimum-image period of a window of a larger grid."""
+    return Grid(g["nx"], g["ny"], g["nz"], g["x0"], g["y0"], g["z0"], g["dx"], g["dy"], g["dz"], int(g["periodic_xy"]),
+                float(g.get("Lx", 0.0)), float(g.get("Ly", 0.0)))
 
 
 def _tip(t):

@@ -46,7 +46,9 @@
 
 typedef struct { int n; const double *x, *y, *z, *R, *eps, *q; } or_atoms;
 typedef struct { double R_pp, eps_pp, Q, coul_rc; int min_image; double core_frac; } or_probe;
-typedef struct { int nx, ny, nz; double x0, y0, z0, dx, dy, dz; int periodic_xy; } or_grid;
+/* Lx, Ly: minimum-image period; 0 means the grid's own extent nx*dx, ny*dy
+ * (a window of a larger periodic grid passes the full grid's extent). */
+typedef struct { int nx, ny, nz; double x0, y0, z0, dx, dy, dz; int periodic_xy; double Lx, Ly; } or_grid;
 typedef struct { double kx, ky, kR, R0, d0x, d0y; } or_tip; /* springs in N/m */
 typedef struct { int nx, ny, nz; double x0, y0, px, py, z_top, dz; } or_scan;
 typedef struct {
@@ -158,8 +160,8 @@ static int sample_point(const or_atoms* A, const or_probe* P, double Lx, double 
 }
 
 static void grid_period(const or_grid* G, double* Lx, double* Ly) {
-    *Lx = G->nx * G->dx;
-    *Ly = G->ny * G->dy;
+    *Lx = G->Lx > 0.0 ? G->Lx : G->nx * G->dx;
+    *Ly = G->Ly > 0.0 ? G->Ly : G->ny * G->dy;
 }
 
 /* Force-field grid, layout [nz][ny][nx][4] = (Fx, Fy, Fz, E); core[node] = 1 where a pair hit the floor. */

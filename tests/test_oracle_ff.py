@@ -215,3 +215,16 @@ def test_interp_z_clamp_and_periodic_wrap(orc):
     # across the periodic seam x in [3.5, 4.0): between node 7 and node 0
     seam, _ = orc.interp_points(ff, grid, np.array([[3.75, 1.0, 1.0]]))
     np.testing.assert_allclose(seam[0], 0.5 * (ff[0, 2, 7, :3] + ff[0, 2, 0, :3]), rtol=1e-12)
+
+
+def test_window_with_full_period_equals_full_grid(orc):
+    # a window of a laterally periodic grid, given the full grid's period for the minimum image,
+    # reproduces the full grid's node values (used to check 512x512 slabs on a few patches)
+    atoms = synth.concat_atoms(synth.random_molecule(31, 12), synth.shift_atoms(synth.random_molecule(32, 9), 7.0, 5.0))
+    probe = synth.default_probe(min_image=1, coul_rc=6.0)
+    full = {"nx": 40, "ny": 30, "nz": 5, "x0": -10.0, "y0": -7.5, "z0": 2.0, "dx": 0.5, "dy": 0.5, "dz": 0.4,
+            "periodic_xy": 1}
+    ff, _ = orc.make_ff(atoms, probe, full)
+    win = dict(full, nx=10, ny=9, x0=-10.0 + 0.5 * 27, y0=-7.5 + 0.5 * 3, periodic_xy=0, Lx=20.0, Ly=15.0)
+    fw, _ = orc.make_ff(atoms, probe, win)
+    np.testing.assert_allclose(fw, ff[:, 3:12, 27:37], rtol=1e-12, atol=1e-15)
