@@ -290,6 +290,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-slab", action="store_true")
+    ap.add_argument("--no-bwdfwd", action="store_true")
+    ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--batch-mol", type=int, default=1024)
     args = ap.parse_args()
     rank, world, local = dist_env()
@@ -312,7 +314,12 @@ def main():
             dist.barrier()
 
     case = synth.flake_case()
-    sim = afm.Simulator(case, layout=args.layout)
+    tuning = None
+    if not args.no_tune:
+        from paper_2401_14564_gb300 import tune
+
+        tuning = tune.tune_case(case)
+    sim = afm.Simulator(case, layout=args.layout, tuning=tuning)
     atoms = afm.atoms_to_device(case["atoms"])
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB
@@ -401,8 +408,10 @@ def main():
             "e2e": {"value": world * units / (e2e_ms * 1e-3), "unit": UNIT,
                     "h2d_bytes_per_step": sim.h2d_bytes(len(case["atoms"]["x"])), "d2h_bytes_per_step": sim.d2h_bytes()},
             "gpu_launches": 2 * args.steps, "clocks": clk, "wall_s_timed": t_wall}
+    if tuning is not None:
+        line["autotune"] = tuning
     g4 = synth.gradient_case()
-    line["bwd_fwd"] = [
+    line["bwd_fwd"] = [] if args.no_bwdfwd else [
         measure_bwd_fwd(g4, max(3, args.steps // 2), args.warmup, flush,
                         "mol40 seed 4040: 40 atoms, grid %dx%dx%d, scan 128x128x20" % (
                             g4["grid"]["nx"], g4["grid"]["ny"], g4["grid"]["nz"])),

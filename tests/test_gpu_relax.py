@@ -103,7 +103,8 @@ def test_empty_sample_and_constant_field(orc):
         fz = torch.empty((nz, ny, nx), device="cuda")
         it = torch.empty((nz, ny, nx), dtype=torch.int32, device="cuda")
         # a 1e4 N/m radial spring against 0.03 eV/A^2 of lateral stiffness needs many FIRE steps
-        fire = synth.parity_fire(max_iter=50000 if kR > 100 else 2000)
+        # (and a FIRE step that respects it: omega = sqrt(624 eV/A^2) = 25 -> dt = 0.04)
+        fire = synth.parity_fire(max_iter=50000, dt0=0.04, dt_max=0.04) if kR > 100 else synth.parity_fire()
         pp.pp_relax_scan(ff.view(-1), grid, pp.make_scan(s), pp.make_tip(c["tip"]), pp.make_fire(fire), pos, fz, it)
         torch.cuda.synchronize()
         ref_ff = np.zeros((g["nz"], g["ny"], g["nx"], 4))
@@ -125,7 +126,7 @@ def test_stiff_springs_give_unrelaxed_lookup(orc):
     # precision and Fz is not quantised by ulp(R0).
     c = case32(synth.benzene_case())
     c["tip"] = synth.default_tip(kx=1e4, ky=1e4, kR=1e4)
-    fire = synth.parity_fire(max_iter=5000)
+    fire = synth.parity_fire(max_iter=20000, dt0=0.04, dt_max=0.04)  # dt ~ 1/omega of the stiff spring
     g = gpu_run(c, fire)
     o = orc.forward(c, fire=fire)
     rng = np.abs(o["fz"]).max()

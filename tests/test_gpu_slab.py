@@ -53,8 +53,19 @@ def test_slab_grid_sampled_nodes(orc, slab):
                     np.float32(g["y0"]) + idx[:, 1] * np.float32(g["dy"]),
                     np.float32(g["z0"]) + idx[:, 0] * np.float32(g["dz"])], axis=1).astype(np.float64)
     ref, core = orc.ff_points(c["atoms"], c["probe"], g, pts)
-    assert (~core).sum() >= 1500
-    assert ff_rel_err(got, ref)[~core].max() <= 1e-4
+    # the minimum-image field jumps where an atom sits half a period away; within 1e-4 A of that
+    # plane (50x the FP32 rounding of a 25 A distance) the image is decided by rounding, so such
+    # nodes are excluded like the clamped core (and must be rare)
+    L = (g["nx"] * g["dx"], g["ny"] * g["dy"])
+    half = np.zeros(len(pts), dtype=bool)
+    for ax, key in ((0, "x"), (1, "y")):
+        d = pts[:, None, ax] - np.asarray(c["atoms"][key])[None]
+        d = np.abs(d - L[ax] * np.rint(d / L[ax]))
+        half |= (np.abs(d - L[ax] / 2) < 1e-4).any(axis=1)
+    assert half.mean() <= 0.05
+    keep = ~core & ~half
+    assert keep.sum() >= 1500
+    assert ff_rel_err(got, ref)[keep].max() <= 1e-4
 
 
 def patch(c):

@@ -107,7 +107,9 @@ def test_stiff_spring_limit_is_unrelaxed_lookup(orc):
     ff, _ = orc.make_ff(c["atoms"], c["probe"], c["grid"])
     tip = synth.default_tip(kx=1e4, ky=1e4, kR=1e4)
     s = dict(c["scan"], nx=8, ny=8, x0=-2.0, y0=-1.5, px=0.5, py=0.45)
-    r = orc.relax_scan(ff, c["grid"], None, None, s, tip, synth.default_fire(ftol=1e-9, max_iter=5000))
+    # the FIRE step must respect the stiffest spring: omega = sqrt(624 eV/A^2) = 25, so dt = 0.04
+    r = orc.relax_scan(ff, c["grid"], None, None, s, tip, synth.default_fire(ftol=1e-9, max_iter=5000, dt0=0.04,
+                                                                             dt_max=0.04))
     k = np.arange(s["nz"])[:, None, None]
     j = np.arange(s["ny"])[None, :, None]
     i = np.arange(s["nx"])[None, None, :]
