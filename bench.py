@@ -33,6 +33,27 @@ UNIT = "pixel·z-steps/s"
 FLOPS_PER_PAIR = 30          # algorithmic FP32 flops per grid-node/atom pair (FMA = 2)
 BYTES_PER_FIRE_ITER = 96     # 8 corners x (Fx, Fy, Fz) FP32 per FIRE iteration
 SM_COUNT = 152
+
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the ncu captures
+# summarised in profiles/, valid only for the kernel sources they were taken on: the bench
+# reports them when the sources still hash the same, else traffic is null.
+TRAFFIC = {
+    "relax_scan": {"bytes": 51.85e6, "sha": "cf6af97e58ae1b80",
+                   "files": ["relax_scan.cu", "relax_core.cuh", "interp.cuh"]},
+    "ff_assemble": {"bytes": 148.45e6, "sha": "cb0ce4397fa71aa1",
+                    "files": ["ff_assemble.cu", "ff_core.cuh", "interp.cuh"]},
+}
+
+
+def measured_traffic(kernel):
+    import hashlib
+
+    t = TRAFFIC[kernel]
+    h = hashlib.sha1()
+    for f in t["files"]:
+        with open(os.path.join(ROOT, "paper_2401_14564_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return t["bytes"] if h.hexdigest()[:16] == t["sha"] else None
 FP32_LANES_PER_SM = 128
 
 
@@ -292,6 +313,8 @@ def main():
     ap.add_argument("--no-slab", action="store_true")
     ap.add_argument("--no-bwdfwd", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--zpt", type=int, default=0, help="FF z-nodes per thread (skips the autotuner)")
+    ap.add_argument("--brick", default="", help="bricked layout bx,by,bz for the scan (skips the autotuner)")
     ap.add_argument("--batch-mol", type=int, default=1024)
     args = ap.parse_args()
     rank, world, local = dist_env()
@@ -315,7 +338,10 @@ def main():
 
     case = synth.flake_case()
     tuning = None
-    if not args.no_tune:
+    if args.zpt or args.brick:
+        tuning = {"ff_zpt": args.zpt or 8, "layout": 1 if args.brick else args.layout,
+                  "brick": [int(v) for v in args.brick.split(",")] if args.brick else None}
+    elif not args.no_tune:
         from paper_2401_14564_gb300 import tune
 
         tuning = tune.tune_case(case)
@@ -392,11 +418,11 @@ def main():
     dom = "ff_assemble" if ff_ms >= rx_ms else "relax_scan"
     if dom == "ff_assemble":
         roof = {"kernel": "ff_assemble", "bound": "alu", "achieved": ff_tflops, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": ff_tflops / alu_peak, "traffic": None,
+                "frac": ff_tflops / alu_peak, "traffic": measured_traffic("ff_assemble"),
                 "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz ({src} max SM clock)"}
     else:
         roof = {"kernel": "relax_scan", "bound": "hbm", "achieved": rx_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": rx_gbs / peaks["hbm_gbs"], "traffic": None,
+                "frac": rx_gbs / peaks["hbm_gbs"], "traffic": measured_traffic("relax_scan"),
                 "peak_source": f"{src} HBM copy bandwidth (gather bytes are L1/L2-served)"}
 
     line = {"metric": METRIC, "value": world * units / (ms_step * 1e-3), "unit": UNIT, "n_gpus": world,

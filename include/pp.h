@@ -153,6 +153,18 @@ PP_API int pp_df_margin(float A_pp, float dz);
 PP_API pp_status pp_make_ff(const pp_atoms* atoms, const pp_probe* probe, const pp_grid* grid,
                      float* ff, pp_stream stream);
 
+/* Launch shape of pp_make_ff_tuned (picked by the autotuner): ff_zpt is the
+ * number of consecutive z-nodes each thread accumulates, 4, 8 or 16; 0 = 8. */
+typedef struct {
+    int ff_zpt;
+} pp_tuning;
+
+/* pp_make_ff with an explicit launch shape; the values written are the same
+ * sums (identical arithmetic per node).  Errors as pp_make_ff, plus
+ * PP_ERR_ARG for an unsupported ff_zpt.  tuning may be NULL. */
+PP_API pp_status pp_make_ff_tuned(const pp_atoms* atoms, const pp_probe* probe, const pp_grid* grid,
+                                  float* ff, const pp_tuning* tuning, pp_stream stream);
+
 /* Relaxed tip scan (Sec. 5.1.1 step 2; Eqs. F_PP, F_tip; Sec. 2.1 readout).
  * One thread per pixel walks the heights k = 0..nz-1: start p = anchor + d0
  * at k = 0 and p = p*(k-1) - dz z_hat after that, relax by FIRE, write

@@ -25,9 +25,14 @@ class Simulator:
     """Preallocated FF grid, positions, Fz, iteration counts and df for one case shape."""
 
     def __init__(self, case, layout=0, brick=(4, 4, 4), fire=None, device="cuda", fused_df=True,
-                 want_pos=True, want_iters=True):
+                 want_pos=True, want_iters=True, tuning=None):
+        """tuning: an autotuner result ({"ff_zpt", "layout", "brick"}) overriding layout and brick."""
         self.case = case
         self.device = torch.device(device)
+        if tuning is not None:
+            layout = tuning["layout"]
+            brick = tuple(tuning["brick"]) if tuning.get("brick") else brick
+        self.zpt = pp.Tuning(int(tuning["ff_zpt"])) if tuning is not None else None
         self.grid = pp.make_grid(case["grid"], layout=layout, brick=brick)
         self.probe = pp.make_probe(case["probe"])
         self.scan = pp.make_scan(case["scan"])
@@ -48,7 +53,10 @@ class Simulator:
         self._host = None
 
     def make_ff(self, atoms_dev, stream=None):
-        pp.pp_make_ff(pp.make_atoms(atoms_dev), self.probe, self.grid, self.ff, stream)
+        if self.zpt is not None:
+            pp.pp_make_ff_tuned(pp.make_atoms(atoms_dev), self.probe, self.grid, self.ff, self.zpt, stream)
+        else:
+            pp.pp_make_ff(pp.make_atoms(atoms_dev), self.probe, self.grid, self.ff, stream)
 
     def relax(self, stream=None):
         if self.fused_df:

@@ -124,7 +124,14 @@ static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
 pp_status pp_make_ff(const pp_atoms* atoms, const pp_probe* probe, const pp_grid* grid, float* ff,
                      pp_stream stream) {
+    return pp_make_ff_tuned(atoms, probe, grid, ff, nullptr, stream);
+}
+
+pp_status pp_make_ff_tuned(const pp_atoms* atoms, const pp_probe* probe, const pp_grid* grid, float* ff,
+                           const pp_tuning* tuning, pp_stream stream) {
     g_error.clear();
+    const int zpt = (tuning && tuning->ff_zpt) ? tuning->ff_zpt : 8;
+    if (zpt != 4 && zpt != 8 && zpt != 16) { set_error("pp_make_ff_tuned: ff_zpt must be 4, 8 or 16"); return PP_ERR_ARG; }
     if (!atoms || !probe || !grid || !ff) { set_error("pp_make_ff: NULL argument"); return PP_ERR_ARG; }
     if (atoms->n < 0) { set_error("pp_make_ff: atoms->n < 0"); return PP_ERR_ARG; }
     if (atoms->n > 0 && (!atoms->x || !atoms->y || !atoms->z || !atoms->R || !atoms->eps || !atoms->q)) {
@@ -161,6 +168,7 @@ pp_status pp_make_ff(const pp_atoms* atoms, const pp_probe* probe, const pp_grid
     L.dx = grid->dx; L.dy = grid->dy; L.dz = grid->dz;
     L.map = map;
     L.ff = reinterpret_cast<float4*>(ff);
+    L.zpt = zpt;
     return cuda_status(launch_ff_assemble(L, s), "pp_make_ff launch");
 }
 

@@ -89,6 +89,8 @@ cudaError_t launch_zpt(const FFLaunch& L, cudaStream_t s) {
 
 cudaError_t launch_ff_assemble(const FFLaunch& L, cudaStream_t s) {
     if (L.map.nx <= 0 || L.map.ny <= 0 || L.map.nz <= 0) return cudaSuccess;
+    if (L.zpt == 4) return launch_zpt<4>(L, s);
+    if (L.zpt == 16) return launch_zpt<16>(L, s);
     return launch_zpt<8>(L, s);
 }
 

@@ -59,6 +59,7 @@ struct FFLaunch {
     float x0, y0, z0, dx, dy, dz;
     GridMap map;
     float4* ff;
+    int zpt;  // z-nodes per thread: 4, 8 or 16
 };
 cudaError_t launch_ff_assemble(const FFLaunch& L, cudaStream_t s);
 

@@ -80,6 +80,10 @@ class BatchParams(C.Structure):
                 ("spin_limit", C.c_longlong), ("wait_extra", C.c_int)]
 
 
+class Tuning(C.Structure):
+    _fields_ = [("ff_zpt", C.c_int)]
+
+
 class Grads(C.Structure):
     _fields_ = [(k, C.c_void_p) for k in ("x", "y", "z", "q", "R", "eps", "tip")]
 
@@ -110,6 +114,9 @@ def lib():
             L.pp_df_margin.restype = C.c_int
             L.pp_make_ff.argtypes = [C.POINTER(Atoms), C.POINTER(Probe), C.POINTER(Grid), vp, vp]
             L.pp_make_ff.restype = st
+            L.pp_make_ff_tuned.argtypes = [C.POINTER(Atoms), C.POINTER(Probe), C.POINTER(Grid), vp,
+                                           C.POINTER(Tuning), vp]
+            L.pp_make_ff_tuned.restype = st
             L.pp_relax_scan.argtypes = [vp, C.POINTER(Grid), C.POINTER(Scan), C.POINTER(Tip), C.POINTER(Fire),
                                         vp, vp, vp, C.POINTER(DF), vp, vp]
             L.pp_relax_scan.restype = st
@@ -195,13 +202,18 @@ def make_df(d):
 
 
 def make_atoms(t):
-    """t: dict of six float32 CUDA tensors x, y, z, R, eps, q (length n)."""
+    """t: dict of six float32 CUDA tensors x, y, z, R, eps, q (length n).
+
+    The returned struct holds references to the tensors, so their device memory
+    stays allocated for as long as the struct is alive."""
     n = int(t["x"].numel())
     ptrs = [_dev(t[k], k) if n > 0 else 0 for k in ("x", "y", "z", "R", "eps", "q")]
     for k in ("x", "y", "z", "R", "eps", "q"):
         if t[k].numel() != n:
             raise ValueError("atom arrays differ in length")
-    return Atoms(n, *ptrs)
+    a = Atoms(n, *ptrs)
+    a._tensors = dict(t)
+    return a
 
 
 # ----------------------------------------------------------------- entry points
@@ -218,6 +230,13 @@ def pp_make_ff(atoms: Atoms, probe: Probe, grid: Grid, ff: torch.Tensor, stream=
     if ff.numel() < pp_ff_floats(grid):
         raise ValueError("ff buffer smaller than pp_ff_floats(grid)")
     _check(lib().pp_make_ff(C.byref(atoms), C.byref(probe), C.byref(grid), _dev(ff, "ff"), _stream(stream)))
+
+
+def pp_make_ff_tuned(atoms: Atoms, probe: Probe, grid: Grid, ff: torch.Tensor, tuning=None, stream=None):
+    if ff.numel() < pp_ff_floats(grid):
+        raise ValueError("ff buffer smaller than pp_ff_floats(grid)")
+    _check(lib().pp_make_ff_tuned(C.byref(atoms), C.byref(probe), C.byref(grid), _dev(ff, "ff"),
+                                  C.byref(tuning) if tuning is not None else None, _stream(stream)))
 
 
 def pp_relax_scan(ff, grid: Grid, scan: Scan, tip: Tip, fire: Fire, pos, fz, iters, fused_df=None, df=None,
@@ -262,7 +281,9 @@ def make_grads(g):
     n = int(g["x"].numel())
     if g["tip"].numel() < 4:
         raise ValueError("tip gradient needs 4 floats")
-    return Grads(*[_dev(g[k], k) if n > 0 else 0 for k in ("x", "y", "z", "q", "R", "eps")], _dev(g["tip"], "tip"))
+    gr = Grads(*[_dev(g[k], k) if n > 0 else 0 for k in ("x", "y", "z", "q", "R", "eps")], _dev(g["tip"], "tip"))
+    gr._tensors = dict(g)
+    return gr
 
 
 def pp_backward(atoms: Atoms, probe: Probe, grid: Grid, ff, scan: Scan, tip: Tip, df_params: DF, pos, g_df,

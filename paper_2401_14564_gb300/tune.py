@@ -1,0 +1,102 @@
+"""Autotuner for the launch shapes of the hot path.
+
+Choices it sweeps, each timed with CUDA events through the C ABI on the
+workload itself (inputs on the device, median of a few repetitions):
+  - pp_make_ff_tuned: z-nodes per thread (4, 8, 16);
+  - pp_relax_scan: force-field layout, linear or bricked (several brick shapes);
+  - pp_batch_run: persistent CTAs (multiples of the SM count).
+Every candidate computes the same values (the layout and the launch shape do
+not change the arithmetic per node or per pixel), so the pick is a pure
+speed decision.  Results are cached in a JSON file keyed by GPU name and
+workload shape.
+"""
+from __future__ import annotations
+
+import json
+import os
+import statistics
+
+import torch
+
+from . import afm, pp
+
+BRICKS = [(0, None), (1, (4, 4, 4)), (1, (8, 8, 2)), (1, (8, 4, 4)), (1, (16, 4, 2)), (1, (4, 4, 8))]
+ZPTS = (4, 8, 16)
+
+
+def _key(case):
+    g, s = case["grid"], case["scan"]
+    return (f"{torch.cuda.get_device_name()}|grid{g['nx']}x{g['ny']}x{g['nz']}|atoms{len(case['atoms']['x'])}"
+            f"|scan{s['nx']}x{s['ny']}x{s['nz']}|mi{case['probe']['min_image']}|rc{case['probe']['coul_rc']}")
+
+
+def _time(fn, reps):
+    stream = torch.cuda.current_stream()
+    ts = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def tune_case(case, reps=3, bricks=BRICKS, zpts=ZPTS):
+    """Time every FF launch shape and every grid layout for the relaxation; return the fastest."""
+    atoms_t = afm.atoms_to_device(case["atoms"])
+    atoms = pp.make_atoms(atoms_t)
+    probe = pp.make_probe(case["probe"])
+    ff_times = {}
+    grid0 = pp.make_grid(case["grid"], 0)
+    ff = torch.empty(pp.pp_ff_floats(grid0), dtype=torch.float32, device="cuda")
+    for z in zpts:
+        t = pp.Tuning(z)
+        pp.pp_make_ff_tuned(atoms, probe, grid0, ff, t)
+        ff_times[z] = _time(lambda: pp.pp_make_ff_tuned(atoms, probe, grid0, ff, t), reps)
+    best_z = min(ff_times, key=ff_times.get)
+    relax_times = {}
+    for layout, brick in bricks:
+        sim = afm.Simulator(case, layout=layout, brick=brick or (4, 4, 4), want_pos=False, want_iters=False)
+        sim.make_ff(atoms_t)
+        sim.relax()
+        relax_times[f"{layout}:{brick}"] = _time(sim.relax, reps)
+        del sim
+    best = min(relax_times, key=relax_times.get)
+    layout, brick = best.split(":", 1)
+    brick = None if brick == "None" else tuple(int(v) for v in brick.strip("()").split(","))
+    return {"ff_zpt": best_z, "layout": int(layout), "brick": list(brick) if brick else None,
+            "ff_ms": ff_times, "relax_ms": relax_times}
+
+
+def tune_batch(batch_obj, reps=2, factors=(1, 2, 3, 4)):
+    """Time pp_batch_run for persistent-CTA counts that are multiples of the SM count."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    times = {}
+    for f in factors:
+        batch_obj.params.ctas = f * sms
+        batch_obj.run()
+        times[f * sms] = _time(batch_obj.run, reps)
+    best = min(times, key=times.get)
+    batch_obj.params.ctas = best
+    return {"ctas": best, "ms": times}
+
+
+def cached(case, path=None, **kw):
+    """tune_case() result from the cache at `path` (JSON), computing and storing it if absent."""
+    path = path or os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning.json")
+    db = {}
+    if os.path.exists(path):
+        with open(path) as f:
+            db = json.load(f)
+    k = _key(case)
+    if k not in db:
+        r = tune_case(case, **kw)
+        db[k] = {"ff_zpt": r["ff_zpt"], "layout": r["layout"], "brick": r["brick"],
+                 "ff_ms": {str(a): b for a, b in r["ff_ms"].items()}, "relax_ms": r["relax_ms"]}
+        tmp = path + f".{os.getpid()}.tmp"
+        with open(tmp, "w") as f:
+            json.dump(db, f, indent=1, sort_keys=True)
+        os.replace(tmp, path)
+    return db[k]
