@@ -324,6 +324,7 @@ def main():
     import torch
 
     from paper_2401_14564_gb300 import afm, synth
+    from paper_2401_14564_gb300 import dist as ppd
 
     torch.cuda.set_device(local)
     dist = None
@@ -377,11 +378,7 @@ def main():
     clk = clocks.stop()
     t_ff = [evs[k][0].elapsed_time(evs[k][1]) for k in range(args.steps)]
     t_rx = [evs[k][1].elapsed_time(evs[k][2]) for k in range(args.steps)]
-    ms_step = sum(a + b for a, b in zip(t_ff, t_rx)) / args.steps
-    if dist is not None:
-        t = torch.tensor([ms_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = ppd.max_over_ranks(sum(a + b for a, b in zip(t_ff, t_rx)) / args.steps)
     iters = sim.iters.to(torch.int64)
     it_total = int(iters.sum().item())
     nonconv = float((sim.iters >= case["fire"]["max_iter"]).float().mean().item())
@@ -396,11 +393,7 @@ def main():
         t0 = time.perf_counter()
         sim.run_host(case["atoms"])
         e2e_t.append(time.perf_counter() - t0)
-    e2e_ms = 1e3 * statistics.mean(e2e_t)
-    if dist is not None:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = ppd.max_over_ranks(1e3 * statistics.mean(e2e_t))
 
     peaks, src = load_peaks()
     sm_max = peaks.get("sm_max_mhz", 2070.0)

@@ -1,5 +1,6 @@
 """The C-ABI library loads without a GPU, exports every entry point that
 include/pp.h declares, and rejects bad arguments on the host before any launch."""
+import ctypes
 import ctypes as C
 
 import pytest
@@ -65,3 +66,30 @@ def test_bad_shapes_rejected_on_host(L):
     assert L.pp_fz_to_df(fake, 5, 7, C.c_float(0.1), C.byref(dfp), fake, None) == 2
     dfp.A_pp = 10.0  # 101 taps
     assert L.pp_fz_to_df(fake, 200, 7, C.c_float(0.1), C.byref(dfp), fake, None) == 6
+
+
+def test_ctypes_structs_match_the_c_header(tmp_path):
+    """Every struct the binding passes has the same size and field offsets as pp.h (gcc)."""
+    import os
+    import subprocess
+
+    structs = {"pp_atoms": pp.Atoms, "pp_probe": pp.Probe, "pp_grid": pp.Grid, "pp_tip": pp.Tip, "pp_scan": pp.Scan,
+               "pp_fire": pp.Fire, "pp_df": pp.DF, "pp_grads": pp.Grads, "pp_mol_desc": pp.MolDesc,
+               "pp_batch_params": pp.BatchParams, "pp_tuning": pp.Tuning}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pp.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(pp.HEADER))
+    subprocess.run(["gcc", "-I", inc, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l}
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
