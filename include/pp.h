@@ -325,6 +325,18 @@ PP_API pp_status pp_backward_noalloc(const pp_atoms* atoms, const pp_probe* prob
 /* Bytes of the static scratch behind pp_backward_noalloc. */
 PP_API size_t pp_backward_noalloc_capacity(void);
 
+/* IETS map (Sec. 3.3): the probe particle's vibration modes at its relaxed
+ * positions pos[nz][ny][nx][3] (from pp_relax_scan with the same ff, grid,
+ * scan and tip).  Per point, the stiffness K = -(J + J^T)/2 with J the exact
+ * Jacobian of F_T + F_S (tip springs + trilinear interpolant); writes its
+ * eigenvalues ascending to eig[((k*ny + j)*nx + i)*3 + c] (eV/A^2) and, when
+ * hw is not NULL, the mode energies hbar sqrt(lambda/m) in meV (0 where
+ * lambda <= 0) for a probe mass of mass_amu atomic mass units.  The two
+ * lower eigenvalues are the lateral modes the IETS signal follows.  Errors:
+ * PP_ERR_ARG, PP_ERR_SHAPE, PP_ERR_CUDA. */
+PP_API pp_status pp_iets(const float* ff, const pp_grid* grid, const pp_scan* scan, const pp_tip* tip,
+                         const float* pos, float mass_amu, float* eig, float* hw, pp_stream stream);
+
 /* Message of the last failed call on this host thread ("" if none). */
 PP_API const char* pp_last_error(void);
 

@@ -88,6 +88,8 @@ def lib():
             L.or_fz_to_df.argtypes = [dp, C.c_int, C.c_int, C.c_double, C.POINTER(DF), dp]
             L.or_backward.argtypes = [vp, C.POINTER(Grid), C.POINTER(Atoms), C.POINTER(Probe), C.POINTER(Scan),
                                       C.POINTER(Tip), C.POINTER(DF), dp, dp, dp, dp, vp, C.c_int]
+            L.or_iets.argtypes = [vp, C.POINTER(Grid), C.POINTER(Atoms), C.POINTER(Probe), C.POINTER(Scan),
+                                  C.POINTER(Tip), dp, C.c_double, dp, vp, C.c_int]
             L.or_max_threads.restype = C.c_int
             _lib = L
     return _lib
@@ -220,6 +222,27 @@ def relax_scan(ff, grid, atoms, probe, scan, tip, fire, polish_tol=1e-11, nthrea
         v = np.moveaxis(v, 1, 0)  # (nz, ncols, ...)
         out[k] = v.reshape((nz, ny, nx) + v.shape[2:])
     return out
+
+
+def iets(ff, grid, atoms, probe, scan, tip, pos, mass_amu=16.0, nthreads=0):
+    """Stiffness eigenvalues (eV/A^2, ascending) and mode energies (meV) at relaxed positions pos[nz][ny][nx][3]."""
+    keep = _Keep()
+    pos = _d(pos)
+    shp = pos.shape[:-1]
+    eig = np.empty(shp + (3,))
+    hw = np.empty(shp + (3,))
+    ffp = None
+    if ff is not None:
+        ff = _d(ff)
+        ffp = ff.ctypes.data_as(C.c_void_p)
+    A = _atoms(atoms, keep) if atoms is not None else None
+    Pr = _probe(probe) if probe is not None else None
+    rc = lib().or_iets(ffp, C.byref(_grid(grid)), C.byref(A) if A is not None else None,
+                       C.byref(Pr) if Pr is not None else None, C.byref(_scan(scan)), C.byref(_tip(tip)), _ptr(pos),
+                       float(mass_amu), _ptr(eig), hw.ctypes.data_as(C.c_void_p), nthreads)
+    if rc:
+        raise ValueError("or_iets rejected its arguments")
+    return eig, hw
 
 
 def df_weights(a, h):

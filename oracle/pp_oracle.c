@@ -431,8 +431,8 @@ static int newton_polish(const or_model* M, const double anchor[3], double p[3],
     return *res < tol;
 }
 
-/* Eigenvalues of a symmetric 3x3 matrix by cyclic Jacobi rotations; returns the smallest. */
-static double sym3_min_eig(const double* S) {
+/* Eigenvalues of a symmetric 3x3 matrix by cyclic Jacobi rotations, ascending in ev[3]. */
+static void sym3_eigs(const double* S, double ev[3]) {
     double a[3][3];
     for (int m = 0; m < 3; ++m)
         for (int n = 0; n < 3; ++n) a[m][n] = S[m * 3 + n];
@@ -456,10 +456,16 @@ static double sym3_min_eig(const double* S) {
             }
         }
     }
-    double e = a[0][0];
-    if (a[1][1] < e) e = a[1][1];
-    if (a[2][2] < e) e = a[2][2];
-    return e;
+    ev[0] = a[0][0]; ev[1] = a[1][1]; ev[2] = a[2][2];
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2 - i; ++j)
+            if (ev[j] > ev[j + 1]) { const double t = ev[j]; ev[j] = ev[j + 1]; ev[j + 1] = t; }
+}
+
+static double sym3_min_eig(const double* S) {
+    double ev[3];
+    sym3_eigs(S, ev);
+    return ev[0];
 }
 
 /* Relax the listed pixel columns over all scan heights.
@@ -513,6 +519,44 @@ int or_relax_columns(const double* ff, const or_grid* G, const or_atoms* A, cons
             if (res) res[o] = r;
             if (lam) lam[o] = sym3_min_eig(Ks);
             if (ok) ok[o] = good;
+        }
+    }
+    return 0;
+}
+
+/* IETS map (Sec. 3.3): the probe particle's vibration modes at the relaxed
+ * position p*: stiffness K = -(J + J^T)/2 with J = dG/dp (tip springs + exact
+ * trilinear Jacobian, or the direct-sum Jacobian when ff == NULL), its three
+ * eigenvalues ascending (eV/A^2) in eig[3*o..], and the mode energies
+ * hbar*sqrt(lambda/m) in meV in hw[3*o..] (0 where lambda <= 0) for a mass in
+ * atomic mass units.  pos and outputs in scan layout [nz][ny][nx]. */
+int or_iets(const double* ff, const or_grid* G, const or_atoms* A, const or_probe* P, const or_scan* S,
+            const or_tip* T, const double* pos, double mass_amu, double* eig, double* hw, int nthreads) {
+    if (!G || !S || !T || !pos || !eig || !(mass_amu > 0.0)) return 1;
+    if (!ff && (!A || !P)) return 1;
+    set_threads(nthreads);
+    or_model M;
+    M.ff = ff; M.G = G; M.A = A; M.P = P;
+    grid_period(G, &M.Lx, &M.Ly);
+    M.tip = tip_units(T);
+    /* hbar sqrt(eV A^-2 / amu) in meV: SI constants */
+    const double hbar = 1.054571817e-34, ev = 1.602176634e-19, amu = 1.66053906660e-27;
+    const double unit = hbar * sqrt(ev / 1e-20 / amu) / ev * 1e3;
+    const long npix = (long)S->nx * S->ny, total = npix * S->nz;
+#pragma omp parallel for schedule(static)
+    for (long o = 0; o < total; ++o) {
+        const int k = (int)(o / npix);
+        const long px = o % npix;
+        const int i = (int)(px % S->nx), j = (int)(px / S->nx);
+        const double anchor[3] = {S->x0 + i * S->px, S->y0 + j * S->py, S->z_top - k * S->dz};
+        double Gv[3], J[9], K[9], ev3[3];
+        total_force(&M, anchor, pos + 3 * o, Gv, J);
+        for (int m = 0; m < 3; ++m)
+            for (int n = 0; n < 3; ++n) K[m * 3 + n] = -0.5 * (J[m * 3 + n] + J[n * 3 + m]);
+        sym3_eigs(K, ev3);
+        for (int m = 0; m < 3; ++m) {
+            eig[3 * o + m] = ev3[m];
+            if (hw) hw[3 * o + m] = ev3[m] > 0.0 ? unit * sqrt(ev3[m] / mass_amu) : 0.0;
         }
     }
     return 0;

@@ -424,6 +424,47 @@ pp_status pp_batch_status(const void* ws, int* flags, pp_stream stream) {
     return PP_OK;
 }
 
+pp_status pp_iets(const float* ff, const pp_grid* grid, const pp_scan* scan, const pp_tip* tip, const float* pos,
+                  float mass_amu, float* eig, float* hw, pp_stream stream) {
+    g_error.clear();
+    if (!ff || !grid || !scan || !tip || !pos || !eig) { set_error("pp_iets: NULL argument"); return PP_ERR_ARG; }
+    if (!aligned16(ff)) { set_error("pp_iets: ff must be 16-byte aligned"); return PP_ERR_ARG; }
+    if (!finite_pos(mass_amu)) { set_error("pp_iets: mass must be > 0"); return PP_ERR_ARG; }
+    GridMap map;
+    std::string why;
+    if (!make_grid_map(grid, &map, &why)) { set_error("pp_iets: " + why); return PP_ERR_SHAPE; }
+    if (scan->nx < 1 || scan->ny < 1 || scan->nz < 1 ||
+        (int64_t)scan->nx * scan->ny * scan->nz * 3 >= (int64_t(1) << 31)) {
+        set_error("pp_iets: invalid scan size");
+        return PP_ERR_SHAPE;
+    }
+    if (!finite_pos(scan->dz)) { set_error("pp_iets: invalid scan geometry"); return PP_ERR_ARG; }
+    pp_fire dummy = {1, 1.f, 1.f, 1.f, 1.f, 1.f, 0.f, 1.f, 1.f, 0};
+    if (!check_tip_fire(tip, &dummy, &why)) { set_error("pp_iets: " + why); return PP_ERR_ARG; }
+    IetsLaunch L;
+    std::memset(&L, 0, sizeof(L));
+    L.ff = reinterpret_cast<const float4*>(ff);
+    L.map = map;
+    L.layout = grid->layout;
+    L.inv_dx = 1.f / grid->dx; L.inv_dy = 1.f / grid->dy; L.inv_dz = 1.f / grid->dz;
+    L.gx0s = (float)(-(double)grid->x0 / grid->dx);
+    L.gy0s = (float)(-(double)grid->y0 / grid->dy);
+    L.gz0s = (float)(-(double)grid->z0 / grid->dz);
+    L.periodic_xy = grid->periodic_xy;
+    L.snx = scan->nx; L.sny = scan->ny; L.snz = scan->nz;
+    L.sx0 = scan->x0; L.sy0 = scan->y0; L.spx = scan->px; L.spy = scan->py; L.z_top = scan->z_top; L.sdz = scan->dz;
+    L.kx = (float)(tip->kx * kNmToEvA2); L.ky = (float)(tip->ky * kNmToEvA2); L.kR = (float)(tip->kR * kNmToEvA2);
+    L.R0 = tip->R0; L.d0x = tip->d0x; L.d0y = tip->d0y;
+    L.d0z = (float)(-sqrt((double)tip->R0 * tip->R0 - (double)tip->d0x * tip->d0x - (double)tip->d0y * tip->d0y));
+    L.R0sq = (float)((double)tip->R0 * tip->R0);
+    L.c0 = (float)((double)L.d0x * L.d0x + (double)L.d0y * L.d0y + (double)L.d0z * L.d0z - (double)tip->R0 * tip->R0);
+    L.pos = pos; L.eig = eig; L.hw = hw;
+    // hbar sqrt(1 eV/A^2 / (m amu)) in meV, from SI constants
+    const double hbar = 1.054571817e-34, ev = 1.602176634e-19, amu = 1.66053906660e-27;
+    L.hw_unit = (float)(hbar * sqrt(ev / 1e-20 / (amu * mass_amu)) / ev * 1e3);
+    return cuda_status(launch_iets(L, (cudaStream_t)stream), "pp_iets launch");
+}
+
 pp_status pp_ff_convert(const float* src, const pp_grid* src_grid, float* dst, const pp_grid* dst_grid,
                         pp_stream stream) {
     g_error.clear();

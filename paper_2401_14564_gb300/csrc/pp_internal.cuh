@@ -137,6 +137,22 @@ struct BatchArgs {
 size_t batch_workspace_bytes(int nmol);
 cudaError_t launch_batch(const BatchArgs& A, cudaStream_t s);
 
+struct IetsLaunch {
+    const float4* ff;
+    GridMap map;
+    int layout;
+    float gx0s, gy0s, gz0s, inv_dx, inv_dy, inv_dz;
+    int periodic_xy;
+    int snx, sny, snz;
+    float sx0, sy0, spx, spy, z_top, sdz;
+    float kx, ky, kR, R0, d0x, d0y, d0z, R0sq, c0;
+    const float* pos;
+    float* eig;
+    float* hw;
+    float hw_unit;  // hbar sqrt(1 eV/A^2 / m) in meV
+};
+cudaError_t launch_iets(const IetsLaunch& L, cudaStream_t s);
+
 // Workspace of pp_backward: a 256-byte header (z-slab bounds) then the grid adjoint.
 constexpr size_t kBwdHeader = 256;
 

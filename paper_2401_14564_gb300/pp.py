@@ -142,6 +142,8 @@ def lib():
             L.pp_batch_run.restype = st
             L.pp_batch_status.argtypes = [vp, C.POINTER(C.c_int), vp]
             L.pp_batch_status.restype = st
+            L.pp_iets.argtypes = [vp, C.POINTER(Grid), C.POINTER(Scan), C.POINTER(Tip), vp, C.c_float, vp, vp, vp]
+            L.pp_iets.restype = st
             L.pp_last_error.argtypes = []
             L.pp_last_error.restype = C.c_char_p
             _lib = L
@@ -336,6 +338,16 @@ def pp_batch_status(ws, stream=None):
     flags = C.c_int(0)
     st = lib().pp_batch_status(_dev(ws, "ws", ws.dtype), C.byref(flags), _stream(stream))
     return int(st), int(flags.value)
+
+
+def pp_iets(ff, grid: Grid, scan: Scan, tip: Tip, pos, mass_amu: float, eig, hw=None, stream=None):
+    npx = scan.nx * scan.ny * scan.nz
+    if pos.numel() < 3 * npx or eig.numel() < 3 * npx or (hw is not None and hw.numel() < 3 * npx):
+        raise ValueError("buffer smaller than the scan")
+    if ff.numel() < pp_ff_floats(grid):
+        raise ValueError("ff buffer smaller than pp_ff_floats(grid)")
+    _check(lib().pp_iets(_dev(ff, "ff"), C.byref(grid), C.byref(scan), C.byref(tip), _dev(pos, "pos"),
+                         float(mass_amu), _dev(eig, "eig"), _dev(hw, "hw", allow_none=True), _stream(stream)))
 
 
 def pp_last_error() -> str:
