@@ -25,6 +25,7 @@ namespace {
 constexpr int kThreads = 128;  // 4 independent warps per CTA
 constexpr int kWarps = kThreads / 32;
 constexpr int kZPT = 8;        // z-nodes per FF tile (4 packed pairs)
+constexpr int kMinCtas = 5;    // resident CTAs per SM the register budget is sized for
 
 struct BatchLaunch {
     const pp_mol_desc* descs;
@@ -206,7 +207,7 @@ __device__ __forceinline__ void ff_tile(const BatchLaunch& B, const pp_mol_desc&
 }
 
 template <bool kMinImage, bool kCutoff>
-__global__ void __launch_bounds__(kThreads) batch_kernel(const BatchLaunch B) {
+__global__ void __launch_bounds__(kThreads, kMinCtas) batch_kernel(const BatchLaunch B) {
     __shared__ float4 st[kWarps][4][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long total = B.seg_start[2 * B.nmol];

@@ -172,3 +172,14 @@ def test_flake_full_size_sampled_columns(orc):
     gdf = g["df"][:, jj, ii]
     kd = df_keep(keep.T, 5)
     assert np.abs(gdf - odf)[kd].max() <= 1e-3 * (g["df"].max() - g["df"].min())
+
+
+def test_asymmetric_tip_on_a_clamped_grid_parity(orc):
+    # a tilted rest displacement (d0x, d0y != 0), unequal lateral springs, and a grid that clamps
+    # instead of wrapping laterally
+    c = synth.small_case(seed=8, n_atoms=10, nxy=36, nz=40, scan_px=11, nz_scan=13)
+    # (springs stiff enough that the lateral stiffness at rest, 0.022 / 0.017 eV/A^2, stays above
+    # the 0.01 eV/A^2 conditioning cut of the comparison)
+    c["tip"] = synth.default_tip(kx=0.35, ky=0.28, d0x=0.35, d0y=-0.25)
+    c["grid"] = dict(c["grid"], periodic_xy=0)
+    check_parity(orc, c)
