@@ -43,7 +43,7 @@ class Atoms(C.Structure):
 
 class Probe(C.Structure):
     _fields_ = [("R_pp", C.c_double), ("eps_pp", C.c_double), ("Q", C.c_double),
-                ("coul_rc", C.c_double), ("min_image", C.c_int), ("core_frac", C.c_double)]
+                ("coul_rc", C.c_double), ("min_image", C.c_int), ("core_frac", C.c_double), ("Qzz", C.c_double)]
 
 
 class Grid(C.Structure):
@@ -120,7 +120,8 @@ def _atoms(a, keep):
 
 
 def _probe(p):
-    return Probe(p["R_pp"], p["eps_pp"], p["Q"], p["coul_rc"], int(p["min_image"]), p["core_frac"])
+    return Probe(p["R_pp"], p["eps_pp"], p["Q"], p["coul_rc"], int(p["min_image"]), p["core_frac"],
+                 float(p.get("Qzz", 0.0)))
 
 
 def _grid(g):
@@ -272,7 +273,7 @@ def backward(ff, grid, atoms, probe, scan, tip, df, pos, g_df, want_grid_adj=Fal
     g_df = _d(g_df)
     n = len(atoms["x"])
     grads = np.zeros((n, 6))
-    gtip = np.zeros(4)
+    gtip = np.zeros(5)
     gadj = np.zeros((grid["nz"], grid["ny"], grid["nx"], 3)) if (want_grid_adj and ff is not None) else None
     ffp = None
     if ff is not None:
@@ -285,7 +286,7 @@ def backward(ff, grid, atoms, probe, scan, tip, df, pos, g_df, want_grid_adj=Fal
     if rc:
         raise ValueError("or_backward rejected its arguments")
     return {"x": grads[:, 0], "y": grads[:, 1], "z": grads[:, 2], "R": grads[:, 3], "eps": grads[:, 4],
-            "q": grads[:, 5], "kx": gtip[0], "ky": gtip[1], "kR": gtip[2], "Q": gtip[3], "grid_adj": gadj}
+            "q": grads[:, 5], "kx": gtip[0], "ky": gtip[1], "kR": gtip[2], "Q": gtip[3], "Qzz": gtip[4], "grid_adj": gadj}
 
 
 def forward(case, grid_free=False, fire=None, polish_tol=1e-11, nthreads=0):

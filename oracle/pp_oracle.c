@@ -21,7 +21,10 @@
  *   - frequency shift of Eq. (df) by product integration of a piecewise
  *     linear Fz against the kernel u / sqrt(a^2 - u^2), a = A/2;
  *   - the implicit-function adjoint of all of the above (the paper has no
- *     gradients; this is the derivative of the same discrete model).
+ *     gradients; this is the derivative of the same discrete model);
+ *   - optionally an axial point quadrupole on the probe (Secs. 2.2.3, 2.2.5: the CO
+ *     tip's quadrupolar charge distribution) in the field of the sample's
+ *     point charges.
  *
  * Readings of the paper that the code fixes (all units: A, eV, e):
  *   d0 = (d0x, d0y, -sqrt(R0^2 - d0x^2 - d0y^2)): the PP hangs below the tip;
@@ -29,7 +32,14 @@
  *   grid nodes x_i = x0 + i*dx, periodic in x,y when periodic_xy, clamped in z
  *   (cell index in [0, nz-2], fraction in [0,1]);
  *   spring constants are given in N/m and converted with 1 eV/A^2 = 16.02176634
- *   N/m; Coulomb constant 14.3996454784 eV*A/e^2.
+ *   N/m; Coulomb constant 14.3996454784 eV*A/e^2;
+ *   the tip quadrupole Qzz (e*A^2) is the second moment sum_k q_k z_k^2 of an
+ *   axial charge distribution with no net charge or dipole, rigidly attached
+ *   to the PP (no rotation, Sec. 2.2.3); its energy in the sample potential
+ *   V(r) = k_e sum_i q_i / |r - r_i| is (Qzz/2) d^2V/dz^2, per atom
+ *   E = (k_e q_i Qzz / 2) (3 dz^2 - r^2) / r^5; with coul_rc > 0 the term is
+ *   cut off (not shifted) at r >= coul_rc; inside the core floor r is
+ *   replaced by the floor radius, as for the other pair terms.
  */
 #include <math.h>
 #include <stdint.h>
@@ -45,7 +55,7 @@
 #define OR_PI 3.14159265358979323846
 
 typedef struct { int n; const double *x, *y, *z, *R, *eps, *q; } or_atoms;
-typedef struct { double R_pp, eps_pp, Q, coul_rc; int min_image; double core_frac; } or_probe;
+typedef struct { double R_pp, eps_pp, Q, coul_rc; int min_image; double core_frac; double Qzz; } or_probe;
 /* Lx, Ly: minimum-image period; 0 means the grid's own extent nx*dx, ny*dy
  * (a window of a larger periodic grid passes the full grid's extent). */
 typedef struct { int nx, ny, nz; double x0, y0, z0, dx, dy, dz; int periodic_xy; double Lx, Ly; } or_grid;
@@ -85,7 +95,36 @@ typedef struct {
     double S_lj_e;      /* LJ part of S per unit e_iPP */
     double S_el_qq;     /* Coulomb part of S per unit k_e Q q_i */
     double e_ij;        /* e_iPP */
+    /* tip quadrupole, per unit k_e q_i Qzz / 2 (zero when Qzz = 0 or beyond coul_rc) */
+    double Phi[3];      /* force */
+    double eq;          /* energy */
+    double dPhi[9];     /* dPhi_a / d delta_b, the floored r held fixed when clamped */
+    double dPhi_dr[3];  /* dPhi_a / dr at fixed delta */
 } or_pair;
+
+/* Quadrupole pair term as a function of delta and r (r = |delta| unless floored):
+ *   e = 3 dz^2 / r^5 - 1 / r^3,
+ *   Phi = -grad e = (15 dz^2 / r^7 - 3 / r^5) delta - (6 dz / r^5) z_hat. */
+static void quad_eval(const double d[3], double r, int clamped, or_pair* o) {
+    const double dz = d[2];
+    const double r2 = r * r, r5 = r2 * r2 * r, r7 = r5 * r2;
+    const double A = 15.0 * dz * dz / r7 - 3.0 / r5;
+    o->eq = 3.0 * dz * dz / r5 - 1.0 / (r2 * r);
+    for (int a = 0; a < 3; ++a) o->Phi[a] = A * d[a];
+    o->Phi[2] -= 6.0 * dz / r5;
+    /* partials at fixed r */
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) o->dPhi[a * 3 + b] = (a == b ? A : 0.0);
+    for (int a = 0; a < 3; ++a) o->dPhi[a * 3 + 2] += 30.0 * dz * d[a] / r7;
+    o->dPhi[2 * 3 + 2] -= 6.0 / r5;
+    /* dPhi/dr at fixed delta */
+    const double dA = -105.0 * dz * dz / (r7 * r) + 15.0 / (r5 * r);
+    for (int a = 0; a < 3; ++a) o->dPhi_dr[a] = dA * d[a];
+    o->dPhi_dr[2] += 30.0 * dz / (r5 * r);
+    if (!clamped && r > 0.0)
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) o->dPhi[a * 3 + b] += o->dPhi_dr[a] * d[b] / r;
+}
 
 static void pair_eval(const or_atoms* A, int i, const or_probe* P, double Lx, double Ly,
                       const double pt[3], or_pair* o) {
@@ -131,6 +170,14 @@ static void pair_eval(const or_atoms* A, int i, const or_probe* P, double Lx, do
     o->S_el_qq = c;
     o->S = eij * o->S_lj_e + qq * c;
     o->E = E_lj + qq * e_el;
+    if (P->Qzz != 0.0 && !(P->coul_rc > 0.0 && r >= P->coul_rc)) {
+        quad_eval(o->d, r, o->clamped, o);
+    } else {
+        memset(o->Phi, 0, sizeof o->Phi);
+        memset(o->dPhi, 0, sizeof o->dPhi);
+        memset(o->dPhi_dr, 0, sizeof o->dPhi_dr);
+        o->eq = 0.0;
+    }
     o->dSdr = dSlj_dr + qq * dc_dr;
     o->dSdR = dSlj_dR + (o->clamped ? o->dSdr * P->core_frac : 0.0);
 }
@@ -144,14 +191,16 @@ static int sample_point(const or_atoms* A, const or_probe* P, double Lx, double 
     for (int i = 0; i < A->n; ++i) {
         or_pair p;
         pair_eval(A, i, P, Lx, Ly, r, &p);
-        for (int a = 0; a < 3; ++a) F[a] += p.S * p.d[a];
-        E += p.E;
+        const double cq = 0.5 * OR_KE * P->Qzz * A->q[i];  /* tip quadrupole, per atom */
+        for (int a = 0; a < 3; ++a) F[a] += p.S * p.d[a] + cq * p.Phi[a];
+        E += p.E + cq * p.eq;
         core |= p.clamped;
         if (Js) {
             for (int a = 0; a < 3; ++a) {
                 Js[a * 3 + a] += p.S;
                 if (!p.clamped && p.r > 0.0)
                     for (int b = 0; b < 3; ++b) Js[a * 3 + b] += p.dSdr * p.d[a] * p.d[b] / p.r;
+                for (int b = 0; b < 3; ++b) Js[a * 3 + b] += cq * p.dPhi[a * 3 + b];
             }
         }
     }
@@ -615,9 +664,9 @@ int or_fz_to_df(const double* fz, int nz, int npix, double dz, const or_df* D, d
 /* ------------------------------------------------------------------ adjoint */
 
 /* Accumulate a . dF/d(theta_i) for one pair into the per-atom gradients
- * g[0..2] (position), g[3] (R_i), g[4] (eps_i), g[5] (q_i), and *gQ. */
+ * g[0..2] (position), g[3] (R_i), g[4] (eps_i), g[5] (q_i), *gQ and *gQzz. */
 static void pair_grad(const or_pair* p, const or_atoms* A, int i, const or_probe* P,
-                      const double a[3], double* g, double* gQ) {
+                      const double a[3], double* g, double* gQ, double* gQzz) {
     const double ad = a[0] * p->d[0] + a[1] * p->d[1] + a[2] * p->d[2];
     for (int m = 0; m < 3; ++m) {
         double v = p->S * a[m];
@@ -628,6 +677,16 @@ static void pair_grad(const or_pair* p, const or_atoms* A, int i, const or_probe
     if (p->e_ij > 0.0) g[4] += ad * p->S_lj_e * P->eps_pp / (2.0 * p->e_ij);
     g[5] += ad * OR_KE * P->Q * p->S_el_qq;
     *gQ += ad * OR_KE * A->q[i] * p->S_el_qq;
+    if (P->Qzz != 0.0) {
+        const double cq = 0.5 * OR_KE * P->Qzz * A->q[i];
+        const double aPhi = a[0] * p->Phi[0] + a[1] * p->Phi[1] + a[2] * p->Phi[2];
+        for (int m = 0; m < 3; ++m)
+            g[m] -= cq * (a[0] * p->dPhi[m] + a[1] * p->dPhi[3 + m] + a[2] * p->dPhi[6 + m]);
+        if (p->clamped)
+            g[3] += cq * P->core_frac * (a[0] * p->dPhi_dr[0] + a[1] * p->dPhi_dr[1] + a[2] * p->dPhi_dr[2]);
+        g[5] += 0.5 * OR_KE * P->Qzz * aPhi;
+        *gQzz += 0.5 * OR_KE * A->q[i] * aPhi;
+    }
 }
 
 /* Gradient of L = sum_c sum_pix g_df[c][pix] * df[c][pix] with respect to the
@@ -638,7 +697,7 @@ static void pair_grad(const or_pair* p, const or_atoms* A, int i, const or_probe
  * Grid mode (ff != NULL): the grid adjoint Gbar_g = -sum lambda w_g(p*) is
  * contracted with the pair derivatives of every node value.  Direct mode:
  * the pair derivatives are taken at p* itself.
- * gtip = {dL/dkx, dL/dky, dL/dkR, dL/dQ}.  grid_adj (optional) gets Gbar [nz][ny][nx][3]. */
+ * gtip = {dL/dkx, dL/dky, dL/dkR, dL/dQ, dL/dQzz}.  grid_adj (optional) gets Gbar [nz][ny][nx][3]. */
 int or_backward(const double* ff, const or_grid* G, const or_atoms* A, const or_probe* P,
                 const or_scan* S, const or_tip* T, const or_df* D, const double* pos,
                 const double* g_df, double* grads /*[n][6]*/, double* gtip, double* grid_adj,
@@ -706,12 +765,13 @@ int or_backward(const double* ff, const or_grid* G, const or_atoms* A, const or_
     gtip[0] = gkx * OR_NM_TO_EVA2;
     gtip[1] = gky * OR_NM_TO_EVA2;
     gtip[2] = gkR * OR_NM_TO_EVA2;
-    double gQ_total = 0.0;
+    double gQ_total = 0.0, gQzz_total = 0.0;
     const int n = A->n;
     double* gQ_atom = (double*)calloc((size_t)n, sizeof(double));
+    double* gQzz_atom = (double*)calloc((size_t)n, sizeof(double));
 #pragma omp parallel for schedule(dynamic, 1)
     for (int ia = 0; ia < n; ++ia) {
-        double g[6] = {0, 0, 0, 0, 0, 0}, gQ = 0.0;
+        double g[6] = {0, 0, 0, 0, 0, 0}, gQ = 0.0, gQzz = 0.0;
         if (gbar) {
             const long nxy = (long)G->nx * G->ny;
             for (long gi = 0; gi < nnode; ++gi) {
@@ -721,7 +781,7 @@ int or_backward(const double* ff, const or_grid* G, const or_atoms* A, const or_
                 const double r[3] = {G->x0 + ii * G->dx, G->y0 + jj * G->dy, G->z0 + kk * G->dz};
                 or_pair pr;
                 pair_eval(A, ia, P, M.Lx, M.Ly, r, &pr);
-                pair_grad(&pr, A, ia, P, av, g, &gQ);
+                pair_grad(&pr, A, ia, P, av, g, &gQ, &gQzz);
             }
         } else {
             for (long o = 0; o < (long)nz * npix; ++o) {
@@ -730,16 +790,22 @@ int or_backward(const double* ff, const or_grid* G, const or_atoms* A, const or_
                 const double av[3] = {-l[0], -l[1], -l[2]};
                 or_pair pr;
                 pair_eval(A, ia, P, M.Lx, M.Ly, pos + 3 * o, &pr);
-                pair_grad(&pr, A, ia, P, av, g, &gQ);
+                pair_grad(&pr, A, ia, P, av, g, &gQ, &gQzz);
             }
         }
         for (int r = 0; r < 6; ++r) grads[6 * ia + r] = g[r];
         gQ_atom[ia] = gQ;
+        gQzz_atom[ia] = gQzz;
     }
-    for (int ia = 0; ia < n; ++ia) gQ_total += gQ_atom[ia];
+    for (int ia = 0; ia < n; ++ia) {
+        gQ_total += gQ_atom[ia];
+        gQzz_total += gQzz_atom[ia];
+    }
     gtip[3] = gQ_total;
+    gtip[4] = gQzz_total;
     if (grid_adj && gbar) memcpy(grid_adj, gbar, (size_t)nnode * 3 * sizeof(double));
     free(gQ_atom);
+    free(gQzz_atom);
     free(gbar);
     free(lam);
     free(gfz);

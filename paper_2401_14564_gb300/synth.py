@@ -45,9 +45,9 @@ def _atoms(sym, xyz, q):
 
 
 def default_probe(**kw):
-    """CO-like probe particle: O parameters, charge Q = -0.1 e."""
+    """CO-like probe particle: O parameters, charge Q = -0.1 e, no tip quadrupole (Qzz in e*A^2)."""
     p = {"R_pp": ELEMENTS["O"][0], "eps_pp": ELEMENTS["O"][1], "Q": -0.1,
-         "coul_rc": 0.0, "min_image": 0, "core_frac": 0.5}
+         "coul_rc": 0.0, "min_image": 0, "core_frac": 0.5, "Qzz": 0.0}
     p.update(kw)
     return p
 
