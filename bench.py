@@ -31,6 +31,8 @@ sys.path.insert(0, ROOT)
 METRIC = "relaxed pixel·z-steps/sec + FF grid·atom evals/sec vs roofline; batched mol/s; bwd/fwd"
 UNIT = "pixel·z-steps/s"
 FLOPS_PER_PAIR = 30          # algorithmic FP32 flops per grid-node/atom pair (FMA = 2)
+FLOPS_PER_PAIR_QUAD = 45     # the same with the tip-quadrupole term (+15)
+QZZ_CO = -0.05               # CO tip quadrupole of the paper's point-charge simulations, e*A^2
 BYTES_PER_FIRE_ITER = 96     # 8 corners x (Fx, Fy, Fz) FP32 per FIRE iteration
 SM_COUNT = 152
 
@@ -40,8 +42,10 @@ SM_COUNT = 152
 TRAFFIC = {
     "relax_scan": {"bytes": 51.85e6, "sha": "cf6af97e58ae1b80",
                    "files": ["relax_scan.cu", "relax_core.cuh", "interp.cuh"]},
-    "ff_assemble": {"bytes": 148.45e6, "sha": "cb0ce4397fa71aa1",
+    "ff_assemble": {"bytes": 148.53e6, "sha": "c55fc7410aa5e833",
                     "files": ["ff_assemble.cu", "ff_core.cuh", "interp.cuh"]},
+    "ff_assemble_quad": {"bytes": 148.37e6, "sha": "c55fc7410aa5e833",
+                         "files": ["ff_assemble.cu", "ff_core.cuh", "interp.cuh"]},
 }
 
 
@@ -124,36 +128,44 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(case, budget_cols=8192, full_ff=True):
+def cpu_baseline(case, target_s=12.0, chunk=8192, max_cols=None, full_ff=True):
     """FP64 oracle on a bounded sample of the flake workload, scaled to pixel.z-steps/s.
 
     Sample: the FF grid (all 256x256x200 nodes when full_ff, else the 71
-    z-layers the probe visits, nodes 20..90, extrapolated by 200/71) and the
-    relaxed scan of `budget_cols` of the 65536 pixel columns x 40 heights with
-    df, extrapolated by 65536/budget_cols.
+    z-layers the probe visits, nodes 20..90, extrapolated by 200/71), then the
+    relaxed scan (40 heights, with df) of seeded random pixel columns in chunks
+    of `chunk` until the whole sample has taken about target_s seconds, all
+    65536 columns are done, or max_cols is reached; the scan time is
+    extrapolated by 65536 / (columns done).
     """
     import oracle
 
     g, s = case["grid"], case["scan"]
+    npix = s["nx"] * s["ny"]
     k0, k1 = (0, g["nz"]) if full_ff else (20, 91)
     slab = dict(g, nz=k1 - k0, z0=g["z0"] + k0 * g["dz"])
     t0 = time.perf_counter()
     ff, _ = oracle.make_ff(case["atoms"], case["probe"], slab)
     t_ff = time.perf_counter() - t0
-    rng = np.random.default_rng(0)
-    cols = np.sort(rng.choice(s["nx"] * s["ny"], budget_cols, replace=False))
-    t0 = time.perf_counter()
-    r = oracle.relax_columns(ff, slab, None, None, s, case["tip"], case["fire"], cols, polish_tol=0.0)
-    oracle.fz_to_df(r["fz"].T, s["dz"], case["df"])
-    t_rx = time.perf_counter() - t0
-    t_full = t_ff * g["nz"] / (k1 - k0) + t_rx * (s["nx"] * s["ny"]) / budget_cols
-    units = s["nx"] * s["ny"] * s["nz"]
+    order = np.random.default_rng(0).permutation(npix)
+    limit = npix if max_cols is None else min(npix, max_cols)
+    done, t_rx = 0, 0.0
+    while done < limit and (done == 0 or t_ff + t_rx < target_s):
+        cols = np.sort(order[done:min(limit, done + chunk)])
+        t0 = time.perf_counter()
+        r = oracle.relax_columns(ff, slab, None, None, s, case["tip"], case["fire"], cols, polish_tol=0.0)
+        oracle.fz_to_df(r["fz"].T, s["dz"], case["df"])
+        t_rx += time.perf_counter() - t0
+        done += len(cols)
+    t_full = t_ff * g["nz"] / (k1 - k0) + t_rx * npix / done
+    units = npix * s["nz"]
     ff_desc = ("FF on all 256x256x200 nodes" if full_ff else "FF on nodes z 20..90 of 256x256x200, scaled by 200/71")
+    scan_desc = (f"all {npix} pixel columns" if done == npix
+                 else f"{done} of {npix} seeded random pixel columns, scaled by {npix}/{done}")
     return {"value": units / t_full, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
             "sample": (f"{ff_desc} ({(k1 - k0) * 256 * 256 * 60 / 1e6:.0f} M pairs, FP64, OpenMP) + FIRE scan "
-                       f"(no Newton polish) of {budget_cols} of 65536 pixel columns x 40 heights + df, "
-                       f"scaled by 65536/{budget_cols}"),
-            "sample_seconds": t_ff + t_rx}
+                       f"(no Newton polish) x 40 heights + df of {scan_desc}"),
+            "sample_seconds": t_ff + t_rx, "ff_seconds": t_ff, "scan_columns": done}
 
 
 def run_reference(args, rank, world):
@@ -163,11 +175,11 @@ def run_reference(args, rank, world):
 
     case = synth.flake_case()
     for _ in range(args.warmup):
-        cpu_baseline(case, budget_cols=64, full_ff=False)
+        cpu_baseline(case, chunk=64, max_cols=64, full_ff=False)
     vals = []
     info = None
     for _ in range(args.steps):
-        info = cpu_baseline(case, budget_cols=256, full_ff=False)
+        info = cpu_baseline(case, chunk=256, max_cols=256, full_ff=False)
         vals.append(info["value"])
     value = statistics.median(vals)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
@@ -199,7 +211,7 @@ def measure_bwd_fwd(case, steps, warmup, flush, tag):
     atoms_t = afm.atoms_to_device(case["atoms"])
     n = len(case["atoms"]["x"])
     grads = {k: torch.empty(n, device="cuda") for k in ("x", "y", "z", "q", "R", "eps")}
-    grads["tip"] = torch.empty(4, device="cuda")
+    grads["tip"] = torch.empty(5, device="cuda")
     ws = torch.empty(pp.pp_backward_workspace(sim.grid) // 4 + 1, dtype=torch.float32, device="cuda")
     w = torch.randn(tuple(sim.df.shape), generator=torch.Generator().manual_seed(7)).to("cuda")
     atoms = pp.make_atoms(atoms_t)
@@ -248,6 +260,42 @@ def measure_slab(steps, warmup, flush):
     r["pairs"] = pairs
     torch.cuda.empty_cache()
     return r
+
+
+def measure_quadrupole(case, tuning, steps, warmup, flush, alu_peak):
+    """The line's workload with the CO tip's quadrupole (Qzz = -0.05 e*A^2): K1's quadrupole
+    variant and the whole step (FF + relaxed scan + fused df), CUDA events, L2 flushed."""
+    import torch
+
+    from paper_2401_14564_gb300 import afm
+
+    qcase = dict(case, probe=dict(case["probe"], Qzz=QZZ_CO))
+    sim = afm.Simulator(qcase, tuning=tuning)
+    atoms = afm.atoms_to_device(qcase["atoms"])
+    for _ in range(max(warmup, 3)):
+        sim.run(atoms)
+    stream = torch.cuda.current_stream()
+    t_ff, t_rx = [], []
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        sim.make_ff(atoms)
+        e1.record(stream)
+        sim.relax()
+        e2.record(stream)
+        torch.cuda.synchronize()
+        t_ff.append(e0.elapsed_time(e1))
+        t_rx.append(e1.elapsed_time(e2))
+    g, s = qcase["grid"], qcase["scan"]
+    pairs = g["nx"] * g["ny"] * g["nz"] * len(qcase["atoms"]["x"])
+    ff_ms, rx_ms = statistics.mean(t_ff), statistics.mean(t_rx)
+    tflops = pairs * FLOPS_PER_PAIR_QUAD / (ff_ms * 1e-3) / 1e12
+    return {"workload": "flake60 with tip quadrupole Qzz = -0.05 e*A^2", "ff_ms": ff_ms, "relax_ms": rx_ms,
+            "ms_per_step": ff_ms + rx_ms, "pixel_z_per_s": s["nx"] * s["ny"] * s["nz"] / ((ff_ms + rx_ms) * 1e-3),
+            "ff_pair_evals_per_s": pairs / (ff_ms * 1e-3), "ff_flops_per_pair": FLOPS_PER_PAIR_QUAD,
+            "ff_achieved_tflops": tflops, "ff_frac_of_alu_peak": tflops / alu_peak,
+            "ff_traffic": measured_traffic("ff_assemble_quad")}
 
 
 def measure_batch(n_mol, steps, warmup, flush, seq_sample=64):
@@ -304,7 +352,7 @@ def measure_batch(n_mol, steps, warmup, flush, seq_sample=64):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--layout", type=int, default=0)
@@ -313,6 +361,7 @@ def main():
     ap.add_argument("--no-slab", action="store_true")
     ap.add_argument("--no-bwdfwd", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--no-quad", action="store_true")
     ap.add_argument("--zpt", type=int, default=0, help="FF z-nodes per thread (skips the autotuner)")
     ap.add_argument("--brick", default="", help="bricked layout bx,by,bz for the scan (skips the autotuner)")
     ap.add_argument("--batch-mol", type=int, default=1024)
@@ -436,6 +485,8 @@ def main():
                             g4["grid"]["nx"], g4["grid"]["ny"], g4["grid"]["nz"])),
         measure_bwd_fwd(case, max(3, args.steps // 2), args.warmup, flush, "flake60 (this line's workload)"),
     ]
+    if not args.no_quad:
+        line["quadrupole"] = measure_quadrupole(case, tuning, max(3, args.steps // 2), args.warmup, flush, alu_peak)
     if not args.no_slab:
         line["slab"] = measure_slab(3, 1, flush)
     if not args.no_batch:

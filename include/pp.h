@@ -72,13 +72,23 @@ typedef struct {
  * infinite; coul_rc > 0 selects a shifted-force Coulomb truncated at coul_rc
  * (F = k_e Q q (1/r^2 - 1/rc^2) r_hat for r < rc, 0 beyond); min_image = 1
  * sums each atom's nearest lateral periodic image, period = grid extent
- * (nx*dx, ny*dy). */
+ * (nx*dx, ny*dy).
+ * Qzz != 0 adds the CO tip's quadrupolar charge distribution (Secs. 2.2.3,
+ * 2.2.5; the paper's point-charge simulations use -0.05 e*A^2): an axial
+ * point quadrupole of second moment Qzz = sum q_k z_k^2 (no net charge or
+ * dipole) riding on the PP without rotation, with energy (Qzz/2) d^2V/dz^2 in
+ * the sample's point-charge potential, i.e. per atom, with delta = r - r_i,
+ *   E = (k_e q_i Qzz / 2) (3 dz^2 - r^2) / r^5,
+ *   F = (k_e q_i Qzz / 2) [(15 dz^2/r^7 - 3/r^5) delta - (6 dz/r^5) z_hat];
+ * r is the floored distance; with coul_rc > 0 the term is cut off (not
+ * shifted) at r >= coul_rc. */
 typedef struct {
     float R_pp, eps_pp; /* A, eV                       */
     float Q;            /* probe charge, e             */
     float coul_rc;      /* A; 0 = plain Coulomb        */
     int min_image;      /* 0 or 1                      */
     float core_frac;    /* floor radius / R_iPP, in (0, 1) */
+    float Qzz;          /* tip quadrupole, e*A^2; 0 = none */
 } pp_probe;
 
 /* Regular force-field grid: node (i,j,k) sits at (x0+i*dx, y0+j*dy, z0+k*dz).
@@ -269,8 +279,8 @@ PP_API pp_status pp_batch_status(const void* ws, int* flags, pp_stream stream);
 
 /* Gradients of pp_backward, device arrays owned by the caller: x, y, z, q, R,
  * eps hold n floats each (dL/dx_i in 1/A, dL/dq_i per e, dL/dR_i per A,
- * dL/deps_i per eV); tip holds 4 floats {dL/dkx, dL/dky, dL/dkR (per N/m),
- * dL/dQ (per e)}.  pp_backward overwrites all of them. */
+ * dL/deps_i per eV); tip holds 5 floats {dL/dkx, dL/dky, dL/dkR (per N/m),
+ * dL/dQ (per e), dL/dQzz (per e*A^2)}.  pp_backward overwrites all of them. */
 typedef struct {
     float *x, *y, *z, *q, *R, *eps;
     float* tip;
@@ -281,7 +291,7 @@ typedef struct {
 PP_API size_t pp_backward_workspace(const pp_grid* grid);
 
 /* Gradient of L = sum_{c,pix} g_df[c][pix] * df[c][pix] with respect to the
- * atoms (x, y, z, q, R, eps) and the tip (kx, ky, kR, Q).  The paper has no
+ * atoms (x, y, z, q, R, eps) and the tip (kx, ky, kR, Q, Qzz).  The paper has no
  * gradients: this is the implicit-function adjoint of the same discrete
  * model at the relaxed positions of a forward pass -- for every relaxed point
  * J^T lambda = (dFz/dp)^T g_Fz with J the exact 3x3 Jacobian of F_T + F_S

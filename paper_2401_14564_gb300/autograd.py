@@ -3,7 +3,7 @@
 Forward runs the three CUDA stages and saves the force-field grid and the
 relaxed positions; backward runs the implicit adjoint (pp_backward) and
 returns gradients for the atom arrays (x, y, z, q, R, eps) and the tip
-scalars (kx, ky, kR, Q).  Only argument marshalling happens here.
+scalars (kx, ky, kR, Q, Qzz).  Only argument marshalling happens here.
 """
 from __future__ import annotations
 
@@ -18,9 +18,9 @@ ATOM_KEYS = ("x", "y", "z", "q", "R", "eps")
 
 class PPFunction(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, x, y, z, q, R, eps, kx, ky, kR, Q, case, layout, fire):
+    def forward(ctx, x, y, z, q, R, eps, kx, ky, kR, Q, Qzz, case, layout, fire):
         dev = x.device
-        probe = dict(case["probe"], Q=float(Q))
+        probe = dict(case["probe"], Q=float(Q), Qzz=float(Qzz))
         tip = dict(case["tip"], kx=float(kx), ky=float(ky), kR=float(kR))
         grid = pp.make_grid(case["grid"], layout)
         scan = pp.make_scan(case["scan"])
@@ -50,7 +50,7 @@ class PPFunction(torch.autograd.Function):
         dev = ff.device
         n = atoms_t["x"].numel()
         grads = {k: torch.empty(n, dtype=torch.float32, device=dev) for k in ATOM_KEYS}
-        grads["tip"] = torch.empty(4, dtype=torch.float32, device=dev)
+        grads["tip"] = torch.empty(5, dtype=torch.float32, device=dev)
         ws = torch.empty(pp.pp_backward_workspace(grid) // 4 + 4, dtype=torch.float32, device=dev)
         if g_df is None:
             g_df = torch.zeros(1, dtype=torch.float32, device=dev)
@@ -58,11 +58,14 @@ class PPFunction(torch.autograd.Function):
                        g_df.contiguous().to(torch.float32), pp.make_grads(grads), ws)
         gt = grads["tip"].cpu()
         return (grads["x"], grads["y"], grads["z"], grads["q"], grads["R"], grads["eps"],
-                gt[0], gt[1], gt[2], gt[3], None, None, None)
+                gt[0], gt[1], gt[2], gt[3], gt[4], None, None, None)
 
 
-def afm_df(atoms_t, kx, ky, kR, Q, case, layout=0, fire=None):
-    """Differentiable df image.  atoms_t: dict of float32 CUDA tensors; kx, ky, kR, Q: 0-dim CPU tensors."""
+def afm_df(atoms_t, kx, ky, kR, Q, case, layout=0, fire=None, Qzz=None):
+    """Differentiable df image.  atoms_t: dict of float32 CUDA tensors; kx, ky, kR, Q and the
+    optional tip quadrupole Qzz (default: the case's): 0-dim CPU tensors."""
+    if Qzz is None:
+        Qzz = torch.tensor(float(case["probe"].get("Qzz", 0.0)))
     df, fz, pos = PPFunction.apply(atoms_t["x"], atoms_t["y"], atoms_t["z"], atoms_t["q"], atoms_t["R"],
-                                   atoms_t["eps"], kx, ky, kR, Q, case, layout, fire)
+                                   atoms_t["eps"], kx, ky, kR, Q, Qzz, case, layout, fire)
     return df

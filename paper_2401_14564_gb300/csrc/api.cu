@@ -139,7 +139,8 @@ pp_status pp_make_ff_tuned(const pp_atoms* atoms, const pp_probe* probe, const p
         return PP_ERR_ARG;
     }
     if (!(probe->core_frac > 0.f && probe->core_frac < 1.f)) { set_error("pp_make_ff: core_frac must be in (0,1)"); return PP_ERR_ARG; }
-    if (!(probe->eps_pp >= 0.f) || !isfinite(probe->R_pp) || !isfinite(probe->Q) || !(probe->coul_rc >= 0.f)) {
+    if (!(probe->eps_pp >= 0.f) || !isfinite(probe->R_pp) || !isfinite(probe->Q) || !(probe->coul_rc >= 0.f) ||
+        !isfinite(probe->Qzz)) {
         set_error("pp_make_ff: invalid probe parameters");
         return PP_ERR_ARG;
     }
@@ -159,6 +160,7 @@ pp_status pp_make_ff_tuned(const pp_atoms* atoms, const pp_probe* probe, const p
     L.R_pp = probe->R_pp;
     L.eps_pp = probe->eps_pp;
     L.kQ = (float)(kCoulomb * (double)probe->Q);
+    L.kQzz = (float)(0.5 * kCoulomb * (double)probe->Qzz);
     L.core_frac = probe->core_frac;
     L.coul_rc = probe->coul_rc;
     L.min_image = probe->min_image;
@@ -293,7 +295,7 @@ pp_status pp_backward(const pp_atoms* atoms, const pp_probe* probe, const pp_gri
     if (!grads->tip) { set_error("pp_backward: NULL tip gradient"); return PP_ERR_ARG; }
     if (!aligned16(ff) || !aligned16(ws)) { set_error("pp_backward: ff and ws must be 16-byte aligned"); return PP_ERR_ARG; }
     if (!(probe->core_frac > 0.f && probe->core_frac < 1.f) || !(probe->eps_pp >= 0.f) || !(probe->coul_rc >= 0.f) ||
-        (probe->min_image != 0 && probe->min_image != 1)) {
+        (probe->min_image != 0 && probe->min_image != 1) || !isfinite(probe->Q) || !isfinite(probe->Qzz)) {
         set_error("pp_backward: invalid probe parameters");
         return PP_ERR_ARG;
     }
@@ -326,6 +328,8 @@ pp_status pp_backward(const pp_atoms* atoms, const pp_probe* probe, const pp_gri
     L.kQ = (float)(kCoulomb * (double)probe->Q);
     L.ke = (float)kCoulomb;
     L.Q = probe->Q;
+    L.Qzz = probe->Qzz;
+    L.kQzz = (float)(0.5 * kCoulomb * (double)probe->Qzz);
     L.core_frac = probe->core_frac; L.coul_rc = probe->coul_rc; L.min_image = probe->min_image;
     L.Lx = grid->nx * grid->dx; L.Ly = grid->ny * grid->dy;
     L.ff = reinterpret_cast<const float4*>(ff);
@@ -353,6 +357,7 @@ pp_status pp_backward(const pp_atoms* atoms, const pp_probe* probe, const pp_gri
     L.gx = grads->x; L.gy = grads->y; L.gz = grads->z; L.gq = grads->q; L.gR = grads->R; L.geps = grads->eps;
     L.gtip = grads->tip;
     L.slab = reinterpret_cast<int*>(ws);
+    L.qsum = reinterpret_cast<float*>(reinterpret_cast<char*>(ws) + 16);
     L.gbar = reinterpret_cast<float4*>(reinterpret_cast<char*>(ws) + kBwdHeader);
     cudaStream_t s = (cudaStream_t)stream;
     pp_status st = cuda_status(cudaMemsetAsync(L.gbar, 0, (size_t)map.stored_nodes * 16, s), "pp_backward memset");
@@ -375,7 +380,8 @@ pp_status pp_batch_run(const pp_mol_desc* descs, int nmol, const pp_batch_params
     if (!aligned16(ff) || !aligned16(ws)) { set_error("pp_batch_run: ff and ws must be 16-byte aligned"); return PP_ERR_ARG; }
     const pp_probe* probe = &bp->probe;
     if (!(probe->core_frac > 0.f && probe->core_frac < 1.f) || !(probe->eps_pp >= 0.f) || !(probe->coul_rc >= 0.f) ||
-        !isfinite(probe->R_pp) || !isfinite(probe->Q) || (probe->min_image != 0 && probe->min_image != 1)) {
+        !isfinite(probe->R_pp) || !isfinite(probe->Q) || !isfinite(probe->Qzz) ||
+        (probe->min_image != 0 && probe->min_image != 1)) {
         set_error("pp_batch_run: invalid probe parameters");
         return PP_ERR_ARG;
     }

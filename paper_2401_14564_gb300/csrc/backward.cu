@@ -14,10 +14,12 @@
 //         dL/dkR = g_Fz (|d|-R0) d_z/|d| + lambda.d (|d|-R0)/|d|;
 //   K5    dL/dtheta_i = sum_g Gbar_g . dF_g/dtheta_i for every atom, by
 //         recomputing the pair terms of the force-field grid (Eqs. LJ and
-//         point charges) on the grid nodes with a nonzero adjoint, restricted
-//         to the z-slab K4 touched;
-//   fin   charges: dL/dq_i = Q C_i, dL/dQ = sum_i q_i C_i with
-//         C_i = sum_g (Gbar_g . delta) k_e c(r); eps via e_iPP = sqrt(e_i e_PP).
+//         point charges, and the tip quadrupole when Qzz != 0) on the grid
+//         nodes with a nonzero adjoint, restricted to the z-slab K4 touched;
+//   fin   charges: dL/dq_i = k_e (Q C_i + (Qzz/2) Cq_i), dL/dQ = k_e sum_i q_i C_i,
+//         dL/dQzz = (k_e/2) sum_i q_i Cq_i, with C_i = sum_g Gbar_g . delta c(r)
+//         and Cq_i = sum_g Gbar_g . Phi (the quadrupole force per unit
+//         k_e q_i Qzz / 2); eps via e_iPP = sqrt(e_i e_PP).
 // No relaxation iterate is stored or replayed: only the saved p*.
 #include "interp.cuh"
 
@@ -39,7 +41,8 @@ __global__ void init_kernel(const BwdLaunch P) {
     if (t == 0) {
         P.slab[0] = 0x7fffffff;
         P.slab[1] = -1;
-        P.gtip[0] = P.gtip[1] = P.gtip[2] = P.gtip[3] = 0.f;
+        P.gtip[0] = P.gtip[1] = P.gtip[2] = P.gtip[3] = P.gtip[4] = 0.f;
+        P.qsum[0] = P.qsum[1] = 0.f;
     }
     for (int a = t; a < P.n; a += gridDim.x * blockDim.x) {
         P.gx[a] = 0.f; P.gy[a] = 0.f; P.gz[a] = 0.f;
@@ -140,8 +143,8 @@ __global__ void __launch_bounds__(kAdjThreads) relax_adjoint_kernel(const BwdLau
 // K5: per-atom contraction of the grid adjoint with the pair derivatives.
 // A CTA stages kFFBNodes consecutive nodes (logical x-fastest order), keeps
 // those with a nonzero adjoint, and each thread then sweeps them for one atom,
-// accumulating (dx, dy, dz, dR, de_iPP, C) in registers.
-template <bool kMinImage, bool kCutoff>
+// accumulating (dx, dy, dz, dR, de_iPP, C, Cq) in registers.
+template <bool kMinImage, bool kCutoff, bool kQuad>
 __global__ void __launch_bounds__(kFFBThreads) ff_backward_kernel(const BwdLaunch P) {
     __shared__ float4 sp[kFFBNodes];  // node position (x, y, z, -)
     __shared__ float4 sg[kFFBNodes];  // adjoint (gx, gy, gz, -)
@@ -185,6 +188,7 @@ __global__ void __launch_bounds__(kFFBThreads) ff_backward_kernel(const BwdLaunc
     const float rc2 = kCutoff ? P.coul_rc * P.coul_rc : 0.f;
     const float irc2 = kCutoff ? 1.f / rc2 : 0.f;
     const float invLx = kMinImage ? 1.f / P.Lx : 0.f, invLy = kMinImage ? 1.f / P.Ly : 0.f;
+    float qC = 0.f, qCq = 0.f;  // this thread's q_i C_i and q_i Cq_i (tip quadrupole only)
     for (int a0 = 0; a0 < P.n; a0 += kFFBThreads) {
         const int ia = a0 + threadIdx.x;
         if (ia >= P.n) break;
@@ -194,7 +198,8 @@ __global__ void __launch_bounds__(kFFBThreads) ff_backward_kernel(const BwdLaunc
         const float qq = P.kQ * P.aq[ia];
         const float rmin2 = (P.core_frac * Rij) * (P.core_frac * Rij);
         const float R2 = Rij * Rij, iR = 1.f / Rij;
-        float gpx = 0.f, gpy = 0.f, gpz = 0.f, gRr = 0.f, ge = 0.f, C = 0.f;
+        const float kqq = kQuad ? P.kQzz * P.aq[ia] : 0.f;
+        float gpx = 0.f, gpy = 0.f, gpz = 0.f, gRr = 0.f, ge = 0.f, C = 0.f, Cq = 0.f;
         for (int s = 0; s < cnt; ++s) {
             const float4 np = sp[s], gb = sg[s];
             float dx = np.x - ax, dy = np.y - ay;
@@ -232,19 +237,63 @@ __global__ void __launch_bounds__(kFFBThreads) ff_backward_kernel(const BwdLaunc
             gRr = fmaf(ad, clamped ? fmaf(dSdr, P.core_frac, dSlj_dR) : dSlj_dR, gRr);
             ge = fmaf(ad, Slj_e, ge);
             C = fmaf(ad, c, C);
+            if (kQuad) {
+                // Phi = A delta - 6 dz r^-5 z_hat, A = 15 dz^2 r^-7 - 3 r^-5 (cut off at rc)
+                const bool inq = !kCutoff || r2 < rc2;
+                const float ir5 = ir2 * ir2 * rs, ir7 = ir5 * ir2, dz2 = dz * dz;
+                const float A = inq ? fmaf(15.f * dz2, ir7, -3.f * ir5) : 0.f;
+                const float a6 = inq ? 6.f * dz * ir5 : 0.f;
+                Cq = fmaf(A, ad, fmaf(-a6, gb.z, Cq));  // a . Phi
+                // a . dPhi/dr at fixed delta, and the z row of a^T dPhi/d delta at fixed r
+                const float W = inq ? rs * fmaf(fmaf(-105.f * dz2, ir7, 15.f * ir5), ad, 30.f * dz * ir5 * gb.z) : 0.f;
+                const float zrow = inq ? fmaf(30.f * dz * ir7, ad, -6.f * ir5 * gb.z) : 0.f;
+                const float wr = clamped ? 0.f : W * rs;  // r follows delta unless floored
+                gpx = fmaf(-kqq, fmaf(A, gb.x, wr * dx), gpx);
+                gpy = fmaf(-kqq, fmaf(A, gb.y, wr * dy), gpy);
+                gpz = fmaf(-kqq, fmaf(A, gb.z, fmaf(wr, dz, zrow)), gpz);
+                if (clamped) gRr = fmaf(kqq * P.core_frac, W, gRr);
+            }
         }
         atomicAdd(P.gx + ia, gpx);
         atomicAdd(P.gy + ia, gpy);
         atomicAdd(P.gz + ia, gpz);
         atomicAdd(P.gR + ia, gRr);
         atomicAdd(P.geps + ia, ge);
-        atomicAdd(P.gq + ia, C);
+        if (kQuad) {
+            atomicAdd(P.gq + ia, fmaf(P.Q, C, 0.5f * P.Qzz * Cq));  // per unit k_e
+            qC = fmaf(P.aq[ia], C, qC);
+            qCq = fmaf(P.aq[ia], Cq, qCq);
+        } else {
+            atomicAdd(P.gq + ia, C);
+        }
+    }
+    if (kQuad) {
+        qC = warp_sum(qC);
+        qCq = warp_sum(qCq);
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd(P.qsum + 0, qC);
+            atomicAdd(P.qsum + 1, qCq);
+        }
     }
 }
 
-// Charges and well depths from the accumulated sums; dL/dQ by a block reduction.
+// Charges and well depths from the accumulated sums; dL/dQ by a block reduction
+// (with a tip quadrupole, K5 has already combined the charge terms and summed
+// q_i C_i and q_i Cq_i).
 __global__ void finalize_kernel(const BwdLaunch P) {
     __shared__ float red[32];
+    if (P.Qzz != 0.f) {
+        for (int a = threadIdx.x; a < P.n; a += blockDim.x) {
+            P.gq[a] *= P.ke;
+            const float eij = sqrtf(P.aeps[a] * P.eps_pp);
+            P.geps[a] = eij > 0.f ? P.geps[a] * P.eps_pp / (2.f * eij) : 0.f;
+        }
+        if (threadIdx.x == 0) {
+            P.gtip[3] = P.ke * P.qsum[0];
+            P.gtip[4] = 0.5f * P.ke * P.qsum[1];
+        }
+        return;
+    }
     float acc = 0.f;
     for (int a = threadIdx.x; a < P.n; a += blockDim.x) {
         const float C = P.gq[a] * P.ke;  // sum (a.delta) k_e c
@@ -274,11 +323,11 @@ cudaError_t launch_backward(const BwdLaunch& L, cudaStream_t s) {
     if (L.n > 0) {
         const int64_t nodes = (int64_t)L.map.nx * L.map.ny * L.map.nz;
         const int fb = (int)((nodes + kFFBNodes - 1) / kFFBNodes);
-        const bool cut = L.coul_rc > 0.f;
-        if (L.min_image && cut) ff_backward_kernel<true, true><<<fb, kFFBThreads, 0, s>>>(L);
-        else if (L.min_image) ff_backward_kernel<true, false><<<fb, kFFBThreads, 0, s>>>(L);
-        else if (cut) ff_backward_kernel<false, true><<<fb, kFFBThreads, 0, s>>>(L);
-        else ff_backward_kernel<false, false><<<fb, kFFBThreads, 0, s>>>(L);
+        with_flags(L.min_image != 0, L.coul_rc > 0.f, L.Qzz != 0.f, [&](auto mi, auto cut, auto quad) {
+            ff_backward_kernel<decltype(mi)::value, decltype(cut)::value, decltype(quad)::value>
+                <<<fb, kFFBThreads, 0, s>>>(L);
+            return 0;
+        });
     }
     finalize_kernel<<<1, 256, 0, s>>>(L);
     return cudaGetLastError();

@@ -38,7 +38,7 @@ struct BatchLaunch {
     int* iters;
     long long out_cap, df_cap;
     // probe (shared)
-    float R_pp, eps_pp, kQ, core_frac, coul_rc;
+    float R_pp, eps_pp, kQ, core_frac, coul_rc, kQzz;
     int min_image, periodic_xy;
     // tip, FIRE and df stencil, under the names relax_pixel expects
     float kx, ky, kR, R0, d0x, d0y, d0z, R0sq, c0;
@@ -165,7 +165,7 @@ __device__ __forceinline__ void add_release(int* p, int v) {
     asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-template <bool kMinImage, bool kCutoff>
+template <bool kMinImage, bool kCutoff, bool kQuad>
 __device__ __forceinline__ void ff_tile(const BatchLaunch& B, const pp_mol_desc& D, long long tile, float4* s0,
                                         float4* s1, float4* s2, float4* s3, int lane) {
     constexpr int ZP = kZPT / 2;
@@ -182,7 +182,7 @@ __device__ __forceinline__ void ff_tile(const BatchLaunch& B, const pp_mol_desc&
 #pragma unroll
     for (int t = 0; t < ZP; ++t) fx[t] = fy[t] = fz[t] = en[t] = make_float2(0.f, 0.f);
     const FFConst cst = ff_const(B.R_pp, B.eps_pp, B.kQ, B.core_frac, D.nx * D.dx, D.ny * D.dy,
-                                 kCutoff ? B.coul_rc : 0.f);
+                                 kCutoff ? B.coul_rc : 0.f, kQuad ? B.kQzz : 0.f);
     for (int base = 0; base < D.n_atoms; base += 32) {
         const int cnt = min(32, D.n_atoms - base);
         __syncwarp();
@@ -192,7 +192,7 @@ __device__ __forceinline__ void ff_tile(const BatchLaunch& B, const pp_mol_desc&
                           s3[lane]);
         }
         __syncwarp();
-        ff_accumulate<ZP, kMinImage, kCutoff>(s0, s1, s2, s3, cnt, cst, gx, gy, gz, fx, fy, fz, en);
+        ff_accumulate<ZP, kMinImage, kCutoff, kQuad>(s0, s1, s2, s3, cnt, cst, gx, gy, gz, fx, fy, fz, en);
     }
     if (i < D.nx && j < D.ny) {
         float4* out = B.ff + D.ff_offset + (long long)j * D.nx + i;
@@ -206,7 +206,7 @@ __device__ __forceinline__ void ff_tile(const BatchLaunch& B, const pp_mol_desc&
     }
 }
 
-template <bool kMinImage, bool kCutoff>
+template <bool kMinImage, bool kCutoff, bool kQuad>
 __global__ void __launch_bounds__(kThreads, kMinCtas) batch_kernel(const BatchLaunch B) {
     __shared__ float4 st[kWarps][4][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(kThreads, kMinCtas) batch_kernel(const BatchLa
         const long long tile = t - B.seg_start[lo];
         const pp_mol_desc D = B.descs[mol];
         if (ff) {
-            ff_tile<kMinImage, kCutoff>(B, D, tile, st[warp][0], st[warp][1], st[warp][2], st[warp][3], lane);
+            ff_tile<kMinImage, kCutoff, kQuad>(B, D, tile, st[warp][0], st[warp][1], st[warp][2], st[warp][3], lane);
             __syncwarp();
             if (lane == 0) {
                 __threadfence();
@@ -302,6 +302,7 @@ cudaError_t launch_batch(const BatchArgs& A, cudaStream_t s) {
     const pp_batch_params& P = A.params;
     B.R_pp = P.probe.R_pp; B.eps_pp = P.probe.eps_pp;
     B.kQ = (float)(kCoulomb * (double)P.probe.Q);
+    B.kQzz = (float)(0.5 * kCoulomb * (double)P.probe.Qzz);
     B.core_frac = P.probe.core_frac; B.coul_rc = P.probe.coul_rc;
     B.min_image = P.probe.min_image; B.periodic_xy = P.periodic_xy;
     B.kx = (float)(P.tip.kx * kNmToEvA2); B.ky = (float)(P.tip.ky * kNmToEvA2); B.kR = (float)(P.tip.kR * kNmToEvA2);
@@ -329,24 +330,19 @@ cudaError_t launch_batch(const BatchArgs& A, cudaStream_t s) {
     B.wait_extra = P.wait_extra;
 
     batch_plan_kernel<<<1, 1024, 0, s>>>(B);
+    const void* fn = with_flags(B.min_image != 0, B.coul_rc > 0.f, B.kQzz != 0.f, [](auto mi, auto cut, auto quad) {
+        return (const void*)batch_kernel<decltype(mi)::value, decltype(cut)::value, decltype(quad)::value>;
+    });
     int ctas = P.ctas;
     if (ctas <= 0) {
         int dev = 0, sms = 148, per_sm = 1;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        const bool mi = B.min_image != 0, cut = B.coul_rc > 0.f;
-        const void* fn = mi && cut ? (const void*)batch_kernel<true, true>
-                       : mi        ? (const void*)batch_kernel<true, false>
-                       : cut       ? (const void*)batch_kernel<false, true>
-                                   : (const void*)batch_kernel<false, false>;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, 0);
         ctas = sms * (per_sm > 0 ? per_sm : 1);
     }
-    if (B.min_image && B.coul_rc > 0.f) batch_kernel<true, true><<<ctas, kThreads, 0, s>>>(B);
-    else if (B.min_image) batch_kernel<true, false><<<ctas, kThreads, 0, s>>>(B);
-    else if (B.coul_rc > 0.f) batch_kernel<false, true><<<ctas, kThreads, 0, s>>>(B);
-    else batch_kernel<false, false><<<ctas, kThreads, 0, s>>>(B);
-    return cudaGetLastError();
+    void* args[] = {&B};
+    return cudaLaunchKernel(fn, dim3(ctas), dim3(kThreads), args, 0, s);
 }
 
 }  // namespace pp

@@ -6,7 +6,9 @@
 //   u3 = (R_iPP^2 / r^2)^3, R_iPP = R_i + R_PP, e_iPP = sqrt(e_i e_PP);
 //   Coulomb (Eq. point charges):  E = k_e Q q_i / r,  S = k_e Q q_i / r^3
 //   (shifted-force variant when coul_rc > 0), F = -grad E (Sec. 2.2);
-// r^2 is floored per pair at (core_frac R_iPP)^2.
+// r^2 is floored per pair at (core_frac R_iPP)^2; optionally the tip's axial
+// quadrupole Qzz (Secs. 2.2.3, 2.2.5) in the sample's point-charge field,
+//   E = (k_e q_i Qzz / 2) (3 dz^2 - r^2) / r^5, F = -grad E.
 //
 // This is compute-bound FP32 arithmetic with no dense contraction, so it runs
 // on the FP32 pipes, not the tensor cores.  A CTA covers a 16x8 (x,y) tile of
@@ -29,7 +31,7 @@ constexpr int kTileY = 8;    // columns per CTA along y (two warps of 4)
 constexpr int kThreads = kTileX * kTileY;
 constexpr int kChunk = 256;  // atoms staged per pass
 
-template <int ZPT, bool kMinImage, bool kCutoff>
+template <int ZPT, bool kMinImage, bool kCutoff, bool kQuad>
 __global__ void __launch_bounds__(kThreads) ff_assemble_kernel(const FFLaunch P) {
     static_assert(ZPT % 2 == 0, "z-nodes come in packed pairs");
     constexpr int ZP = ZPT / 2;
@@ -51,7 +53,8 @@ __global__ void __launch_bounds__(kThreads) ff_assemble_kernel(const FFLaunch P)
 #pragma unroll
     for (int t = 0; t < ZP; ++t) fx[t] = fy[t] = fz[t] = en[t] = make_float2(0.f, 0.f);
 
-    const FFConst cst = ff_const(P.R_pp, P.eps_pp, P.kQ, P.core_frac, P.Lx, P.Ly, kCutoff ? P.coul_rc : 0.f);
+    const FFConst cst = ff_const(P.R_pp, P.eps_pp, P.kQ, P.core_frac, P.Lx, P.Ly, kCutoff ? P.coul_rc : 0.f,
+                                 kQuad ? P.kQzz : 0.f);
     for (int base = 0; base < P.n; base += kChunk) {
         const int cnt = min(kChunk, P.n - base);
         __syncthreads();
@@ -60,7 +63,7 @@ __global__ void __launch_bounds__(kThreads) ff_assemble_kernel(const FFLaunch P)
             ff_stage_atom(cst, P.x[g], P.y[g], P.z[g], P.R[g], P.eps[g], P.q[g], s0[a], s1[a], s2[a], s3[a]);
         }
         __syncthreads();
-        ff_accumulate<ZP, kMinImage, kCutoff>(s0, s1, s2, s3, cnt, cst, gx, gy, gz, fx, fy, fz, en);
+        ff_accumulate<ZP, kMinImage, kCutoff, kQuad>(s0, s1, s2, s3, cnt, cst, gx, gy, gz, fx, fy, fz, en);
     }
 
     if (i >= P.map.nx || j >= P.map.ny) return;
@@ -77,11 +80,11 @@ __global__ void __launch_bounds__(kThreads) ff_assemble_kernel(const FFLaunch P)
 template <int ZPT>
 cudaError_t launch_zpt(const FFLaunch& L, cudaStream_t s) {
     dim3 grid((L.map.nx + kTileX - 1) / kTileX, (L.map.ny + kTileY - 1) / kTileY, (L.map.nz + ZPT - 1) / ZPT);
-    const bool cut = L.coul_rc > 0.f;
-    if (L.min_image && cut) ff_assemble_kernel<ZPT, true, true><<<grid, kThreads, 0, s>>>(L);
-    else if (L.min_image) ff_assemble_kernel<ZPT, true, false><<<grid, kThreads, 0, s>>>(L);
-    else if (cut) ff_assemble_kernel<ZPT, false, true><<<grid, kThreads, 0, s>>>(L);
-    else ff_assemble_kernel<ZPT, false, false><<<grid, kThreads, 0, s>>>(L);
+    with_flags(L.min_image != 0, L.coul_rc > 0.f, L.kQzz != 0.f, [&](auto mi, auto cut, auto quad) {
+        ff_assemble_kernel<ZPT, decltype(mi)::value, decltype(cut)::value, decltype(quad)::value>
+            <<<grid, kThreads, 0, s>>>(L);
+        return 0;
+    });
     return cudaGetLastError();
 }
 

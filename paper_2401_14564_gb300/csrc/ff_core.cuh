@@ -6,13 +6,17 @@
 // constant stored twice so that one 16-byte broadcast load yields a ready
 // packed f32x2 operand:
 //   s0 = (x, y, rmin^2, 0)     s1 = (-z, -z, R_iPP^2, R_iPP^2)
-//   s2 = (12 e, 12 e, kq, kq)  s3 = (e, e, 0, 0)
-// with R_iPP = R_i + R_PP, e = e_iPP = sqrt(e_i e_PP), kq = k_e Q q_i and
-// rmin = core_frac R_iPP.  A thread accumulates ZP packed pairs of z-nodes
-// of one grid column: per node and atom, u3 = (R_iPP^2 / r^2)^3,
-//   F += [12 e (u3^2 - u3) / r^2 + kq / r^3] (r_node - r_atom),
+//   s2 = (12 e, 12 e, kq, kq)  s3 = (e, e, kqq, kqq)
+// with R_iPP = R_i + R_PP, e = e_iPP = sqrt(e_i e_PP), kq = k_e Q q_i,
+// kqq = k_e Qzz q_i / 2 and rmin = core_frac R_iPP.  A thread accumulates ZP
+// packed pairs of z-nodes of one grid column: per node and atom, with
+// delta = r_node - r_atom and u3 = (R_iPP^2 / r^2)^3,
+//   F += [12 e (u3^2 - u3) / r^2 + kq / r^3] delta,
 //   E += e (u3^2 - 2 u3) + kq / r,
-// with r^2 floored at rmin^2 (shifted-force Coulomb when kCutoff).
+// with r^2 floored at rmin^2 (shifted-force Coulomb when kCutoff), and with
+// the tip quadrupole (kQuad; cut off at coul_rc when kCutoff)
+//   F += kqq [(15 dz^2/r^2 - 3) delta - 6 dz z_hat] / r^5,
+//   E += kqq (3 dz^2 - r^2) / r^5.
 #pragma once
 
 #include "interp.cuh"
@@ -20,15 +24,15 @@
 namespace pp {
 
 struct FFConst {
-    float R_pp, eps_pp, kQ, core_frac;
+    float R_pp, eps_pp, kQ, core_frac, kQzz;
     float Lx, Ly, invLx, invLy;  // minimum-image period
     float rc2, irc2, two_irc;    // shifted-force cutoff
 };
 
 __device__ __forceinline__ FFConst ff_const(float R_pp, float eps_pp, float kQ, float core_frac, float Lx, float Ly,
-                                            float coul_rc) {
+                                            float coul_rc, float kQzz) {
     FFConst c;
-    c.R_pp = R_pp; c.eps_pp = eps_pp; c.kQ = kQ; c.core_frac = core_frac;
+    c.R_pp = R_pp; c.eps_pp = eps_pp; c.kQ = kQ; c.core_frac = core_frac; c.kQzz = kQzz;
     c.Lx = Lx; c.Ly = Ly;
     c.invLx = 1.f / Lx; c.invLy = 1.f / Ly;
     c.rc2 = coul_rc * coul_rc;
@@ -44,17 +48,20 @@ __device__ __forceinline__ void ff_stage_atom(const FFConst& c, float x, float y
     const float eij = sqrtf(eps * c.eps_pp);
     const float rmin = c.core_frac * Rij;
     const float kq = c.kQ * q;
+    const float kqq = c.kQzz * q;
     s0 = make_float4(x, y, rmin * rmin, 0.f);
     s1 = make_float4(-z, -z, Rij * Rij, Rij * Rij);
     s2 = make_float4(12.f * eij, 12.f * eij, kq, kq);
-    s3 = make_float4(eij, eij, 0.f, 0.f);
+    s3 = make_float4(eij, eij, kqq, kqq);
 }
 
-template <int ZP, bool kMinImage, bool kCutoff>
+template <int ZP, bool kMinImage, bool kCutoff, bool kQuad>
 __device__ __forceinline__ void ff_accumulate(const float4* s0, const float4* s1, const float4* s2, const float4* s3,
                                               int cnt, const FFConst& c, float gx, float gy, const float2 (&gz)[ZP],
                                               float2 (&fx)[ZP], float2 (&fy)[ZP], float2 (&fz)[ZP], float2 (&en)[ZP]) {
     const float2 minus1 = make_float2(-1.f, -1.f);
+    const float2 minus3 = make_float2(-3.f, -3.f), minus6 = make_float2(-6.f, -6.f);
+    const float2 three = make_float2(3.f, 3.f), fifteen = make_float2(15.f, 15.f);
 #pragma unroll 1
     for (int a = 0; a < cnt; ++a) {
         const float4 A0 = s0[a], A1 = s1[a], A2 = s2[a], A3 = s3[a];
@@ -68,7 +75,7 @@ __device__ __forceinline__ void ff_accumulate(const float4* s0, const float4* s1
         const float2 RX = make_float2(rx, rx), RY = make_float2(ry, ry), RXY = make_float2(rxy2, rxy2);
         const float2 NZ = make_float2(A1.x, A1.y), R2 = make_float2(A1.z, A1.w);
         const float2 E12 = make_float2(A2.x, A2.y), KQ = make_float2(A2.z, A2.w);
-        const float2 EE = make_float2(A3.x, A3.y);
+        const float2 EE = make_float2(A3.x, A3.y), KQQ = make_float2(A3.z, A3.w);
 #pragma unroll
         for (int t = 0; t < ZP; ++t) {
             const float2 rz = f2add(gz[t], NZ);
@@ -95,9 +102,21 @@ __device__ __forceinline__ void ff_accumulate(const float4* s0, const float4* s1
             } else {
                 f = f2mul(f2fma(E12, lj, eel), ir2);  // (12 e (u6 - u3) + kq / r) / r^2
             }
+            float2 fzf = f;
+            if (kQuad) {
+                float2 c5 = f2mul(KQQ, f2mul(f2mul(ir2, ir2), rs));  // kqq / r^5
+                if (kCutoff) {
+                    c5.x = (r2.x < c.rc2) ? c5.x : 0.f;
+                    c5.y = (r2.y < c.rc2) ? c5.y : 0.f;
+                }
+                const float2 rz2 = f2mul(rz, rz);
+                f = f2fma(c5, f2fma(f2mul(rz2, ir2), fifteen, minus3), f);  // + kqq (15 dz^2/r^2 - 3) / r^5
+                fzf = f2fma(c5, minus6, f);                                 // axial -6 kqq dz / r^5
+                eel = f2fma(c5, f2sub(f2mul(rz2, three), r2), eel);        // + kqq (3 dz^2 - r^2) / r^5
+            }
             fx[t] = f2fma(f, RX, fx[t]);
             fy[t] = f2fma(f, RY, fy[t]);
-            fz[t] = f2fma(f, rz, fz[t]);
+            fz[t] = f2fma(fzf, rz, fz[t]);
             en[t] = f2add(f2fma(EE, f2sub(lj, u3), en[t]), eel);  // e (u6 - 2 u3) + E_el
         }
     }

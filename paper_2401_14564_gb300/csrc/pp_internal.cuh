@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <type_traits>
 
 #include "pp.h"
 
@@ -40,6 +41,21 @@ __host__ __device__ __forceinline__ int node_index(const GridMap& g, int i, int 
     return axis_off(g.ax, i) + axis_off(g.ay, j) + axis_off(g.az, k);
 }
 
+// Calls f(std::bool_constant<a>, std::bool_constant<b>, std::bool_constant<c>)
+// for the runtime flags a, b, c: one place that turns the pair-term options
+// (minimum image, Coulomb cutoff, tip quadrupole) into kernel template arguments.
+template <class F>
+inline auto with_flags(bool a, bool b, bool c, F&& f) {
+    using T = std::true_type;
+    using N = std::false_type;
+    if (a) {
+        if (b) return c ? f(T{}, T{}, T{}) : f(T{}, T{}, N{});
+        return c ? f(T{}, N{}, T{}) : f(T{}, N{}, N{});
+    }
+    if (b) return c ? f(N{}, T{}, T{}) : f(N{}, T{}, N{});
+    return c ? f(N{}, N{}, T{}) : f(N{}, N{}, N{});
+}
+
 // Host-side helpers (api.cu).
 bool make_grid_map(const pp_grid* g, GridMap* out, std::string* why);
 void set_error(const std::string& msg);
@@ -54,6 +70,7 @@ struct FFLaunch {
     const float *x, *y, *z, *R, *eps, *q;
     int n;
     float R_pp, eps_pp, kQ, core_frac, coul_rc;
+    float kQzz;  // k_e Qzz / 2 (0: no tip quadrupole)
     int min_image;
     float Lx, Ly;
     float x0, y0, z0, dx, dy, dz;
@@ -97,6 +114,7 @@ struct BwdLaunch {
     const float *ax, *ay, *az, *aR, *aeps, *aq;
     int n;
     float R_pp, eps_pp, kQ, ke, Q, core_frac, coul_rc;
+    float Qzz, kQzz;  // tip quadrupole and k_e Qzz / 2
     int min_image;
     float Lx, Ly;
     // grid (node positions x0 + i*dx ..., cell coordinate p * inv_d + g0s)
@@ -119,6 +137,7 @@ struct BwdLaunch {
     float *gx, *gy, *gz, *gq, *gR, *geps, *gtip;
     float4* gbar;
     int* slab;
+    float* qsum;  // {sum_i q_i C_i, sum_i q_i Cq_i} when Qzz != 0
 };
 cudaError_t launch_backward(const BwdLaunch& L, cudaStream_t s);
 

@@ -37,7 +37,7 @@ class Atoms(C.Structure):
 
 class Probe(C.Structure):
     _fields_ = [("R_pp", C.c_float), ("eps_pp", C.c_float), ("Q", C.c_float), ("coul_rc", C.c_float),
-                ("min_image", C.c_int), ("core_frac", C.c_float)]
+                ("min_image", C.c_int), ("core_frac", C.c_float), ("Qzz", C.c_float)]
 
 
 class Grid(C.Structure):
@@ -183,7 +183,8 @@ def make_grid(g, layout=0, brick=(4, 4, 4)):
 
 
 def make_probe(p):
-    return Probe(p["R_pp"], p["eps_pp"], p["Q"], p["coul_rc"], int(p["min_image"]), p["core_frac"])
+    return Probe(p["R_pp"], p["eps_pp"], p["Q"], p["coul_rc"], int(p["min_image"]), p["core_frac"],
+                 float(p.get("Qzz", 0.0)))
 
 
 def make_tip(t):
@@ -279,10 +280,10 @@ def pp_backward_workspace(grid: Grid) -> int:
 
 
 def make_grads(g):
-    """g: dict of float32 CUDA tensors x, y, z, q, R, eps (n each) and tip (4)."""
+    """g: dict of float32 CUDA tensors x, y, z, q, R, eps (n each) and tip (5)."""
     n = int(g["x"].numel())
-    if g["tip"].numel() < 4:
-        raise ValueError("tip gradient needs 4 floats")
+    if g["tip"].numel() < 5:
+        raise ValueError("tip gradient needs 5 floats")
     gr = Grads(*[_dev(g[k], k) if n > 0 else 0 for k in ("x", "y", "z", "q", "R", "eps")], _dev(g["tip"], "tip"))
     gr._tensors = dict(g)
     return gr

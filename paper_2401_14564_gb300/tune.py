@@ -27,7 +27,8 @@ ZPTS = (4, 8, 16)
 def _key(case):
     g, s = case["grid"], case["scan"]
     return (f"{torch.cuda.get_device_name()}|grid{g['nx']}x{g['ny']}x{g['nz']}|atoms{len(case['atoms']['x'])}"
-            f"|scan{s['nx']}x{s['ny']}x{s['nz']}|mi{case['probe']['min_image']}|rc{case['probe']['coul_rc']}")
+            f"|scan{s['nx']}x{s['ny']}x{s['nz']}|mi{case['probe']['min_image']}|rc{case['probe']['coul_rc']}"
+            f"|qzz{case['probe'].get('Qzz', 0.0)}")
 
 
 def _time(fn, reps):

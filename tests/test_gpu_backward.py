@@ -29,8 +29,8 @@ def weights(c, seed=7):
     return np.random.default_rng(seed).standard_normal((s["nz"] - 2 * m, s["ny"], s["nx"]))
 
 
-def gpu_backward(c, pos, w, layout=0):
-    """CUDA adjoint at the given relaxed positions, on the CUDA FF grid."""
+def gpu_backward(c, pos, w, layout=0, want_qzz=False):
+    """CUDA adjoint at the given relaxed positions, on the CUDA FF grid (dL/dQzz too if want_qzz)."""
     grid = pp.make_grid(c["grid"], layout)
     atoms_t = afm.atoms_to_device(c["atoms"])
     atoms = pp.make_atoms(atoms_t)
@@ -38,7 +38,7 @@ def gpu_backward(c, pos, w, layout=0):
     pp.pp_make_ff(atoms, pp.make_probe(c["probe"]), grid, ff)
     n = len(c["atoms"]["x"])
     g = {k: torch.full((n,), float("nan"), device="cuda") for k in KEYS}
-    g["tip"] = torch.full((4,), float("nan"), device="cuda")
+    g["tip"] = torch.full((5,), float("nan"), device="cuda")
     ws = torch.empty(pp.pp_backward_workspace(grid) // 4 + 1, dtype=torch.float32, device="cuda")
     pos_t = torch.as_tensor(np.asarray(pos, dtype=np.float32), device="cuda").contiguous()
     w_t = torch.as_tensor(np.asarray(w, dtype=np.float32), device="cuda").contiguous()
@@ -48,6 +48,8 @@ def gpu_backward(c, pos, w, layout=0):
     out = {k: g[k].cpu().numpy().astype(np.float64) for k in KEYS}
     t = g["tip"].cpu().numpy().astype(np.float64)
     out.update({k: t[i] for i, k in enumerate(TIP)})
+    if want_qzz:
+        out["Qzz"] = t[4]
     return out
 
 
@@ -157,7 +159,7 @@ def test_workspace_too_small_is_rejected():
     ws = torch.empty(need // 4 - 4, dtype=torch.float32, device="cuda")
     n = len(c["atoms"]["x"])
     g = {k: torch.empty(n, device="cuda") for k in KEYS}
-    g["tip"] = torch.empty(4, device="cuda")
+    g["tip"] = torch.empty(5, device="cuda")
     at = afm.atoms_to_device(c["atoms"])
     ff = torch.zeros(pp.pp_ff_floats(grid), device="cuda")
     s = c["scan"]

@@ -102,7 +102,7 @@ def test_slab_patch_relaxation_and_adjoint(orc, slab):
     ref = orc.backward(ffw, win, c["atoms"], c["probe"], s, c["tip"], c["df"], pos, w)
     n = len(c["atoms"]["x"])
     g = {k: torch.empty(n, device="cuda") for k in KEYS}
-    g["tip"] = torch.empty(4, device="cuda")
+    g["tip"] = torch.empty(5, device="cuda")
     ws = torch.empty(pp.pp_backward_workspace(sim.grid) // 4 + 1, device="cuda")
     pp.pp_backward(pp.make_atoms(at), sim.probe, sim.grid, sim.ff, sim.scan, sim.tip, sim.dfp,
                    torch.as_tensor(pos, dtype=torch.float32, device="cuda"),

@@ -31,7 +31,7 @@ def setup_case():
 
 def new_grads(n):
     g = {k: torch.full((n,), float("nan"), device="cuda") for k in KEYS}
-    g["tip"] = torch.full((4,), float("nan"), device="cuda")
+    g["tip"] = torch.full((5,), float("nan"), device="cuda")
     return g
 
 
