@@ -49,7 +49,7 @@ class Probe(C.Structure):
 class Grid(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int)] + \
                [(k, C.c_double) for k in ("x0", "y0", "z0", "dx", "dy", "dz")] + [("periodic_xy", C.c_int)] + \
-               [("Lx", C.c_double), ("Ly", C.c_double)]
+               [("Lx", C.c_double), ("Ly", C.c_double), ("interp", C.c_int)]
 
 
 class Tip(C.Structure):
@@ -125,9 +125,10 @@ def _probe(p):
 
 
 def _grid(g):
-    """Grid dict -> struct; optional "Lx", "Ly" set the minimum-image period of a window of a larger grid."""
+    """Grid dict -> struct; optional "Lx", "Ly" set the minimum-image period of a window of a larger grid,
+    optional "interp" = 1 selects tricubic interpolation of the node energies."""
     return Grid(g["nx"], g["ny"], g["nz"], g["x0"], g["y0"], g["z0"], g["dx"], g["dy"], g["dz"], int(g["periodic_xy"]),
-                float(g.get("Lx", 0.0)), float(g.get("Ly", 0.0)))
+                float(g.get("Lx", 0.0)), float(g.get("Ly", 0.0)), int(g.get("interp", 0)))
 
 
 def _tip(t):
@@ -175,8 +176,18 @@ def ff_points(atoms, probe, grid, pts, nthreads=0):
     return out, core.astype(bool)
 
 
+def interp_energy_points(ff, grid, pts):
+    """Tricubic interpolated energy at pts[n][3] (grid["interp"] must be 1)."""
+    ff = _d(ff)
+    pts = _d(pts).reshape(-1, 3)
+    E = np.empty(len(pts))
+    if lib().or_interp_energy_points(_ptr(ff), C.byref(_grid(grid)), len(pts), _ptr(pts), _ptr(E)):
+        raise ValueError("energy interpolation needs a tricubic grid")
+    return E
+
+
 def interp_points(ff, grid, pts):
-    """Trilinear force and its Jacobian dF_a/dp_b at pts[n][3]."""
+    """Interpolated force (trilinear, or -grad of the tricubic energy) and its Jacobian dF_a/dp_b at pts[n][3]."""
     ff = _d(ff)
     pts = _d(pts).reshape(-1, 3)
     F = np.empty((len(pts), 3))

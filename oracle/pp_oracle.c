@@ -22,6 +22,9 @@
  *     linear Fz against the kernel u / sqrt(a^2 - u^2), a = A/2;
  *   - the implicit-function adjoint of all of the above (the paper has no
  *     gradients; this is the derivative of the same discrete model);
+ *   - optionally tricubic interpolation of the grid potential instead of
+ *     trilinear interpolation of the grid forces (Sec. 5.1.1 step 2: the
+ *     paper's suggestion for larger spacings with no stored forces);
  *   - optionally an axial point quadrupole on the probe (Secs. 2.2.3, 2.2.5: the CO
  *     tip's quadrupolar charge distribution) in the field of the sample's
  *     point charges.
@@ -33,6 +36,12 @@
  *   (cell index in [0, nz-2], fraction in [0,1]);
  *   spring constants are given in N/m and converted with 1 eV/A^2 = 16.02176634
  *   N/m; Coulomb constant 14.3996454784 eV*A/e^2;
+ *   tricubic = tensor product of 1D cubic convolution (Catmull-Rom) through
+ *   the node energies: weights of nodes i-1..i+2 at fraction t are
+ *   ((-t^3+2t^2-t), (3t^3-5t^2+2), (-3t^3+4t^2+t), (t^3-t^2)) / 2, i.e. the
+ *   cubic Hermite curve with central-difference slopes; F = -grad E_interp is
+ *   continuous across cell faces.  Periodic in x,y; in z the cell index and
+ *   fraction clamp as for trilinear and stencil nodes clamp into [0, nz-1];
  *   the tip quadrupole Qzz (e*A^2) is the second moment sum_k q_k z_k^2 of an
  *   axial charge distribution with no net charge or dipole, rigidly attached
  *   to the PP (no rotation, Sec. 2.2.3); its energy in the sample potential
@@ -57,8 +66,12 @@
 typedef struct { int n; const double *x, *y, *z, *R, *eps, *q; } or_atoms;
 typedef struct { double R_pp, eps_pp, Q, coul_rc; int min_image; double core_frac; double Qzz; } or_probe;
 /* Lx, Ly: minimum-image period; 0 means the grid's own extent nx*dx, ny*dy
- * (a window of a larger periodic grid passes the full grid's extent). */
-typedef struct { int nx, ny, nz; double x0, y0, z0, dx, dy, dz; int periodic_xy; double Lx, Ly; } or_grid;
+ * (a window of a larger periodic grid passes the full grid's extent).
+ * interp: 0 trilinear interpolation of the node forces, 1 tricubic
+ * interpolation of the node energies with F = -grad of the interpolant. */
+typedef struct {
+    int nx, ny, nz; double x0, y0, z0, dx, dy, dz; int periodic_xy; double Lx, Ly; int interp;
+} or_grid;
 typedef struct { double kx, ky, kR, R0, d0x, d0y; } or_tip; /* springs in N/m */
 typedef struct { int nx, ny, nz; double x0, y0, px, py, z_top, dz; } or_scan;
 typedef struct {
@@ -275,8 +288,15 @@ static void axis_locate(double p, double o, double h, int n, int periodic,
 
 /* Trilinear interpolant of (Fx,Fy,Fz) at p and, optionally, its exact Jacobian
  * J[a*3+b] = dF_a/dp_b and the 8 corner node indices and weights. */
+static void interp_tricubic(const double* ff, const or_grid* G, const double p[3], double* E, double F[3],
+                            double* J);
+
 static void interp(const double* ff, const or_grid* G, const double p[3], double F[3], double* J,
                    long node[8], double w8[8]) {
+    if (G->interp == 1) {  /* no corner list: the grid-mode adjoint is trilinear only */
+        interp_tricubic(ff, G, p, NULL, F, J);
+        return;
+    }
     long ix[2], iy[2], iz[2];
     double tx, ty, tz, gx, gy, gz;
     axis_locate(p[0], G->x0, G->dx, G->nx, G->periodic_xy, &ix[0], &ix[1], &tx, &gx);
@@ -303,9 +323,98 @@ static void interp(const double* ff, const or_grid* G, const double p[3], double
             }
 }
 
+/* Stencil of 4 nodes (i-1 .. i+2) around p along one axis for the tricubic
+ * interpolant, with the fraction t in the cell [i, i+1] and dt/dp (0 where
+ * clamped); same cell and fraction as axis_locate. */
+static void axis_stencil(double p, double o, double h, int n, int periodic, long idx[4], double* t,
+                         double* dtdp) {
+    long i0, i1;
+    axis_locate(p, o, h, n, periodic, &i0, &i1, t, dtdp);
+    for (int q = 0; q < 4; ++q) {
+        long k = i0 - 1 + q;
+        if (periodic) {
+            k %= n;
+            if (k < 0) k += n;
+        } else {
+            if (k < 0) k = 0;
+            if (k > n - 1) k = n - 1;
+        }
+        idx[q] = k;
+    }
+}
+
+/* Catmull-Rom (cubic convolution, a = -1/2) weights of nodes -1, 0, 1, 2 at t,
+ * and their first and second derivatives in t. */
+static void cr_weights(double t, double w[4], double dw[4], double d2w[4]) {
+    const double t2 = t * t, t3 = t2 * t;
+    w[0] = 0.5 * (-t3 + 2.0 * t2 - t);
+    w[1] = 0.5 * (3.0 * t3 - 5.0 * t2 + 2.0);
+    w[2] = 0.5 * (-3.0 * t3 + 4.0 * t2 + t);
+    w[3] = 0.5 * (t3 - t2);
+    dw[0] = 0.5 * (-3.0 * t2 + 4.0 * t - 1.0);
+    dw[1] = 0.5 * (9.0 * t2 - 10.0 * t);
+    dw[2] = 0.5 * (-9.0 * t2 + 8.0 * t + 1.0);
+    dw[3] = 0.5 * (3.0 * t2 - 2.0 * t);
+    d2w[0] = 0.5 * (-6.0 * t + 4.0);
+    d2w[1] = 0.5 * (18.0 * t - 10.0);
+    d2w[2] = 0.5 * (-18.0 * t + 8.0);
+    d2w[3] = 0.5 * (6.0 * t - 2.0);
+}
+
+/* Tricubic interpolant of the node energies ff[g][3] at p: E, F = -grad E and,
+ * optionally, J[a*3+b] = dF_a/dp_b = -d2E/dp_a dp_b. */
+static void interp_tricubic(const double* ff, const or_grid* G, const double p[3], double* E, double F[3],
+                            double* J) {
+    long ix[4], iy[4], iz[4];
+    double tx, ty, tz, sx, sy, sz;
+    axis_stencil(p[0], G->x0, G->dx, G->nx, G->periodic_xy, ix, &tx, &sx);
+    axis_stencil(p[1], G->y0, G->dy, G->ny, G->periodic_xy, iy, &ty, &sy);
+    axis_stencil(p[2], G->z0, G->dz, G->nz, 0, iz, &tz, &sz);
+    double wx[4], dwx[4], d2wx[4], wy[4], dwy[4], d2wy[4], wz[4], dwz[4], d2wz[4];
+    cr_weights(tx, wx, dwx, d2wx);
+    cr_weights(ty, wy, dwy, d2wy);
+    cr_weights(tz, wz, dwz, d2wz);
+    double e = 0.0, g[3] = {0, 0, 0}, H[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int c = 0; c < 4; ++c)
+        for (int b = 0; b < 4; ++b)
+            for (int a = 0; a < 4; ++a) {
+                const double v = ff[4 * ((iz[c] * G->ny + iy[b]) * G->nx + ix[a]) + 3];
+                e += wx[a] * wy[b] * wz[c] * v;
+                g[0] += dwx[a] * wy[b] * wz[c] * v;
+                g[1] += wx[a] * dwy[b] * wz[c] * v;
+                g[2] += wx[a] * wy[b] * dwz[c] * v;
+                if (J) {
+                    H[0] += d2wx[a] * wy[b] * wz[c] * v;
+                    H[4] += wx[a] * d2wy[b] * wz[c] * v;
+                    H[8] += wx[a] * wy[b] * d2wz[c] * v;
+                    H[1] += dwx[a] * dwy[b] * wz[c] * v;
+                    H[2] += dwx[a] * wy[b] * dwz[c] * v;
+                    H[5] += wx[a] * dwy[b] * dwz[c] * v;
+                }
+            }
+    const double s[3] = {sx, sy, sz};
+    if (E) *E = e;
+    for (int m = 0; m < 3; ++m) F[m] = -g[m] * s[m];
+    if (J) {
+        H[3] = H[1];
+        H[6] = H[2];
+        H[7] = H[5];
+        for (int m = 0; m < 3; ++m)
+            for (int n = 0; n < 3; ++n) J[m * 3 + n] = -H[m * 3 + n] * s[m] * s[n];
+    }
+}
+
 int or_interp_points(const double* ff, const or_grid* G, int npts, const double* pts,
                      double* F, double* J) {
     for (int t = 0; t < npts; ++t) interp(ff, G, pts + 3 * t, F + 3 * t, J ? J + 9 * t : NULL, NULL, NULL);
+    return 0;
+}
+
+/* Interpolated energy at pts: tricubic grids only (trilinear grids interpolate forces). */
+int or_interp_energy_points(const double* ff, const or_grid* G, int npts, const double* pts, double* E) {
+    if (G->interp != 1) return 1;
+    double F[3];
+    for (int t = 0; t < npts; ++t) interp_tricubic(ff, G, pts + 3 * t, E + t, F, NULL);
     return 0;
 }
 
@@ -703,6 +812,7 @@ int or_backward(const double* ff, const or_grid* G, const or_atoms* A, const or_
                 const double* g_df, double* grads /*[n][6]*/, double* gtip, double* grid_adj,
                 int nthreads) {
     if (!G || !A || !P || !S || !T || !D || !pos || !g_df || !grads || !gtip) return 1;
+    if (ff && G->interp == 1) return 2;  /* grid-mode adjoint: trilinear force grids only */
     set_threads(nthreads);
     or_model M;
     M.ff = ff; M.G = G; M.A = A; M.P = P;
