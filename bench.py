@@ -298,6 +298,49 @@ def measure_quadrupole(case, tuning, steps, warmup, flush, alu_peak):
             "ff_traffic": measured_traffic("ff_assemble_quad")}
 
 
+def measure_tricubic(case, steps, warmup, flush):
+    """The line's workload on tricubic energy grids (one float per node, F = -grad of the tricubic
+    interpolant): at the same 0.1 A spacing and at 0.2 A (8x fewer nodes); FF and relaxed scan
+    (fused df) times by CUDA events, L2 flushed, grid bytes."""
+    import torch
+
+    from paper_2401_14564_gb300 import afm
+
+    out = []
+    g0 = case["grid"]
+    for h in (0.1, 0.2):
+        f = round(h / g0["dx"])
+        g = dict(g0, nx=g0["nx"] // f, ny=g0["ny"] // f, nz=(g0["nz"] - 1) // f + 1, dx=h, dy=h, dz=h, interp=1)
+        tcase = dict(case, grid=g)
+        sim = afm.Simulator(tcase)
+        atoms = afm.atoms_to_device(tcase["atoms"])
+        for _ in range(max(warmup, 3)):
+            sim.run(atoms)
+        stream = torch.cuda.current_stream()
+        t_ff, t_rx = [], []
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+            sim.make_ff(atoms)
+            e1.record(stream)
+            sim.relax()
+            e2.record(stream)
+            torch.cuda.synchronize()
+            t_ff.append(e0.elapsed_time(e1))
+            t_rx.append(e1.elapsed_time(e2))
+        s = tcase["scan"]
+        ff_ms, rx_ms = statistics.mean(t_ff), statistics.mean(t_rx)
+        pairs = g["nx"] * g["ny"] * g["nz"] * len(tcase["atoms"]["x"])
+        out.append({"spacing": h, "grid": [g["nx"], g["ny"], g["nz"]], "grid_bytes": g["nx"] * g["ny"] * g["nz"] * 4,
+                    "ff_ms": ff_ms, "relax_ms": rx_ms, "ms_per_step": ff_ms + rx_ms,
+                    "pixel_z_per_s": s["nx"] * s["ny"] * s["nz"] / ((ff_ms + rx_ms) * 1e-3),
+                    "ff_pair_evals_per_s": pairs / (ff_ms * 1e-3),
+                    "fire_iters_mean": float(sim.iters.float().mean().item())})
+        del sim
+    return out
+
+
 def measure_batch(n_mol, steps, warmup, flush, seq_sample=64):
     """Batched molecules/s: pp_batch_run over n_mol seeded molecules replayed from a CUDA graph,
     beside the same molecules run one by one through pp_make_ff + pp_relax_scan."""
@@ -362,6 +405,7 @@ def main():
     ap.add_argument("--no-bwdfwd", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-quad", action="store_true")
+    ap.add_argument("--no-tricubic", action="store_true")
     ap.add_argument("--zpt", type=int, default=0, help="FF z-nodes per thread (skips the autotuner)")
     ap.add_argument("--brick", default="", help="bricked layout bx,by,bz for the scan (skips the autotuner)")
     ap.add_argument("--batch-mol", type=int, default=1024)
@@ -485,6 +529,8 @@ def main():
                             g4["grid"]["nx"], g4["grid"]["ny"], g4["grid"]["nz"])),
         measure_bwd_fwd(case, max(3, args.steps // 2), args.warmup, flush, "flake60 (this line's workload)"),
     ]
+    if not args.no_tricubic:
+        line["tricubic"] = measure_tricubic(case, max(3, args.steps // 2), args.warmup, flush)
     if not args.no_quad:
         line["quadrupole"] = measure_quadrupole(case, tuning, max(3, args.steps // 2), args.warmup, flush, alu_peak)
     if not args.no_slab:

@@ -94,12 +94,21 @@ typedef struct {
 /* Regular force-field grid: node (i,j,k) sits at (x0+i*dx, y0+j*dy, z0+k*dz).
  * Interpolation wraps i,j periodically when periodic_xy = 1, else clamps; it
  * always clamps in z (cell index in [0, nz-2], fraction in [0,1]).
- * layout 0: node (i,j,k) at float4 index (k*ny + j)*nx + i.
+ * layout 0: node (i,j,k) at index (k*ny + j)*nx + i.
  * layout 1: bricks of bx*by*bz nodes (each a power of two, 1..16), bricks in
  *           x-fastest order, nodes x-fastest inside a brick; dimensions are
  *           padded up to whole bricks.  pp_ff_floats() gives the size.
- * Every node holds 4 floats (Fx, Fy, Fz, E) in eV/A and eV; the buffer must be
- * 16-byte aligned. */
+ * interp 0: every node holds 4 floats (Fx, Fy, Fz, E) in eV/A and eV and the
+ *           scan interpolates the forces trilinearly (Sec. 5.1.1 step 2).
+ * interp 1: every node holds the energy E only (eV), layout 0; the scan
+ *           interpolates E tricubically (the paper's suggestion for larger
+ *           spacings without stored forces) and takes F = -grad of the
+ *           interpolant: along each axis the cubic convolution (Catmull-Rom)
+ *           weights of nodes i-1..i+2 at fraction t,
+ *           ((-t^3+2t^2-t), (3t^3-5t^2+2), (-3t^3+4t^2+t), (t^3-t^2)) / 2,
+ *           stencil nodes wrapping like the cell (periodic) or clamped into
+ *           the grid (z, and x,y when not periodic).
+ * The buffer must be 16-byte aligned. */
 typedef struct {
     int nx, ny, nz;
     float x0, y0, z0;
@@ -107,6 +116,7 @@ typedef struct {
     int periodic_xy;
     int layout;
     int bx, by, bz;
+    int interp;  /* 0 trilinear forces, 1 tricubic energy */
 } pp_grid;
 
 /* Tip springs of Eq. F_tip, with d = r_PP - r_TIP and
@@ -146,7 +156,7 @@ typedef struct {
 } pp_df;
 
 /* Number of floats of a force-field buffer for `grid` (4 per stored node,
- * brick padding included); 0 if the grid is invalid. */
+ * brick padding included; 1 per node for interp = 1); 0 if the grid is invalid. */
 PP_API size_t pp_ff_floats(const pp_grid* grid);
 
 /* Half-width in samples of the df stencil: m = ceil(A_pp/2 / dz).  A scan of
@@ -157,7 +167,8 @@ PP_API int pp_df_margin(float A_pp, float dz);
 /* FF grid assembly (Sec. 5.1.1 step 1; Eqs. LJ and point charges; Sec. 2.2).
  * Writes all nodes of `ff` (pp_ff_floats(grid) floats, padding nodes
  * included) with (Fx, Fy, Fz, E) = sum over atoms of the pair force and
- * energy at the node.  atoms->n may be 0 (all zeros).  Errors: PP_ERR_ARG
+ * energy at the node, or E alone when grid->interp = 1 (then the launch
+ * shape is fixed and tuning is ignored).  atoms->n may be 0 (all zeros).  Errors: PP_ERR_ARG
  * (NULL, core_frac outside (0,1), negative eps), PP_ERR_SHAPE (nx, ny, nz < 2,
  * spacing <= 0, brick not a power of two), PP_ERR_CUDA. */
 PP_API pp_status pp_make_ff(const pp_atoms* atoms, const pp_probe* probe, const pp_grid* grid,
@@ -176,6 +187,8 @@ PP_API pp_status pp_make_ff_tuned(const pp_atoms* atoms, const pp_probe* probe, 
                                   float* ff, const pp_tuning* tuning, pp_stream stream);
 
 /* Relaxed tip scan (Sec. 5.1.1 step 2; Eqs. F_PP, F_tip; Sec. 2.1 readout).
+ * F_S comes from the grid by trilinear force interpolation, or by the
+ * gradient of the tricubic energy interpolant when grid->interp = 1.
  * One thread per pixel walks the heights k = 0..nz-1: start p = anchor + d0
  * at k = 0 and p = p*(k-1) - dz z_hat after that, relax by FIRE, write
  *   pos[((k*ny + j)*nx + i)*3 + c]  relaxed PP position (nullable),
@@ -204,7 +217,8 @@ PP_API pp_status pp_fz_to_df(const float* fz, int nz, int npix, float dz, const 
 /* Layout conversion of a force-field buffer: src laid out as `src_grid`,
  * dst as `dst_grid`; the two must describe the same nodes (nx, ny, nz) and
  * may differ in layout and brick shape.  Padding nodes of dst are zeroed.
- * Errors: PP_ERR_ARG, PP_ERR_SHAPE, PP_ERR_CUDA. */
+ * Errors: PP_ERR_ARG, PP_ERR_SHAPE, PP_ERR_UNSUPPORTED (interp = 1 grids),
+ * PP_ERR_CUDA. */
 PP_API pp_status pp_ff_convert(const float* src, const pp_grid* src_grid, float* dst,
                         const pp_grid* dst_grid, pp_stream stream);
 
@@ -305,7 +319,7 @@ PP_API size_t pp_backward_workspace(const pp_grid* grid);
  * aligned, >= pp_backward_workspace(grid) bytes) is overwritten; FP32
  * atomics make the sums order-dependent at rounding level.  Errors:
  * PP_ERR_ARG, PP_ERR_SHAPE, PP_ERR_CAPACITY (ws too small), PP_ERR_UNSUPPORTED
- * (df stencil wider than 63 taps), PP_ERR_CUDA. */
+ * (df stencil wider than 63 taps, or an interp = 1 grid), PP_ERR_CUDA. */
 PP_API pp_status pp_backward(const pp_atoms* atoms, const pp_probe* probe, const pp_grid* grid,
                              const float* ff, const pp_scan* scan, const pp_tip* tip,
                              const pp_df* df_params, const float* pos, const float* g_df,
@@ -343,7 +357,7 @@ PP_API size_t pp_backward_noalloc_capacity(void);
  * hw is not NULL, the mode energies hbar sqrt(lambda/m) in meV (0 where
  * lambda <= 0) for a probe mass of mass_amu atomic mass units.  The two
  * lower eigenvalues are the lateral modes the IETS signal follows.  Errors:
- * PP_ERR_ARG, PP_ERR_SHAPE, PP_ERR_CUDA. */
+ * PP_ERR_ARG, PP_ERR_SHAPE, PP_ERR_UNSUPPORTED (interp = 1 grid), PP_ERR_CUDA. */
 PP_API pp_status pp_iets(const float* ff, const pp_grid* grid, const pp_scan* scan, const pp_tip* tip,
                          const float* pos, float mass_amu, float* eig, float* hw, pp_stream stream);
 

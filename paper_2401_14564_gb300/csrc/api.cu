@@ -33,8 +33,11 @@ bool make_grid_map(const pp_grid* g, GridMap* out, std::string* why) {
     if (!finite_pos(g->dx) || !finite_pos(g->dy) || !finite_pos(g->dz)) { *why = "grid spacing must be > 0"; return false; }
     if (!isfinite(g->x0) || !isfinite(g->y0) || !isfinite(g->z0)) { *why = "grid origin must be finite"; return false; }
     if (g->periodic_xy != 0 && g->periodic_xy != 1) { *why = "periodic_xy must be 0 or 1"; return false; }
+    if (g->interp != 0 && g->interp != 1) { *why = "interp must be 0 (trilinear) or 1 (tricubic)"; return false; }
+    if (g->interp == 1 && g->layout != 0) { *why = "tricubic (energy) grids use the linear layout"; return false; }
     GridMap m;
     m.nx = g->nx; m.ny = g->ny; m.nz = g->nz;
+    m.interp = g->interp;
     if (g->layout == 0) {
         const int64_t n = (int64_t)g->nx * g->ny * g->nz;
         if (n >= (int64_t(1) << 31)) { *why = "grid has 2^31 or more nodes"; return false; }
@@ -115,7 +118,7 @@ size_t pp_ff_floats(const pp_grid* grid) {
     GridMap m;
     std::string why;
     if (!make_grid_map(grid, &m, &why)) return 0;
-    return (size_t)m.stored_nodes * 4;
+    return (size_t)m.stored_nodes * (m.interp ? 1 : 4);
 }
 
 int pp_df_margin(float A_pp, float dz) { return df_half_width(A_pp, dz); }
@@ -169,7 +172,8 @@ pp_status pp_make_ff_tuned(const pp_atoms* atoms, const pp_probe* probe, const p
     L.x0 = grid->x0; L.y0 = grid->y0; L.z0 = grid->z0;
     L.dx = grid->dx; L.dy = grid->dy; L.dz = grid->dz;
     L.map = map;
-    L.ff = reinterpret_cast<float4*>(ff);
+    L.ff = map.interp ? nullptr : reinterpret_cast<float4*>(ff);
+    L.ffE = map.interp ? ff : nullptr;
     L.zpt = zpt;
     return cuda_status(launch_ff_assemble(L, s), "pp_make_ff launch");
 }
@@ -212,7 +216,8 @@ pp_status pp_relax_scan(const float* ff, const pp_grid* grid, const pp_scan* sca
     if (!check_tip_fire(tip, fire, &why)) { set_error("pp_relax_scan: " + why); return PP_ERR_ARG; }
     RelaxLaunch L;
     std::memset(&L, 0, sizeof(L));
-    L.ff = reinterpret_cast<const float4*>(ff);
+    L.ff = map.interp ? nullptr : reinterpret_cast<const float4*>(ff);
+    L.ffE = map.interp ? ff : nullptr;
     L.map = map;
     L.inv_dx = 1.f / grid->dx; L.inv_dy = 1.f / grid->dy; L.inv_dz = 1.f / grid->dz;
     L.gx0s = (float)(-(double)grid->x0 / grid->dx);
@@ -302,6 +307,7 @@ pp_status pp_backward(const pp_atoms* atoms, const pp_probe* probe, const pp_gri
     GridMap map;
     std::string why;
     if (!make_grid_map(grid, &map, &why)) { set_error("pp_backward: " + why); return PP_ERR_SHAPE; }
+    if (map.interp) { set_error("pp_backward: tricubic (energy) grids are not supported"); return PP_ERR_UNSUPPORTED; }
     if (scan->nx < 1 || scan->ny < 1 || scan->nz < 1 ||
         (int64_t)scan->nx * scan->ny * scan->nz * 3 >= (int64_t(1) << 31)) {
         set_error("pp_backward: invalid scan size");
@@ -439,6 +445,7 @@ pp_status pp_iets(const float* ff, const pp_grid* grid, const pp_scan* scan, con
     GridMap map;
     std::string why;
     if (!make_grid_map(grid, &map, &why)) { set_error("pp_iets: " + why); return PP_ERR_SHAPE; }
+    if (map.interp) { set_error("pp_iets: tricubic (energy) grids are not supported"); return PP_ERR_UNSUPPORTED; }
     if (scan->nx < 1 || scan->ny < 1 || scan->nz < 1 ||
         (int64_t)scan->nx * scan->ny * scan->nz * 3 >= (int64_t(1) << 31)) {
         set_error("pp_iets: invalid scan size");
@@ -482,6 +489,7 @@ pp_status pp_ff_convert(const float* src, const pp_grid* src_grid, float* dst, c
         set_error("pp_ff_convert: " + why);
         return PP_ERR_SHAPE;
     }
+    if (sm.interp || dm.interp) { set_error("pp_ff_convert: tricubic (energy) grids are not supported"); return PP_ERR_UNSUPPORTED; }
     if (sm.nx != dm.nx || sm.ny != dm.ny || sm.nz != dm.nz) { set_error("pp_ff_convert: node counts differ"); return PP_ERR_SHAPE; }
     cudaStream_t s = (cudaStream_t)stream;
     if (dm.stored_nodes > (int64_t)dm.nx * dm.ny * dm.nz) {

@@ -31,7 +31,9 @@ constexpr int kTileY = 8;    // columns per CTA along y (two warps of 4)
 constexpr int kThreads = kTileX * kTileY;
 constexpr int kChunk = 256;  // atoms staged per pass
 
-template <int ZPT, bool kMinImage, bool kCutoff, bool kQuad>
+// kEnergy: write E alone, one float per node (tricubic grids); the force sums
+// are then never formed (the compiler drops them with their stores).
+template <int ZPT, bool kMinImage, bool kCutoff, bool kQuad, bool kEnergy = false>
 __global__ void __launch_bounds__(kThreads) ff_assemble_kernel(const FFLaunch P) {
     static_assert(ZPT % 2 == 0, "z-nodes come in packed pairs");
     constexpr int ZP = ZPT / 2;
@@ -68,12 +70,21 @@ __global__ void __launch_bounds__(kThreads) ff_assemble_kernel(const FFLaunch P)
 
     if (i >= P.map.nx || j >= P.map.ny) return;
     const int base_xy = axis_off(P.map.ax, i) + axis_off(P.map.ay, j);
+    if constexpr (kEnergy) {
 #pragma unroll
-    for (int t = 0; t < ZP; ++t) {
-        const int k = k0 + 2 * t;
-        if (k < P.map.nz) P.ff[base_xy + axis_off(P.map.az, k)] = make_float4(fx[t].x, fy[t].x, fz[t].x, en[t].x);
-        if (k + 1 < P.map.nz)
-            P.ff[base_xy + axis_off(P.map.az, k + 1)] = make_float4(fx[t].y, fy[t].y, fz[t].y, en[t].y);
+        for (int t = 0; t < ZP; ++t) {
+            const int k = k0 + 2 * t;
+            if (k < P.map.nz) P.ffE[base_xy + axis_off(P.map.az, k)] = en[t].x;
+            if (k + 1 < P.map.nz) P.ffE[base_xy + axis_off(P.map.az, k + 1)] = en[t].y;
+        }
+    } else {
+#pragma unroll
+        for (int t = 0; t < ZP; ++t) {
+            const int k = k0 + 2 * t;
+            if (k < P.map.nz) P.ff[base_xy + axis_off(P.map.az, k)] = make_float4(fx[t].x, fy[t].x, fz[t].x, en[t].x);
+            if (k + 1 < P.map.nz)
+                P.ff[base_xy + axis_off(P.map.az, k + 1)] = make_float4(fx[t].y, fy[t].y, fz[t].y, en[t].y);
+        }
     }
 }
 
@@ -92,6 +103,16 @@ cudaError_t launch_zpt(const FFLaunch& L, cudaStream_t s) {
 
 cudaError_t launch_ff_assemble(const FFLaunch& L, cudaStream_t s) {
     if (L.map.nx <= 0 || L.map.ny <= 0 || L.map.nz <= 0) return cudaSuccess;
+    if (L.map.interp == 1) {
+        constexpr int ZPT = 8;
+        dim3 grid((L.map.nx + kTileX - 1) / kTileX, (L.map.ny + kTileY - 1) / kTileY, (L.map.nz + ZPT - 1) / ZPT);
+        with_flags(L.min_image != 0, L.coul_rc > 0.f, L.kQzz != 0.f, [&](auto mi, auto cut, auto quad) {
+            ff_assemble_kernel<ZPT, decltype(mi)::value, decltype(cut)::value, decltype(quad)::value, true>
+                <<<grid, kThreads, 0, s>>>(L);
+            return 0;
+        });
+        return cudaGetLastError();
+    }
     if (L.zpt == 4) return launch_zpt<4>(L, s);
     if (L.zpt == 16) return launch_zpt<16>(L, s);
     return launch_zpt<8>(L, s);

@@ -63,7 +63,7 @@ __device__ __forceinline__ Cell axis_cell(float f, int n, int periodic) {
     Cell c;
     c.i0 = __float2int_rd(f);  // floor, saturating (NaN -> 0)
     c.i1 = c.i0 + 1;
-    c.t = f - (float)c.i0;
+    c.t = f - floorf(f);       // = f - (float)i0 in range, one conversion shorter
     c.dtdf = 1.f;
     if ((unsigned)c.i0 > (unsigned)(n - 2)) {
         if (periodic) {
@@ -146,6 +146,82 @@ __device__ __forceinline__ float3 sample_force(const L& P, float px, float py, f
     float4 v[8];
     load_corners<LAYOUT>(P.ff, P.map, c, v);
     return trilinear(v, c);
+}
+
+// ---- tricubic interpolation of the node energies (grids with interp = 1)
+
+// Cubic convolution (Catmull-Rom) weights of nodes i-1..i+2 at fraction t and
+// their derivatives in t:
+//   w = ((-t^3+2t^2-t), (3t^3-5t^2+2), (-3t^3+4t^2+t), (t^3-t^2)) / 2.
+__device__ __forceinline__ void cr_weights(float t, float w[4], float dw[4]) {
+    const float t2 = t * t, tm = t - 1.f;
+    w[0] = -0.5f * t * tm * tm;
+    w[1] = fmaf(t2, fmaf(1.5f, t, -2.5f), 1.f);
+    w[2] = t * fmaf(t, fmaf(-1.5f, t, 2.f), 0.5f);
+    w[3] = 0.5f * t2 * tm;
+    dw[0] = fmaf(t, fmaf(-1.5f, t, 2.f), -0.5f);
+    dw[1] = t * fmaf(4.5f, t, -5.f);
+    dw[2] = fmaf(t, fmaf(-4.5f, t, 4.f), 0.5f);
+    dw[3] = t * fmaf(1.5f, t, -1.f);
+}
+
+// Offsets of the 4 stencil nodes i0-1, i0, i1, i1+1 along one axis: they
+// wrap like the cell on a periodic axis and clamp into [0, n-1] otherwise.
+__device__ __forceinline__ void stencil4(const Cell& c, int n, bool periodic, int mul, int off[4]) {
+    int im = c.i0 - 1, ip = c.i1 + 1;
+    if (periodic) {
+        im = c.i0 == 0 ? n - 1 : im;
+        ip = c.i1 == n - 1 ? 0 : ip;
+    } else {
+        im = max(im, 0);
+        ip = min(ip, n - 1);
+    }
+    off[0] = im * mul;
+    off[1] = c.i0 * mul;
+    off[2] = c.i1 * mul;
+    off[3] = ip * mul;
+}
+
+// F = -grad E of the tricubic interpolant of the node energies E (linear
+// layout) at the located point: the 64 stencil values are contracted along x
+// into (value, x-derivative) pairs, then along y and z, two sums per packed
+// instruction.  Where a fraction is clamped (outside the grid in z, or x,y
+// without periodicity) that derivative is zero, as for trilinear.
+__device__ __forceinline__ float3 tricubic_force(const float* __restrict__ E, const GridMap& m, const Cells& c,
+                                                 float inv_dx, float inv_dy, float inv_dz, int periodic) {
+    int xo[4], yo[4], zo[4];
+    stencil4(c.x, m.nx, periodic != 0, 1, xo);
+    stencil4(c.y, m.ny, periodic != 0, m.ay.mul, yo);
+    stencil4(c.z, m.nz, false, m.az.mul, zo);
+    float wx[4], dwx[4], wy[4], dwy[4], wz[4], dwz[4];
+    cr_weights(c.x.t, wx, dwx);
+    cr_weights(c.y.t, wy, dwy);
+    cr_weights(c.z.t, wz, dwz);
+    float2 WX[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) WX[a] = make_float2(wx[a], dwx[a]);
+    float2 gzx = make_float2(0.f, 0.f);  // (d/dz, d/dx) sums
+    float gy = 0.f;
+#pragma unroll
+    for (int cz = 0; cz < 4; ++cz) {
+        float2 s02 = make_float2(0.f, 0.f);  // (sum_b wy R0, sum_b wy R1)
+        float s1 = 0.f;                      // sum_b dwy R0
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const float* row = E + zo[cz] + yo[b];
+            const float e0 = __ldg(row + xo[0]), e1 = __ldg(row + xo[1]);
+            const float e2 = __ldg(row + xo[2]), e3 = __ldg(row + xo[3]);
+            float2 r = f2mul(WX[0], make_float2(e0, e0));  // (R0, R1) = sum_a (wx, dwx) e_a
+            r = f2fma(WX[1], make_float2(e1, e1), r);
+            r = f2fma(WX[2], make_float2(e2, e2), r);
+            r = f2fma(WX[3], make_float2(e3, e3), r);
+            s02 = f2fma(make_float2(wy[b], wy[b]), r, s02);
+            s1 = fmaf(dwy[b], r.x, s1);
+        }
+        gzx = f2fma(make_float2(dwz[cz], wz[cz]), s02, gzx);
+        gy = fmaf(wz[cz], s1, gy);
+    }
+    return make_float3(-gzx.y * (c.x.dtdf * inv_dx), -gy * (c.y.dtdf * inv_dy), -gzx.x * (c.z.dtdf * inv_dz));
 }
 
 // Trilinear weights of the 8 corners (same order as corner_index).

@@ -30,7 +30,8 @@ struct AxisMap {
 struct GridMap {
     AxisMap ax, ay, az;
     int nx, ny, nz;
-    int64_t stored_nodes;  // float4 slots including brick padding
+    int64_t stored_nodes;  // node slots including brick padding
+    int interp;            // 0: float4 (Fx, Fy, Fz, E) per node; 1: E per node (tricubic)
 };
 
 __host__ __device__ __forceinline__ int axis_off(const AxisMap& a, int v) {
@@ -75,13 +76,15 @@ struct FFLaunch {
     float Lx, Ly;
     float x0, y0, z0, dx, dy, dz;
     GridMap map;
-    float4* ff;
+    float4* ff;   // map.interp == 0
+    float* ffE;   // map.interp == 1: energies only
     int zpt;  // z-nodes per thread: 4, 8 or 16
 };
 cudaError_t launch_ff_assemble(const FFLaunch& L, cudaStream_t s);
 
 struct RelaxLaunch {
-    const float4* ff;
+    const float4* ff;   // map.interp == 0
+    const float* ffE;   // map.interp == 1
     GridMap map;
     float gx0s, gy0s, gz0s, inv_dx, inv_dy, inv_dz;  // cell coordinate f = p * inv_d + g0s, g0s = -origin/d
     int periodic_xy;

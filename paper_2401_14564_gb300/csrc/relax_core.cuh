@@ -41,8 +41,10 @@ __device__ __forceinline__ float3 total_force_tip(const Q_t& P, float3 e, float 
 // heights, FIRE per height, outputs, and the fused df epilogue.  All 32 lanes
 // of the warp must call it (the FIRE loop ends on a warp vote).  kCoherent
 // selects plain cached loads of the force field instead of the read-only
-// path, for grids written earlier in the same kernel.
-template <int LAYOUT, bool kCoherent, class G_t, class Q_t>
+// path, for grids written earlier in the same kernel.  kTricubic takes F_S
+// from the tricubic energy grid P.ffE (linear layout) instead of the
+// trilinear force grid.
+template <int LAYOUT, bool kCoherent, bool kTricubic = false, class G_t, class Q_t>
 __device__ __forceinline__ void relax_pixel(const G_t& P, const Q_t& Q, int i, int j) {
     const bool valid = (i < P.snx) && (j < P.sny);
     const int npix = P.snx * P.sny;
@@ -65,13 +67,18 @@ __device__ __forceinline__ void relax_pixel(const G_t& P, const Q_t& Q, int i, i
         const float az = P.z_top - k * Q.sdz;
         const float s = radial_factor(Q, e);
         const Cells cl = locate(P, bx + e.x, by + e.y, (az + Q.d0z) + e.z);
-        if (cl.x.i0 != cell_x || cl.y.i0 != cell_y || cl.z.i0 != cell_z) {
-            load_corners<LAYOUT, kCoherent>(P.ff, P.map, cl, cv);
-            cell_x = cl.x.i0;
-            cell_y = cl.y.i0;
-            cell_z = cl.z.i0;
+        float3 Fs;
+        if constexpr (kTricubic) {
+            Fs = tricubic_force(P.ffE, P.map, cl, P.inv_dx, P.inv_dy, P.inv_dz, P.periodic_xy);
+        } else {
+            if (cl.x.i0 != cell_x || cl.y.i0 != cell_y || cl.z.i0 != cell_z) {
+                load_corners<LAYOUT, kCoherent>(P.ff, P.map, cl, cv);
+                cell_x = cl.x.i0;
+                cell_y = cl.y.i0;
+                cell_z = cl.z.i0;
+            }
+            Fs = trilinear(cv, cl);
         }
-        const float3 Fs = trilinear(cv, cl);
         const float3 G = total_force_tip(Q, e, s, Fs);
         const float g2 = fmaf(G.x, G.x, fmaf(G.y, G.y, G.z * G.z));
         if (g2 < Q.ftol2 || it >= Q.max_iter) {

@@ -29,16 +29,66 @@ constexpr int kThreads = 32;  // one warp per CTA: an 8x4 pixel tile (evens out 
 constexpr int kTileX = 8;
 constexpr int kTileY = 4;
 
+// Node range [lo, hi] (clamped to the grid) covering coordinates a..b along one axis.
+__device__ __forceinline__ int2 node_range(float a, float b, float inv_d, float g0s, int n) {
+    const float fa = fmaf(fminf(a, b), inv_d, g0s), fb = fmaf(fmaxf(a, b), inv_d, g0s);
+    const int lo = min(max(__float2int_rd(fa), 0), n - 1);
+    const int hi = min(max(__float2int_rd(fb) + 1, 0), n - 1);
+    return make_int2(lo, hi);
+}
+
+// Linear layout: ask L2 for the grid rows under this warp's 8x4 tile over the
+// z-range its PPs will visit (anchor heights + d0, 0.5 A margin), so that the
+// scan's first touches of the slab are served in parallel at the start instead
+// of one demand miss at a time inside the FIRE loops.  Rows are contiguous in
+// x; each lane issues a bulk prefetch (a hint: it never faults and changes no
+// result) for every 32nd row.  Lateral deflections reach the neighbouring
+// tiles' rows, which those warps prefetch.
+__device__ __forceinline__ void prefetch_tile_slab(const RelaxLaunch& P, int tx, int ty, int lane) {
+    const int ia = tx * kTileX, ib = min(ia + kTileX, P.snx) - 1;
+    const int ja = ty * kTileY, jb = min(ja + kTileY, P.sny) - 1;
+    const int2 ri = node_range(fmaf((float)ia, P.spx, P.sx0) + P.d0x, fmaf((float)ib, P.spx, P.sx0) + P.d0x,
+                               P.inv_dx, P.gx0s, P.map.nx);
+    const int2 rj = node_range(fmaf((float)ja, P.spy, P.sy0) + P.d0y, fmaf((float)jb, P.spy, P.sy0) + P.d0y,
+                               P.inv_dy, P.gy0s, P.map.ny);
+    const float ztop = P.z_top + P.d0z, zbot = P.z_top - (P.snz - 1) * P.sdz + P.d0z;
+    const int2 rk = node_range(fminf(ztop, zbot) - 0.5f, fmaxf(ztop, zbot) + 0.5f, P.inv_dz, P.gz0s, P.map.nz);
+    const int nj = rj.y - rj.x + 1, rows = nj * (rk.y - rk.x + 1);
+    for (int r = lane; r < rows; r += kThreads) {
+        const int j = rj.x + r % nj, k = rk.x + r / nj;
+        const int first = node_index(P.map, ri.x, j, k);
+        if (P.map.interp == 0) {
+            const unsigned bytes = (unsigned)(ri.y - ri.x + 1) * 16u;
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(P.ff + first), "r"(bytes) : "memory");
+        } else {
+            // one float per node: the whole 16-byte groups inside the row (one node wider
+            // on the left for the tricubic stencil); up to 3 nodes at the right end are left out
+            const int lo = max(first - 1, 0) & ~3, hi = (first + (ri.y - ri.x) + 1) & ~3;
+            if (hi > lo)
+                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(P.ffE + lo), "r"((unsigned)(hi - lo) * 4u)
+                             : "memory");
+        }
+    }
+}
+
 template <int LAYOUT>
 __global__ void __launch_bounds__(kThreads) relax_scan_kernel(const RelaxLaunch P) {
+    if (LAYOUT == 0) prefetch_tile_slab(P, blockIdx.x, blockIdx.y, threadIdx.x);
     relax_pixel<LAYOUT, false>(P, P, blockIdx.x * kTileX + (threadIdx.x & 7), blockIdx.y * kTileY + (threadIdx.x >> 3));
+}
+
+// Tricubic energy grid (linear layout).
+__global__ void __launch_bounds__(kThreads) relax_scan_tricubic_kernel(const RelaxLaunch P) {
+    prefetch_tile_slab(P, blockIdx.x, blockIdx.y, threadIdx.x);
+    relax_pixel<0, false, true>(P, P, blockIdx.x * kTileX + (threadIdx.x & 7), blockIdx.y * kTileY + (threadIdx.x >> 3));
 }
 
 }  // namespace
 
 cudaError_t launch_relax_scan(const RelaxLaunch& L, cudaStream_t s) {
     dim3 grid((L.snx + kTileX - 1) / kTileX, (L.sny + kTileY - 1) / kTileY, 1);
-    if (L.layout == 0) relax_scan_kernel<0><<<grid, kThreads, 0, s>>>(L);
+    if (L.map.interp == 1) relax_scan_tricubic_kernel<<<grid, kThreads, 0, s>>>(L);
+    else if (L.layout == 0) relax_scan_kernel<0><<<grid, kThreads, 0, s>>>(L);
     else relax_scan_kernel<1><<<grid, kThreads, 0, s>>>(L);
     return cudaGetLastError();
 }

@@ -43,7 +43,7 @@ class Probe(C.Structure):
 class Grid(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int)] + \
                [(k, C.c_float) for k in ("x0", "y0", "z0", "dx", "dy", "dz")] + \
-               [(k, C.c_int) for k in ("periodic_xy", "layout", "bx", "by", "bz")]
+               [(k, C.c_int) for k in ("periodic_xy", "layout", "bx", "by", "bz", "interp")]
 
 
 class Tip(C.Structure):
@@ -178,8 +178,11 @@ def _dev(t, name, dtype=torch.float32, allow_none=False):
 # ----------------------------------------------------------------- structs
 
 def make_grid(g, layout=0, brick=(4, 4, 4)):
+    """Grid dict -> pp_grid; g["interp"] = 1 (optional) selects a tricubic energy grid (linear layout)."""
+    interp = int(g.get("interp", 0))
     return Grid(int(g["nx"]), int(g["ny"]), int(g["nz"]), g["x0"], g["y0"], g["z0"], g["dx"], g["dy"], g["dz"],
-                int(g["periodic_xy"]), int(g.get("layout", layout)), *[int(b) for b in g.get("brick", brick)])
+                int(g["periodic_xy"]), 0 if interp else int(g.get("layout", layout)),
+                *[int(b) for b in g.get("brick", brick)], interp)
 
 
 def make_probe(p):

@@ -28,7 +28,7 @@ def _key(case):
     g, s = case["grid"], case["scan"]
     return (f"{torch.cuda.get_device_name()}|grid{g['nx']}x{g['ny']}x{g['nz']}|atoms{len(case['atoms']['x'])}"
             f"|scan{s['nx']}x{s['ny']}x{s['nz']}|mi{case['probe']['min_image']}|rc{case['probe']['coul_rc']}"
-            f"|qzz{case['probe'].get('Qzz', 0.0)}")
+            f"|qzz{case['probe'].get('Qzz', 0.0)}|interp{case['grid'].get('interp', 0)}")
 
 
 def _time(fn, reps):
@@ -57,6 +57,8 @@ def tune_case(case, reps=3, bricks=BRICKS, zpts=ZPTS):
         pp.pp_make_ff_tuned(atoms, probe, grid0, ff, t)
         ff_times[z] = _time(lambda: pp.pp_make_ff_tuned(atoms, probe, grid0, ff, t), reps)
     best_z = min(ff_times, key=ff_times.get)
+    if case["grid"].get("interp", 0):
+        bricks = [(0, None)]  # tricubic energy grids are linear
     relax_times = {}
     for layout, brick in bricks:
         sim = afm.Simulator(case, layout=layout, brick=brick or (4, 4, 4), want_pos=False, want_iters=False)

@@ -93,3 +93,24 @@ def test_ctypes_structs_match_the_c_header(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(py), cname
         for fname, _ in py._fields_:
             assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
+
+
+def test_tricubic_grids_are_validated_on_host(L):
+    g = pp.make_grid({"nx": 10, "ny": 6, "nz": 5, "x0": 0, "y0": 0, "z0": 0, "dx": 0.1, "dy": 0.1, "dz": 0.1,
+                      "periodic_xy": 1, "interp": 1})
+    assert pp.pp_ff_floats(g) == 10 * 6 * 5
+    g.layout = 1
+    assert pp.pp_ff_floats(g) == 0  # energy grids are linear
+    g.layout = 0
+    g.interp = 2
+    assert pp.pp_ff_floats(g) == 0
+    g.interp = 1
+    fake = C.c_void_p(16)  # never dereferenced: the grid check fails first
+    scan = pp.make_scan({"nx": 4, "ny": 4, "nz": 12, "x0": 0.0, "y0": 0.0, "px": 0.1, "py": 0.1, "z_top": 0.3,
+                         "dz": 0.1})
+    tip = pp.make_tip({"kx": 0.25, "ky": 0.25, "kR": 20.0, "R0": 4.0, "d0x": 0.0, "d0y": 0.0})
+    assert L.pp_iets(fake, C.byref(g), C.byref(scan), C.byref(tip), fake, C.c_float(16.0), fake, None, None) == 6
+    assert b"tricubic" in L.pp_last_error()
+    lin = pp.make_grid({"nx": 10, "ny": 6, "nz": 5, "x0": 0, "y0": 0, "z0": 0, "dx": 0.1, "dy": 0.1, "dz": 0.1,
+                        "periodic_xy": 1})
+    assert L.pp_ff_convert(fake, C.byref(g), fake, C.byref(lin), None) == 6
