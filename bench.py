@@ -40,8 +40,10 @@ SM_COUNT = 152
 # summarised in profiles/, valid only for the kernel sources they were taken on: the bench
 # reports them when the sources still hash the same, else traffic is null.
 TRAFFIC = {
-    "relax_scan": {"bytes": 51.85e6, "sha": "cf6af97e58ae1b80",
+    "relax_scan": {"bytes": 66.47e6, "sha": "02f83c921c15e42f",
                    "files": ["relax_scan.cu", "relax_core.cuh", "interp.cuh"]},
+    "relax_scan_tricubic": {"bytes": 23.80e6, "sha": "02f83c921c15e42f",
+                            "files": ["relax_scan.cu", "relax_core.cuh", "interp.cuh"]},
     "ff_assemble": {"bytes": 148.53e6, "sha": "c55fc7410aa5e833",
                     "files": ["ff_assemble.cu", "ff_core.cuh", "interp.cuh"]},
     "ff_assemble_quad": {"bytes": 148.37e6, "sha": "c55fc7410aa5e833",
@@ -336,7 +338,8 @@ def measure_tricubic(case, steps, warmup, flush):
                     "ff_ms": ff_ms, "relax_ms": rx_ms, "ms_per_step": ff_ms + rx_ms,
                     "pixel_z_per_s": s["nx"] * s["ny"] * s["nz"] / ((ff_ms + rx_ms) * 1e-3),
                     "ff_pair_evals_per_s": pairs / (ff_ms * 1e-3),
-                    "fire_iters_mean": float(sim.iters.float().mean().item())})
+                    "fire_iters_mean": float(sim.iters.float().mean().item()),
+                    "relax_traffic": measured_traffic("relax_scan_tricubic") if h == 0.1 else None})
         del sim
     return out
 
