@@ -90,6 +90,9 @@ def lib():
                                       C.POINTER(Tip), C.POINTER(DF), dp, dp, dp, dp, vp, C.c_int]
             L.or_iets.argtypes = [vp, C.POINTER(Grid), C.POINTER(Atoms), C.POINTER(Probe), C.POINTER(Scan),
                                   C.POINTER(Tip), dp, C.c_double, dp, vp, C.c_int]
+            L.or_correlate.argtypes = [dp, dp, C.POINTER(Grid), C.c_double, C.c_double, dp, C.c_int]
+            L.or_correlate_nodes.argtypes = [dp, dp, C.POINTER(Grid), C.c_double, C.c_double, C.c_int,
+                                             C.POINTER(C.c_long), dp, C.c_int]
             L.or_max_threads.restype = C.c_int
             _lib = L
     return _lib
@@ -312,3 +315,23 @@ def forward(case, grid_free=False, fire=None, polish_tol=1e-11, nthreads=0):
     r["ff"] = ff
     r["core"] = core
     return r
+
+
+def correlate(f, g, grid, scale=1.0, power=1.0, nthreads=0):
+    """Cross-correlation force field [nz][ny][nx][4] = (Fx, Fy, Fz, E) of the periodic sample
+    field f[nz][ny][nx] seen by the tip density g[nz][ny][nx] (offsets from the PP, wrapped)."""
+    f, g = _d(f), _d(g)
+    ff = np.empty((grid["nz"], grid["ny"], grid["nx"], 4))
+    if lib().or_correlate(_ptr(f), _ptr(g), C.byref(_grid(grid)), scale, power, _ptr(ff), nthreads):
+        raise ValueError("or_correlate rejected its arguments (sizes must be even)")
+    return ff
+
+
+def correlate_nodes(f, g, grid, nodes, scale=1.0, power=1.0, nthreads=0):
+    """E of correlate() at the flat node indices `nodes` only."""
+    f, g = _d(f), _d(g)
+    nodes = np.ascontiguousarray(nodes, dtype=np.int64)
+    E = np.empty(len(nodes))
+    lib().or_correlate_nodes(_ptr(f), _ptr(g), C.byref(_grid(grid)), scale, power, len(nodes),
+                             nodes.ctypes.data_as(C.POINTER(C.c_long)), _ptr(E), nthreads)
+    return E

@@ -25,6 +25,9 @@
  *   - optionally tricubic interpolation of the grid potential instead of
  *     trilinear interpolation of the grid forces (Sec. 5.1.1 step 2: the
  *     paper's suggestion for larger spacings with no stored forces);
+ *   - the cross-correlation force fields of the Hartree-potential and
+ *     full-density models (Eqs. El_conv and Pauli_FDBM) on periodic grids,
+ *     by direct summation, with the spectral derivative for F;
  *   - optionally an axial point quadrupole on the probe (Secs. 2.2.3, 2.2.5: the CO
  *     tip's quadrupolar charge distribution) in the field of the sample's
  *     point charges.
@@ -919,5 +922,103 @@ int or_backward(const double* ff, const or_grid* G, const or_atoms* A, const or_
     free(gbar);
     free(lam);
     free(gfz);
+    return 0;
+}
+
+/* ------------------------------------------------- FFT-type force fields */
+
+/* Spectral derivative weights of periodic samples along one axis (n even):
+ * the derivative of the trigonometric interpolant with its Nyquist term
+ * dropped, written in real space, f'_i = sum_j D_{i-j} f_j with
+ * D_0 = 0 and D_m = (pi / (n h)) (-1)^m cot(pi m / n). */
+static double spectral_d(long m, long n, double h) {
+    m %= n;
+    if (m < 0) m += n;
+    if (m == 0) return 0.0;
+    const double sgn = (m % 2) ? -1.0 : 1.0;
+    return OR_PI / ((double)n * h) * sgn / tan(OR_PI * (double)m / (double)n);
+}
+
+static double powered(double v, double p) {
+    if (p == 1.0) return v;
+    return v > 0.0 ? pow(v, p) : 0.0;
+}
+
+/* Cross-correlation force field of Eqs. (El_conv) and (Pauli_FDBM) on a grid
+ * periodic in x, y and z: the sample field f (Hartree potential, or density)
+ * seen by the tip's density g placed at every node n,
+ *   E[n] = scale * dV * sum_h g[h]^p f[n + h]^p      (indices modulo the grid),
+ * with dV = dx dy dz, g[h] the tip density at offset h from the PP, p = 1 for
+ * electrostatics (scale = 1) and p = beta, scale = A for the Pauli term (the
+ * product [g f]^beta factors into g^beta f^beta); F = -grad E by the spectral
+ * derivative of each axis.  ff[n] = (Fx, Fy, Fz, E), layout [nz][ny][nx][4].
+ * p != 1 takes densities: negative samples count as 0.  Sizes must be even. */
+int or_correlate(const double* f, const double* g, const or_grid* G, double scale, double p, double* ff,
+                 int nthreads) {
+    if (!f || !g || !G || !ff) return 1;
+    const long nx = G->nx, ny = G->ny, nz = G->nz;
+    if (nx < 2 || ny < 2 || nz < 2 || nx % 2 || ny % 2 || nz % 2) return 1;
+    set_threads(nthreads);
+    const long nxy = nx * ny, N = nxy * nz;
+    const double dV = G->dx * G->dy * G->dz;
+    double* fp = (double*)malloc((size_t)N * sizeof(double));
+    double* gp = (double*)malloc((size_t)N * sizeof(double));
+    double* E = (double*)malloc((size_t)N * sizeof(double));
+    for (long q = 0; q < N; ++q) {
+        fp[q] = powered(f[q], p);
+        gp[q] = powered(g[q], p);
+    }
+#pragma omp parallel for schedule(static)
+    for (long n = 0; n < N; ++n) {
+        const long k = n / nxy, j = (n % nxy) / nx, i = n % nx;
+        double s = 0.0;
+        for (long c = 0; c < nz; ++c)
+            for (long b = 0; b < ny; ++b)
+                for (long a = 0; a < nx; ++a) {
+                    const double gv = gp[(c * ny + b) * nx + a];
+                    if (gv == 0.0) continue;
+                    s += gv * fp[(((k + c) % nz) * ny + (j + b) % ny) * nx + (i + a) % nx];
+                }
+        E[n] = scale * dV * s;
+    }
+#pragma omp parallel for schedule(static)
+    for (long n = 0; n < N; ++n) {
+        const long k = n / nxy, j = (n % nxy) / nx, i = n % nx;
+        double gx = 0.0, gy = 0.0, gz = 0.0;
+        for (long a = 0; a < nx; ++a) gx += spectral_d(i - a, nx, G->dx) * E[(k * ny + j) * nx + a];
+        for (long b = 0; b < ny; ++b) gy += spectral_d(j - b, ny, G->dy) * E[(k * ny + b) * nx + i];
+        for (long c = 0; c < nz; ++c) gz += spectral_d(k - c, nz, G->dz) * E[(c * ny + j) * nx + i];
+        ff[4 * n] = -gx;
+        ff[4 * n + 1] = -gy;
+        ff[4 * n + 2] = -gz;
+        ff[4 * n + 3] = E[n];
+    }
+    free(fp);
+    free(gp);
+    free(E);
+    return 0;
+}
+
+/* E[n] alone at the listed nodes (for spot checks of large grids). */
+int or_correlate_nodes(const double* f, const double* g, const or_grid* G, double scale, double p, int nnodes,
+                       const long* nodes, double* E, int nthreads) {
+    if (!f || !g || !G || !nodes || !E) return 1;
+    const long nx = G->nx, ny = G->ny, nz = G->nz, nxy = nx * ny;
+    set_threads(nthreads);
+    const double dV = G->dx * G->dy * G->dz;
+#pragma omp parallel for schedule(static)
+    for (int t = 0; t < nnodes; ++t) {
+        const long n = nodes[t];
+        const long k = n / nxy, j = (n % nxy) / nx, i = n % nx;
+        double s = 0.0;
+        for (long c = 0; c < nz; ++c)
+            for (long b = 0; b < ny; ++b)
+                for (long a = 0; a < nx; ++a) {
+                    const double gv = powered(g[(c * ny + b) * nx + a], p);
+                    if (gv == 0.0) continue;
+                    s += gv * powered(f[(((k + c) % nz) * ny + (j + b) % ny) * nx + (i + a) % nx], p);
+                }
+        E[t] = scale * dV * s;
+    }
     return 0;
 }
