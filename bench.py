@@ -344,6 +344,72 @@ def measure_tricubic(case, steps, warmup, flush):
     return out
 
 
+FFT_BYTES_PER_NODE = 224  # one correlation: pack 16 + 3 forward passes 48 + spectral 32 + 6 inverse passes 96 + output 32
+FDBM_A, FDBM_BETA = 18.0, 1.0  # Pauli prefactor and exponent of the synthetic full-density workload
+
+
+def measure_fdbm_sweep(reps, flush, sizes=((5, 3), (10, 6), (20, 12))):
+    """Force-field step on periodic graphene sheets of growing size (grid points proportional to
+    atoms, as in the paper's performance figure): Lennard-Jones + point charges by direct summation
+    (K1, minimum image) against the full-density model's two FFT correlations (Hartree electrostatics
+    of a quadrupolar tip charge + Pauli repulsion) on the same grid.  Synthetic densities."""
+    import torch
+
+    from paper_2401_14564_gb300 import afm, pp, synth
+
+    out = []
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    for na, nb in sizes:
+        case = synth.graphene_sweep_case(na, nb)
+        g = case["grid"]
+        dev = lambda a: torch.as_tensor(np.asarray(a, np.float32), device="cuda").contiguous()  # noqa: E731
+        rho = dev(synth.valence_density(g, case["atoms"]))
+        V = dev(synth.hartree_potential(g, case["atoms"]))
+        pauli, quad = (dev(t) for t in synth.tip_densities(g))
+        grid = pp.make_grid(g, 0)
+        ff = torch.empty(pp.pp_ff_floats(grid), dtype=torch.float32, device="cuda")
+        ws = torch.empty(pp.pp_fft_workspace(grid) // 4, dtype=torch.float32, device="cuda")
+        atoms = pp.make_atoms(afm.atoms_to_device(case["atoms"]))
+        probe = pp.make_probe(case["probe"])
+
+        def lj():
+            pp.pp_make_ff(atoms, probe, grid, ff)
+
+        def fdbm():
+            pp.pp_fft_correlate(V, quad, grid, 1.0, 1.0, ff, ws)
+            pp.pp_fft_correlate(rho, pauli, grid, FDBM_A, FDBM_BETA, ff, ws, accumulate=True)
+
+        for _ in range(2):
+            lj()
+            fdbm()
+        t_lj, t_fd = timed(lj), timed(fdbm)
+        nodes = g["nx"] * g["ny"] * g["nz"]
+        n = len(case["atoms"]["x"])
+        fft_bytes = nodes * (2 * FFT_BYTES_PER_NODE + 16)
+        out.append({"sheet": f"{na}x{nb} cells", "atoms": n, "grid": [g["nx"], g["ny"], g["nz"]], "nodes": nodes,
+                    "lj_pc_ms": t_lj, "fdbm_ms": t_fd, "lj_pc_pairs_per_s": nodes * n / (t_lj * 1e-3),
+                    "fdbm_nodes_per_s": nodes / (t_fd * 1e-3), "fdbm_gbs": fft_bytes / (t_fd * 1e-3) / 1e9})
+        del rho, V, pauli, quad, ff, ws
+        torch.cuda.empty_cache()
+    return {"workload": "periodic graphene sheets, grid ~0.1 A x 0.1 A x 0.125 A (powers of two), synthetic "
+                        "Gaussian valence densities and Poisson Hartree potential; FDBM A = %g, beta = %g"
+                        % (FDBM_A, FDBM_BETA),
+            "fft_bytes_per_node": FFT_BYTES_PER_NODE, "points": out}
+
+
 def measure_batch(n_mol, steps, warmup, flush, seq_sample=64):
     """Batched molecules/s: pp_batch_run over n_mol seeded molecules replayed from a CUDA graph,
     beside the same molecules run one by one through pp_make_ff + pp_relax_scan."""
@@ -409,6 +475,7 @@ def main():
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-quad", action="store_true")
     ap.add_argument("--no-tricubic", action="store_true")
+    ap.add_argument("--no-fdbm", action="store_true")
     ap.add_argument("--zpt", type=int, default=0, help="FF z-nodes per thread (skips the autotuner)")
     ap.add_argument("--brick", default="", help="bricked layout bx,by,bz for the scan (skips the autotuner)")
     ap.add_argument("--batch-mol", type=int, default=1024)
@@ -532,6 +599,8 @@ def main():
                             g4["grid"]["nx"], g4["grid"]["ny"], g4["grid"]["nz"])),
         measure_bwd_fwd(case, max(3, args.steps // 2), args.warmup, flush, "flake60 (this line's workload)"),
     ]
+    if not args.no_fdbm:
+        line["fdbm_sweep"] = measure_fdbm_sweep(5, flush)
     if not args.no_tricubic:
         line["tricubic"] = measure_tricubic(case, max(3, args.steps // 2), args.warmup, flush)
     if not args.no_quad:

@@ -361,6 +361,30 @@ PP_API size_t pp_backward_noalloc_capacity(void);
 PP_API pp_status pp_iets(const float* ff, const pp_grid* grid, const pp_scan* scan, const pp_tip* tip,
                          const float* pos, float mass_amu, float* eig, float* hw, pp_stream stream);
 
+/* Bytes of scratch pp_fft_correlate needs for `grid` (3 complex FP32 values
+ * per node); 0 if the grid is invalid or not supported by it. */
+PP_API size_t pp_fft_workspace(const pp_grid* grid);
+
+/* Cross-correlation force field of the Hartree-potential and full-density
+ * models (Eqs. El_conv and Pauli_FDBM, evaluated by the convolution theorem
+ * as in Sec. 5.1.2): for a sample field f (the Hartree potential V_S in V,
+ * or the density rho_S in e/A^3) and the tip's density g (e/A^3, g[h] at
+ * offset h from the PP, wrapped), on a grid periodic along x, y and z,
+ *   E[n] = scale * dx dy dz * sum_h g[h]^p f[n + h]^p   (indices modulo the grid),
+ * F = -grad E by the spectral derivative (Nyquist terms dropped).  With
+ * scale = 1, p = 1 this is the electrostatic energy of Eq. El_conv; with
+ * scale = A, p = beta the Pauli energy of Eq. Pauli_FDBM ([g f]^beta =
+ * g^beta f^beta; negative density samples count as 0 when p != 1).  f and g
+ * are device arrays [nz][ny][nx] of floats; ff is a force-field buffer of the
+ * grid (layout 0, interp 0): (Fx, Fy, Fz, E) per node is written
+ * (accumulate = 0) or added to what ff holds (accumulate = 1), e.g. to the
+ * Lennard-Jones grid of pp_make_ff.  ws: pp_fft_workspace(grid) bytes,
+ * 16-byte aligned, overwritten.  nx, ny, nz must be powers of two in
+ * [2, 1024].  Errors: PP_ERR_ARG, PP_ERR_SHAPE, PP_ERR_UNSUPPORTED (sizes,
+ * bricked or energy-only grid), PP_ERR_CAPACITY (ws too small), PP_ERR_CUDA. */
+PP_API pp_status pp_fft_correlate(const float* f, const float* g, const pp_grid* grid, float scale, float power,
+                                  int accumulate, float* ff, void* ws, size_t ws_bytes, pp_stream stream);
+
 /* Message of the last failed call on this host thread ("" if none). */
 PP_API const char* pp_last_error(void);
 

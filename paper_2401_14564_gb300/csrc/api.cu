@@ -501,3 +501,56 @@ pp_status pp_ff_convert(const float* src, const pp_grid* src_grid, float* dst, c
 }
 
 }  // extern "C"
+
+static bool pow2_fft(int n) { return n >= 2 && n <= 1024 && (n & (n - 1)) == 0; }
+
+static bool fft_grid(const pp_grid* grid, GridMap* map, std::string* why, pp_status* st) {
+    if (!make_grid_map(grid, map, why)) { *st = PP_ERR_SHAPE; return false; }
+    if (grid->layout != 0 || map->interp != 0) {
+        *why = "needs a linear force grid (layout 0, interp 0)";
+        *st = PP_ERR_UNSUPPORTED;
+        return false;
+    }
+    if (!pow2_fft(grid->nx) || !pow2_fft(grid->ny) || !pow2_fft(grid->nz)) {
+        *why = "grid sizes must be powers of two in [2, 1024]";
+        *st = PP_ERR_UNSUPPORTED;
+        return false;
+    }
+    return true;
+}
+
+size_t pp_fft_workspace(const pp_grid* grid) {
+    GridMap m;
+    std::string why;
+    pp_status st;
+    if (!grid || !fft_grid(grid, &m, &why, &st)) return 0;
+    return fft_workspace_bytes(grid->nx, grid->ny, grid->nz);
+}
+
+pp_status pp_fft_correlate(const float* f, const float* g, const pp_grid* grid, float scale, float power,
+                           int accumulate, float* ff, void* ws, size_t ws_bytes, pp_stream stream) {
+    g_error.clear();
+    if (!f || !g || !grid || !ff || !ws) { set_error("pp_fft_correlate: NULL argument"); return PP_ERR_ARG; }
+    if (!isfinite(scale) || !(power > 0.f) || !isfinite(power) || (accumulate != 0 && accumulate != 1)) {
+        set_error("pp_fft_correlate: scale must be finite, power > 0, accumulate 0 or 1");
+        return PP_ERR_ARG;
+    }
+    if (!aligned16(ff) || !aligned16(ws)) { set_error("pp_fft_correlate: ff and ws must be 16-byte aligned"); return PP_ERR_ARG; }
+    GridMap map;
+    std::string why;
+    pp_status st = PP_OK;
+    if (!fft_grid(grid, &map, &why, &st)) { set_error("pp_fft_correlate: " + why); return st; }
+    const size_t need = fft_workspace_bytes(grid->nx, grid->ny, grid->nz);
+    if (ws_bytes < need) {
+        set_error("pp_fft_correlate: workspace too small (need " + std::to_string(need) + " bytes)");
+        return PP_ERR_CAPACITY;
+    }
+    FftLaunch L;
+    L.f = f; L.g = g;
+    L.ff = reinterpret_cast<float4*>(ff);
+    L.ws = ws;
+    L.nx = grid->nx; L.ny = grid->ny; L.nz = grid->nz;
+    L.dx = grid->dx; L.dy = grid->dy; L.dz = grid->dz;
+    L.scale = scale; L.power = power; L.accumulate = accumulate;
+    return cuda_status(launch_fft_correlate(L, (cudaStream_t)stream), "pp_fft_correlate launch");
+}

@@ -159,6 +159,18 @@ struct BatchArgs {
 size_t batch_workspace_bytes(int nmol);
 cudaError_t launch_batch(const BatchArgs& A, cudaStream_t s);
 
+struct FftLaunch {
+    const float *f, *g;  // sample field and tip density, [nz][ny][nx]
+    float4* ff;          // (Fx, Fy, Fz, E) per node, linear layout
+    void* ws;            // 3 complex values per node
+    int nx, ny, nz;
+    float dx, dy, dz;
+    float scale, power;
+    int accumulate;
+};
+size_t fft_workspace_bytes(int nx, int ny, int nz);
+cudaError_t launch_fft_correlate(const FftLaunch& L, cudaStream_t s);
+
 struct IetsLaunch {
     const float4* ff;
     GridMap map;

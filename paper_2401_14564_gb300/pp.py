@@ -144,6 +144,11 @@ def lib():
             L.pp_batch_status.restype = st
             L.pp_iets.argtypes = [vp, C.POINTER(Grid), C.POINTER(Scan), C.POINTER(Tip), vp, C.c_float, vp, vp, vp]
             L.pp_iets.restype = st
+            L.pp_fft_workspace.argtypes = [C.POINTER(Grid)]
+            L.pp_fft_workspace.restype = C.c_size_t
+            L.pp_fft_correlate.argtypes = [vp, vp, C.POINTER(Grid), C.c_float, C.c_float, C.c_int, vp, vp,
+                                           C.c_size_t, vp]
+            L.pp_fft_correlate.restype = st
             L.pp_last_error.argtypes = []
             L.pp_last_error.restype = C.c_char_p
             _lib = L
@@ -352,6 +357,24 @@ def pp_iets(ff, grid: Grid, scan: Scan, tip: Tip, pos, mass_amu: float, eig, hw=
         raise ValueError("ff buffer smaller than pp_ff_floats(grid)")
     _check(lib().pp_iets(_dev(ff, "ff"), C.byref(grid), C.byref(scan), C.byref(tip), _dev(pos, "pos"),
                          float(mass_amu), _dev(eig, "eig"), _dev(hw, "hw", allow_none=True), _stream(stream)))
+
+
+def pp_fft_workspace(grid: Grid) -> int:
+    return int(lib().pp_fft_workspace(C.byref(grid)))
+
+
+def pp_fft_correlate(f, g, grid: Grid, scale: float, power: float, ff, ws, accumulate=False, stream=None):
+    """Cross-correlation force field of the sample field f and the tip density g ([nz][ny][nx]
+    float32 CUDA tensors) into ff (written, or added when accumulate)."""
+    n = grid.nx * grid.ny * grid.nz
+    if f.numel() < n or g.numel() < n:
+        raise ValueError("f and g need nx*ny*nz floats")
+    if ff.numel() < pp_ff_floats(grid):
+        raise ValueError("ff buffer smaller than pp_ff_floats(grid)")
+    nbytes = ws.numel() * ws.element_size()
+    _check(lib().pp_fft_correlate(_dev(f, "f"), _dev(g, "g"), C.byref(grid), float(scale), float(power),
+                                  int(bool(accumulate)), _dev(ff, "ff"), _dev(ws, "ws", ws.dtype), nbytes,
+                                  _stream(stream)))
 
 
 def pp_last_error() -> str:

@@ -349,3 +349,112 @@ def small_case(seed=3, n_atoms=12, nxy=32, nz=40, scan_px=12, nz_scan=12, d=0.2)
                  0.7 * nxy * d / scan_px, 0.7 * (nxy + 4) * d / (scan_px + 3),
                  atoms["z"].max() + 5.0 + 4.0, 0.1)
     return _case(f"small_seed{seed}", atoms, grid, scan)
+
+
+# ------------------------------------------- densities for the FFT force fields
+#
+# Stand-ins for the DFT inputs of the Hartree and full-density models (the
+# paper's densities and potentials come from DFT; none are available here):
+# valence densities as sums of normalised Gaussians on a grid periodic in x, y
+# and z, and the Hartree potential of a neutral Gaussian charge distribution
+# from Poisson's equation, solved spectrally.  Input generation only.
+
+VALENCE = {"H": (1.0, 0.45), "C": (4.0, 0.55), "N": (5.0, 0.52), "O": (6.0, 0.50), "F": (7.0, 0.48)}
+
+
+def periodic_gaussians(grid, xyz, weights, sigmas, cut=6.0):
+    """sum_i w_i * normalised Gaussian(sigma_i) at xyz_i on a grid periodic in x, y and z (period
+    n * d), each Gaussian evaluated within cut * sigma of its nearest image (plus the next images
+    when the window spans the whole axis); float64 [nz][ny][nx]."""
+    n = (grid["nx"], grid["ny"], grid["nz"])
+    d = (grid["dx"], grid["dy"], grid["dz"])
+    o = (grid["x0"], grid["y0"], grid["z0"])
+    L = [n[a] * d[a] for a in range(3)]
+    out = np.zeros((n[2], n[1], n[0]))
+    for p, w, sg in zip(np.asarray(xyz, dtype=float), weights, sigmas):
+        idx, prof = [], []
+        for a in range(3):
+            half = int(math.ceil(cut * sg / d[a]))
+            if 2 * half + 1 >= n[a]:
+                i = np.arange(n[a])
+                r = o[a] + i * d[a] - p[a]
+                r = r - L[a] * np.round(r / L[a])
+                g = sum(np.exp(-(r + m * L[a]) ** 2 / (2 * sg * sg)) for m in (-1, 0, 1))
+            else:
+                c = int(round((p[a] - o[a]) / d[a]))
+                i = np.arange(c - half, c + half + 1)
+                r = o[a] + i * d[a] - p[a]
+                i = i % n[a]
+                g = np.exp(-r * r / (2 * sg * sg))
+            idx.append(i)
+            prof.append(g)
+        amp = w * (2 * np.pi * sg * sg) ** -1.5
+        out[np.ix_(idx[2], idx[1], idx[0])] += amp * prof[2][:, None, None] * prof[1][None, :, None] * prof[0][None, None, :]
+    return out
+
+
+def valence_density(grid, atoms):
+    """Synthetic valence density (e/A^3) of the atoms: one Gaussian per atom with the element's
+    valence electron count and width."""
+    xyz = np.c_[atoms["x"], atoms["y"], atoms["z"]]
+    w = [VALENCE[s][0] for s in atoms["sym"]]
+    sg = [VALENCE[s][1] for s in atoms["sym"]]
+    return periodic_gaussians(grid, xyz, w, sg)
+
+
+def hartree_potential(grid, atoms, sigma=0.35):
+    """Hartree potential (V) of the atoms' partial charges smeared into Gaussians of width sigma,
+    periodic in x, y and z: Poisson's equation del^2 V = -4 pi k_e rho solved in Fourier space
+    (the k = 0 term, the mean, set to zero)."""
+    k_e = 14.3996454784
+    xyz = np.c_[atoms["x"], atoms["y"], atoms["z"]]
+    q = np.asarray(atoms["q"], dtype=float)
+    rho = periodic_gaussians(grid, xyz, q - q.mean(), [sigma] * len(q))
+    kx = 2 * np.pi * np.fft.fftfreq(grid["nx"], grid["dx"])
+    ky = 2 * np.pi * np.fft.fftfreq(grid["ny"], grid["dy"])
+    kz = 2 * np.pi * np.fft.fftfreq(grid["nz"], grid["dz"])
+    K2 = kz[:, None, None] ** 2 + ky[None, :, None] ** 2 + kx[None, None, :] ** 2
+    R = np.fft.fftn(rho)
+    V = np.zeros_like(R)
+    nz = K2 > 0
+    V[nz] = 4 * np.pi * k_e * R[nz] / K2[nz]
+    return np.real(np.fft.ifftn(V))
+
+
+def tip_densities(grid, sigma_pauli=0.55, n_pauli=6.0, qzz=-0.05, sigma_q=0.7, s_q=0.3):
+    """Tip densities at offsets from the PP (centred on node 0, wrapped): the Pauli density of the
+    CO tip (n_pauli electrons in one Gaussian) and an axial quadrupolar charge density (charges
+    +c, -2c, +c at z = +s_q, 0, -s_q smeared by sigma_q, second moment 2 c s_q^2 = qzz)."""
+    g0 = dict(grid, x0=0.0, y0=0.0, z0=0.0)
+    pauli = periodic_gaussians(g0, [(0.0, 0.0, 0.0)], [n_pauli], [sigma_pauli])
+    c = qzz / (2 * s_q * s_q)
+    quad = periodic_gaussians(g0, [(0.0, 0.0, s_q), (0.0, 0.0, 0.0), (0.0, 0.0, -s_q)], [c, -2 * c, c],
+                              [sigma_q] * 3)
+    return pauli, quad
+
+
+def graphene_sheet(na, nb, z=0.0):
+    """Flat graphene: na x nb rectangular 4-atom cells (a = 2.46 A), small alternating charges."""
+    a = 2.46
+    ay = a * math.sqrt(3.0)
+    basis = np.array([[0.0, 0.0], [a / 2, ay / 6], [a / 2, ay / 2], [0.0, 2 * ay / 3]])
+    P = np.concatenate([basis + np.array([i * a, j * ay]) for i in range(na) for j in range(nb)])
+    q = np.tile([0.02, -0.02, 0.02, -0.02], na * nb)
+    return _atoms(["C"] * len(P), np.c_[P, np.full(len(P), z)], q)
+
+
+def graphene_sweep_case(na, nb, nz=128, lz=16.0):
+    """Periodic graphene sheet of na x nb cells for the size sweep of the force-field step (the
+    paper's Fig. on performance): grid points proportional to atoms, about 0.1 A apart in x, y;
+    sizes rounded to powers of two for the FFT path."""
+    atoms = graphene_sheet(na, nb, z=4.0)
+    a = 2.46
+    lx, ly = na * a, nb * a * math.sqrt(3.0)
+
+    def p2(v):
+        return 1 << int(round(math.log2(v)))
+
+    nx, ny = p2(lx / 0.1), p2(ly / 0.1)
+    grid = {"nx": nx, "ny": ny, "nz": nz, "x0": 0.0, "y0": 0.0, "z0": 0.0, "dx": lx / nx, "dy": ly / ny,
+            "dz": lz / nz, "periodic_xy": 1}
+    return {"name": f"graphene{na}x{nb}", "atoms": atoms, "grid": grid, "probe": default_probe(min_image=1)}

@@ -114,3 +114,20 @@ def test_tricubic_grids_are_validated_on_host(L):
     lin = pp.make_grid({"nx": 10, "ny": 6, "nz": 5, "x0": 0, "y0": 0, "z0": 0, "dx": 0.1, "dy": 0.1, "dz": 0.1,
                         "periodic_xy": 1})
     assert L.pp_ff_convert(fake, C.byref(g), fake, C.byref(lin), None) == 6
+
+
+def test_fft_correlate_validated_on_host(L):
+    def grid(nx, ny, nz, **kw):
+        return pp.make_grid({"nx": nx, "ny": ny, "nz": nz, "x0": 0, "y0": 0, "z0": 0, "dx": 0.1, "dy": 0.1, "dz": 0.1,
+                             "periodic_xy": 1, **kw})
+    assert pp.pp_fft_workspace(grid(16, 8, 32)) == 3 * 16 * 8 * 32 * 8
+    assert pp.pp_fft_workspace(grid(12, 8, 32)) == 0       # not a power of two
+    assert pp.pp_fft_workspace(grid(16, 8, 2048)) == 0     # longer than 1024
+    assert pp.pp_fft_workspace(grid(16, 8, 32, interp=1)) == 0
+    fake = C.c_void_p(16)  # never dereferenced: the host checks fail first
+    g = grid(12, 8, 32)
+    assert L.pp_fft_correlate(fake, fake, C.byref(g), C.c_float(1), C.c_float(1), 0, fake, fake, 1 << 20, None) == 6
+    g = grid(16, 8, 32)
+    assert L.pp_fft_correlate(fake, fake, C.byref(g), C.c_float(1), C.c_float(1), 0, fake, fake, 100, None) == 4
+    assert L.pp_fft_correlate(fake, fake, C.byref(g), C.c_float(1), C.c_float(0), 0, fake, fake, 1 << 20, None) == 1
+    assert L.pp_fft_correlate(None, fake, C.byref(g), C.c_float(1), C.c_float(1), 0, fake, fake, 1 << 20, None) == 1
