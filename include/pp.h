@@ -361,8 +361,9 @@ PP_API size_t pp_backward_noalloc_capacity(void);
 PP_API pp_status pp_iets(const float* ff, const pp_grid* grid, const pp_scan* scan, const pp_tip* tip,
                          const float* pos, float mass_amu, float* eig, float* hw, pp_stream stream);
 
-/* Bytes of scratch pp_fft_correlate needs for `grid` (3 complex FP32 values
- * per node); 0 if the grid is invalid or not supported by it. */
+/* Bytes of scratch pp_fft_correlate needs for `grid`: three complex FP32
+ * arrays in a padded layout, 3 * nz * ((nx + 16) * ny + 16) * 8 bytes; 0 if
+ * the grid is invalid or not supported by it. */
 PP_API size_t pp_fft_workspace(const pp_grid* grid);
 
 /* Cross-correlation force field of the Hartree-potential and full-density
