@@ -50,24 +50,49 @@ __global__ void init_kernel(const BwdLaunch P) {
     }
 }
 
-template <int LAYOUT>
-__global__ void __launch_bounds__(kAdjThreads) relax_adjoint_kernel(const BwdLaunch P) {
-    const int npix = P.snx * P.sny;
-    const int64_t total = (int64_t)npix * P.snz;
-    const int64_t o = (int64_t)blockIdx.x * kAdjThreads + threadIdx.x;
-    float gkx = 0.f, gky = 0.f, gkR = 0.f;
-    int kmin = 0x7fffffff, kmax = -1;
-    if (o < total) {
-        const int k = (int)(o / npix), pix = (int)(o - (int64_t)k * npix);
-        // g_Fz = (df stencil)^T g_df: df[c] = sum_s coef[s+m] Fz[c+m+s]
-        float gf = 0.f;
+// g_Fz at height k = (df stencil)^T g_df: df[c] = sum_s coef[s+m] Fz[c+m+s].  With the half
+// width M known at compile time the 2M+1 loads are independent and issue back to back; M < 0
+// takes the run-time half width P.m.
+template <int M>
+__device__ __forceinline__ float df_transpose(const BwdLaunch& P, int k, int pix, int npix) {
+    float gf = 0.f;
+    if constexpr (M >= 0) {
+        float t[2 * M + 1];
+#pragma unroll
+        for (int s = -M; s <= M; ++s) {
+            const int c = k - M - s;
+            t[s + M] = (c >= 0 && c < P.nzo) ? __ldg(P.g_df + (int64_t)c * npix + pix) : 0.f;
+        }
+#pragma unroll
+        for (int s = -M; s <= M; ++s) gf = fmaf(P.coef[s + M], t[s + M], gf);
+    } else {
         for (int s = -P.m; s <= P.m; ++s) {
             const int c = k - P.m - s;
             if (c >= 0 && c < P.nzo) gf = fmaf(P.coef[s + P.m], __ldg(P.g_df + (int64_t)c * npix + pix), gf);
         }
+    }
+    return gf;
+}
+
+// Grid-stride over the relaxed points: each thread sums its points' tip-parameter terms and
+// z-slab bounds in registers, and a block adds them to the five shared scalars once (atomics
+// from every warp to the same five addresses would serialise in L2).
+template <int LAYOUT, int M>
+__global__ void __launch_bounds__(kAdjThreads) relax_adjoint_kernel(const BwdLaunch P) {
+    __shared__ float sred[3][kAdjThreads / 32];
+    __shared__ int sk[2][kAdjThreads / 32];
+    const int npix = P.snx * P.sny;
+    const int64_t total = (int64_t)npix * P.snz;
+    float gkx = 0.f, gky = 0.f, gkR = 0.f;
+    int kmin = 0x7fffffff, kmax = -1;
+    for (int64_t o = (int64_t)blockIdx.x * kAdjThreads + threadIdx.x; o < total;
+         o += (int64_t)gridDim.x * kAdjThreads) {
+        const int k = (int)(o / npix), pix = (int)(o - (int64_t)k * npix);
+        // the relaxed position is loaded together with the g_df taps (one memory round trip)
+        const float px = __ldg(P.pos + 3 * o), py = __ldg(P.pos + 3 * o + 1), pz = __ldg(P.pos + 3 * o + 2);
+        const float gf = df_transpose<M>(P, k, pix, npix);
         if (gf != 0.f) {
             const int i = pix % P.snx, j = pix / P.snx;
-            const float px = __ldg(P.pos + 3 * o), py = __ldg(P.pos + 3 * o + 1), pz = __ldg(P.pos + 3 * o + 2);
             const float ax = fmaf((float)i, P.spx, P.sx0), ay = fmaf((float)j, P.spy, P.sy0);
             const float az = P.z_top - k * P.sdz;
             const float dx = px - ax, dy = py - ay, dz = pz - az;
@@ -108,9 +133,9 @@ __global__ void __launch_bounds__(kAdjThreads) relax_adjoint_kernel(const BwdLau
                 const float lx = (c00 * r0 + c01 * r1 + c02 * r2) * id;
                 const float ly = (c10 * r0 + c11 * r1 + c12 * r2) * id;
                 const float lz = (c20 * r0 + c21 * r1 + c22 * r2) * id;
-                gkx = lx * ex;
-                gky = ly * ey;
-                gkR = gf * ext * dz + (lx * dx + ly * dy + lz * dz) * ext;
+                gkx = fmaf(lx, ex, gkx);
+                gky = fmaf(ly, ey, gky);
+                gkR += gf * ext * dz + (lx * dx + ly * dy + lz * dz) * ext;
                 // grid adjoint: Gbar += -lambda w_g at the 8 corners
                 int idx[8];
                 corner_index<LAYOUT>(P.map, cl, idx);
@@ -119,17 +144,33 @@ __global__ void __launch_bounds__(kAdjThreads) relax_adjoint_kernel(const BwdLau
 #pragma unroll
                 for (int c = 0; c < 8; ++c)
                     if (w[c] != 0.f) atomicAdd(P.gbar + idx[c], make_float4(-lx * w[c], -ly * w[c], -lz * w[c], 0.f));
-                kmin = cl.z.i0;
-                kmax = cl.z.i1;
+                kmin = min(kmin, cl.z.i0);
+                kmax = max(kmax, cl.z.i1);
             }
         }
     }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     gkx = warp_sum(gkx);
     gky = warp_sum(gky);
     gkR = warp_sum(gkR);
     kmin = __reduce_min_sync(0xffffffffu, kmin);
     kmax = __reduce_max_sync(0xffffffffu, kmax);
-    if ((threadIdx.x & 31) == 0) {
+    if (lane == 0) {
+        sred[0][warp] = gkx;
+        sred[1][warp] = gky;
+        sred[2][warp] = gkR;
+        sk[0][warp] = kmin;
+        sk[1][warp] = kmax;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < kAdjThreads / 32; ++w) {
+            gkx += sred[0][w];
+            gky += sred[1][w];
+            gkR += sred[2][w];
+            kmin = min(kmin, sk[0][w]);
+            kmax = max(kmax, sk[1][w]);
+        }
         if (gkx != 0.f) atomicAdd(P.gtip + 0, gkx * P.nm);
         if (gky != 0.f) atomicAdd(P.gtip + 1, gky * P.nm);
         if (gkR != 0.f) atomicAdd(P.gtip + 2, gkR * P.nm);
@@ -312,14 +353,44 @@ __global__ void finalize_kernel(const BwdLaunch P) {
     }
 }
 
+template <int LAYOUT, int M>
+void launch_adjoint_m(const BwdLaunch& L, int blocks, cudaStream_t s) {
+    relax_adjoint_kernel<LAYOUT, M><<<blocks, kAdjThreads, 0, s>>>(L);
+}
+
+// Compile-time stencil half widths 1..8 (A_pp / dz up to 16), the run-time loop beyond.
+template <int LAYOUT>
+void launch_adjoint_layout(const BwdLaunch& L, int blocks, cudaStream_t s) {
+    switch (L.m) {
+        case 1: launch_adjoint_m<LAYOUT, 1>(L, blocks, s); break;
+        case 2: launch_adjoint_m<LAYOUT, 2>(L, blocks, s); break;
+        case 3: launch_adjoint_m<LAYOUT, 3>(L, blocks, s); break;
+        case 4: launch_adjoint_m<LAYOUT, 4>(L, blocks, s); break;
+        case 5: launch_adjoint_m<LAYOUT, 5>(L, blocks, s); break;
+        case 6: launch_adjoint_m<LAYOUT, 6>(L, blocks, s); break;
+        case 7: launch_adjoint_m<LAYOUT, 7>(L, blocks, s); break;
+        case 8: launch_adjoint_m<LAYOUT, 8>(L, blocks, s); break;
+        default: launch_adjoint_m<LAYOUT, -1>(L, blocks, s); break;
+    }
+}
+
+void launch_adjoint(const BwdLaunch& L, int blocks, cudaStream_t s) {
+    if (L.layout == 0) launch_adjoint_layout<0>(L, blocks, s);
+    else launch_adjoint_layout<1>(L, blocks, s);
+}
+
 }  // namespace
 
 cudaError_t launch_backward(const BwdLaunch& L, cudaStream_t s) {
     init_kernel<<<(L.n + 255) / 256 + 1, 256, 0, s>>>(L);
     const int64_t total = (int64_t)L.snx * L.sny * L.snz;
-    const int blocks = (int)((total + kAdjThreads - 1) / kAdjThreads);
-    if (L.layout == 0) relax_adjoint_kernel<0><<<blocks, kAdjThreads, 0, s>>>(L);
-    else relax_adjoint_kernel<1><<<blocks, kAdjThreads, 0, s>>>(L);
+    // one wave of resident blocks (8 per SM at this register count), grid-stride inside
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t need = (total + kAdjThreads - 1) / kAdjThreads;
+    const int blocks = (int)(need < 8LL * sms ? (need > 0 ? need : 1) : 8LL * sms);
+    launch_adjoint(L, blocks, s);
     if (L.n > 0) {
         const int64_t nodes = (int64_t)L.map.nx * L.map.ny * L.map.nz;
         const int fb = (int)((nodes + kFFBNodes - 1) / kFFBNodes);
