@@ -184,11 +184,19 @@ __global__ void __launch_bounds__(kAdjThreads) relax_adjoint_kernel(const BwdLau
 // K5: per-atom contraction of the grid adjoint with the pair derivatives.
 // A CTA stages kFFBNodes consecutive nodes (logical x-fastest order), keeps
 // those with a nonzero adjoint, and each thread then sweeps them for one atom,
-// accumulating (dx, dy, dz, dR, de_iPP, C, Cq) in registers.
+// accumulating (dx, dy, dz, dR, de_iPP, C, Cq) in registers.  The kept nodes
+// are stored in pairs, (x0, x1, y0, y1), (z0, z1, gx0, gx1), (gy0, gy1, gz0,
+// gz1), so that two nodes go through each packed f32x2 instruction (the floor
+// test, the rsqrt and the minimum image stay per node).
+__device__ __forceinline__ float2 sel2(bool c0, bool c1, float2 a, float2 b) {
+    return make_float2(c0 ? a.x : b.x, c1 ? a.y : b.y);
+}
+
 template <bool kMinImage, bool kCutoff, bool kQuad>
 __global__ void __launch_bounds__(kFFBThreads) ff_backward_kernel(const BwdLaunch P) {
-    __shared__ float4 sp[kFFBNodes];  // node position (x, y, z, -)
-    __shared__ float4 sg[kFFBNodes];  // adjoint (gx, gy, gz, -)
+    __shared__ float4 sxy[kFFBNodes / 2];  // (x0, x1, y0, y1)
+    __shared__ float4 szg[kFFBNodes / 2];  // (z0, z1, gx0, gx1)
+    __shared__ float4 sgg[kFFBNodes / 2];  // (gy0, gy1, gz0, gz1)
     __shared__ int scount;
     const int nx = P.map.nx, ny = P.map.ny;
     const int64_t nxy = (int64_t)nx * ny;
@@ -199,6 +207,9 @@ __global__ void __launch_bounds__(kFFBThreads) ff_backward_kernel(const BwdLaunc
     if (klast < klo || kfirst > khi) return;
     if (threadIdx.x == 0) scount = 0;
     __syncthreads();
+    float* fxy = reinterpret_cast<float*>(sxy);
+    float* fzg = reinterpret_cast<float*>(szg);
+    float* fgg = reinterpret_cast<float*>(sgg);
     const int64_t total = nxy * P.map.nz;
     for (int t = threadIdx.x; t < kFFBNodes; t += kFFBThreads) {
         const int64_t g = first + t;
@@ -219,16 +230,35 @@ __global__ void __launch_bounds__(kFFBThreads) ff_backward_kernel(const BwdLaunc
         base = __shfl_sync(0xffffffffu, base, 0);
         if (keep) {
             const int slot = base + __popc(mask & ((1u << (threadIdx.x & 31)) - 1u));
-            sp[slot] = make_float4(P.x0 + i * P.dx, P.y0 + j * P.dy, P.z0 + k * P.dz, 0.f);
-            sg[slot] = a;
+            const int q = (slot >> 1) * 4, l = slot & 1;
+            fxy[q + l] = P.x0 + i * P.dx;
+            fxy[q + 2 + l] = P.y0 + j * P.dy;
+            fzg[q + l] = P.z0 + k * P.dz;
+            fzg[q + 2 + l] = a.x;
+            fgg[q + l] = a.y;
+            fgg[q + 2 + l] = a.z;
         }
     }
     __syncthreads();
     const int cnt = scount;
     if (cnt == 0) return;
+    if ((cnt & 1) && threadIdx.x == 0) {
+        // pad the last pair with a copy of its node and a zero adjoint (it adds nothing)
+        const int q = (cnt >> 1) * 4;
+        fxy[q + 1] = fxy[q];
+        fxy[q + 3] = fxy[q + 2];
+        fzg[q + 1] = fzg[q];
+        fzg[q + 3] = 0.f;
+        fgg[q + 1] = 0.f;
+        fgg[q + 3] = 0.f;
+    }
+    __syncthreads();
+    const int npairs = (cnt + 1) >> 1;
     const float rc2 = kCutoff ? P.coul_rc * P.coul_rc : 0.f;
     const float irc2 = kCutoff ? 1.f / rc2 : 0.f;
     const float invLx = kMinImage ? 1.f / P.Lx : 0.f, invLy = kMinImage ? 1.f / P.Ly : 0.f;
+    const float2 TWELVE = make_float2(12.f, 12.f), EIGHT = make_float2(8.f, 8.f), M14 = make_float2(-14.f, -14.f);
+    const float2 M6 = make_float2(-6.f, -6.f), M3 = make_float2(-3.f, -3.f), CF = make_float2(P.core_frac, P.core_frac);
     float qC = 0.f, qCq = 0.f;  // this thread's q_i C_i and q_i Cq_i (tip quadrupole only)
     for (int a0 = 0; a0 < P.n; a0 += kFFBThreads) {
         const int ia = a0 + threadIdx.x;
@@ -238,63 +268,81 @@ __global__ void __launch_bounds__(kFFBThreads) ff_backward_kernel(const BwdLaunc
         const float eij = sqrtf(P.aeps[ia] * P.eps_pp);
         const float qq = P.kQ * P.aq[ia];
         const float rmin2 = (P.core_frac * Rij) * (P.core_frac * Rij);
-        const float R2 = Rij * Rij, iR = 1.f / Rij;
         const float kqq = kQuad ? P.kQzz * P.aq[ia] : 0.f;
-        float gpx = 0.f, gpy = 0.f, gpz = 0.f, gRr = 0.f, ge = 0.f, C = 0.f, Cq = 0.f;
-        for (int s = 0; s < cnt; ++s) {
-            const float4 np = sp[s], gb = sg[s];
-            float dx = np.x - ax, dy = np.y - ay;
-            const float dz = np.z - azz;
+        const float2 AX = make_float2(ax, ax), AY = make_float2(ay, ay), AZ = make_float2(azz, azz);
+        const float2 RR2 = make_float2(Rij * Rij, Rij * Rij), EIJ = make_float2(eij, eij), QQ = make_float2(qq, qq);
+        const float2 E12 = make_float2(12.f * eij, 12.f * eij), E12R = make_float2(12.f * eij / Rij, 12.f * eij / Rij);
+        float2 GPX = make_float2(0.f, 0.f), GPY = GPX, GPZ = GPX, GR = GPX, GE = GPX, CC = GPX, CQ = GPX;
+        for (int pr = 0; pr < npairs; ++pr) {
+            const float4 A = sxy[pr], B = szg[pr], G = sgg[pr];
+            float2 DX = f2sub(make_float2(A.x, A.y), AX), DY = f2sub(make_float2(A.z, A.w), AY);
+            const float2 DZ = f2sub(make_float2(B.x, B.y), AZ);
+            const float2 GX = make_float2(B.z, B.w), GY = make_float2(G.x, G.y), GZ = make_float2(G.z, G.w);
             if (kMinImage) {
-                dx = fmaf(-P.Lx, rintf(dx * invLx), dx);
-                dy = fmaf(-P.Ly, rintf(dy * invLy), dy);
+                DX.x = fmaf(-P.Lx, rintf(DX.x * invLx), DX.x);
+                DX.y = fmaf(-P.Lx, rintf(DX.y * invLx), DX.y);
+                DY.x = fmaf(-P.Ly, rintf(DY.x * invLy), DY.x);
+                DY.y = fmaf(-P.Ly, rintf(DY.y * invLy), DY.y);
             }
-            const float r2raw = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            const bool clamped = r2raw < rmin2;
-            const float r2 = clamped ? rmin2 : r2raw;
-            const float rs = rsqrtf(r2);
-            const float ir2 = rs * rs;
-            const float s6 = R2 * ir2 * (R2 * ir2) * (R2 * ir2);
-            const float s12 = s6 * s6;
-            const float Slj_e = 12.f * (s12 - s6) * ir2;                 // LJ S per unit e_iPP
-            const float dSlj_dr = 12.f * eij * (8.f * s6 - 14.f * s12) * ir2 * rs;
-            const float dSlj_dR = 12.f * eij * (12.f * s12 - 6.f * s6) * ir2 * iR;
-            float c, dc_dr;
+            const float2 R2raw = f2fma(DX, DX, f2fma(DY, DY, f2mul(DZ, DZ)));
+            const bool c0 = R2raw.x < rmin2, c1 = R2raw.y < rmin2;  // core floor per node
+            const float2 R2v = make_float2(c0 ? rmin2 : R2raw.x, c1 ? rmin2 : R2raw.y);
+            const float2 RS = make_float2(rsqrtf(R2v.x), rsqrtf(R2v.y));
+            const float2 IR2 = f2mul(RS, RS);
+            const float2 U = f2mul(RR2, IR2);
+            const float2 S6 = f2mul(f2mul(U, U), U);
+            const float2 S12 = f2mul(S6, S6);
+            const float2 SLJ = f2mul(f2mul(TWELVE, f2sub(S12, S6)), IR2);                 // LJ S per unit e_iPP
+            const float2 DSLJDR = f2mul(f2mul(E12, f2fma(EIGHT, S6, f2mul(M14, S12))), f2mul(IR2, RS));
+            const float2 DSLJDRR = f2mul(f2mul(E12R, f2fma(TWELVE, S12, f2mul(M6, S6))), IR2);
+            float2 Cv, DC;
             if (kCutoff) {
-                const bool in = r2 < rc2;
-                c = in ? rs * (ir2 - irc2) : 0.f;                        // 1/r^3 - 1/(r rc^2)
-                dc_dr = in ? ir2 * (irc2 - 3.f * ir2) : 0.f;             // -3/r^4 + 1/(r^2 rc^2)
+                const bool i0 = R2v.x < rc2, i1 = R2v.y < rc2;
+                const float2 z = make_float2(0.f, 0.f);
+                Cv = sel2(i0, i1, f2mul(RS, f2sub(IR2, make_float2(irc2, irc2))), z);     // 1/r^3 - 1/(r rc^2)
+                DC = sel2(i0, i1, f2mul(IR2, f2fma(M3, IR2, make_float2(irc2, irc2))), z);  // -3/r^4 + 1/(r^2 rc^2)
             } else {
-                c = rs * ir2;
-                dc_dr = -3.f * ir2 * ir2;
+                Cv = f2mul(RS, IR2);
+                DC = f2mul(M3, f2mul(IR2, IR2));
             }
-            const float S = fmaf(eij, Slj_e, qq * c);
-            const float dSdr = fmaf(qq, dc_dr, dSlj_dr);
-            const float ad = fmaf(gb.x, dx, fmaf(gb.y, dy, gb.z * dz));
-            const float rad = clamped ? 0.f : dSdr * ad * rs;            // dS/dr (a.delta) / r
-            gpx -= fmaf(S, gb.x, rad * dx);
-            gpy -= fmaf(S, gb.y, rad * dy);
-            gpz -= fmaf(S, gb.z, rad * dz);
-            gRr = fmaf(ad, clamped ? fmaf(dSdr, P.core_frac, dSlj_dR) : dSlj_dR, gRr);
-            ge = fmaf(ad, Slj_e, ge);
-            C = fmaf(ad, c, C);
+            const float2 S = f2fma(EIJ, SLJ, f2mul(QQ, Cv));
+            const float2 DSDR = f2fma(QQ, DC, DSLJDR);
+            const float2 AD = f2fma(GX, DX, f2fma(GY, DY, f2mul(GZ, DZ)));
+            const float2 RAD = sel2(c0, c1, make_float2(0.f, 0.f), f2mul(f2mul(DSDR, AD), RS));  // dS/dr (a.delta)/r
+            GPX = f2sub(GPX, f2fma(S, GX, f2mul(RAD, DX)));
+            GPY = f2sub(GPY, f2fma(S, GY, f2mul(RAD, DY)));
+            GPZ = f2sub(GPZ, f2fma(S, GZ, f2mul(RAD, DZ)));
+            GR = f2fma(AD, sel2(c0, c1, f2fma(DSDR, CF, DSLJDRR), DSLJDRR), GR);
+            GE = f2fma(AD, SLJ, GE);
+            CC = f2fma(AD, Cv, CC);
             if (kQuad) {
                 // Phi = A delta - 6 dz r^-5 z_hat, A = 15 dz^2 r^-7 - 3 r^-5 (cut off at rc)
-                const bool inq = !kCutoff || r2 < rc2;
-                const float ir5 = ir2 * ir2 * rs, ir7 = ir5 * ir2, dz2 = dz * dz;
-                const float A = inq ? fmaf(15.f * dz2, ir7, -3.f * ir5) : 0.f;
-                const float a6 = inq ? 6.f * dz * ir5 : 0.f;
-                Cq = fmaf(A, ad, fmaf(-a6, gb.z, Cq));  // a . Phi
+                const bool q0 = !kCutoff || R2v.x < rc2, q1 = !kCutoff || R2v.y < rc2;
+                const float2 z = make_float2(0.f, 0.f);
+                const float2 IR5 = f2mul(f2mul(IR2, IR2), RS), IR7 = f2mul(IR5, IR2), DZ2 = f2mul(DZ, DZ);
+                const float2 Aq = sel2(q0, q1, f2fma(f2mul(make_float2(15.f, 15.f), DZ2), IR7, f2mul(M3, IR5)), z);
+                const float2 A6 = sel2(q0, q1, f2mul(make_float2(6.f, 6.f), f2mul(DZ, IR5)), z);
+                CQ = f2fma(Aq, AD, f2fma(f2mul(make_float2(-1.f, -1.f), A6), GZ, CQ));  // a . Phi
                 // a . dPhi/dr at fixed delta, and the z row of a^T dPhi/d delta at fixed r
-                const float W = inq ? rs * fmaf(fmaf(-105.f * dz2, ir7, 15.f * ir5), ad, 30.f * dz * ir5 * gb.z) : 0.f;
-                const float zrow = inq ? fmaf(30.f * dz * ir7, ad, -6.f * ir5 * gb.z) : 0.f;
-                const float wr = clamped ? 0.f : W * rs;  // r follows delta unless floored
-                gpx = fmaf(-kqq, fmaf(A, gb.x, wr * dx), gpx);
-                gpy = fmaf(-kqq, fmaf(A, gb.y, wr * dy), gpy);
-                gpz = fmaf(-kqq, fmaf(A, gb.z, fmaf(wr, dz, zrow)), gpz);
-                if (clamped) gRr = fmaf(kqq * P.core_frac, W, gRr);
+                const float2 W = sel2(q0, q1,
+                                      f2mul(RS, f2fma(f2fma(f2mul(make_float2(-105.f, -105.f), DZ2), IR7,
+                                                            f2mul(make_float2(15.f, 15.f), IR5)),
+                                                      AD, f2mul(f2mul(make_float2(30.f, 30.f), DZ), f2mul(IR5, GZ)))),
+                                      z);
+                const float2 ZROW = sel2(q0, q1,
+                                         f2fma(f2mul(make_float2(30.f, 30.f), f2mul(DZ, IR7)), AD,
+                                               f2mul(f2mul(M6, IR5), GZ)),
+                                         z);
+                const float2 WR = sel2(c0, c1, z, f2mul(W, RS));  // r follows delta unless floored
+                const float2 MK = make_float2(-kqq, -kqq);
+                GPX = f2fma(MK, f2fma(Aq, GX, f2mul(WR, DX)), GPX);
+                GPY = f2fma(MK, f2fma(Aq, GY, f2mul(WR, DY)), GPY);
+                GPZ = f2fma(MK, f2fma(Aq, GZ, f2fma(WR, DZ, ZROW)), GPZ);
+                GR = sel2(c0, c1, f2fma(make_float2(kqq * P.core_frac, kqq * P.core_frac), W, GR), GR);
             }
         }
+        const float gpx = GPX.x + GPX.y, gpy = GPY.x + GPY.y, gpz = GPZ.x + GPZ.y;
+        const float gRr = GR.x + GR.y, ge = GE.x + GE.y, C = CC.x + CC.y, Cq = CQ.x + CQ.y;
         atomicAdd(P.gx + ia, gpx);
         atomicAdd(P.gy + ia, gpy);
         atomicAdd(P.gz + ia, gpz);
