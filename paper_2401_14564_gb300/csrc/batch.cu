@@ -264,6 +264,7 @@ __global__ void __launch_bounds__(kThreads, kMinCtas) batch_kernel(const BatchLa
         G.map.ay = {0, D.nx, 0, 0};
         G.map.az = {0, D.nx * D.ny, 0, 0};
         G.map.stored_nodes = (int64_t)D.nx * D.ny * D.nz;
+        G.map.interp = 0;
         G.inv_dx = 1.f / D.dx; G.inv_dy = 1.f / D.dy; G.inv_dz = 1.f / D.dz;
         G.gx0s = (float)(-(double)D.x0 / (double)D.dx);
         G.gy0s = (float)(-(double)D.y0 / (double)D.dy);
