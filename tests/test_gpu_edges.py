@@ -1,0 +1,67 @@
+"""Minimum-size and degenerate inputs of the GPU path against the FP64 oracle:
+a single pixel with exactly 2m+1 heights (one df value), FIRE with no
+iterations allowed, a grid two nodes high, and the smallest FFT grids.
+"""
+import copy
+
+import numpy as np
+import pytest
+import torch
+
+from helpers import case32
+from paper_2401_14564_gb300 import afm, pp, synth
+from test_gpu_fft import check as fft_check
+from test_gpu_fft import run as fft_run
+from test_gpu_relax import check_parity
+
+pytestmark = pytest.mark.gpu
+
+
+def test_single_pixel_with_the_minimum_number_of_heights(orc):
+    c = copy.deepcopy(synth.benzene_case())
+    m = pp.pp_df_margin(c["df"]["A_pp"], c["scan"]["dz"])
+    c["scan"] = dict(c["scan"], nx=1, ny=1, nz=2 * m + 1, x0=0.71, y0=-0.33)
+    c = case32(c)
+    fire = synth.parity_fire()
+    g = afm.afm(c, fire=fire)
+    o = orc.forward(c, fire=fire)
+    assert g["df"].shape == (1, 1, 1) and o["df"].shape == (1, 1, 1)
+    assert np.abs(g["pos"] - o["pos"]).max() <= 1e-3
+    # one df value: the image has no range, so the bar is 1e-3 of the value itself
+    assert abs(g["df"].item() - o["df"].item()) <= 1e-3 * abs(o["df"].item())
+
+
+def test_no_iterations_allowed_leaves_the_probe_at_rest(orc):
+    c = case32(synth.small_case(seed=4, n_atoms=9, nxy=24, nz=30, scan_px=9, nz_scan=11))
+    fire = synth.parity_fire(max_iter=0)
+    g = afm.afm(c, fire=fire)
+    assert (g["iters"] == 0).all()
+    o = orc.relax_scan(orc.make_ff(c["atoms"], c["probe"], c["grid"])[0], c["grid"], None, None, c["scan"],
+                       c["tip"], fire, polish_tol=0.0)
+    # no update: every height starts (and stays) at anchor + d0
+    s = c["scan"]
+    k, j, i = np.meshgrid(np.arange(s["nz"]), np.arange(s["ny"]), np.arange(s["nx"]), indexing="ij")
+    rest = np.stack([s["x0"] + i * s["px"], s["y0"] + j * s["py"], s["z_top"] - k * s["dz"] - c["tip"]["R0"]], -1)
+    assert np.abs(g["pos"] - rest).max() < 1e-5
+    assert np.abs(o["pos"] - rest).max() < 1e-12
+    assert np.abs(g["fz"]).max() < 1e-6
+
+
+def test_grid_two_nodes_high(orc):
+    # nz = 2: one cell in z, every probe position clamps into it (fractions clamped to [0, 1])
+    c = copy.deepcopy(synth.small_case(seed=5, n_atoms=8, nxy=24, nz=40, scan_px=8, nz_scan=11))
+    g = c["grid"]
+    c["grid"] = dict(g, nz=2, z0=g["z0"] + 1.5, dz=1.2)
+    # a weak image (about 2 Hz of range): FIRE is stopped at 1e-6 eV/A so that its stopping
+    # tolerance (positions within ftol / lambda) stays below the 1e-3-of-range df bar
+    check_parity(orc, c, fire=synth.parity_fire(ftol=1e-6, max_iter=20000))
+
+
+@pytest.mark.parametrize("shape", [(2, 2, 2), (2, 4, 8), (8, 2, 4)])
+def test_smallest_fft_grids(orc, shape):
+    g = {"nx": shape[0], "ny": shape[1], "nz": shape[2], "x0": 0.0, "y0": 0.0, "z0": 0.0, "dx": 0.4, "dy": 0.5,
+         "dz": 0.3, "periodic_xy": 1}
+    rng = np.random.default_rng(sum(shape))
+    f = rng.standard_normal((shape[2], shape[1], shape[0]))
+    t = rng.random((shape[2], shape[1], shape[0]))
+    fft_check(fft_run(f, t, g, scale=1.3), orc.correlate(f, t, g, scale=1.3))

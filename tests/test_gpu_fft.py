@@ -30,8 +30,11 @@ def run(f, g, grid, scale=1.0, power=1.0, ff=None, accumulate=False):
 
 
 def check(got, ref):
+    # a component that vanishes identically (an axis of length 2 has only its Nyquist mode, whose
+    # derivative is dropped) is measured against the field's largest component
+    floor = 1e-6 * np.abs(ref).max()
     for c in range(4):
-        scale = np.abs(ref[..., c]).max()
+        scale = max(np.abs(ref[..., c]).max(), floor)
         err = np.abs(got[..., c] - ref[..., c]).max() / scale
         assert err <= TOL, (c, err)
 

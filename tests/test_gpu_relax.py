@@ -29,9 +29,9 @@ def gpu_run(c, fire=None, layout=0, fused=True):
     return out
 
 
-def check_parity(orc, case, max_excluded_frac=0.02):
+def check_parity(orc, case, max_excluded_frac=0.02, fire=None):
     c = case32(case)
-    fire = synth.parity_fire()
+    fire = fire or synth.parity_fire()
     g = gpu_run(c, fire)
     o = orc.forward(c, fire=fire)
     assert o["ok"].all()
