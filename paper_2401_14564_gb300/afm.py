@@ -58,21 +58,22 @@ class Simulator:
         else:
             pp.pp_make_ff(pp.make_atoms(atoms_dev), self.probe, self.grid, self.ff, stream)
 
-    def relax(self, stream=None):
+    def relax(self, stream=None, df=None):
+        """Relaxed scan and df image (into `df`, default self.df)."""
+        out = self.df if df is None else df
         if self.fused_df:
             pp.pp_relax_scan(self.ff, self.grid, self.scan, self.tip, self.fire, self.pos, self.fz, self.iters,
-                             self.dfp, self.df, stream)
+                             self.dfp, out, stream)
         else:
             pp.pp_relax_scan(self.ff, self.grid, self.scan, self.tip, self.fire, self.pos, self.fz, self.iters,
                              None, None, stream)
-            pp.pp_fz_to_df(self.fz, self.scan.nz, self.scan.nx * self.scan.ny, self.scan.dz, self.dfp, self.df,
-                           stream)
+            pp.pp_fz_to_df(self.fz, self.scan.nz, self.scan.nx * self.scan.ny, self.scan.dz, self.dfp, out, stream)
 
-    def run(self, atoms_dev, stream=None):
+    def run(self, atoms_dev, stream=None, df=None):
         """Device-resident forward pass; returns the df tensor (device)."""
         self.make_ff(atoms_dev, stream)
-        self.relax(stream)
-        return self.df
+        self.relax(stream, df)
+        return self.df if df is None else df
 
     # ---- end to end from host memory
     def _host_buffers(self, n_atoms):
@@ -107,6 +108,67 @@ class Simulator:
             out.copy_(hb["df_h"])
             return out
         return hb["df_h"]
+
+    def host_outputs(self, n_items):
+        """n_items pinned host tensors shaped like the df image, for run_host_many(outs=...)."""
+        pin = torch.cuda.is_available()
+        return [torch.empty(tuple(self.df.shape), dtype=torch.float32, pin_memory=pin) for _ in range(n_items)]
+
+    def run_host_many(self, atoms_list, outs=None):
+        """Host df images for a sequence of host atom sets, end to end: every item's atoms go host ->
+        device and its df image device -> host, as in run_host.  The device-to-host copy of item k
+        runs on a second stream while item k+1 computes (two device df buffers), so the copies
+        overlap the neighbouring compute; the compute itself stays in order on the current stream.
+        outs: pinned host tensors to write (see host_outputs), else allocated here."""
+        n_items = len(atoms_list)
+        if n_items == 0:
+            return []
+        n = int(len(atoms_list[0]["x"]))
+        if any(int(len(a["x"])) != n for a in atoms_list):
+            raise ValueError("run_host_many: every item needs the same number of atoms")
+        cs = torch.cuda.current_stream()
+        if getattr(self, "_copy_stream", None) is None:
+            self._copy_stream = torch.cuda.Stream()
+        xs = self._copy_stream
+        pin = torch.cuda.is_available()
+        if getattr(self, "_pipe", None) is None or self._pipe["n"] != n:
+            self._pipe = {
+                "n": n,
+                "atoms_h": [torch.empty((6, n), dtype=torch.float32, pin_memory=pin) for _ in range(2)],
+                "atoms_d": [torch.empty((6, n), dtype=torch.float32, device=self.device) for _ in range(2)],
+                "df_d": [self.df, torch.empty_like(self.df)],
+            }
+        P = self._pipe
+        if outs is None:
+            outs = self.host_outputs(n_items)
+        elif len(outs) < n_items:
+            raise ValueError("run_host_many: fewer output buffers than items")
+        h2d_done = [None, None]
+        copy_done = [None, None]
+        for k, atoms_host in enumerate(atoms_list):
+            b = k & 1
+            if h2d_done[b] is not None:
+                h2d_done[b].synchronize()  # the staging buffer of item k-2 has been read
+            for r, key in enumerate(ATOM_KEYS):
+                P["atoms_h"][b][r].copy_(torch.from_numpy(np.asarray(atoms_host[key], dtype=np.float32)))
+            with torch.cuda.stream(cs):
+                P["atoms_d"][b].copy_(P["atoms_h"][b], non_blocking=True)
+                h2d_done[b] = torch.cuda.Event()
+                h2d_done[b].record(cs)
+                if copy_done[b] is not None:
+                    cs.wait_event(copy_done[b])  # item k-2's image has left this df buffer
+                dev = {key: P["atoms_d"][b][r] for r, key in enumerate(ATOM_KEYS)}
+                self.run(dev, cs, df=P["df_d"][b])
+                computed = torch.cuda.Event()
+                computed.record(cs)
+            xs.wait_event(computed)
+            with torch.cuda.stream(xs):
+                outs[k].copy_(P["df_d"][b], non_blocking=True)
+                copy_done[b] = torch.cuda.Event()
+                copy_done[b].record(xs)
+        xs.synchronize()
+        cs.synchronize()
+        return outs
 
     def h2d_bytes(self, n_atoms):
         return 6 * 4 * n_atoms

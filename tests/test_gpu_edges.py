@@ -65,3 +65,21 @@ def test_smallest_fft_grids(orc, shape):
     f = rng.standard_normal((shape[2], shape[1], shape[0]))
     t = rng.random((shape[2], shape[1], shape[0]))
     fft_check(fft_run(f, t, g, scale=1.3), orc.correlate(f, t, g, scale=1.3))
+
+
+def test_streamed_host_path_equals_one_call_per_item():
+    # run_host_many overlaps each item's copy-out with the next item's compute; the images must be
+    # those of run_host, item by item
+    c = case32(synth.small_case(seed=11, n_atoms=10, nxy=32, nz=36, scan_px=10, nz_scan=12))
+    items = []
+    for t in range(5):
+        a = copy.deepcopy(c["atoms"])
+        a["x"] = a["x"] + 0.07 * t
+        a["q"] = a["q"] * (1.0 - 0.1 * t)
+        items.append(a)
+    sim = afm.Simulator(c)
+    many = [o.clone() for o in sim.run_host_many(items)]
+    one = [sim.run_host(a).clone() for a in items]
+    for k in range(len(items)):
+        assert torch.equal(many[k], one[k]), k
+    assert not torch.equal(many[0], many[-1])
