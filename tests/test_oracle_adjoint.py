@@ -99,3 +99,31 @@ def test_grid_adjoint_touches_only_the_scanned_slab(orc):
     zmax = r["pos"][..., 2].max()
     gz = c["grid"]["z0"] + c["grid"]["dz"] * nz_touched
     assert gz.min() >= zmin - c["grid"]["dz"] - 1e-9 and gz.max() <= zmax + c["grid"]["dz"] + 1e-9
+
+
+def test_gradient_workload_adjoint_matches_central_differences_on_20_coordinates(orc):
+    """The 40-atom gradient workload (176x176x60 grid, 128x128x20 scan, loss sum(w df) with
+    w ~ N(0,1) seed 7): the oracle's grid-model adjoint against FP64 central differences of its
+    whole forward pass on 20 atom coordinates chosen with seed 11, h = 1e-4 A."""
+    c = synth.gradient_case()
+    fire = synth.parity_fire(ftol=1e-9, max_iter=20000)
+
+    def L(cc):
+        r = orc.forward(cc, fire=fire, polish_tol=1e-12)
+        assert r["ok"].all()
+        return float((c["w"] * r["df"]).sum()), r
+
+    _, r = L(c)
+    g = orc.backward(r["ff"], c["grid"], c["atoms"], c["probe"], c["scan"], c["tip"], c["df"], r["pos"], c["w"])
+    rng = np.random.default_rng(c["fd_seed"])
+    n = len(c["atoms"]["x"])
+    picks = rng.choice(3 * n, 20, replace=False)
+    h = 1e-4
+    an, fd = [], []
+    for p in picks:
+        ia, ax = int(p // 3), "xyz"[int(p % 3)]
+        fd.append((L(perturbed(c, ax, ia, h))[0] - L(perturbed(c, ax, ia, -h))[0]) / (2 * h))
+        an.append(g[ax][ia])
+    an, fd = np.array(an), np.array(fd)
+    # grid model: relaxed points that cross a cell face within +-h see the trilinear kink
+    assert np.abs(an - fd).max() < 1e-3 * np.abs(fd).max(), (an, fd)
