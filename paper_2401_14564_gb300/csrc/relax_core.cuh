@@ -61,6 +61,7 @@ __device__ __forceinline__ void relax_pixel(const G_t& P, const Q_t& Q, int i, i
     // Corner values of the cell holding the PP, reloaded only when the PP
     // changes cell (a converging PP rarely does after its first steps).
     float4 cv[8];
+    float ec[kTricubic ? 64 : 1];  // tricubic: the cached stencil energies
     int cell_x = -1, cell_y = -1, cell_z = -1;
     while (__any_sync(0xffffffffu, active)) {
         if (!active) continue;
@@ -69,7 +70,14 @@ __device__ __forceinline__ void relax_pixel(const G_t& P, const Q_t& Q, int i, i
         const Cells cl = locate(P, bx + e.x, by + e.y, (az + Q.d0z) + e.z);
         float3 Fs;
         if constexpr (kTricubic) {
-            Fs = tricubic_force(P.ffE, P.map, cl, P.inv_dx, P.inv_dy, P.inv_dz, P.periodic_xy);
+            // the 64 stencil energies stay in registers until the PP changes cell
+            if (cl.x.i0 != cell_x || cl.y.i0 != cell_y || cl.z.i0 != cell_z) {
+                tricubic_load(P.ffE, P.map, cl, P.periodic_xy, ec);
+                cell_x = cl.x.i0;
+                cell_y = cl.y.i0;
+                cell_z = cl.z.i0;
+            }
+            Fs = tricubic_eval(ec, cl, P.inv_dx, P.inv_dy, P.inv_dz);
         } else {
             if (cl.x.i0 != cell_x || cl.y.i0 != cell_y || cl.z.i0 != cell_z) {
                 load_corners<LAYOUT, kCoherent>(P.ff, P.map, cl, cv);
