@@ -44,7 +44,7 @@ TRAFFIC = {
                    "files": ["relax_scan.cu", "relax_core.cuh", "interp.cuh"]},
     "relax_scan_tricubic": {"bytes": 23.74e6, "sha": "32d2349880b0a507",
                             "files": ["relax_scan.cu", "relax_core.cuh", "interp.cuh"]},
-    "ff_assemble": {"bytes": 147.72e6, "sha": "8a5e7e112192e134",
+    "ff_assemble": {"bytes": 148.14e6, "sha": "7fa35941718ffa5e",
                     "files": ["ff_assemble.cu", "ff_core.cuh", "interp.cuh"]},
     "ff_assemble_quad": {"bytes": 148.37e6, "sha": "c55fc7410aa5e833",
                          "files": ["ff_assemble.cu", "ff_core.cuh", "interp.cuh"]},
