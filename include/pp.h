@@ -356,8 +356,9 @@ PP_API size_t pp_backward_noalloc_capacity(void);
  * eigenvalues ascending to eig[((k*ny + j)*nx + i)*3 + c] (eV/A^2) and, when
  * hw is not NULL, the mode energies hbar sqrt(lambda/m) in meV (0 where
  * lambda <= 0) for a probe mass of mass_amu atomic mass units.  The two
- * lower eigenvalues are the lateral modes the IETS signal follows.  Errors:
- * PP_ERR_ARG, PP_ERR_SHAPE, PP_ERR_UNSUPPORTED (interp = 1 grid), PP_ERR_CUDA. */
+ * lower eigenvalues are the lateral modes the IETS signal follows.  On a
+ * tricubic energy grid (interp = 1) F_S's Jacobian is minus the Hessian of the
+ * energy interpolant.  Errors: PP_ERR_ARG, PP_ERR_SHAPE, PP_ERR_CUDA. */
 PP_API pp_status pp_iets(const float* ff, const pp_grid* grid, const pp_scan* scan, const pp_tip* tip,
                          const float* pos, float mass_amu, float* eig, float* hw, pp_stream stream);
 

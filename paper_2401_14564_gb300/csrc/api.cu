@@ -445,7 +445,7 @@ pp_status pp_iets(const float* ff, const pp_grid* grid, const pp_scan* scan, con
     GridMap map;
     std::string why;
     if (!make_grid_map(grid, &map, &why)) { set_error("pp_iets: " + why); return PP_ERR_SHAPE; }
-    if (map.interp) { set_error("pp_iets: tricubic (energy) grids are not supported"); return PP_ERR_UNSUPPORTED; }
+
     if (scan->nx < 1 || scan->ny < 1 || scan->nz < 1 ||
         (int64_t)scan->nx * scan->ny * scan->nz * 3 >= (int64_t(1) << 31)) {
         set_error("pp_iets: invalid scan size");
@@ -456,7 +456,8 @@ pp_status pp_iets(const float* ff, const pp_grid* grid, const pp_scan* scan, con
     if (!check_tip_fire(tip, &dummy, &why)) { set_error("pp_iets: " + why); return PP_ERR_ARG; }
     IetsLaunch L;
     std::memset(&L, 0, sizeof(L));
-    L.ff = reinterpret_cast<const float4*>(ff);
+    L.ff = map.interp ? nullptr : reinterpret_cast<const float4*>(ff);
+    L.ffE = map.interp ? ff : nullptr;
     L.map = map;
     L.layout = grid->layout;
     L.inv_dx = 1.f / grid->dx; L.inv_dy = 1.f / grid->dy; L.inv_dz = 1.f / grid->dz;

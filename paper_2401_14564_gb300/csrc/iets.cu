@@ -3,6 +3,7 @@
 // curvature of the tip-sample potential; per relaxed point this kernel forms
 // the stiffness K = -(J + J^T)/2, J = dG/dp = tip-spring Jacobian + exact
 // Jacobian of the trilinear force interpolant (the same J the adjoint uses),
+// or, on a tricubic energy grid, minus the Hessian of the energy interpolant,
 // and writes its three eigenvalues ascending (cyclic Jacobi rotations, FP32)
 // and the mode energies hbar sqrt(lambda/m).
 #include "interp.cuh"
@@ -33,7 +34,7 @@ __device__ __forceinline__ void jacobi_rotate(float a[3][3], int p, int q) {
     }
 }
 
-template <int LAYOUT>
+template <int LAYOUT, bool kTricubic>
 __global__ void __launch_bounds__(kThreads) iets_kernel(const IetsLaunch P) {
     const int npix = P.snx * P.sny;
     const int64_t total = (int64_t)npix * P.snz;
@@ -52,10 +53,16 @@ __global__ void __launch_bounds__(kThreads) iets_kernel(const IetsLaunch P) {
     const float ar = -P.kR * __fdividef(q, fmaf(P.R0, dn, d2));  // -kR (1 - R0/|d|)
     const float br = -P.kR * P.R0 * rs * rs * rs;                // -kR R0 / |d|^3
     const Cells cl = locate(P, px, py, pz);
-    float4 v[8];
-    load_corners<LAYOUT>(P.ff, P.map, cl, v);
     float J[3][3];
-    trilinear_jacobian(v, cl, P.inv_dx, P.inv_dy, P.inv_dz, J);
+    if constexpr (kTricubic) {
+        float ec[64];
+        tricubic_load(P.ffE, P.map, cl, P.periodic_xy, ec);
+        tricubic_jacobian(ec, cl, P.inv_dx, P.inv_dy, P.inv_dz, J);
+    } else {
+        float4 v[8];
+        load_corners<LAYOUT>(P.ff, P.map, cl, v);
+        trilinear_jacobian(v, cl, P.inv_dx, P.inv_dy, P.inv_dz, J);
+    }
     const float dd[3] = {dx, dy, dz};
     float a[3][3];
 #pragma unroll
@@ -90,8 +97,9 @@ __global__ void __launch_bounds__(kThreads) iets_kernel(const IetsLaunch P) {
 cudaError_t launch_iets(const IetsLaunch& L, cudaStream_t s) {
     const int64_t total = (int64_t)L.snx * L.sny * L.snz;
     const int blocks = (int)((total + kThreads - 1) / kThreads);
-    if (L.layout == 0) iets_kernel<0><<<blocks, kThreads, 0, s>>>(L);
-    else iets_kernel<1><<<blocks, kThreads, 0, s>>>(L);
+    if (L.map.interp == 1) iets_kernel<0, true><<<blocks, kThreads, 0, s>>>(L);
+    else if (L.layout == 0) iets_kernel<0, false><<<blocks, kThreads, 0, s>>>(L);
+    else iets_kernel<1, false><<<blocks, kThreads, 0, s>>>(L);
     return cudaGetLastError();
 }
 

@@ -198,6 +198,61 @@ __device__ __forceinline__ void tricubic_load(const float* __restrict__ E, const
             for (int a = 0; a < 4; ++a) ec[(cz * 4 + b) * 4 + a] = __ldg(E + zo[cz] + yo[b] + xo[a]);
 }
 
+// Second derivatives in t of the cubic convolution weights.
+__device__ __forceinline__ void cr_weights2(float t, float d2w[4]) {
+    d2w[0] = fmaf(-3.f, t, 2.f);   // (-6t + 4)/2
+    d2w[1] = fmaf(9.f, t, -5.f);   // (18t - 10)/2
+    d2w[2] = fmaf(-9.f, t, 4.f);   // (-18t + 8)/2
+    d2w[3] = fmaf(3.f, t, -1.f);   // (6t - 2)/2
+}
+
+// Exact Jacobian J[a][b] = dF_a/dp_b = -d2E/dp_a dp_b of the tricubic interpolant from the
+// stencil energies (symmetric; zero rows/columns along axes whose fraction is clamped).
+__device__ __forceinline__ void tricubic_jacobian(const float ec[64], const Cells& c, float inv_dx, float inv_dy,
+                                                  float inv_dz, float J[3][3]) {
+    float wx[4], dwx[4], ddx[4], wy[4], dwy[4], ddy[4], wz[4], dwz[4], ddz[4];
+    cr_weights(c.x.t, wx, dwx);
+    cr_weights(c.y.t, wy, dwy);
+    cr_weights(c.z.t, wz, dwz);
+    cr_weights2(c.x.t, ddx);
+    cr_weights2(c.y.t, ddy);
+    cr_weights2(c.z.t, ddz);
+    // H_ab from row sums R0 = sum wx e, R1 = sum dwx e, R2 = sum ddx e, then along y and z
+    float hxx = 0.f, hyy = 0.f, hzz = 0.f, hxy = 0.f, hxz = 0.f, hyz = 0.f;
+#pragma unroll
+    for (int cz = 0; cz < 4; ++cz) {
+        float s00 = 0.f, s01 = 0.f, s02 = 0.f, s10 = 0.f, s11 = 0.f, s20 = 0.f;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const float* e = ec + (cz * 4 + b) * 4;
+            float r0 = 0.f, r1 = 0.f, r2 = 0.f;
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                r0 = fmaf(wx[a], e[a], r0);
+                r1 = fmaf(dwx[a], e[a], r1);
+                r2 = fmaf(ddx[a], e[a], r2);
+            }
+            s00 = fmaf(wy[b], r0, s00);
+            s01 = fmaf(dwy[b], r0, s01);
+            s02 = fmaf(ddy[b], r0, s02);
+            s10 = fmaf(wy[b], r1, s10);
+            s11 = fmaf(dwy[b], r1, s11);
+            s20 = fmaf(wy[b], r2, s20);
+        }
+        hxx = fmaf(wz[cz], s20, hxx);
+        hyy = fmaf(wz[cz], s02, hyy);
+        hzz = fmaf(ddz[cz], s00, hzz);
+        hxy = fmaf(wz[cz], s11, hxy);
+        hxz = fmaf(dwz[cz], s10, hxz);
+        hyz = fmaf(dwz[cz], s01, hyz);
+    }
+    const float sx = c.x.dtdf * inv_dx, sy = c.y.dtdf * inv_dy, sz = c.z.dtdf * inv_dz;
+    J[0][0] = -hxx * sx * sx; J[1][1] = -hyy * sy * sy; J[2][2] = -hzz * sz * sz;
+    J[0][1] = J[1][0] = -hxy * sx * sy;
+    J[0][2] = J[2][0] = -hxz * sx * sz;
+    J[1][2] = J[2][1] = -hyz * sy * sz;
+}
+
 // F = -grad E of the tricubic interpolant from the cached stencil energies (see tricubic_force).
 __device__ __forceinline__ float3 tricubic_eval(const float ec[64], const Cells& c, float inv_dx, float inv_dy,
                                                 float inv_dz) {

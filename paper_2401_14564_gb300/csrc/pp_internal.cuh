@@ -172,7 +172,8 @@ size_t fft_workspace_bytes(int nx, int ny, int nz);
 cudaError_t launch_fft_correlate(const FftLaunch& L, cudaStream_t s);
 
 struct IetsLaunch {
-    const float4* ff;
+    const float4* ff;   // map.interp == 0
+    const float* ffE;   // map.interp == 1
     GridMap map;
     int layout;
     float gx0s, gy0s, gz0s, inv_dx, inv_dy, inv_dz;

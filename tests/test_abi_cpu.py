@@ -106,10 +106,17 @@ def test_tricubic_grids_are_validated_on_host(L):
     assert pp.pp_ff_floats(g) == 0
     g.interp = 1
     fake = C.c_void_p(16)  # never dereferenced: the grid check fails first
+    atoms = pp.Atoms(0, None, None, None, None, None, None)
+    probe = pp.make_probe({"R_pp": 1.66, "eps_pp": 0.0091, "Q": -0.1, "coul_rc": 0.0, "min_image": 0,
+                           "core_frac": 0.5})
     scan = pp.make_scan({"nx": 4, "ny": 4, "nz": 12, "x0": 0.0, "y0": 0.0, "px": 0.1, "py": 0.1, "z_top": 0.3,
                          "dz": 0.1})
     tip = pp.make_tip({"kx": 0.25, "ky": 0.25, "kR": 20.0, "R0": 4.0, "d0x": 0.0, "d0y": 0.0})
-    assert L.pp_iets(fake, C.byref(g), C.byref(scan), C.byref(tip), fake, C.c_float(16.0), fake, None, None) == 6
+    dfp = pp.DF(1.0, 1800.0, 30300.0)
+    grads = pp.Grads(*([16] * 7))
+    # the adjoint takes trilinear force grids only: refused before anything is read or launched
+    assert L.pp_backward(C.byref(atoms), C.byref(probe), C.byref(g), fake, C.byref(scan), C.byref(tip),
+                         C.byref(dfp), fake, fake, C.byref(grads), fake, 1 << 30, None) == 6
     assert b"tricubic" in L.pp_last_error()
     lin = pp.make_grid({"nx": 10, "ny": 6, "nz": 5, "x0": 0, "y0": 0, "z0": 0, "dx": 0.1, "dy": 0.1, "dz": 0.1,
                         "periodic_xy": 1})

@@ -58,3 +58,17 @@ def test_at_rest_eigenvalues_are_the_springs(orc):
     want = np.sort(np.array([c["tip"]["kx"], c["tip"]["ky"], c["tip"]["kR"]]) * nm)
     np.testing.assert_allclose(eig.cpu().numpy().reshape(-1, 3), np.broadcast_to(want, (pos.size // 3, 3)),
                                rtol=2e-5)
+
+
+def test_tricubic_grid_iets_matches_oracle(orc):
+    # on an energy grid the sample part of the stiffness is the Hessian of the tricubic
+    # interpolant: continuous across cell faces, so every point is compared
+    c = case32(synth.benzene_case())
+    c["grid"] = dict(c["grid"], interp=1)
+    o = orc.forward(c)
+    pos = o["pos"].astype(np.float32).astype(np.float64)
+    ref, ref_hw = orc.iets(o["ff"], c["grid"], None, None, c["scan"], c["tip"], pos)
+    got, got_hw = gpu_iets(c, pos)
+    assert np.abs(got - ref).max() <= 1e-4, np.abs(got - ref).max()
+    stiff = ref > 1e-3
+    assert (np.abs(got_hw - ref_hw) / np.maximum(ref_hw, 1e-12))[stiff].max() <= 1e-3
