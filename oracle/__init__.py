@@ -281,7 +281,8 @@ def fz_to_df(fz, dz, df):
 
 
 def backward(ff, grid, atoms, probe, scan, tip, df, pos, g_df, want_grid_adj=False, nthreads=0):
-    """Gradient of sum(g_df * df) by the implicit adjoint.  ff=None -> grid-free model."""
+    """Gradient of sum(g_df * df) by the implicit adjoint.  ff=None -> grid-free model.
+    grid_adj is dL/dF_g [nz][ny][nx][3] on a force grid and dL/dE_g [nz][ny][nx] on an energy grid."""
     keep = _Keep()
     pos = _d(pos)
     g_df = _d(g_df)
@@ -299,6 +300,8 @@ def backward(ff, grid, atoms, probe, scan, tip, df, pos, g_df, want_grid_adj=Fal
                            nthreads)
     if rc:
         raise ValueError("or_backward rejected its arguments")
+    if gadj is not None and grid.get("interp", 0) == 1:
+        gadj = gadj[..., 0].copy()
     return {"x": grads[:, 0], "y": grads[:, 1], "z": grads[:, 2], "R": grads[:, 3], "eps": grads[:, 4],
             "q": grads[:, 5], "kx": gtip[0], "ky": gtip[1], "kR": gtip[2], "Q": gtip[3], "Qzz": gtip[4], "grid_adj": gadj}
 

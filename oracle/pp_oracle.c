@@ -116,6 +116,14 @@ typedef struct {
     double eq;          /* energy */
     double dPhi[9];     /* dPhi_a / d delta_b, the floored r held fixed when clamped */
     double dPhi_dr[3];  /* dPhi_a / dr at fixed delta */
+    /* energy derivatives (adjoint of an energy grid): LJ + Coulomb part, then the quadrupole's
+     * per unit k_e q_i Qzz / 2; inside the floor r is the floor radius, constant in delta */
+    double E_lj_e;      /* LJ energy per unit e_iPP */
+    double E_el_qq;     /* Coulomb energy per unit k_e Q q_i */
+    double dE_dd[3];    /* dE / d delta */
+    double dE_dR;       /* dE / dR_iPP */
+    double deq_dd[3];   /* d eq / d delta */
+    double deq_dr;      /* d eq / dr at fixed delta */
 } or_pair;
 
 /* Quadrupole pair term as a function of delta and r (r = |delta| unless floored):
@@ -133,6 +141,14 @@ static void quad_eval(const double d[3], double r, int clamped, or_pair* o) {
         for (int b = 0; b < 3; ++b) o->dPhi[a * 3 + b] = (a == b ? A : 0.0);
     for (int a = 0; a < 3; ++a) o->dPhi[a * 3 + 2] += 30.0 * dz * d[a] / r7;
     o->dPhi[2 * 3 + 2] -= 6.0 / r5;
+    /* energy: eq = 3 dz^2 / r^5 - 1 / r^3 */
+    o->deq_dr = -15.0 * dz * dz / (r5 * r) + 3.0 / (r2 * r2);
+    if (clamped) {
+        o->deq_dd[0] = o->deq_dd[1] = 0.0;
+        o->deq_dd[2] = 6.0 * dz / r5;
+    } else {
+        for (int a = 0; a < 3; ++a) o->deq_dd[a] = -o->Phi[a];
+    }
     /* dPhi/dr at fixed delta */
     const double dA = -105.0 * dz * dz / (r7 * r) + 15.0 / (r5 * r);
     for (int a = 0; a < 3; ++a) o->dPhi_dr[a] = dA * d[a];
@@ -168,31 +184,45 @@ static void pair_eval(const or_atoms* A, int i, const or_probe* P, double Lx, do
     const double dSlj_dr = 12.0 * eij * (-14.0 * s12 + 8.0 * s6) / (r * r * r);
     const double dSlj_dR = 12.0 * eij * (12.0 * s12 - 6.0 * s6) / (Rij * r * r);
     /* E_el = qq / r (optionally shifted-force truncated at rc) */
-    double c, e_el, dc_dr;
+    double c, e_el, dc_dr, de_dr;
     if (P->coul_rc > 0.0) {
         const double rc = P->coul_rc;
         if (r < rc) {
             c = 1.0 / (r * r * r) - 1.0 / (rc * rc * r);
             e_el = 1.0 / r - 1.0 / rc + (r - rc) / (rc * rc);
             dc_dr = -3.0 / (r * r * r * r) + 1.0 / (rc * rc * r * r);
+            de_dr = -1.0 / (r * r) + 1.0 / (rc * rc);
         } else {
-            c = 0.0; e_el = 0.0; dc_dr = 0.0;
+            c = 0.0; e_el = 0.0; dc_dr = 0.0; de_dr = 0.0;
         }
     } else {
         c = 1.0 / (r * r * r);
         e_el = 1.0 / r;
         dc_dr = -3.0 / (r * r * r * r);
+        de_dr = -1.0 / (r * r);
     }
     o->S_el_qq = c;
     o->S = eij * o->S_lj_e + qq * c;
     o->E = E_lj + qq * e_el;
+    o->E_lj_e = s12 - 2.0 * s6;
+    o->E_el_qq = e_el;
+    if (o->clamped) {
+        /* r = core_frac R_iPP: the LJ energy is the constant e (cf^-12 - 2 cf^-6) */
+        o->dE_dd[0] = o->dE_dd[1] = o->dE_dd[2] = 0.0;
+        o->dE_dR = qq * de_dr * P->core_frac;
+    } else {
+        for (int a = 0; a < 3; ++a) o->dE_dd[a] = -o->S * o->d[a];  /* F = -grad E */
+        o->dE_dR = 12.0 * eij * (s12 - s6) / Rij;
+    }
     if (P->Qzz != 0.0 && !(P->coul_rc > 0.0 && r >= P->coul_rc)) {
         quad_eval(o->d, r, o->clamped, o);
     } else {
         memset(o->Phi, 0, sizeof o->Phi);
         memset(o->dPhi, 0, sizeof o->dPhi);
         memset(o->dPhi_dr, 0, sizeof o->dPhi_dr);
+        memset(o->deq_dd, 0, sizeof o->deq_dd);
         o->eq = 0.0;
+        o->deq_dr = 0.0;
     }
     o->dSdr = dSlj_dr + qq * dc_dr;
     o->dSdR = dSlj_dR + (o->clamped ? o->dSdr * P->core_frac : 0.0);
@@ -296,7 +326,7 @@ static void interp_tricubic(const double* ff, const or_grid* G, const double p[3
 
 static void interp(const double* ff, const or_grid* G, const double p[3], double F[3], double* J,
                    long node[8], double w8[8]) {
-    if (G->interp == 1) {  /* no corner list: the grid-mode adjoint is trilinear only */
+    if (G->interp == 1) {  /* energy grid: no corner list */
         interp_tricubic(ff, G, p, NULL, F, J);
         return;
     }
@@ -801,21 +831,59 @@ static void pair_grad(const or_pair* p, const or_atoms* A, int i, const or_probe
     }
 }
 
+/* Accumulate eb * dE/d(theta_i) for one pair into the per-atom gradients (energy grids). */
+static void pair_grad_energy(const or_pair* p, const or_atoms* A, int i, const or_probe* P, double eb, double* g,
+                             double* gQ, double* gQzz) {
+    const double cq = 0.5 * OR_KE * P->Qzz * A->q[i];
+    for (int m = 0; m < 3; ++m) g[m] -= eb * (p->dE_dd[m] + cq * p->deq_dd[m]);  /* d delta / d r_i = -I */
+    g[3] += eb * (p->dE_dR + (p->clamped ? cq * p->deq_dr * P->core_frac : 0.0));
+    if (p->e_ij > 0.0) g[4] += eb * p->E_lj_e * P->eps_pp / (2.0 * p->e_ij);
+    g[5] += eb * (OR_KE * P->Q * p->E_el_qq + 0.5 * OR_KE * P->Qzz * p->eq);
+    *gQ += eb * OR_KE * A->q[i] * p->E_el_qq;
+    *gQzz += eb * 0.5 * OR_KE * A->q[i] * p->eq;
+}
+
+/* The 64 stencil nodes of the tricubic interpolant at p and the gradients in p of their
+ * weights, grad w_g(p) (zero along an axis whose fraction is clamped). */
+static void tricubic_grad_weights(const or_grid* G, const double p[3], long node[64], double gw[64][3]) {
+    long ix[4], iy[4], iz[4];
+    double tx, ty, tz, sx, sy, sz;
+    axis_stencil(p[0], G->x0, G->dx, G->nx, G->periodic_xy, ix, &tx, &sx);
+    axis_stencil(p[1], G->y0, G->dy, G->ny, G->periodic_xy, iy, &ty, &sy);
+    axis_stencil(p[2], G->z0, G->dz, G->nz, 0, iz, &tz, &sz);
+    double wx[4], dwx[4], d2wx[4], wy[4], dwy[4], d2wy[4], wz[4], dwz[4], d2wz[4];
+    cr_weights(tx, wx, dwx, d2wx);
+    cr_weights(ty, wy, dwy, d2wy);
+    cr_weights(tz, wz, dwz, d2wz);
+    int q = 0;
+    for (int c = 0; c < 4; ++c)
+        for (int b = 0; b < 4; ++b)
+            for (int a = 0; a < 4; ++a, ++q) {
+                node[q] = (iz[c] * G->ny + iy[b]) * G->nx + ix[a];
+                gw[q][0] = dwx[a] * wy[b] * wz[c] * sx;
+                gw[q][1] = wx[a] * dwy[b] * wz[c] * sy;
+                gw[q][2] = wx[a] * wy[b] * dwz[c] * sz;
+            }
+}
+
 /* Gradient of L = sum_c sum_pix g_df[c][pix] * df[c][pix] with respect to the
  * atoms (x, y, z, q, R, eps) and the tip (kx, ky, kR in per N/m, Q), by the
  * implicit function theorem at the relaxed positions pos[nz][ny][nx][3]:
  *   g_Fz = K^T g_df;  J^T lambda = g_Fz grad_p Fz;
  *   dL/dtheta = g_Fz dFz/dtheta - lambda . dG/dtheta.
  * Grid mode (ff != NULL): the grid adjoint Gbar_g = -sum lambda w_g(p*) is
- * contracted with the pair derivatives of every node value.  Direct mode:
+ * contracted with the pair derivatives of every node value; on a tricubic
+ * energy grid the node values are energies, F_S = -sum_g E_g grad w_g, and
+ * the grid adjoint is the scalar Ebar_g = sum lambda . grad w_g(p*),
+ * contracted with the pair energies' derivatives.  Direct mode:
  * the pair derivatives are taken at p* itself.
- * gtip = {dL/dkx, dL/dky, dL/dkR, dL/dQ, dL/dQzz}.  grid_adj (optional) gets Gbar [nz][ny][nx][3]. */
+ * gtip = {dL/dkx, dL/dky, dL/dkR, dL/dQ, dL/dQzz}.  grid_adj (optional) gets Gbar [nz][ny][nx][3]
+ * (on an energy grid Ebar in component 0, the others zero). */
 int or_backward(const double* ff, const or_grid* G, const or_atoms* A, const or_probe* P,
                 const or_scan* S, const or_tip* T, const or_df* D, const double* pos,
                 const double* g_df, double* grads /*[n][6]*/, double* gtip, double* grid_adj,
                 int nthreads) {
     if (!G || !A || !P || !S || !T || !D || !pos || !g_df || !grads || !gtip) return 1;
-    if (ff && G->interp == 1) return 2;  /* grid-mode adjoint: trilinear force grids only */
     set_threads(nthreads);
     or_model M;
     M.ff = ff; M.G = G; M.A = A; M.P = P;
@@ -867,7 +935,13 @@ int or_backward(const double* ff, const or_grid* G, const or_atoms* A, const or_
             gkx += l[0] * (d[0] - t->d0x);
             gky += l[1] * (d[1] - t->d0y);
             gkR += gf * (dn - t->R0) * d[2] / dn + (l[0] * d[0] + l[1] * d[1] + l[2] * d[2]) * (dn - t->R0) / dn;
-            if (gbar) {
+            if (gbar && G->interp == 1) {
+                /* F_S = -sum_g E_g grad w_g: dL/dE_g = -lambda . (-grad w_g) */
+                long node[64];
+                double gw[64][3];
+                tricubic_grad_weights(G, p, node, gw);
+                for (int q = 0; q < 64; ++q) gbar[3 * node[q]] += l[0] * gw[q][0] + l[1] * gw[q][1] + l[2] * gw[q][2];
+            } else if (gbar) {
                 long node[8];
                 double w8[8], F[3];
                 interp(ff, G, p, F, NULL, node, w8);
@@ -894,7 +968,10 @@ int or_backward(const double* ff, const or_grid* G, const or_atoms* A, const or_
                 const double r[3] = {G->x0 + ii * G->dx, G->y0 + jj * G->dy, G->z0 + kk * G->dz};
                 or_pair pr;
                 pair_eval(A, ia, P, M.Lx, M.Ly, r, &pr);
-                pair_grad(&pr, A, ia, P, av, g, &gQ, &gQzz);
+                if (G->interp == 1)
+                    pair_grad_energy(&pr, A, ia, P, av[0], g, &gQ, &gQzz);
+                else
+                    pair_grad(&pr, A, ia, P, av, g, &gQ, &gQzz);
             }
         } else {
             for (long o = 0; o < (long)nz * npix; ++o) {

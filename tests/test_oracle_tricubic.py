@@ -14,7 +14,10 @@ oracle's formula by:
   - F = -grad E and J = dF/dp by central differences of the interpolant;
   - periodicity in x and y;
   - convergence to the grid-free model at second order in the spacing, and
-    the relaxed scan converging to the grid-free relaxed scan.
+    the relaxed scan converging to the grid-free relaxed scan;
+  - the adjoint on an energy grid (atom, tip and charge gradients and the
+    node-energy adjoint) against central differences of the whole forward
+    pass, the charge scaling identity and a rigid shift of all atoms.
 """
 import numpy as np
 import pytest
@@ -184,3 +187,107 @@ def test_relaxed_scan_converges_to_the_grid_free_scan(orc):
         errs.append(np.abs(r["pos"] - free["pos"]).max())
     order = np.polyfit(np.log(hs), np.log(errs), 1)[0]
     assert errs[-1] < 1e-3 and order > 1.8, (errs, order)
+
+
+def energy_grid_case(qzz=0.0):
+    from test_oracle_adjoint import tiny_case
+
+    c = tiny_case()
+    c["grid"] = dict(c["grid"], interp=1)
+    c["probe"] = dict(c["probe"], Qzz=qzz)
+    return c
+
+
+E_PARAMS = [("x", 0, 1e-4), ("y", 2, 1e-4), ("z", 1, 1e-4), ("z", 4, 1e-4), ("q", 3, 1e-4), ("R", 5, 1e-4),
+            ("eps", 0, 1e-6), ("kx", None, 1e-4), ("ky", None, 1e-4), ("kR", None, 1e-3), ("Q", None, 1e-4),
+            ("Qzz", None, 1e-4)]
+
+
+def _perturbed(c, what, idx, h):
+    import copy
+
+    c2 = copy.deepcopy(c)
+    if what in ("x", "y", "z", "q", "R", "eps"):
+        c2["atoms"][what] = c2["atoms"][what].copy()
+        c2["atoms"][what][idx] += h
+    elif what in ("Q", "Qzz"):
+        c2["probe"][what] += h
+    else:
+        c2["tip"][what] += h
+    return c2
+
+
+def _loss(orc, c):
+    r = orc.forward(c, polish_tol=1e-13)
+    assert r["ok"].all()
+    return float((c["w"] * r["df"]).sum()), r
+
+
+@pytest.mark.parametrize("qzz", [0.0, -0.05])
+def test_energy_grid_adjoint_matches_central_differences(orc, qzz):
+    # the interpolated force is C1 but its Jacobian jumps on cell faces, so a relaxed point that
+    # crosses a face within +-h leaves an O(h) difference error: bar 1e-4 of the gradient's scale
+    c = energy_grid_case(qzz)
+    _, r = _loss(orc, c)
+    g = orc.backward(r["ff"], c["grid"], c["atoms"], c["probe"], c["scan"], c["tip"], c["df"], r["pos"], c["w"])
+    an, fd = [], []
+    for what, idx, h in E_PARAMS:
+        if what == "Qzz" and qzz == 0.0:
+            continue
+        fd.append((_loss(orc, _perturbed(c, what, idx, h))[0] - _loss(orc, _perturbed(c, what, idx, -h))[0]) / (2 * h))
+        an.append(g[what][idx] if idx is not None else g[what])
+    an, fd = np.array(an), np.array(fd)
+    assert np.abs(an - fd).max() < 1e-4 * np.abs(fd).max(), (an, fd)
+
+
+def test_energy_grid_adjoint_of_node_energies_matches_central_differences(orc):
+    # dL/dE_g for nodes the relaxed scan reads: perturb one node energy, re-relax, re-image
+    c = energy_grid_case()
+    _, r = _loss(orc, c)
+    g = orc.backward(r["ff"], c["grid"], c["atoms"], c["probe"], c["scan"], c["tip"], c["df"], r["pos"], c["w"],
+                     want_grid_adj=True)
+    adj = g["grid_adj"]
+    assert adj.shape == (c["grid"]["nz"], c["grid"]["ny"], c["grid"]["nx"])
+    flat = np.argsort(-np.abs(adj).ravel())[:6]
+
+    def L(ff):
+        rr = orc.relax_scan(ff, c["grid"], c["atoms"], c["probe"], c["scan"], c["tip"], c["fire"], 1e-13)
+        return float((c["w"] * orc.fz_to_df(rr["fz"], c["scan"]["dz"], c["df"])).sum())
+
+    # one node's energy moves the soft-spring probe by ~(h / dx) / k: the difference is taken at
+    # h = 1e-6 eV, where its O(h^2) error is below 1e-5 of the value
+    h = 1e-6
+    for f in flat:
+        k, j, i = np.unravel_index(f, adj.shape)
+        fp, fm = r["ff"].copy(), r["ff"].copy()
+        fp[k, j, i, 3] += h
+        fm[k, j, i, 3] -= h
+        fd = (L(fp) - L(fm)) / (2 * h)
+        assert adj[k, j, i] == pytest.approx(fd, rel=5e-5), (k, j, i)
+
+
+def test_energy_grid_charge_scaling_identity(orc):
+    # the energy is linear in each product q_i Q and q_i Qzz, so sum_i q_i dL/dq_i = Q dL/dQ + Qzz dL/dQzz
+    c = energy_grid_case(-0.05)
+    _, r = _loss(orc, c)
+    g = orc.backward(r["ff"], c["grid"], c["atoms"], c["probe"], c["scan"], c["tip"], c["df"], r["pos"], c["w"])
+    lhs = float((c["atoms"]["q"] * g["q"]).sum())
+    assert lhs == pytest.approx(c["probe"]["Q"] * g["Q"] + c["probe"]["Qzz"] * g["Qzz"], rel=1e-10)
+
+
+def test_energy_grid_adjoint_along_a_rigid_shift_of_all_atoms(orc):
+    # the directional derivative along moving every atom by the same dx is sum_i dL/dx_i
+    c = energy_grid_case()
+    _, r = _loss(orc, c)
+    g = orc.backward(r["ff"], c["grid"], c["atoms"], c["probe"], c["scan"], c["tip"], c["df"], r["pos"], c["w"])
+    h = 1e-4
+
+    def shifted(s):
+        import copy
+
+        c2 = copy.deepcopy(c)
+        c2["atoms"]["x"] = c2["atoms"]["x"] + s
+        return c2
+
+    fd = (_loss(orc, shifted(h))[0] - _loss(orc, shifted(-h))[0]) / (2 * h)
+    assert g["x"].sum() == pytest.approx(fd, rel=1e-4, abs=1e-4 * np.abs(g["x"]).max())
