@@ -335,11 +335,11 @@ def measure_quadrupole(case, tuning, steps, warmup, flush, alu_peak):
 
 def measure_tricubic(case, steps, warmup, flush):
     """The line's workload on tricubic energy grids (one float per node, F = -grad of the tricubic
-    interpolant): at the same 0.1 A spacing and at 0.2 A (8x fewer nodes); FF and relaxed scan
-    (fused df) times by CUDA events, L2 flushed, grid bytes."""
+    interpolant): at the same 0.1 A spacing and at 0.2 A (8x fewer nodes); FF, relaxed scan
+    (fused df) and adjoint (pp_backward) times by CUDA events, L2 flushed, grid bytes."""
     import torch
 
-    from paper_2401_14564_gb300 import afm
+    from paper_2401_14564_gb300 import afm, pp
 
     out = []
     g0 = case["grid"]
@@ -349,31 +349,47 @@ def measure_tricubic(case, steps, warmup, flush):
         tcase = dict(case, grid=g)
         sim = afm.Simulator(tcase)
         atoms = afm.atoms_to_device(tcase["atoms"])
+        n = len(tcase["atoms"]["x"])
+        grads = {k: torch.empty(n, device="cuda") for k in ("x", "y", "z", "q", "R", "eps")}
+        grads["tip"] = torch.empty(5, device="cuda")
+        ws = torch.empty(pp.pp_backward_workspace(sim.grid) // 4 + 1, dtype=torch.float32, device="cuda")
+        w = torch.randn(tuple(sim.df.shape), generator=torch.Generator().manual_seed(7)).to("cuda")
+        pa, pg = pp.make_atoms(atoms), pp.make_grads(grads)
+
+        def bwd():
+            pp.pp_backward(pa, sim.probe, sim.grid, sim.ff, sim.scan, sim.tip, sim.dfp, sim.pos, w, pg, ws)
+
         for _ in range(max(warmup, 3)):
             sim.run(atoms)
+            bwd()
         stream = torch.cuda.current_stream()
-        t_ff, t_rx = [], []
+        t_ff, t_rx, t_bw = [], [], []
         for _ in range(steps):
             flush.zero_()
-            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0, e1, e2, e3, e4 = (torch.cuda.Event(enable_timing=True) for _ in range(5))
             e0.record(stream)
             sim.make_ff(atoms)
             e1.record(stream)
             sim.relax()
             e2.record(stream)
+            flush.zero_()
+            e3.record(stream)
+            bwd()
+            e4.record(stream)
             torch.cuda.synchronize()
             t_ff.append(e0.elapsed_time(e1))
             t_rx.append(e1.elapsed_time(e2))
+            t_bw.append(e3.elapsed_time(e4))
         s = tcase["scan"]
         ff_ms, rx_ms = statistics.mean(t_ff), statistics.mean(t_rx)
         pairs = g["nx"] * g["ny"] * g["nz"] * len(tcase["atoms"]["x"])
         out.append({"spacing": h, "grid": [g["nx"], g["ny"], g["nz"]], "grid_bytes": g["nx"] * g["ny"] * g["nz"] * 4,
-                    "ff_ms": ff_ms, "relax_ms": rx_ms, "ms_per_step": ff_ms + rx_ms,
+                    "ff_ms": ff_ms, "relax_ms": rx_ms, "ms_per_step": ff_ms + rx_ms, "bwd_ms": statistics.mean(t_bw),
                     "pixel_z_per_s": s["nx"] * s["ny"] * s["nz"] / ((ff_ms + rx_ms) * 1e-3),
                     "ff_pair_evals_per_s": pairs / (ff_ms * 1e-3),
                     "fire_iters_mean": float(sim.iters.float().mean().item()),
                     "relax_traffic": measured_traffic("relax_scan_tricubic") if h == 0.1 else None})
-        del sim
+        del sim, ws
     return out
 
 

@@ -300,8 +300,9 @@ typedef struct {
     float* tip;
 } pp_grads;
 
-/* Bytes of scratch pp_backward needs for `grid`: a 256-byte header plus one
- * float4 per stored grid node (the grid adjoint); 0 if the grid is invalid. */
+/* Bytes of scratch pp_backward needs for `grid`: a 256-byte header plus the
+ * grid adjoint, one float4 per stored node (one float on an interp = 1
+ * grid); 0 if the grid is invalid. */
 PP_API size_t pp_backward_workspace(const pp_grid* grid);
 
 /* Gradient of L = sum_{c,pix} g_df[c][pix] * df[c][pix] with respect to the
@@ -312,14 +313,17 @@ PP_API size_t pp_backward_workspace(const pp_grid* grid);
  * (trilinear interpolant included), g_Fz the transpose of the df stencil
  * (Eq. df) applied to g_df, then a grid adjoint -lambda (x) trilinear weights
  * contracted with the pair derivatives of Eqs. LJ and point charges on the
- * nodes it touches.  Inputs: the forward's atoms, probe, grid, force field
+ * nodes it touches.  On a tricubic energy grid (interp = 1) J holds minus the
+ * Hessian of the energy interpolant, the grid adjoint is the scalar
+ * lambda . grad w_g over the 64 stencil nodes of each point, and it is
+ * contracted with the derivatives of the pair energies.  Inputs: the forward's atoms, probe, grid, force field
  * `ff`, scan, tip and df parameters, and its relaxed positions
  * pos[nz][ny][nx][3]; g_df[nz-2m][ny][nx].  Points where FIRE stopped at
  * max_iter are differentiated as if converged.  Scratch `ws` (16-byte
  * aligned, >= pp_backward_workspace(grid) bytes) is overwritten; FP32
  * atomics make the sums order-dependent at rounding level.  Errors:
  * PP_ERR_ARG, PP_ERR_SHAPE, PP_ERR_CAPACITY (ws too small), PP_ERR_UNSUPPORTED
- * (df stencil wider than 63 taps, or an interp = 1 grid), PP_ERR_CUDA. */
+ * (df stencil wider than 63 taps), PP_ERR_CUDA. */
 PP_API pp_status pp_backward(const pp_atoms* atoms, const pp_probe* probe, const pp_grid* grid,
                              const float* ff, const pp_scan* scan, const pp_tip* tip,
                              const pp_df* df_params, const float* pos, const float* g_df,

@@ -280,7 +280,7 @@ size_t pp_backward_workspace(const pp_grid* grid) {
     GridMap m;
     std::string why;
     if (!make_grid_map(grid, &m, &why)) return 0;
-    return kBwdHeader + (size_t)m.stored_nodes * 16;
+    return kBwdHeader + (size_t)m.stored_nodes * (m.interp ? 4 : 16);
 }
 
 pp_status pp_backward(const pp_atoms* atoms, const pp_probe* probe, const pp_grid* grid, const float* ff,
@@ -307,7 +307,6 @@ pp_status pp_backward(const pp_atoms* atoms, const pp_probe* probe, const pp_gri
     GridMap map;
     std::string why;
     if (!make_grid_map(grid, &map, &why)) { set_error("pp_backward: " + why); return PP_ERR_SHAPE; }
-    if (map.interp) { set_error("pp_backward: tricubic (energy) grids are not supported"); return PP_ERR_UNSUPPORTED; }
     if (scan->nx < 1 || scan->ny < 1 || scan->nz < 1 ||
         (int64_t)scan->nx * scan->ny * scan->nz * 3 >= (int64_t(1) << 31)) {
         set_error("pp_backward: invalid scan size");
@@ -321,7 +320,8 @@ pp_status pp_backward(const pp_atoms* atoms, const pp_probe* probe, const pp_gri
     if (m < 0) { set_error("pp_backward: invalid df amplitude"); return PP_ERR_ARG; }
     if (m > kMaxDfHalfWidth) { set_error("pp_backward: df stencil wider than 63 taps"); return PP_ERR_UNSUPPORTED; }
     if (scan->nz < 2 * m + 1) { set_error("pp_backward: fewer heights than the df stencil"); return PP_ERR_SHAPE; }
-    const size_t need = kBwdHeader + (size_t)map.stored_nodes * 16;
+    const size_t adj_bytes = (size_t)map.stored_nodes * (map.interp ? 4 : 16);
+    const size_t need = kBwdHeader + adj_bytes;
     if (ws_bytes < need) {
         set_error("pp_backward: workspace too small (need " + std::to_string(need) + " bytes)");
         return PP_ERR_CAPACITY;
@@ -338,7 +338,8 @@ pp_status pp_backward(const pp_atoms* atoms, const pp_probe* probe, const pp_gri
     L.kQzz = (float)(0.5 * kCoulomb * (double)probe->Qzz);
     L.core_frac = probe->core_frac; L.coul_rc = probe->coul_rc; L.min_image = probe->min_image;
     L.Lx = grid->nx * grid->dx; L.Ly = grid->ny * grid->dy;
-    L.ff = reinterpret_cast<const float4*>(ff);
+    L.ff = map.interp ? nullptr : reinterpret_cast<const float4*>(ff);
+    L.ffE = map.interp ? ff : nullptr;
     L.map = map;
     L.layout = grid->layout;
     L.x0 = grid->x0; L.y0 = grid->y0; L.z0 = grid->z0; L.dx = grid->dx; L.dy = grid->dy; L.dz = grid->dz;
@@ -364,9 +365,12 @@ pp_status pp_backward(const pp_atoms* atoms, const pp_probe* probe, const pp_gri
     L.gtip = grads->tip;
     L.slab = reinterpret_cast<int*>(ws);
     L.qsum = reinterpret_cast<float*>(reinterpret_cast<char*>(ws) + 16);
-    L.gbar = reinterpret_cast<float4*>(reinterpret_cast<char*>(ws) + kBwdHeader);
+    L.gbar = map.interp ? nullptr : reinterpret_cast<float4*>(reinterpret_cast<char*>(ws) + kBwdHeader);
+    L.gbarE = map.interp ? reinterpret_cast<float*>(reinterpret_cast<char*>(ws) + kBwdHeader) : nullptr;
+    L.qsumd = reinterpret_cast<double*>(reinterpret_cast<char*>(ws) + 32);
     cudaStream_t s = (cudaStream_t)stream;
-    pp_status st = cuda_status(cudaMemsetAsync(L.gbar, 0, (size_t)map.stored_nodes * 16, s), "pp_backward memset");
+    pp_status st = cuda_status(cudaMemsetAsync(reinterpret_cast<char*>(ws) + kBwdHeader, 0, adj_bytes, s),
+                               "pp_backward memset");
     if (st != PP_OK) return st;
     return cuda_status(launch_backward(L, s), "pp_backward launch");
 }

@@ -43,6 +43,7 @@ __global__ void init_kernel(const BwdLaunch P) {
         P.slab[1] = -1;
         P.gtip[0] = P.gtip[1] = P.gtip[2] = P.gtip[3] = P.gtip[4] = 0.f;
         P.qsum[0] = P.qsum[1] = 0.f;
+        P.qsumd[0] = P.qsumd[1] = 0.0;
     }
     for (int a = t; a < P.n; a += gridDim.x * blockDim.x) {
         P.gx[a] = 0.f; P.gy[a] = 0.f; P.gz[a] = 0.f;
@@ -77,7 +78,10 @@ __device__ __forceinline__ float df_transpose(const BwdLaunch& P, int k, int pix
 // Grid-stride over the relaxed points: each thread sums its points' tip-parameter terms and
 // z-slab bounds in registers, and a block adds them to the five shared scalars once (atomics
 // from every warp to the same five addresses would serialise in L2).
-template <int LAYOUT, int M>
+// On a tricubic energy grid (kTri) J takes minus the Hessian of the interpolant and the grid
+// adjoint is one scalar per node, Ebar_g = sum lambda . grad w_g(p*) over the 64 stencil nodes
+// (F_S = -sum_g E_g grad w_g).
+template <int LAYOUT, int M, bool kTri>
 __global__ void __launch_bounds__(kAdjThreads) relax_adjoint_kernel(const BwdLaunch P) {
     __shared__ float sred[3][kAdjThreads / 32];
     __shared__ int sk[2][kAdjThreads / 32];
@@ -107,10 +111,16 @@ __global__ void __launch_bounds__(kAdjThreads) relax_adjoint_kernel(const BwdLau
             const float br = -P.kR * P.R0 * rs * rs * rs;          // -kR R0 / |d|^3
             // J = dF_T/dd + dF_S/dp
             const Cells cl = locate(P, px, py, pz);
-            float4 v[8];
-            load_corners<LAYOUT>(P.ff, P.map, cl, v);
             float J[3][3];
-            trilinear_jacobian(v, cl, P.inv_dx, P.inv_dy, P.inv_dz, J);
+            if constexpr (kTri) {
+                float ec[64];
+                tricubic_load(P.ffE, P.map, cl, P.periodic_xy, ec);
+                tricubic_jacobian(ec, cl, P.inv_dx, P.inv_dy, P.inv_dz, J);
+            } else {
+                float4 v[8];
+                load_corners<LAYOUT>(P.ff, P.map, cl, v);
+                trilinear_jacobian(v, cl, P.inv_dx, P.inv_dy, P.inv_dz, J);
+            }
             const float dd[3] = {dx, dy, dz};
 #pragma unroll
             for (int a = 0; a < 3; ++a)
@@ -136,16 +146,46 @@ __global__ void __launch_bounds__(kAdjThreads) relax_adjoint_kernel(const BwdLau
                 gkx = fmaf(lx, ex, gkx);
                 gky = fmaf(ly, ey, gky);
                 gkR += gf * ext * dz + (lx * dx + ly * dy + lz * dz) * ext;
-                // grid adjoint: Gbar += -lambda w_g at the 8 corners
-                int idx[8];
-                corner_index<LAYOUT>(P.map, cl, idx);
-                float w[8];
-                corner_weights(cl, w);
+                if constexpr (kTri) {
+                    // Ebar_g += lambda . grad w_g, w_g = wx_a wy_b wz_c:
+                    //   = wz_c (lx' dwx_a wy_b + ly' wx_a dwy_b) + lz' dwz_c wx_a wy_b, l' = lambda dt/dp
+                    float wx[4], dwx[4], wy[4], dwy[4], wz[4], dwz[4];
+                    cr_weights(cl.x.t, wx, dwx);
+                    cr_weights(cl.y.t, wy, dwy);
+                    cr_weights(cl.z.t, wz, dwz);
+                    const float lxs = lx * cl.x.dtdf * P.inv_dx, lys = ly * cl.y.dtdf * P.inv_dy;
+                    const float lzs = lz * cl.z.dtdf * P.inv_dz;
+                    int xo[4], yo[4], zo[4];
+                    stencil4(cl.x, P.map.nx, P.periodic_xy != 0, 1, xo);
+                    stencil4(cl.y, P.map.ny, P.periodic_xy != 0, P.map.ay.mul, yo);
+                    stencil4(cl.z, P.map.nz, false, P.map.az.mul, zo);
 #pragma unroll
-                for (int c = 0; c < 8; ++c)
-                    if (w[c] != 0.f) atomicAdd(P.gbar + idx[c], make_float4(-lx * w[c], -ly * w[c], -lz * w[c], 0.f));
-                kmin = min(kmin, cl.z.i0);
-                kmax = max(kmax, cl.z.i1);
+                    for (int b = 0; b < 4; ++b)
+#pragma unroll
+                        for (int a = 0; a < 4; ++a) {
+                            const float pab = fmaf(lxs * dwx[a], wy[b], lys * wx[a] * dwy[b]);
+                            const float qab = wx[a] * wy[b];
+#pragma unroll
+                            for (int c = 0; c < 4; ++c) {
+                                const float v = fmaf(wz[c], pab, lzs * dwz[c] * qab);
+                                if (v != 0.f) atomicAdd(P.gbarE + zo[c] + yo[b] + xo[a], v);
+                            }
+                        }
+                    kmin = min(kmin, max(cl.z.i0 - 1, 0));
+                    kmax = max(kmax, min(cl.z.i1 + 1, P.map.nz - 1));
+                } else {
+                    // grid adjoint: Gbar += -lambda w_g at the 8 corners
+                    int idx[8];
+                    corner_index<LAYOUT>(P.map, cl, idx);
+                    float w[8];
+                    corner_weights(cl, w);
+#pragma unroll
+                    for (int c = 0; c < 8; ++c)
+                        if (w[c] != 0.f)
+                            atomicAdd(P.gbar + idx[c], make_float4(-lx * w[c], -ly * w[c], -lz * w[c], 0.f));
+                    kmin = min(kmin, cl.z.i0);
+                    kmax = max(kmax, cl.z.i1);
+                }
             }
         }
     }
@@ -366,20 +406,200 @@ __global__ void __launch_bounds__(kFFBThreads) ff_backward_kernel(const BwdLaunc
     }
 }
 
+// s + t with the rounding error carried in c (Kahan): the f32x2 instructions are not reassociated.
+__device__ __forceinline__ void kahan_add(float2& s, float2& c, float2 t) {
+    const float2 y = f2sub(t, c);
+    const float2 u = f2add(s, y);
+    c = f2sub(f2sub(u, s), y);
+    s = u;
+}
+
+// K5 on an energy grid: dL/dtheta_i = sum_g Ebar_g dE_g/dtheta_i.  Same staging as the force
+// variant, with the nodes' scalar adjoints in pairs, (x0, x1, y0, y1), (z0, z1, e0, e1).  Per
+// node, with delta = r_g - r_i and r = |delta| (floored at core_frac R_iPP):
+//   position  -dE/d delta = F: S delta (+ cq Phi), and inside the floor only the quadrupole's
+//             explicit dz term remains (r is then constant in delta);
+//   R_iPP     12 e (s12 - s6) / R, or core_frac (qq de_el/dr + cq deq/dr) inside the floor;
+//   e_iPP     s12 - 2 s6 per unit e_iPP;  charges  C = sum Ebar e_el, Cq = sum Ebar eq,
+// with e_el = 1/r (shifted-force: 1/r + r/rc^2 - 2/rc) and eq = 3 dz^2/r^5 - 1/r^3.
+// The node adjoint sums to zero over every stencil (the weight gradients do), so the charge
+// sums are differences of terms about r/dx larger than themselves (thousands of times larger
+// for the long-ranged e_el): C and Cq are accumulated with compensation, and the cross-CTA
+// sums of q_i C_i and q_i Cq_i (dL/dQ, dL/dQzz, which cancel again across a neutral molecule)
+// in FP64.
+template <bool kMinImage, bool kCutoff, bool kQuad>
+__global__ void __launch_bounds__(kFFBThreads) ff_backward_energy_kernel(const BwdLaunch P) {
+    __shared__ float4 sxy[kFFBNodes / 2];  // (x0, x1, y0, y1)
+    __shared__ float4 sze[kFFBNodes / 2];  // (z0, z1, e0, e1)
+    __shared__ int scount;
+    const int nx = P.map.nx, ny = P.map.ny;
+    const int64_t nxy = (int64_t)nx * ny;
+    const int64_t first = (int64_t)blockIdx.x * kFFBNodes;
+    const int klo = P.slab[0], khi = P.slab[1];
+    if (khi < 0) return;
+    const int kfirst = (int)(first / nxy), klast = (int)((first + kFFBNodes - 1) / nxy);
+    if (klast < klo || kfirst > khi) return;
+    if (threadIdx.x == 0) scount = 0;
+    __syncthreads();
+    float* fxy = reinterpret_cast<float*>(sxy);
+    float* fze = reinterpret_cast<float*>(sze);
+    const int64_t total = nxy * P.map.nz;
+    for (int t = threadIdx.x; t < kFFBNodes; t += kFFBThreads) {
+        const int64_t g = first + t;
+        bool keep = false;
+        float e = 0.f;
+        int i = 0, j = 0, k = 0;
+        if (g < total) {
+            k = (int)(g / nxy);
+            const int64_t r = g - (int64_t)k * nxy;
+            j = (int)(r / nx);
+            i = (int)(r - (int64_t)j * nx);
+            e = P.gbarE[node_index(P.map, i, j, k)];
+            keep = e != 0.f;
+        }
+        const unsigned mask = __ballot_sync(0xffffffffu, keep);
+        int base = 0;
+        if ((threadIdx.x & 31) == 0 && mask) base = atomicAdd(&scount, __popc(mask));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (keep) {
+            const int slot = base + __popc(mask & ((1u << (threadIdx.x & 31)) - 1u));
+            const int q = (slot >> 1) * 4, l = slot & 1;
+            fxy[q + l] = P.x0 + i * P.dx;
+            fxy[q + 2 + l] = P.y0 + j * P.dy;
+            fze[q + l] = P.z0 + k * P.dz;
+            fze[q + 2 + l] = e;
+        }
+    }
+    __syncthreads();
+    const int cnt = scount;
+    if (cnt == 0) return;
+    if ((cnt & 1) && threadIdx.x == 0) {
+        const int q = (cnt >> 1) * 4;  // pad the last pair with its node and a zero adjoint
+        fxy[q + 1] = fxy[q];
+        fxy[q + 3] = fxy[q + 2];
+        fze[q + 1] = fze[q];
+        fze[q + 3] = 0.f;
+    }
+    __syncthreads();
+    const int npairs = (cnt + 1) >> 1;
+    const float rc2 = kCutoff ? P.coul_rc * P.coul_rc : 0.f;
+    const float irc = kCutoff ? 1.f / P.coul_rc : 0.f, irc2 = irc * irc;
+    const float invLx = kMinImage ? 1.f / P.Lx : 0.f, invLy = kMinImage ? 1.f / P.Ly : 0.f;
+    const float2 TWELVE = make_float2(12.f, 12.f), M2 = make_float2(-2.f, -2.f);
+    const float2 Z2 = make_float2(0.f, 0.f);
+    double qC = 0.0, qCq = 0.0;  // this thread's q_i C_i and q_i Cq_i, summed in FP64
+    for (int a0 = 0; a0 < P.n; a0 += kFFBThreads) {
+        const int ia = a0 + threadIdx.x;
+        if (ia >= P.n) break;
+        const float ax = P.ax[ia], ay = P.ay[ia], azz = P.az[ia];
+        const float Rij = P.aR[ia] + P.R_pp;
+        const float eij = sqrtf(P.aeps[ia] * P.eps_pp);
+        const float qq = P.kQ * P.aq[ia];
+        const float rmin2 = (P.core_frac * Rij) * (P.core_frac * Rij);
+        const float kqq = kQuad ? P.kQzz * P.aq[ia] : 0.f;
+        const float2 AX = make_float2(ax, ax), AY = make_float2(ay, ay), AZ = make_float2(azz, azz);
+        const float2 RR2 = make_float2(Rij * Rij, Rij * Rij), EIJ = make_float2(eij, eij), QQ = make_float2(qq, qq);
+        const float2 E12R = make_float2(12.f * eij / Rij, 12.f * eij / Rij);
+        const float2 QCF = make_float2(qq * P.core_frac, qq * P.core_frac);
+        const float2 KCF = make_float2(kqq * P.core_frac, kqq * P.core_frac), KQ = make_float2(kqq, kqq);
+        float2 GPX = Z2, GPY = Z2, GPZ = Z2, GR = Z2, GE = Z2, CC = Z2, CQ = Z2;
+        float2 KC = Z2, KQ2 = Z2;  // compensations of CC and CQ
+        for (int pr = 0; pr < npairs; ++pr) {
+            const float4 A = sxy[pr], B = sze[pr];
+            float2 DX = f2sub(make_float2(A.x, A.y), AX), DY = f2sub(make_float2(A.z, A.w), AY);
+            const float2 DZ = f2sub(make_float2(B.x, B.y), AZ);
+            const float2 EB = make_float2(B.z, B.w);
+            if (kMinImage) {
+                DX.x = fmaf(-P.Lx, rintf(DX.x * invLx), DX.x);
+                DX.y = fmaf(-P.Lx, rintf(DX.y * invLx), DX.y);
+                DY.x = fmaf(-P.Ly, rintf(DY.x * invLy), DY.x);
+                DY.y = fmaf(-P.Ly, rintf(DY.y * invLy), DY.y);
+            }
+            const float2 R2raw = f2fma(DX, DX, f2fma(DY, DY, f2mul(DZ, DZ)));
+            const bool c0 = R2raw.x < rmin2, c1 = R2raw.y < rmin2;
+            const float2 R2v = make_float2(c0 ? rmin2 : R2raw.x, c1 ? rmin2 : R2raw.y);
+            const float2 RS = make_float2(rsqrtf(R2v.x), rsqrtf(R2v.y));
+            const float2 IR2 = f2mul(RS, RS);
+            const float2 U = f2mul(RR2, IR2);
+            const float2 S6 = f2mul(f2mul(U, U), U);
+            const float2 S12 = f2mul(S6, S6);
+            float2 Cv, EEL, DE;
+            if (kCutoff) {
+                const bool i0 = R2v.x < rc2, i1 = R2v.y < rc2;
+                const float2 R = f2mul(R2v, RS);
+                Cv = sel2(i0, i1, f2mul(RS, f2sub(IR2, make_float2(irc2, irc2))), Z2);
+                EEL = sel2(i0, i1, f2fma(R, make_float2(irc2, irc2), f2sub(RS, make_float2(2.f * irc, 2.f * irc))), Z2);
+                DE = sel2(i0, i1, f2sub(make_float2(irc2, irc2), IR2), Z2);
+            } else {
+                Cv = f2mul(RS, IR2);
+                EEL = RS;
+                DE = f2mul(make_float2(-1.f, -1.f), IR2);
+            }
+            // S = e 12 (s12 - s6) / r^2 + qq c
+            const float2 S = f2fma(f2mul(EIJ, f2mul(TWELVE, f2sub(S12, S6))), IR2, f2mul(QQ, Cv));
+            float2 FS = S;       // coefficient of delta in F (zero inside the floor)
+            float2 FZ = Z2;      // extra z component of F
+            float2 GRc = f2mul(QCF, DE);  // dE/dR inside the floor
+            if (kQuad) {
+                const bool q0 = !kCutoff || R2v.x < rc2, q1 = !kCutoff || R2v.y < rc2;
+                const float2 IR5 = f2mul(f2mul(IR2, IR2), RS), DZ2 = f2mul(DZ, DZ);
+                const float2 T = f2mul(DZ2, IR2);  // dz^2 / r^2
+                // Phi = (15 dz^2/r^7 - 3/r^5) delta - (6 dz/r^5) z_hat
+                const float2 Aq = sel2(q0, q1, f2mul(IR5, f2fma(make_float2(15.f, 15.f), T, make_float2(-3.f, -3.f))), Z2);
+                const float2 A6 = sel2(q0, q1, f2mul(make_float2(6.f, 6.f), f2mul(DZ, IR5)), Z2);
+                const float2 EQ = sel2(q0, q1, f2mul(f2mul(RS, IR2), f2fma(make_float2(3.f, 3.f), T, make_float2(-1.f, -1.f))), Z2);
+                const float2 DEQ = sel2(q0, q1, f2mul(f2mul(IR2, IR2), f2fma(make_float2(-15.f, -15.f), T, make_float2(3.f, 3.f))), Z2);
+                FS = f2fma(KQ, Aq, FS);
+                FZ = f2mul(KQ, A6);  // F_z gets -cq 6 dz / r^5 (subtracted below)
+                GRc = f2fma(KCF, DEQ, GRc);
+                kahan_add(CQ, KQ2, f2mul(EB, EQ));
+            }
+            const float2 EF = sel2(c0, c1, Z2, f2mul(EB, FS));
+            GPX = f2fma(EF, DX, GPX);
+            GPY = f2fma(EF, DY, GPY);
+            GPZ = f2sub(f2fma(EF, DZ, GPZ), f2mul(EB, FZ));
+            GR = f2fma(EB, sel2(c0, c1, GRc, f2mul(E12R, f2sub(S12, S6))), GR);
+            GE = f2fma(EB, f2fma(M2, S6, S12), GE);
+            kahan_add(CC, KC, f2mul(EB, EEL));
+        }
+        const float gpx = GPX.x + GPX.y, gpy = GPY.x + GPY.y, gpz = GPZ.x + GPZ.y;
+        const double Cd = ((double)CC.x - KC.x) + ((double)CC.y - KC.y);
+        const double Cqd = ((double)CQ.x - KQ2.x) + ((double)CQ.y - KQ2.y);
+        const float gRr = GR.x + GR.y, ge = GE.x + GE.y, C = (float)Cd, Cq = (float)Cqd;
+        atomicAdd(P.gx + ia, gpx);
+        atomicAdd(P.gy + ia, gpy);
+        atomicAdd(P.gz + ia, gpz);
+        atomicAdd(P.gR + ia, gRr);
+        atomicAdd(P.geps + ia, ge);
+        atomicAdd(P.gq + ia, fmaf(P.Q, C, 0.5f * P.Qzz * Cq));  // per unit k_e
+        qC += (double)P.aq[ia] * Cd;
+        if (kQuad) qCq += (double)P.aq[ia] * Cqd;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        qC += __shfl_xor_sync(0xffffffffu, qC, o);
+        qCq += __shfl_xor_sync(0xffffffffu, qCq, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (qC != 0.0) atomicAdd(P.qsumd + 0, qC);
+        if (kQuad && qCq != 0.0) atomicAdd(P.qsumd + 1, qCq);
+    }
+}
+
 // Charges and well depths from the accumulated sums; dL/dQ by a block reduction
-// (with a tip quadrupole, K5 has already combined the charge terms and summed
-// q_i C_i and q_i Cq_i).
+// (with a tip quadrupole, or on an energy grid, K5 has already combined the charge
+// terms and summed q_i C_i and q_i Cq_i).
 __global__ void finalize_kernel(const BwdLaunch P) {
     __shared__ float red[32];
-    if (P.Qzz != 0.f) {
+    if (P.Qzz != 0.f || P.map.interp) {
         for (int a = threadIdx.x; a < P.n; a += blockDim.x) {
             P.gq[a] *= P.ke;
             const float eij = sqrtf(P.aeps[a] * P.eps_pp);
             P.geps[a] = eij > 0.f ? P.geps[a] * P.eps_pp / (2.f * eij) : 0.f;
         }
         if (threadIdx.x == 0) {
-            P.gtip[3] = P.ke * P.qsum[0];
-            P.gtip[4] = 0.5f * P.ke * P.qsum[1];
+            P.gtip[3] = P.map.interp ? (float)((double)P.ke * P.qsumd[0]) : P.ke * P.qsum[0];
+            P.gtip[4] = P.map.interp ? (float)(0.5 * (double)P.ke * P.qsumd[1]) : 0.5f * P.ke * P.qsum[1];
         }
         return;
     }
@@ -403,7 +623,13 @@ __global__ void finalize_kernel(const BwdLaunch P) {
 
 template <int LAYOUT, int M>
 void launch_adjoint_m(const BwdLaunch& L, int blocks, cudaStream_t s) {
-    relax_adjoint_kernel<LAYOUT, M><<<blocks, kAdjThreads, 0, s>>>(L);
+    if constexpr (LAYOUT == 0) {
+        if (L.map.interp) {  // energy grids are stored in the linear layout
+            relax_adjoint_kernel<0, M, true><<<blocks, kAdjThreads, 0, s>>>(L);
+            return;
+        }
+    }
+    relax_adjoint_kernel<LAYOUT, M, false><<<blocks, kAdjThreads, 0, s>>>(L);
 }
 
 // Compile-time stencil half widths 1..8 (A_pp / dz up to 16), the run-time loop beyond.
@@ -443,8 +669,9 @@ cudaError_t launch_backward(const BwdLaunch& L, cudaStream_t s) {
         const int64_t nodes = (int64_t)L.map.nx * L.map.ny * L.map.nz;
         const int fb = (int)((nodes + kFFBNodes - 1) / kFFBNodes);
         with_flags(L.min_image != 0, L.coul_rc > 0.f, L.Qzz != 0.f, [&](auto mi, auto cut, auto quad) {
-            ff_backward_kernel<decltype(mi)::value, decltype(cut)::value, decltype(quad)::value>
-                <<<fb, kFFBThreads, 0, s>>>(L);
+            constexpr bool MI = decltype(mi)::value, CUT = decltype(cut)::value, QUAD = decltype(quad)::value;
+            if (L.map.interp) ff_backward_energy_kernel<MI, CUT, QUAD><<<fb, kFFBThreads, 0, s>>>(L);
+            else ff_backward_kernel<MI, CUT, QUAD><<<fb, kFFBThreads, 0, s>>>(L);
             return 0;
         });
     }

@@ -183,7 +183,11 @@ __device__ __forceinline__ void stencil4(const Cell& c, int n, bool periodic, in
 }
 
 // The 64 stencil energies of the located cell, ec[(cz*4 + b)*4 + a] for
-// nodes (i0-1+a, j0-1+b, k0-1+cz) with the wrap/clamp of stencil4.
+// nodes (i0-1+a, j0-1+b, k0-1+cz) with the wrap/clamp of stencil4, relative to
+// the cell's node (i0, j0, k0).  Every derivative weight sums to zero along
+// its axis, so forces and Hessians are unchanged by the shift, while the
+// products they sum are of the energy differences within the stencil rather
+// than of energies up to eV near the core.
 __device__ __forceinline__ void tricubic_load(const float* __restrict__ E, const GridMap& m, const Cells& c,
                                               int periodic, float ec[64]) {
     int xo[4], yo[4], zo[4];
@@ -196,6 +200,9 @@ __device__ __forceinline__ void tricubic_load(const float* __restrict__ E, const
         for (int b = 0; b < 4; ++b)
 #pragma unroll
             for (int a = 0; a < 4; ++a) ec[(cz * 4 + b) * 4 + a] = __ldg(E + zo[cz] + yo[b] + xo[a]);
+    const float ref = ec[21];
+#pragma unroll
+    for (int q = 0; q < 64; ++q) ec[q] -= ref;
 }
 
 // Second derivatives in t of the cubic convolution weights.

@@ -122,6 +122,7 @@ struct BwdLaunch {
     float Lx, Ly;
     // grid (node positions x0 + i*dx ..., cell coordinate p * inv_d + g0s)
     const float4* ff;
+    const float* ffE;  // node energies of a tricubic grid (map.interp = 1), else null
     GridMap map;
     int layout;
     float x0, y0, z0, dx, dy, dz;
@@ -138,9 +139,11 @@ struct BwdLaunch {
     const float* g_df;
     // outputs (accumulated) and caller scratch
     float *gx, *gy, *gz, *gq, *gR, *geps, *gtip;
-    float4* gbar;
+    float4* gbar;   // grid adjoint dL/dF_g (force grids)
+    float* gbarE;   // grid adjoint dL/dE_g (energy grids)
     int* slab;
-    float* qsum;  // {sum_i q_i C_i, sum_i q_i Cq_i} when Qzz != 0
+    float* qsum;    // {sum_i q_i C_i, sum_i q_i Cq_i} when Qzz != 0 (force grids)
+    double* qsumd;  // the same sums on energy grids
 };
 cudaError_t launch_backward(const BwdLaunch& L, cudaStream_t s);
 

@@ -114,10 +114,12 @@ def test_tricubic_grids_are_validated_on_host(L):
     tip = pp.make_tip({"kx": 0.25, "ky": 0.25, "kR": 20.0, "R0": 4.0, "d0x": 0.0, "d0y": 0.0})
     dfp = pp.DF(1.0, 1800.0, 30300.0)
     grads = pp.Grads(*([16] * 7))
-    # the adjoint takes trilinear force grids only: refused before anything is read or launched
+    # the adjoint of an energy grid keeps one float per node; a smaller workspace is refused
+    # before anything is read or launched
+    assert L.pp_backward_workspace(C.byref(g)) == 256 + 4 * 10 * 6 * 5
     assert L.pp_backward(C.byref(atoms), C.byref(probe), C.byref(g), fake, C.byref(scan), C.byref(tip),
-                         C.byref(dfp), fake, fake, C.byref(grads), fake, 1 << 30, None) == 6
-    assert b"tricubic" in L.pp_last_error()
+                         C.byref(dfp), fake, fake, C.byref(grads), fake, 256 + 4 * 10 * 6 * 5 - 4, None) == 4
+    assert b"workspace too small" in L.pp_last_error()
     lin = pp.make_grid({"nx": 10, "ny": 6, "nz": 5, "x0": 0, "y0": 0, "z0": 0, "dx": 0.1, "dy": 0.1, "dz": 0.1,
                         "periodic_xy": 1})
     assert L.pp_ff_convert(fake, C.byref(g), fake, C.byref(lin), None) == 6

@@ -29,13 +29,19 @@ def weights(c, seed=7):
     return np.random.default_rng(seed).standard_normal((s["nz"] - 2 * m, s["ny"], s["nx"]))
 
 
-def gpu_backward(c, pos, w, layout=0, want_qzz=False):
-    """CUDA adjoint at the given relaxed positions, on the CUDA FF grid (dL/dQzz too if want_qzz)."""
+def gpu_backward(c, pos, w, layout=0, want_qzz=False, want_grid_adj=False, ff_host=None):
+    """CUDA adjoint at the given relaxed positions, on the CUDA FF grid, or on ff_host (a grid the
+    oracle made, rounded to FP32) when given; dL/dQzz too if want_qzz; on an energy grid the node
+    adjoint dL/dE_g [nz][ny][nx] from the workspace if want_grid_adj."""
     grid = pp.make_grid(c["grid"], layout)
     atoms_t = afm.atoms_to_device(c["atoms"])
     atoms = pp.make_atoms(atoms_t)
-    ff = torch.empty(pp.pp_ff_floats(grid), dtype=torch.float32, device="cuda")
-    pp.pp_make_ff(atoms, pp.make_probe(c["probe"]), grid, ff)
+    if ff_host is None:
+        ff = torch.empty(pp.pp_ff_floats(grid), dtype=torch.float32, device="cuda")
+        pp.pp_make_ff(atoms, pp.make_probe(c["probe"]), grid, ff)
+    else:
+        assert layout == 0 and np.asarray(ff_host).size == pp.pp_ff_floats(grid)
+        ff = torch.as_tensor(np.ascontiguousarray(ff_host, dtype=np.float32).ravel(), device="cuda")
     n = len(c["atoms"]["x"])
     g = {k: torch.full((n,), float("nan"), device="cuda") for k in KEYS}
     g["tip"] = torch.full((5,), float("nan"), device="cuda")
@@ -50,6 +56,11 @@ def gpu_backward(c, pos, w, layout=0, want_qzz=False):
     out.update({k: t[i] for i, k in enumerate(TIP)})
     if want_qzz:
         out["Qzz"] = t[4]
+    if want_grid_adj:
+        assert c["grid"].get("interp", 0) == 1
+        gg = c["grid"]
+        nn = gg["nx"] * gg["ny"] * gg["nz"]
+        out["grid_adj"] = ws[64:64 + nn].cpu().numpy().astype(np.float64).reshape(gg["nz"], gg["ny"], gg["nx"])
     return out
 
 
