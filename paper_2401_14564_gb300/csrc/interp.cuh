@@ -183,11 +183,7 @@ __device__ __forceinline__ void stencil4(const Cell& c, int n, bool periodic, in
 }
 
 // The 64 stencil energies of the located cell, ec[(cz*4 + b)*4 + a] for
-// nodes (i0-1+a, j0-1+b, k0-1+cz) with the wrap/clamp of stencil4, relative to
-// the cell's node (i0, j0, k0).  Every derivative weight sums to zero along
-// its axis, so forces and Hessians are unchanged by the shift, while the
-// products they sum are of the energy differences within the stencil rather
-// than of energies up to eV near the core.
+// nodes (i0-1+a, j0-1+b, k0-1+cz) with the wrap/clamp of stencil4.
 __device__ __forceinline__ void tricubic_load(const float* __restrict__ E, const GridMap& m, const Cells& c,
                                               int periodic, float ec[64]) {
     int xo[4], yo[4], zo[4];
@@ -200,9 +196,6 @@ __device__ __forceinline__ void tricubic_load(const float* __restrict__ E, const
         for (int b = 0; b < 4; ++b)
 #pragma unroll
             for (int a = 0; a < 4; ++a) ec[(cz * 4 + b) * 4 + a] = __ldg(E + zo[cz] + yo[b] + xo[a]);
-    const float ref = ec[21];
-#pragma unroll
-    for (int q = 0; q < 64; ++q) ec[q] -= ref;
 }
 
 // Second derivatives in t of the cubic convolution weights.
@@ -260,7 +253,10 @@ __device__ __forceinline__ void tricubic_jacobian(const float ec[64], const Cell
     J[1][2] = J[2][1] = -hyz * sy * sz;
 }
 
-// F = -grad E of the tricubic interpolant from the cached stencil energies (see tricubic_force).
+// F = -grad E of the tricubic interpolant from the cached stencil energies: the 64 values are
+// contracted along x into (value, x-derivative) pairs, then along y and z, two sums per packed
+// instruction.  Where a fraction is clamped (outside the grid in z, or x,y without periodicity)
+// that derivative is zero, as for trilinear.
 __device__ __forceinline__ float3 tricubic_eval(const float ec[64], const Cells& c, float inv_dx, float inv_dy,
                                                 float inv_dz) {
     float wx[4], dwx[4], wy[4], dwy[4], wz[4], dwz[4];
@@ -283,48 +279,6 @@ __device__ __forceinline__ float3 tricubic_eval(const float ec[64], const Cells&
             r = f2fma(WX[1], make_float2(e[1], e[1]), r);
             r = f2fma(WX[2], make_float2(e[2], e[2]), r);
             r = f2fma(WX[3], make_float2(e[3], e[3]), r);
-            s02 = f2fma(make_float2(wy[b], wy[b]), r, s02);
-            s1 = fmaf(dwy[b], r.x, s1);
-        }
-        gzx = f2fma(make_float2(dwz[cz], wz[cz]), s02, gzx);
-        gy = fmaf(wz[cz], s1, gy);
-    }
-    return make_float3(-gzx.y * (c.x.dtdf * inv_dx), -gy * (c.y.dtdf * inv_dy), -gzx.x * (c.z.dtdf * inv_dz));
-}
-
-// F = -grad E of the tricubic interpolant of the node energies E (linear
-// layout) at the located point: the 64 stencil values are contracted along x
-// into (value, x-derivative) pairs, then along y and z, two sums per packed
-// instruction.  Where a fraction is clamped (outside the grid in z, or x,y
-// without periodicity) that derivative is zero, as for trilinear.
-__device__ __forceinline__ float3 tricubic_force(const float* __restrict__ E, const GridMap& m, const Cells& c,
-                                                 float inv_dx, float inv_dy, float inv_dz, int periodic) {
-    int xo[4], yo[4], zo[4];
-    stencil4(c.x, m.nx, periodic != 0, 1, xo);
-    stencil4(c.y, m.ny, periodic != 0, m.ay.mul, yo);
-    stencil4(c.z, m.nz, false, m.az.mul, zo);
-    float wx[4], dwx[4], wy[4], dwy[4], wz[4], dwz[4];
-    cr_weights(c.x.t, wx, dwx);
-    cr_weights(c.y.t, wy, dwy);
-    cr_weights(c.z.t, wz, dwz);
-    float2 WX[4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) WX[a] = make_float2(wx[a], dwx[a]);
-    float2 gzx = make_float2(0.f, 0.f);  // (d/dz, d/dx) sums
-    float gy = 0.f;
-#pragma unroll
-    for (int cz = 0; cz < 4; ++cz) {
-        float2 s02 = make_float2(0.f, 0.f);  // (sum_b wy R0, sum_b wy R1)
-        float s1 = 0.f;                      // sum_b dwy R0
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            const float* row = E + zo[cz] + yo[b];
-            const float e0 = __ldg(row + xo[0]), e1 = __ldg(row + xo[1]);
-            const float e2 = __ldg(row + xo[2]), e3 = __ldg(row + xo[3]);
-            float2 r = f2mul(WX[0], make_float2(e0, e0));  // (R0, R1) = sum_a (wx, dwx) e_a
-            r = f2fma(WX[1], make_float2(e1, e1), r);
-            r = f2fma(WX[2], make_float2(e2, e2), r);
-            r = f2fma(WX[3], make_float2(e3, e3), r);
             s02 = f2fma(make_float2(wy[b], wy[b]), r, s02);
             s1 = fmaf(dwy[b], r.x, s1);
         }
