@@ -3,7 +3,8 @@
 `Simulator` owns the device buffers of one workload shape (grid and scan) and
 runs the three C-ABI stages on the current torch stream; `run_host` is the
 end-to-end call that starts from host atom arrays and returns the df image
-in host memory.  Nothing here computes: it allocates with torch and calls
+in host memory.  `Pipeline` keeps several independent items in flight on
+their own streams and buffers.  Nothing here computes: it allocates with torch and calls
 libpp through `pp.py`.
 """
 from __future__ import annotations
@@ -175,6 +176,108 @@ class Simulator:
 
     def d2h_bytes(self):
         return self.df.numel() * 4
+
+
+class Pipeline:
+    """Independent forward passes in flight `slots` at a time.
+
+    Item k runs on slot k % slots, which owns a Simulator (grid, positions, Fz, df) and a stream,
+    so the force fields and scans of later items overlap the relaxed scan of item k.  The scan is
+    bound by the latency of its FIRE chains: one item's pixel columns give few warps per SM, and in
+    its tail the slowest columns run alone; the other items' tiles fill those idle issue slots.
+    Every item computes exactly what Simulator.run computes (same kernels, same inputs,
+    bit-identical images).  Device memory: one Simulator's buffers per slot.
+    """
+
+    def __init__(self, case, slots=4, **sim_kwargs):
+        if slots < 1:
+            raise ValueError("Pipeline needs at least one slot")
+        self.sims = [Simulator(case, **sim_kwargs) for _ in range(slots)]
+        self.streams = [torch.cuda.Stream() for _ in range(slots)]
+        self._host = None
+
+    @property
+    def slots(self):
+        return len(self.sims)
+
+    def _fork(self):
+        cur = torch.cuda.current_stream()
+        ev = torch.cuda.Event()
+        ev.record(cur)
+        for st in self.streams:
+            st.wait_event(ev)
+        return cur
+
+    def _join(self, cur):
+        for st in self.streams:
+            ev = torch.cuda.Event()
+            ev.record(st)
+            cur.wait_event(ev)
+
+    def run_many(self, atoms_devs, outs=None):
+        """Device atoms of each item -> df images.  outs[k] (device tensors shaped like the df image)
+        receive item k's image; with outs=None each image stays in its slot's df buffer until the
+        slot's next item overwrites it.  Ordered after the current stream's work; the current
+        stream waits for every item before its next launch."""
+        if outs is not None and len(outs) < len(atoms_devs):
+            raise ValueError("run_many: fewer output buffers than items")
+        cur = self._fork()
+        for k, dev in enumerate(atoms_devs):
+            b = k % self.slots
+            self.sims[b].run(dev, self.streams[b], df=None if outs is None else outs[k])
+        self._join(cur)
+        return outs
+
+    def host_outputs(self, n_items):
+        return self.sims[0].host_outputs(n_items)
+
+    def run_host_many(self, atoms_list, outs=None):
+        """Host atom sets -> host df images (pinned outs, see host_outputs), end to end: item k's
+        atoms go host -> device, its force field, scan and df run, and its image comes back, all on
+        its slot's stream, so the copies and the compute of neighbouring items overlap."""
+        n_items = len(atoms_list)
+        if n_items == 0:
+            return []
+        n = int(len(atoms_list[0]["x"]))
+        if any(int(len(a["x"])) != n for a in atoms_list):
+            raise ValueError("run_host_many: every item needs the same number of atoms")
+        if outs is None:
+            outs = self.host_outputs(n_items)
+        elif len(outs) < n_items:
+            raise ValueError("run_host_many: fewer output buffers than items")
+        pin = torch.cuda.is_available()
+        if self._host is None or self._host["n"] != n:
+            self._host = {
+                "n": n,
+                "atoms_h": [torch.empty((6, n), dtype=torch.float32, pin_memory=pin) for _ in self.sims],
+                "atoms_d": [torch.empty((6, n), dtype=torch.float32, device=sim.device) for sim in self.sims],
+            }
+        H = self._host
+        staged = [None] * self.slots
+        cur = self._fork()
+        for k, atoms_host in enumerate(atoms_list):
+            b = k % self.slots
+            if staged[b] is not None:
+                staged[b].synchronize()  # the slot's previous item has left the pinned staging buffer
+            for r, key in enumerate(ATOM_KEYS):
+                H["atoms_h"][b][r].copy_(torch.from_numpy(np.asarray(atoms_host[key], dtype=np.float32)))
+            st = self.streams[b]
+            with torch.cuda.stream(st):
+                H["atoms_d"][b].copy_(H["atoms_h"][b], non_blocking=True)
+                staged[b] = torch.cuda.Event()
+                staged[b].record(st)
+                dev = {key: H["atoms_d"][b][r] for r, key in enumerate(ATOM_KEYS)}
+                self.sims[b].run(dev, st)
+                outs[k].copy_(self.sims[b].df, non_blocking=True)
+        self._join(cur)
+        cur.synchronize()
+        return outs
+
+    def h2d_bytes(self, n_atoms):
+        return self.sims[0].h2d_bytes(n_atoms)
+
+    def d2h_bytes(self):
+        return self.sims[0].d2h_bytes()
 
 
 def afm(case, atoms=None, layout=0, fire=None, device="cuda"):

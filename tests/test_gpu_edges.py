@@ -1,6 +1,7 @@
 """Minimum-size and degenerate inputs of the GPU path against the FP64 oracle:
 a single pixel with exactly 2m+1 heights (one df value), FIRE with no
-iterations allowed, a grid two nodes high, and the smallest FFT grids.
+iterations allowed, a grid two nodes high, and the smallest FFT grids; the
+streamed and pipelined multi-item paths against one call per item.
 """
 import copy
 
@@ -83,3 +84,28 @@ def test_streamed_host_path_equals_one_call_per_item():
     for k in range(len(items)):
         assert torch.equal(many[k], one[k]), k
     assert not torch.equal(many[0], many[-1])
+
+
+def test_pipeline_items_equal_one_run_per_item():
+    # two items in flight on two streams with their own grids: every image is the single-item one
+    c = case32(synth.small_case(seed=12, n_atoms=11, nxy=32, nz=36, scan_px=10, nz_scan=12))
+    items = []
+    for t in range(5):
+        a = copy.deepcopy(c["atoms"])
+        a["y"] = a["y"] - 0.05 * t
+        a["eps"] = a["eps"] * (1.0 + 0.2 * t)
+        items.append(a)
+    sim = afm.Simulator(c)
+    one = []
+    for a in items:
+        sim.run(afm.atoms_to_device(a))
+        one.append(sim.df.clone())
+    pipe = afm.Pipeline(c, slots=2)
+    outs = [torch.empty_like(one[0]) for _ in items]
+    pipe.run_many([afm.atoms_to_device(a) for a in items], outs)
+    torch.cuda.synchronize()
+    host = [o.clone() for o in pipe.run_host_many(items)]
+    for k in range(len(items)):
+        assert torch.equal(outs[k], one[k]), k
+        assert torch.equal(host[k], one[k].cpu()), k
+    assert not torch.equal(one[0], one[-1])
