@@ -14,7 +14,7 @@ import numpy as np
 import pytest
 import torch
 
-from helpers import case32
+from helpers import case32, df_keep, ill_conditioned_within_bound
 from paper_2401_14564_gb300 import afm, pp, synth
 from test_gpu_relax import check_parity, gpu_run
 
@@ -160,3 +160,42 @@ def test_energy_grid_autograd_matches_direct_call(orc):
     direct = gpu_backward(c, afm.afm(c, fire=fire)["pos"], w)
     for k in KEYS:
         assert rel(leaves[k].grad.cpu().numpy(), direct[k]) < 1e-4, k
+
+
+@pytest.mark.parametrize("h", [0.1, 0.2])
+def test_flake_full_size_sampled_columns_on_energy_grids(orc, h):
+    # the bench's tricubic leg: flake60 on energy grids at 0.1 A (256x256x200) and 0.2 A
+    # (128x128x100), the 256 x 256 x 40 scan in its launch shape; 48 seeded columns against the
+    # oracle relaxing on its own energy grid, 2000 sampled node energies against direct sums
+    c = case32(synth.flake_case())
+    g0 = c["grid"]
+    f = round(h / g0["dx"])
+    c["grid"] = dict(g0, nx=g0["nx"] // f, ny=g0["ny"] // f, nz=(g0["nz"] - 1) // f + 1, dx=h, dy=h, dz=h, interp=1)
+    gr, s = c["grid"], c["scan"]
+    fire = synth.parity_fire()
+    g = gpu_run(c, fire)
+    E = gpu_grid(c, 1).reshape(gr["nz"], gr["ny"], gr["nx"]).astype(np.float64)
+    rng = np.random.default_rng(2)
+    idx = np.stack([rng.integers(0, gr[n], 2000) for n in ("nz", "ny", "nx")], axis=1)
+    pts = np.stack([np.float32(gr["x0"]) + idx[:, 2] * np.float32(gr["dx"]),
+                    np.float32(gr["y0"]) + idx[:, 1] * np.float32(gr["dy"]),
+                    np.float32(gr["z0"]) + idx[:, 0] * np.float32(gr["dz"])], axis=1).astype(np.float64)
+    ref, core = orc.ff_points(c["atoms"], c["probe"], gr, pts)
+    got = E[idx[:, 0], idx[:, 1], idx[:, 2]]
+    assert (np.abs(got - ref[:, 3]) / np.maximum(np.abs(ref[:, 3]), 1e-2))[~core].max() <= 1e-4
+    cols = np.sort(rng.choice(s["nx"] * s["ny"], 48, replace=False))
+    ff, _ = orc.make_ff(c["atoms"], c["probe"], gr)
+    o = orc.relax_columns(ff, gr, None, None, s, c["tip"], fire, cols)
+    jj, ii = cols // s["nx"], cols % s["nx"]
+    gp = np.moveaxis(g["pos"][:, jj, ii], 0, 1)
+    gfz = g["fz"][:, jj, ii].T
+    dp = np.linalg.norm(gp - o["pos"], axis=-1)
+    keep = (o["lam"] >= 0.01) & (dp < 0.05)
+    assert keep.mean() > 0.9
+    assert dp[keep].max() <= 1e-3
+    n_sel, n_ok = ill_conditioned_within_bound(gp, o, fire["ftol"])
+    assert n_ok == n_sel, (n_ok, n_sel)
+    assert np.abs(gfz - o["fz"])[keep].max() <= 1e-3 * np.abs(o["fz"]).max()
+    odf = orc.fz_to_df(o["fz"].T, s["dz"], c["df"])
+    kd = df_keep(keep.T, 5)
+    assert np.abs(g["df"][:, jj, ii] - odf)[kd].max() <= 1e-3 * (g["df"].max() - g["df"].min())
