@@ -44,10 +44,14 @@ TRAFFIC = {
                    "files": ["relax_scan.cu", "relax_core.cuh", "interp.cuh"]},
     "relax_scan_tricubic": {"bytes": 21.34e6, "sha": "02c28f5256973be5",
                             "files": ["relax_scan.cu", "relax_core.cuh", "interp.cuh"]},
-    "ff_assemble": {"bytes": 144.93e6, "sha": "60f4c5c6753e3dbb",
+    "ff_assemble": {"bytes": 144.52e6, "sha": "ba1c6157cd47c875",
                     "files": ["ff_assemble.cu", "ff_core.cuh", "interp.cuh"]},
-    "ff_assemble_quad": {"bytes": 144.76e6, "sha": "60f4c5c6753e3dbb",
+    "ff_assemble_quad": {"bytes": 145.20e6, "sha": "ba1c6157cd47c875",
                          "files": ["ff_assemble.cu", "ff_core.cuh", "interp.cuh"]},
+    "ff_assemble_split": {"bytes": 354.32e6, "sha": "ba1c6157cd47c875",
+                          "files": ["ff_assemble.cu", "ff_core.cuh", "interp.cuh"]},
+    "ff_combine": {"bytes": 597.65e6, "sha": "ba1c6157cd47c875",
+                   "files": ["ff_assemble.cu", "ff_core.cuh", "interp.cuh"]},
 }
 
 
@@ -395,6 +399,52 @@ def measure_tricubic(case, steps, warmup, flush):
     return out
 
 
+def measure_split(case, steps, warmup, flush, hbm_gbs):
+    """The line's workload with the electrostatics kept apart (pp_make_ff_split: LJ grid + point-charge
+    grid per unit probe charge) and recombined for the probe charge (pp_ff_combine, 12 bytes moved per
+    float); CUDA events, L2 flushed before each."""
+    import torch
+
+    from paper_2401_14564_gb300 import afm, pp
+
+    grid = pp.make_grid(case["grid"], 0)
+    n = pp.pp_ff_floats(grid)
+    ff = torch.empty(n, dtype=torch.float32, device="cuda")
+    el = torch.empty(n, dtype=torch.float32, device="cuda")
+    out = torch.empty(n, dtype=torch.float32, device="cuda")
+    atoms = pp.make_atoms(afm.atoms_to_device(case["atoms"]))
+    probe = pp.make_probe(case["probe"])
+    Q = float(case["probe"]["Q"])
+    for _ in range(max(warmup, 3)):
+        pp.pp_make_ff_split(atoms, probe, grid, ff, el)
+        pp.pp_ff_combine(ff, el, Q, grid, out)
+    stream = torch.cuda.current_stream()
+    t_split, t_comb = [], []
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pp.pp_make_ff_split(atoms, probe, grid, ff, el)
+        e1.record(stream)
+        flush.zero_()
+        e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e2.record(stream)
+        pp.pp_ff_combine(ff, el, Q, grid, out)
+        e3.record(stream)
+        torch.cuda.synchronize()
+        t_split.append(e0.elapsed_time(e1))
+        t_comb.append(e2.elapsed_time(e3))
+    g = case["grid"]
+    pairs = g["nx"] * g["ny"] * g["nz"] * len(case["atoms"]["x"])
+    sm, cm = statistics.mean(t_split), statistics.mean(t_comb)
+    gbs = 12 * n / (cm * 1e-3) / 1e9
+    del ff, el, out
+    return {"workload": "flake60, LJ and point-charge grids apart, recombined for Q = -0.1",
+            "split_ff_ms": sm, "split_pair_evals_per_s": pairs / (sm * 1e-3), "combine_ms": cm,
+            "combine_bytes": 12 * n, "combine_gbs": gbs, "combine_frac_of_hbm": gbs / hbm_gbs,
+            "split_ff_traffic": measured_traffic("ff_assemble_split"), "combine_traffic": measured_traffic("ff_combine")}
+
+
 FFT_BYTES_PER_NODE = 224  # one correlation: pack 16 + 3 forward passes 48 + spectral 32 + 6 inverse passes 96 + output 32
 FDBM_A, FDBM_BETA = 18.0, 1.0  # Pauli prefactor and exponent of the synthetic full-density workload
 
@@ -527,6 +577,7 @@ def main():
     ap.add_argument("--no-quad", action="store_true")
     ap.add_argument("--no-tricubic", action="store_true")
     ap.add_argument("--no-fdbm", action="store_true")
+    ap.add_argument("--no-split", action="store_true")
     ap.add_argument("--zpt", type=int, default=0, help="FF z-nodes per thread (skips the autotuner)")
     ap.add_argument("--brick", default="", help="bricked layout bx,by,bz for the scan (skips the autotuner)")
     ap.add_argument("--batch-mol", type=int, default=1024)
@@ -694,6 +745,8 @@ def main():
         line["tricubic"] = measure_tricubic(case, max(3, args.steps // 2), args.warmup, flush)
     if not args.no_quad:
         line["quadrupole"] = measure_quadrupole(case, tuning, max(3, args.steps // 2), args.warmup, flush, alu_peak)
+    if not args.no_split:
+        line["split"] = measure_split(case, max(3, args.steps // 2), args.warmup, flush, peaks["hbm_gbs"])
     if not args.no_slab:
         line["slab"] = measure_slab(3, 1, flush)
     if not args.no_batch:

@@ -174,6 +174,27 @@ PP_API int pp_df_margin(float A_pp, float dz);
 PP_API pp_status pp_make_ff(const pp_atoms* atoms, const pp_probe* probe, const pp_grid* grid,
                      float* ff, pp_stream stream);
 
+/* pp_make_ff with the point-charge electrostatics kept apart, for scanning the
+ * probe charge Q without reassembling the grid: `ff` gets the Lennard-Jones
+ * terms (and the tip quadrupole when probe->Qzz != 0), `ff_el` the Coulomb
+ * field of the sample's point charges per unit probe charge (Eq. point
+ * charges with Q = 1; shifted-force when coul_rc > 0); probe->Q is not used.
+ * F = ff + Q ff_el is the grid pp_make_ff writes for charge Q (up to FP32
+ * rounding of the two sums); pp_ff_combine forms it.  Both buffers hold
+ * pp_ff_floats(grid) floats in the grid's layout (energies only when
+ * grid->interp = 1), 16-byte aligned and distinct.  Launch shape fixed (8
+ * z-nodes per thread).  Errors as pp_make_ff. */
+PP_API pp_status pp_make_ff_split(const pp_atoms* atoms, const pp_probe* probe, const pp_grid* grid,
+                                  float* ff, float* ff_el, pp_stream stream);
+
+/* out = ff + Q ff_el over the pp_ff_floats(grid) floats of a split grid (any
+ * layout or interp; padding included), i.e. the grid for probe charge Q.
+ * `out` may be `ff` itself.  HBM-bound elementwise pass (12 bytes moved per
+ * float).  Errors: PP_ERR_ARG (NULL, unaligned, Q not finite), PP_ERR_SHAPE,
+ * PP_ERR_CUDA. */
+PP_API pp_status pp_ff_combine(const float* ff, const float* ff_el, float Q, const pp_grid* grid, float* out,
+                               pp_stream stream);
+
 /* Launch shape of pp_make_ff_tuned (picked by the autotuner): ff_zpt is the
  * number of consecutive z-nodes each thread accumulates, 4, 8 or 16; 0 = 8. */
 typedef struct {

@@ -125,44 +125,44 @@ int pp_df_margin(float A_pp, float dz) { return df_half_width(A_pp, dz); }
 
 static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
-pp_status pp_make_ff(const pp_atoms* atoms, const pp_probe* probe, const pp_grid* grid, float* ff,
-                     pp_stream stream) {
-    return pp_make_ff_tuned(atoms, probe, grid, ff, nullptr, stream);
-}
-
-pp_status pp_make_ff_tuned(const pp_atoms* atoms, const pp_probe* probe, const pp_grid* grid, float* ff,
-                           const pp_tuning* tuning, pp_stream stream) {
-    g_error.clear();
-    const int zpt = (tuning && tuning->ff_zpt) ? tuning->ff_zpt : 8;
-    if (zpt != 4 && zpt != 8 && zpt != 16) { set_error("pp_make_ff_tuned: ff_zpt must be 4, 8 or 16"); return PP_ERR_ARG; }
-    if (!atoms || !probe || !grid || !ff) { set_error("pp_make_ff: NULL argument"); return PP_ERR_ARG; }
-    if (atoms->n < 0) { set_error("pp_make_ff: atoms->n < 0"); return PP_ERR_ARG; }
+// Validation and launch shared by pp_make_ff, pp_make_ff_tuned and pp_make_ff_split.
+static pp_status make_ff_impl(const char* name, const pp_atoms* atoms, const pp_probe* probe, const pp_grid* grid,
+                              float* ff, float* ff_el, int zpt, pp_stream stream) {
+    const std::string who(name);
+    if (!atoms || !probe || !grid || !ff) { set_error(who + ": NULL argument"); return PP_ERR_ARG; }
+    if (atoms->n < 0) { set_error(who + ": atoms->n < 0"); return PP_ERR_ARG; }
     if (atoms->n > 0 && (!atoms->x || !atoms->y || !atoms->z || !atoms->R || !atoms->eps || !atoms->q)) {
-        set_error("pp_make_ff: NULL atom array");
+        set_error(who + ": NULL atom array");
         return PP_ERR_ARG;
     }
-    if (!(probe->core_frac > 0.f && probe->core_frac < 1.f)) { set_error("pp_make_ff: core_frac must be in (0,1)"); return PP_ERR_ARG; }
+    if (!(probe->core_frac > 0.f && probe->core_frac < 1.f)) { set_error(who + ": core_frac must be in (0,1)"); return PP_ERR_ARG; }
     if (!(probe->eps_pp >= 0.f) || !isfinite(probe->R_pp) || !isfinite(probe->Q) || !(probe->coul_rc >= 0.f) ||
         !isfinite(probe->Qzz)) {
-        set_error("pp_make_ff: invalid probe parameters");
+        set_error(who + ": invalid probe parameters");
         return PP_ERR_ARG;
     }
-    if (probe->min_image != 0 && probe->min_image != 1) { set_error("pp_make_ff: min_image must be 0 or 1"); return PP_ERR_ARG; }
-    if (!aligned16(ff)) { set_error("pp_make_ff: ff must be 16-byte aligned"); return PP_ERR_ARG; }
+    if (probe->min_image != 0 && probe->min_image != 1) { set_error(who + ": min_image must be 0 or 1"); return PP_ERR_ARG; }
+    if (!aligned16(ff) || (ff_el && !aligned16(ff_el))) { set_error(who + ": grids must be 16-byte aligned"); return PP_ERR_ARG; }
+    if (ff_el == ff) { set_error(who + ": ff and ff_el must be different buffers"); return PP_ERR_ARG; }
     GridMap map;
     std::string why;
-    if (!make_grid_map(grid, &map, &why)) { set_error("pp_make_ff: " + why); return PP_ERR_SHAPE; }
+    if (!make_grid_map(grid, &map, &why)) { set_error(who + ": " + why); return PP_ERR_SHAPE; }
     cudaStream_t s = (cudaStream_t)stream;
     if (map.stored_nodes > (int64_t)grid->nx * grid->ny * grid->nz) {
-        pp_status st = cuda_status(cudaMemsetAsync(ff, 0, (size_t)map.stored_nodes * 16, s), "pp_make_ff memset");
-        if (st != PP_OK) return st;
+        for (float* g : {ff, ff_el}) {
+            if (!g) continue;
+            pp_status st = cuda_status(cudaMemsetAsync(g, 0, (size_t)map.stored_nodes * 16, s), (who + " memset").c_str());
+            if (st != PP_OK) return st;
+        }
     }
     FFLaunch L;
+    std::memset(&L, 0, sizeof(L));
     L.x = atoms->x; L.y = atoms->y; L.z = atoms->z; L.R = atoms->R; L.eps = atoms->eps; L.q = atoms->q;
     L.n = atoms->n;
     L.R_pp = probe->R_pp;
     L.eps_pp = probe->eps_pp;
-    L.kQ = (float)(kCoulomb * (double)probe->Q);
+    // split: the point-charge grid is per unit probe charge
+    L.kQ = (float)(kCoulomb * (ff_el ? 1.0 : (double)probe->Q));
     L.kQzz = (float)(0.5 * kCoulomb * (double)probe->Qzz);
     L.core_frac = probe->core_frac;
     L.coul_rc = probe->coul_rc;
@@ -175,7 +175,47 @@ pp_status pp_make_ff_tuned(const pp_atoms* atoms, const pp_probe* probe, const p
     L.ff = map.interp ? nullptr : reinterpret_cast<float4*>(ff);
     L.ffE = map.interp ? ff : nullptr;
     L.zpt = zpt;
-    return cuda_status(launch_ff_assemble(L, s), "pp_make_ff launch");
+    L.split = ff_el != nullptr;
+    L.ffel = (ff_el && !map.interp) ? reinterpret_cast<float4*>(ff_el) : nullptr;
+    L.ffelE = (ff_el && map.interp) ? ff_el : nullptr;
+    return cuda_status(launch_ff_assemble(L, s), (who + " launch").c_str());
+}
+
+pp_status pp_make_ff(const pp_atoms* atoms, const pp_probe* probe, const pp_grid* grid, float* ff,
+                     pp_stream stream) {
+    g_error.clear();
+    return make_ff_impl("pp_make_ff", atoms, probe, grid, ff, nullptr, 8, stream);
+}
+
+pp_status pp_make_ff_tuned(const pp_atoms* atoms, const pp_probe* probe, const pp_grid* grid, float* ff,
+                           const pp_tuning* tuning, pp_stream stream) {
+    g_error.clear();
+    const int zpt = (tuning && tuning->ff_zpt) ? tuning->ff_zpt : 8;
+    if (zpt != 4 && zpt != 8 && zpt != 16) { set_error("pp_make_ff_tuned: ff_zpt must be 4, 8 or 16"); return PP_ERR_ARG; }
+    return make_ff_impl("pp_make_ff_tuned", atoms, probe, grid, ff, nullptr, zpt, stream);
+}
+
+pp_status pp_make_ff_split(const pp_atoms* atoms, const pp_probe* probe, const pp_grid* grid, float* ff,
+                           float* ff_el, pp_stream stream) {
+    g_error.clear();
+    if (!ff_el) { set_error("pp_make_ff_split: NULL ff_el"); return PP_ERR_ARG; }
+    return make_ff_impl("pp_make_ff_split", atoms, probe, grid, ff, ff_el, 8, stream);
+}
+
+pp_status pp_ff_combine(const float* ff, const float* ff_el, float Q, const pp_grid* grid, float* out,
+                        pp_stream stream) {
+    g_error.clear();
+    if (!ff || !ff_el || !grid || !out) { set_error("pp_ff_combine: NULL argument"); return PP_ERR_ARG; }
+    if (!isfinite(Q)) { set_error("pp_ff_combine: Q must be finite"); return PP_ERR_ARG; }
+    if (!aligned16(ff) || !aligned16(ff_el) || !aligned16(out)) {
+        set_error("pp_ff_combine: grids must be 16-byte aligned");
+        return PP_ERR_ARG;
+    }
+    GridMap map;
+    std::string why;
+    if (!make_grid_map(grid, &map, &why)) { set_error("pp_ff_combine: " + why); return PP_ERR_SHAPE; }
+    const int64_t nfloats = map.stored_nodes * (map.interp ? 1 : 4);
+    return cuda_status(launch_ff_combine(ff, ff_el, Q, out, nfloats, (cudaStream_t)stream), "pp_ff_combine launch");
 }
 
 static bool check_tip_fire(const pp_tip* tip, const pp_fire* fire, std::string* why) {

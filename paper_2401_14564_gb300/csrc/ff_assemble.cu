@@ -33,7 +33,9 @@ constexpr int kChunk = 256;  // atoms staged per pass
 
 // kEnergy: write E alone, one float per node (tricubic grids); the force sums
 // are then never formed (the compiler drops them with their stores).
-template <int ZPT, bool kMinImage, bool kCutoff, bool kQuad, bool kEnergy = false>
+// kSplit: the point-charge field per unit probe charge goes to a second grid
+// (ffel / ffelE), the rest (LJ and the tip quadrupole) to the first.
+template <int ZPT, bool kMinImage, bool kCutoff, bool kQuad, bool kEnergy = false, bool kSplit = false>
 __global__ void __launch_bounds__(kThreads) ff_assemble_kernel(const FFLaunch P) {
     static_assert(ZPT % 2 == 0, "z-nodes come in packed pairs");
     constexpr int ZP = ZPT / 2;
@@ -52,8 +54,9 @@ __global__ void __launch_bounds__(kThreads) ff_assemble_kernel(const FFLaunch P)
     for (int t = 0; t < ZP; ++t) gz[t] = make_float2(P.z0 + (k0 + 2 * t) * P.dz, P.z0 + (k0 + 2 * t + 1) * P.dz);
 
     float2 fx[ZP], fy[ZP], fz[ZP], en[ZP];
+    float2 fxe[ZP], fye[ZP], fze[ZP], ene[ZP];  // kSplit only
 #pragma unroll
-    for (int t = 0; t < ZP; ++t) fx[t] = fy[t] = fz[t] = en[t] = make_float2(0.f, 0.f);
+    for (int t = 0; t < ZP; ++t) fx[t] = fy[t] = fz[t] = en[t] = fxe[t] = fye[t] = fze[t] = ene[t] = make_float2(0.f, 0.f);
 
     const FFConst cst = ff_const(P.R_pp, P.eps_pp, P.kQ, P.core_frac, P.Lx, P.Ly, kCutoff ? P.coul_rc : 0.f,
                                  kQuad ? P.kQzz : 0.f);
@@ -65,7 +68,8 @@ __global__ void __launch_bounds__(kThreads) ff_assemble_kernel(const FFLaunch P)
             ff_stage_atom(cst, P.x[g], P.y[g], P.z[g], P.R[g], P.eps[g], P.q[g], s0[a], s1[a], s2[a], s3[a]);
         }
         __syncthreads();
-        ff_accumulate<ZP, kMinImage, kCutoff, kQuad>(s0, s1, s2, s3, cnt, cst, gx, gy, gz, fx, fy, fz, en);
+        ff_accumulate_impl<ZP, kMinImage, kCutoff, kQuad, kSplit>(s0, s1, s2, s3, cnt, cst, gx, gy, gz, fx, fy, fz, en,
+                                                                  fxe, fye, fze, ene);
     }
 
     if (i >= P.map.nx || j >= P.map.ny) return;
@@ -76,6 +80,10 @@ __global__ void __launch_bounds__(kThreads) ff_assemble_kernel(const FFLaunch P)
             const int k = k0 + 2 * t;
             if (k < P.map.nz) P.ffE[base_xy + axis_off(P.map.az, k)] = en[t].x;
             if (k + 1 < P.map.nz) P.ffE[base_xy + axis_off(P.map.az, k + 1)] = en[t].y;
+            if constexpr (kSplit) {
+                if (k < P.map.nz) P.ffelE[base_xy + axis_off(P.map.az, k)] = ene[t].x;
+                if (k + 1 < P.map.nz) P.ffelE[base_xy + axis_off(P.map.az, k + 1)] = ene[t].y;
+            }
         }
     } else {
 #pragma unroll
@@ -84,7 +92,30 @@ __global__ void __launch_bounds__(kThreads) ff_assemble_kernel(const FFLaunch P)
             if (k < P.map.nz) P.ff[base_xy + axis_off(P.map.az, k)] = make_float4(fx[t].x, fy[t].x, fz[t].x, en[t].x);
             if (k + 1 < P.map.nz)
                 P.ff[base_xy + axis_off(P.map.az, k + 1)] = make_float4(fx[t].y, fy[t].y, fz[t].y, en[t].y);
+            if constexpr (kSplit) {
+                if (k < P.map.nz)
+                    P.ffel[base_xy + axis_off(P.map.az, k)] = make_float4(fxe[t].x, fye[t].x, fze[t].x, ene[t].x);
+                if (k + 1 < P.map.nz)
+                    P.ffel[base_xy + axis_off(P.map.az, k + 1)] = make_float4(fxe[t].y, fye[t].y, fze[t].y, ene[t].y);
+            }
         }
+    }
+}
+
+// out = a + Q b over n floats (a split force field recombined for probe charge Q): float4
+// grid-stride body, the last n mod 4 floats by the first threads of CTA 0; out may alias a.
+__global__ void ff_combine_kernel(const float* a, const float* __restrict__ b, float Q, float* out, int64_t n) {
+    const int64_t n4 = n >> 2;
+    const float4* a4 = reinterpret_cast<const float4*>(a);
+    const float4* b4 = reinterpret_cast<const float4*>(b);
+    float4* o4 = reinterpret_cast<float4*>(out);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 u = a4[i], v = __ldg(b4 + i);
+        o4[i] = make_float4(fmaf(Q, v.x, u.x), fmaf(Q, v.y, u.y), fmaf(Q, v.z, u.z), fmaf(Q, v.w, u.w));
+    }
+    if (blockIdx.x == 0 && threadIdx.x < (int)(n & 3)) {
+        const int64_t j = (n4 << 2) + threadIdx.x;
+        out[j] = fmaf(Q, b[j], a[j]);
     }
 }
 
@@ -101,8 +132,31 @@ cudaError_t launch_zpt(const FFLaunch& L, cudaStream_t s) {
 
 }  // namespace
 
+cudaError_t launch_ff_combine(const float* a, const float* b, float Q, float* out, int64_t nfloats, cudaStream_t s) {
+    if (nfloats <= 0) return cudaSuccess;
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t want = ((nfloats >> 2) + 255) / 256;
+    // one wave of 8 resident 256-thread CTAs per SM, grid-stride inside
+    const int blocks = (int)(want < 1 ? 1 : (want < 8LL * sms ? want : 8LL * sms));
+    ff_combine_kernel<<<blocks, 256, 0, s>>>(a, b, Q, out, nfloats);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_ff_assemble(const FFLaunch& L, cudaStream_t s) {
     if (L.map.nx <= 0 || L.map.ny <= 0 || L.map.nz <= 0) return cudaSuccess;
+    if (L.split) {  // one launch shape: 8 z-nodes per thread
+        constexpr int ZPT = 8;
+        dim3 grid((L.map.nx + kTileX - 1) / kTileX, (L.map.ny + kTileY - 1) / kTileY, (L.map.nz + ZPT - 1) / ZPT);
+        with_flags(L.min_image != 0, L.coul_rc > 0.f, L.kQzz != 0.f, [&](auto mi, auto cut, auto quad) {
+            constexpr bool MI = decltype(mi)::value, CUT = decltype(cut)::value, QUAD = decltype(quad)::value;
+            if (L.map.interp == 1) ff_assemble_kernel<ZPT, MI, CUT, QUAD, true, true><<<grid, kThreads, 0, s>>>(L);
+            else ff_assemble_kernel<ZPT, MI, CUT, QUAD, false, true><<<grid, kThreads, 0, s>>>(L);
+            return 0;
+        });
+        return cudaGetLastError();
+    }
     if (L.map.interp == 1) {
         constexpr int ZPT = 8;
         dim3 grid((L.map.nx + kTileX - 1) / kTileX, (L.map.ny + kTileY - 1) / kTileY, (L.map.nz + ZPT - 1) / ZPT);

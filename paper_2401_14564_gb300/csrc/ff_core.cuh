@@ -55,10 +55,14 @@ __device__ __forceinline__ void ff_stage_atom(const FFConst& c, float x, float y
     s3 = make_float4(eij, eij, kqq, kqq);
 }
 
-template <int ZP, bool kMinImage, bool kCutoff, bool kQuad>
-__device__ __forceinline__ void ff_accumulate(const float4* s0, const float4* s1, const float4* s2, const float4* s3,
-                                              int cnt, const FFConst& c, float gx, float gy, const float2 (&gz)[ZP],
-                                              float2 (&fx)[ZP], float2 (&fy)[ZP], float2 (&fz)[ZP], float2 (&en)[ZP]) {
+// kSplit: the point-charge terms go to (fxe, fye, fze, ene) instead (staged with kq = k_e q_i, i.e.
+// per unit probe charge), the LJ and quadrupole terms stay in (fx, fy, fz, en).
+template <int ZP, bool kMinImage, bool kCutoff, bool kQuad, bool kSplit>
+__device__ __forceinline__ void ff_accumulate_impl(const float4* s0, const float4* s1, const float4* s2,
+                                                   const float4* s3, int cnt, const FFConst& c, float gx, float gy,
+                                                   const float2 (&gz)[ZP], float2 (&fx)[ZP], float2 (&fy)[ZP],
+                                                   float2 (&fz)[ZP], float2 (&en)[ZP], float2 (&fxe)[ZP],
+                                                   float2 (&fye)[ZP], float2 (&fze)[ZP], float2 (&ene)[ZP]) {
     const float2 minus1 = make_float2(-1.f, -1.f);
     const float2 minus3 = make_float2(-3.f, -3.f), minus6 = make_float2(-6.f, -6.f);
     const float2 three = make_float2(3.f, 3.f), fifteen = make_float2(15.f, 15.f);
@@ -88,21 +92,31 @@ __device__ __forceinline__ void ff_accumulate(const float4* s0, const float4* s1
             const float2 u3 = f2mul(f2mul(u, u), u);
             const float2 lj = f2mul(u3, f2add(u3, minus1));  // u6 - u3
             float2 eel = f2mul(KQ, rs);                         // kq / r
-            float2 f;
+            float2 f;   // radial factor of every term (of the LJ and quadrupole terms when kSplit)
+            float2 fe;  // kSplit: radial factor of the point-charge term
             if (kCutoff) {
                 eel.x = (r2.x < c.rc2) ? eel.x : 0.f;
                 eel.y = (r2.y < c.rc2) ? eel.y : 0.f;
-                // kq (1/r^3 - 1/(r rc^2)) + 12 e (u6 - u3) / r^2
-                f = f2fma(eel, make_float2(-c.irc2, -c.irc2), f2mul(f2fma(E12, lj, eel), ir2));
+                if (kSplit) {
+                    fe = f2fma(eel, make_float2(-c.irc2, -c.irc2), f2mul(eel, ir2));  // kq (1/r^3 - 1/(r rc^2))
+                    f = f2mul(f2mul(E12, lj), ir2);
+                } else {
+                    // kq (1/r^3 - 1/(r rc^2)) + 12 e (u6 - u3) / r^2
+                    f = f2fma(eel, make_float2(-c.irc2, -c.irc2), f2mul(f2fma(E12, lj, eel), ir2));
+                }
                 // shifted-force energy kq (1/r + r/rc^2 - 2/rc)
                 float2 ee = f2fma(eel, f2mul(r2, make_float2(c.irc2, c.irc2)), eel);
                 ee.x -= (r2.x < c.rc2) ? KQ.x * c.two_irc : 0.f;
                 ee.y -= (r2.y < c.rc2) ? KQ.y * c.two_irc : 0.f;
                 eel = ee;
+            } else if (kSplit) {
+                fe = f2mul(eel, ir2);
+                f = f2mul(f2mul(E12, lj), ir2);
             } else {
                 f = f2mul(f2fma(E12, lj, eel), ir2);  // (12 e (u6 - u3) + kq / r) / r^2
             }
             float2 fzf = f;
+            float2 eq = make_float2(0.f, 0.f);  // quadrupole energy
             if (kQuad) {
                 float2 c5 = f2mul(KQQ, f2mul(f2mul(ir2, ir2), rs));  // kqq / r^5
                 if (kCutoff) {
@@ -112,14 +126,32 @@ __device__ __forceinline__ void ff_accumulate(const float4* s0, const float4* s1
                 const float2 rz2 = f2mul(rz, rz);
                 f = f2fma(c5, f2fma(f2mul(rz2, ir2), fifteen, minus3), f);  // + kqq (15 dz^2/r^2 - 3) / r^5
                 fzf = f2fma(c5, minus6, f);                                 // axial -6 kqq dz / r^5
-                eel = f2fma(c5, f2sub(f2mul(rz2, three), r2), eel);        // + kqq (3 dz^2 - r^2) / r^5
+                // + kqq (3 dz^2 - r^2) / r^5
+                if (kSplit) eq = f2mul(c5, f2sub(f2mul(rz2, three), r2));
+                else eel = f2fma(c5, f2sub(f2mul(rz2, three), r2), eel);
             }
             fx[t] = f2fma(f, RX, fx[t]);
             fy[t] = f2fma(f, RY, fy[t]);
             fz[t] = f2fma(fzf, rz, fz[t]);
-            en[t] = f2add(f2fma(EE, f2sub(lj, u3), en[t]), eel);  // e (u6 - 2 u3) + E_el
+            if (kSplit) {
+                en[t] = f2add(f2fma(EE, f2sub(lj, u3), en[t]), eq);  // e (u6 - 2 u3) + E_quad
+                fxe[t] = f2fma(fe, RX, fxe[t]);
+                fye[t] = f2fma(fe, RY, fye[t]);
+                fze[t] = f2fma(fe, rz, fze[t]);
+                ene[t] = f2add(ene[t], eel);
+            } else {
+                en[t] = f2add(f2fma(EE, f2sub(lj, u3), en[t]), eel);  // e (u6 - 2 u3) + E_el
+            }
         }
     }
+}
+
+template <int ZP, bool kMinImage, bool kCutoff, bool kQuad>
+__device__ __forceinline__ void ff_accumulate(const float4* s0, const float4* s1, const float4* s2, const float4* s3,
+                                              int cnt, const FFConst& c, float gx, float gy, const float2 (&gz)[ZP],
+                                              float2 (&fx)[ZP], float2 (&fy)[ZP], float2 (&fz)[ZP], float2 (&en)[ZP]) {
+    ff_accumulate_impl<ZP, kMinImage, kCutoff, kQuad, false>(s0, s1, s2, s3, cnt, c, gx, gy, gz, fx, fy, fz, en, fx,
+                                                             fy, fz, en);
 }
 
 }  // namespace pp

@@ -79,8 +79,13 @@ struct FFLaunch {
     float4* ff;   // map.interp == 0
     float* ffE;   // map.interp == 1: energies only
     int zpt;  // z-nodes per thread: 4, 8 or 16
+    int split;     // 1: point charges per unit probe charge into ffel / ffelE, the rest into ff / ffE
+    float4* ffel;  // split, map.interp == 0
+    float* ffelE;  // split, map.interp == 1
 };
 cudaError_t launch_ff_assemble(const FFLaunch& L, cudaStream_t s);
+// out = a + Q b over nfloats floats (16-byte aligned buffers; out may alias a)
+cudaError_t launch_ff_combine(const float* a, const float* b, float Q, float* out, int64_t nfloats, cudaStream_t s);
 
 struct RelaxLaunch {
     const float4* ff;   // map.interp == 0

@@ -117,6 +117,10 @@ def lib():
             L.pp_make_ff_tuned.argtypes = [C.POINTER(Atoms), C.POINTER(Probe), C.POINTER(Grid), vp,
                                            C.POINTER(Tuning), vp]
             L.pp_make_ff_tuned.restype = st
+            L.pp_make_ff_split.argtypes = [C.POINTER(Atoms), C.POINTER(Probe), C.POINTER(Grid), vp, vp, vp]
+            L.pp_make_ff_split.restype = st
+            L.pp_ff_combine.argtypes = [vp, vp, C.c_float, C.POINTER(Grid), vp, vp]
+            L.pp_ff_combine.restype = st
             L.pp_relax_scan.argtypes = [vp, C.POINTER(Grid), C.POINTER(Scan), C.POINTER(Tip), C.POINTER(Fire),
                                         vp, vp, vp, C.POINTER(DF), vp, vp]
             L.pp_relax_scan.restype = st
@@ -248,6 +252,24 @@ def pp_make_ff_tuned(atoms: Atoms, probe: Probe, grid: Grid, ff: torch.Tensor, t
         raise ValueError("ff buffer smaller than pp_ff_floats(grid)")
     _check(lib().pp_make_ff_tuned(C.byref(atoms), C.byref(probe), C.byref(grid), _dev(ff, "ff"),
                                   C.byref(tuning) if tuning is not None else None, _stream(stream)))
+
+
+def pp_make_ff_split(atoms: Atoms, probe: Probe, grid: Grid, ff: torch.Tensor, ff_el: torch.Tensor, stream=None):
+    """LJ (+ quadrupole) into ff, point-charge electrostatics per unit probe charge into ff_el."""
+    n = pp_ff_floats(grid)
+    if ff.numel() < n or ff_el.numel() < n:
+        raise ValueError("ff / ff_el buffer smaller than pp_ff_floats(grid)")
+    _check(lib().pp_make_ff_split(C.byref(atoms), C.byref(probe), C.byref(grid), _dev(ff, "ff"), _dev(ff_el, "ff_el"),
+                                  _stream(stream)))
+
+
+def pp_ff_combine(ff: torch.Tensor, ff_el: torch.Tensor, Q: float, grid: Grid, out: torch.Tensor, stream=None):
+    """out = ff + Q ff_el (the grid for probe charge Q); out may be ff."""
+    n = pp_ff_floats(grid)
+    if ff.numel() < n or ff_el.numel() < n or out.numel() < n:
+        raise ValueError("buffer smaller than pp_ff_floats(grid)")
+    _check(lib().pp_ff_combine(_dev(ff, "ff"), _dev(ff_el, "ff_el"), float(Q), C.byref(grid), _dev(out, "out"),
+                               _stream(stream)))
 
 
 def pp_relax_scan(ff, grid: Grid, scan: Scan, tip: Tip, fire: Fire, pos, fz, iters, fused_df=None, df=None,

@@ -140,3 +140,23 @@ def test_fft_correlate_validated_on_host(L):
     assert L.pp_fft_correlate(fake, fake, C.byref(g), C.c_float(1), C.c_float(1), 0, fake, fake, 100, None) == 4
     assert L.pp_fft_correlate(fake, fake, C.byref(g), C.c_float(1), C.c_float(0), 0, fake, fake, 1 << 20, None) == 1
     assert L.pp_fft_correlate(None, fake, C.byref(g), C.c_float(1), C.c_float(1), 0, fake, fake, 1 << 20, None) == 1
+
+
+def test_split_and_combine_are_validated_on_host(L):
+    g = pp.make_grid({"nx": 10, "ny": 6, "nz": 5, "x0": 0, "y0": 0, "z0": 0, "dx": 0.1, "dy": 0.1, "dz": 0.1,
+                      "periodic_xy": 1})
+    fake, other = C.c_void_p(16), C.c_void_p(32)  # never dereferenced: the host checks fail first
+    atoms = pp.Atoms(0, None, None, None, None, None, None)
+    probe = pp.make_probe({"R_pp": 1.66, "eps_pp": 0.0091, "Q": -0.1, "coul_rc": 0.0, "min_image": 0,
+                           "core_frac": 0.5})
+    assert L.pp_make_ff_split(C.byref(atoms), C.byref(probe), C.byref(g), fake, None, None) == 1
+    assert b"ff_el" in L.pp_last_error()
+    assert L.pp_make_ff_split(C.byref(atoms), C.byref(probe), C.byref(g), fake, fake, None) == 1
+    assert b"different" in L.pp_last_error()
+    assert L.pp_make_ff_split(C.byref(atoms), C.byref(probe), C.byref(g), fake, C.c_void_p(40), None) == 1
+    assert b"aligned" in L.pp_last_error()
+    assert L.pp_ff_combine(fake, other, C.c_float(float("nan")), C.byref(g), fake, None) == 1
+    assert L.pp_ff_combine(fake, other, C.c_float(0.5), C.byref(g), C.c_void_p(8), None) == 1
+    bad = pp.make_grid({"nx": 1, "ny": 6, "nz": 5, "x0": 0, "y0": 0, "z0": 0, "dx": 0.1, "dy": 0.1, "dz": 0.1,
+                        "periodic_xy": 1})
+    assert L.pp_ff_combine(fake, other, C.c_float(0.5), C.byref(bad), fake, None) == 2
