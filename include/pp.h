@@ -402,7 +402,7 @@ PP_API size_t pp_fft_workspace(const pp_grid* grid);
  * scale = 1, p = 1 this is the electrostatic energy of Eq. El_conv; with
  * scale = A, p = beta the Pauli energy of Eq. Pauli_FDBM ([g f]^beta =
  * g^beta f^beta; negative density samples count as 0 when p != 1).  f and g
- * are device arrays [nz][ny][nx] of floats; ff is a force-field buffer of the
+ * are device arrays [nz][ny][nx] of floats, 16-byte aligned; ff is a force-field buffer of the
  * grid (layout 0, interp 0): (Fx, Fy, Fz, E) per node is written
  * (accumulate = 0) or added to what ff holds (accumulate = 1), e.g. to the
  * Lennard-Jones grid of pp_make_ff.  ws: pp_fft_workspace(grid) bytes,

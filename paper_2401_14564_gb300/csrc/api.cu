@@ -580,7 +580,10 @@ pp_status pp_fft_correlate(const float* f, const float* g, const pp_grid* grid, 
         set_error("pp_fft_correlate: scale must be finite, power > 0, accumulate 0 or 1");
         return PP_ERR_ARG;
     }
-    if (!aligned16(ff) || !aligned16(ws)) { set_error("pp_fft_correlate: ff and ws must be 16-byte aligned"); return PP_ERR_ARG; }
+    if (!aligned16(f) || !aligned16(g) || !aligned16(ff) || !aligned16(ws)) {
+        set_error("pp_fft_correlate: f, g, ff and ws must be 16-byte aligned");
+        return PP_ERR_ARG;
+    }
     GridMap map;
     std::string why;
     pp_status st = PP_OK;

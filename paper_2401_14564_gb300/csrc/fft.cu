@@ -12,10 +12,10 @@
 //   output    ff[n] = (Fx, Fy, Fz, E), written or added.
 // The 1D passes are Stockham auto-sort FFTs with radix-8 stages (and one
 // radix-2 or radix-4 stage) in registers, for power-of-two lengths up to 1024:
-// the first stage reads global memory, the last writes it, the ones between
-// exchange through shared memory; a block transforms 16 lines, and along y
-// and z those are 16 neighbouring columns, so every global access is a row of
-// consecutive complex values.
+// a CTA transforms a tile of neighbouring lines (rows along x, columns along y
+// and z, so every global access is a row of consecutive complex values); the
+// first stage reads global memory, the last writes it, the ones between
+// exchange through shared memory.
 #include <cuda_runtime.h>
 
 #include "pp_internal.cuh"
@@ -23,10 +23,11 @@
 namespace pp {
 namespace {
 
-constexpr int kFftThreads = 512;  // 2 blocks per SM at 64 registers: 32 warps to keep loads in flight
-constexpr int kUnits = 2;         // stage units per thread per trip
-constexpr int kLines = 16;         // lines per block along x
-constexpr int kStridedLines = 64;  // columns per block along y and z (at most)
+constexpr int kFftThreads = 256;  // 4 CTAs per SM at 64 registers, tiles of up to 36 KB
+constexpr int kFftBlocksPerSm = 4;
+constexpr int kUnits = 2;          // stage units per thread per trip
+constexpr int kLines = 16;         // lines per tile along x (at most)
+constexpr int kStridedLines = 64;  // columns per tile along y and z (at most)
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
@@ -76,102 +77,144 @@ __device__ __forceinline__ void dft<8>(float2 (&x)[8], float sign) {
     x[7] = csub(e[3], o3);
 }
 
-// Address of element p of line l within a block: base + l * lstride + p * pstride.
-struct Lines {
-    long long base;
-    long long lstride, pstride;
-    bool contiguous;  // pstride == 1: consecutive threads take consecutive elements of a line
-    __device__ __forceinline__ long long at(int l, int p) const { return base + l * lstride + p * pstride; }
+// A pass transforms tiles of nl = 2^log2nl lines of n = 2^LOG2N elements.  kContig: lines along x
+// (element p of line l at base + l lstride + p); else columns along y or z (at base + l +
+// p pstride).  In shared memory, columns are interleaved (element p of line l at p nl + l:
+// consecutive threads take consecutive lines, so a warp touches consecutive banks).  Rows lie
+// one after the other, element e = l n + p, in a layout chosen by the stage that writes them so
+// that both its writes and the next stage's reads (runs of 16 consecutive elements) spread over
+// the 32 banks (a complex value spans two): after the first radix-8 stage (stride-8 writes) the
+// low 3 bits of e are XORed with bits 4-6; after the second (runs of 8 at stride 64) every 64
+// elements are followed by 8 pad slots; later stages write runs of 16 or more and keep e.  n is
+// a template parameter: every stage's index arithmetic folds to shifts and masks of constants.
+struct Pass {
+    int log2nl, nbi, ntiles;
+    long long outer_pitch, stride;  // stride: lstride for rows, pstride for columns
+    float sign;
 };
 
-// Shared-memory slot of element p of line l: lines one after the other when
-// consecutive threads walk along a line, interleaved when they walk across
-// lines (strided passes), so that a warp's accesses hit consecutive banks.
-__device__ __forceinline__ int sidx(const Lines& ln, int l, int p, int n, int nl) {
-    return ln.contiguous ? l * n + p : p * nl + l;
+template <int LOG2N, bool kContig>
+struct TileAt {
+    long long base, stride;
+    int log2nl;
+    __device__ __forceinline__ long long at(int l, int p) const {
+        return kContig ? base + l * stride + p : base + l + p * stride;
+    }
+    // slot of element p of line l in the layout written by the stage after radices L = 2^LOG2W
+    template <int LOG2W>
+    __device__ __forceinline__ int slot(int l, int p) const {
+        if (!kContig) return (p << log2nl) + l;
+        const int e = (l << LOG2N) + p;
+        if constexpr (LOG2W == 0) return e ^ ((e >> 4) & 7);
+        else if constexpr (LOG2W == 3) return e + 8 * (e >> 6);
+        else return e;
+    }
+};
+
+// Slots of the largest layout (8 pad slots per 64 elements along rows).
+template <int LOG2N, bool kContig>
+__host__ __device__ __forceinline__ int tile_slots(int nl) {
+    return kContig ? (nl << LOG2N) + (nl << LOG2N) / 8 : nl << LOG2N;
 }
 
-// One Stockham stage of radix R with L = product of the earlier radices: unit
-// (line l, t), t < n/R, j = t mod L, k = t / L, reads a_m = x[t + m n/R],
-// twiddles a_m by w_{LR}^{m j}, transforms, writes y[k L R + j + m L].  The
-// first stage reads global memory, the last writes it, the others work in
-// shared memory (in place: every read of a stage precedes its writes).
-template <int R>
-__device__ __forceinline__ void stockham_stage(float2* data, const Lines& ln, float2* x, const float2* tw, int n,
-                                               int nlines, int L, bool first, bool last, float sign) {
-    const int nr = n / R, units = nlines * nr;
-    const int tws = n / (L * R);
-    // middle stages (neither first nor last) have units <= kUnits * kFftThreads: one trip
-    for (int u0 = 0; u0 < units; u0 += kFftThreads * kUnits) {
-        float2 a[kUnits][R];
-        int ul[kUnits], ut[kUnits];
+// Twiddles of the stage after radices L = 2^LOG2L (all radix 8 before it), radix R = 2^LR:
+// w_{LR}^{m j} for m = 1..R-1, j = 0..L-1 at tw[(L - 1) + (m - 1) L + j], so that threads with
+// consecutive j read consecutive slots; the stages' tables together fill tw[0 .. n-2].
+template <int LOG2L, int LR>
+__device__ __forceinline__ void stage_twiddles(float2* tw, float sign) {
+    constexpr int L = 1 << LOG2L, R = 1 << LR;
+    for (int e = threadIdx.x; e < (R - 1) * L; e += kFftThreads) {
+        const int m = (e >> LOG2L) + 1, j = e & (L - 1);
+        float sn, cs;
+        sincospif((float)(m * j) * (2.f / (float)(L * R)), &sn, &cs);
+        tw[(L - 1) + e] = make_float2(cs, sign * sn);
+    }
+}
+
+// One Stockham stage of radix R = 2^LR after stages whose radices multiply to L = 2^LOG2L: unit
+// (line l, t), t < n/R, j = t mod L, k = t / L, reads a_m = x[t + m n/R], twiddles a_m by
+// w_{LR}^{m j}, transforms, writes y[k L R + j + m L].  kFirst reads global memory, kLast
+// writes it; the others read and write the tile in place (every read of a stage precedes its
+// writes: a stage that writes the tile runs in one trip, see lines_per_block).
+template <int LOG2N, bool kContig, int LR, int LOG2L, bool kFirst, bool kLast>
+__device__ __forceinline__ void stage(float2* data, const TileAt<LOG2N, kContig>& T, float2* x, const float2* tw,
+                                      float sign) {
+    constexpr int R = 1 << LR, LOG2NR = LOG2N - LR, NR = 1 << LOG2NR;
+    const int units = 1 << (T.log2nl + LOG2NR);
+    const int nl_mask = (1 << T.log2nl) - 1;
+    constexpr int U = kUnits;
+    for (int u0 = 0; u0 < units; u0 += kFftThreads * U) {
+        float2 a[U][R];
+        int ul[U], ut[U];
 #pragma unroll
-        for (int q = 0; q < kUnits; ++q) {
+        for (int q = 0; q < U; ++q) {
             const int u = u0 + q * kFftThreads + threadIdx.x;
-            // consecutive threads: consecutive t for contiguous lines, consecutive lines otherwise
-            ul[q] = ln.contiguous ? u / nr : u % nlines;
-            ut[q] = ln.contiguous ? u - ul[q] * nr : u / nlines;
+            // consecutive threads: consecutive t along rows, consecutive lines across columns
+            ul[q] = kContig ? u >> LOG2NR : u & nl_mask;
+            ut[q] = kContig ? u & (NR - 1) : u >> T.log2nl;
             if (u < units) {
 #pragma unroll
                 for (int m = 0; m < R; ++m) {
-                    const int p = ut[q] + m * nr;
-                    a[q][m] = first ? data[ln.at(ul[q], p)] : x[sidx(ln, ul[q], p, n, nlines)];
+                    const int p = ut[q] + m * NR;
+                    if constexpr (kFirst) a[q][m] = data[T.at(ul[q], p)];
+                    else a[q][m] = x[T.template slot<LOG2L - 3>(ul[q], p)];
                 }
             }
         }
-        if (!first) __syncthreads();
+        if (!kFirst) __syncthreads();
 #pragma unroll
-        for (int q = 0; q < kUnits; ++q) {
+        for (int q = 0; q < U; ++q) {
             const int u = u0 + q * kFftThreads + threadIdx.x;
             if (u >= units) continue;
-            const int t = ut[q], j = t % L, k = t / L;
+            const int t = ut[q], j = t & ((1 << LOG2L) - 1), k = t >> LOG2L;
 #pragma unroll
-            for (int m = 1; m < R; ++m) a[q][m] = cmul(tw[m * j * tws], a[q][m]);
+            for (int m = 1; m < R; ++m) a[q][m] = cmul(tw[((1 << LOG2L) - 1) + ((m - 1) << LOG2L) + j], a[q][m]);
             dft<R>(a[q], sign);
 #pragma unroll
             for (int m = 0; m < R; ++m) {
-                const int p = k * L * R + j + m * L;
-                if (last) data[ln.at(ul[q], p)] = a[q][m];
-                else x[sidx(ln, ul[q], p, n, nlines)] = a[q][m];
+                const int p = (k << (LOG2L + LR)) + j + (m << LOG2L);
+                if constexpr (kLast) data[T.at(ul[q], p)] = a[q][m];
+                else x[T.template slot<LOG2L>(ul[q], p)] = a[q][m];
             }
         }
-        if (!last) __syncthreads();
+        if (!kLast) __syncthreads();
     }
 }
 
-// One 1D pass: block b transforms nl lines of n elements, element p of line
-// l at (b / nbi) * outer_pitch + (b % nbi) * nl * lstride + l * lstride +
-// p * pstride (see fft3 for the three axes of the padded layout).  sign = -1
-// forward, +1 inverse (unnormalised).  Radix-8 stages, then one radix-4 or
-// radix-2 stage for the rest of log2 n.
-__global__ void __launch_bounds__(kFftThreads, 2) fft_pass_kernel(float2* data, int n, int log2n, int nl, int nbi,
-                                                                  long long outer_pitch, long long lstride,
-                                                                  long long pstride, float sign) {
-    extern __shared__ float2 sm[];
-    float2* tw = sm;      // n twiddles exp(sign 2 pi i q / n)
-    float2* x = sm + n;   // nl lines of n
-    for (int q = threadIdx.x; q < n; q += kFftThreads) {
-        float s, c;
-        sincospif(2.f * (float)q / (float)n, &s, &c);
-        tw[q] = make_float2(c, sign * s);
-    }
-    Lines ln;
-    ln.base = (long long)(blockIdx.x / nbi) * outer_pitch + (long long)(blockIdx.x % nbi) * nl * lstride;
-    ln.lstride = lstride;
-    ln.pstride = pstride;
-    ln.contiguous = pstride == 1;
+// All stages of one tile: radix-8 stages first (the first reading global memory), the radix-2
+// or radix-4 remainder last.
+template <int LOG2N, bool kContig>
+__device__ __forceinline__ void fft_tile(float2* data, const TileAt<LOG2N, kContig>& T, float2* x, const float2* tw,
+                                         float sign) {
+    constexpr int N8 = LOG2N / 3, REST = LOG2N - 3 * N8;
+    if constexpr (N8 >= 1) stage<LOG2N, kContig, 3, 0, true, N8 == 1 && REST == 0>(data, T, x, tw, sign);
+    if constexpr (N8 >= 2) stage<LOG2N, kContig, 3, 3, false, N8 == 2 && REST == 0>(data, T, x, tw, sign);
+    if constexpr (N8 >= 3) stage<LOG2N, kContig, 3, 6, false, N8 == 3 && REST == 0>(data, T, x, tw, sign);
+    if constexpr (REST == 1) stage<LOG2N, kContig, 1, 3 * N8, N8 == 0, true>(data, T, x, tw, sign);
+    if constexpr (REST == 2) stage<LOG2N, kContig, 2, 3 * N8, N8 == 0, true>(data, T, x, tw, sign);
+}
+
+// One 1D pass: CTA b takes tile b, i.e. outer index b / nbi and lines (b % nbi) nl onwards, at
+// (b / nbi) outer_pitch + line lstride + p pstride (see fft3 for the three axes of the padded
+// layout).  sign = -1 forward, +1 inverse (unnormalised).
+template <int LOG2N, bool kContig>
+__global__ void __launch_bounds__(kFftThreads, kFftBlocksPerSm) fft_pass_kernel(float2* data, const Pass P) {
+    extern __shared__ __align__(128) unsigned char smraw[];
+    constexpr int N = 1 << LOG2N;
+    float2* tw = reinterpret_cast<float2*>(smraw);  // the stages' twiddle tables, N - 1 values
+    float2* x = tw + N;
+    constexpr int N8 = LOG2N / 3, REST = LOG2N - 3 * N8;
+    if constexpr (N8 >= 1) stage_twiddles<0, 3>(tw, P.sign);
+    if constexpr (N8 >= 2) stage_twiddles<3, 3>(tw, P.sign);
+    if constexpr (N8 >= 3) stage_twiddles<6, 3>(tw, P.sign);
+    if constexpr (REST > 0) stage_twiddles<3 * N8, REST>(tw, P.sign);
+    TileAt<LOG2N, kContig> T;
+    const int b = blockIdx.x;
+    T.base = (long long)(b / P.nbi) * P.outer_pitch + ((long long)(b % P.nbi) << P.log2nl) * (kContig ? P.stride : 1);
+    T.stride = P.stride;
+    T.log2nl = P.log2nl;
     __syncthreads();
-    // radix-8 stages first (the first stage, read from global memory, then has 8 loads per
-    // unit in flight), the radix-2 or radix-4 remainder last
-    const int n8 = log2n / 3, rest = log2n - 3 * n8;
-    const int nstages = n8 + (rest ? 1 : 0);
-    int L = 1;
-    for (int s = 0; s < n8; ++s) {
-        stockham_stage<8>(data, ln, x, tw, n, nl, L, s == 0, s == nstages - 1, sign);
-        L <<= 3;
-    }
-    if (rest == 1) stockham_stage<2>(data, ln, x, tw, n, nl, L, n8 == 0, true, sign);
-    else if (rest == 2) stockham_stage<4>(data, ln, x, tw, n, nl, L, n8 == 0, true, sign);
+    fft_tile<LOG2N, kContig>(data, T, x, tw, P.sign);
 }
 
 __device__ __forceinline__ float powered(float v, float p) {
@@ -200,13 +243,26 @@ Pad make_pad(int nx, int ny, int nz) {
 
 // Elementwise kernels walk rows (j, k) of the grid: blocks take rows, threads the
 // x index, so no per-element division is needed.
+// Rows of nx >= 4 go four nodes per thread: two 16-byte loads, two 16-byte stores (row starts
+// are 16-byte aligned on both sides: nx, nx + 16 and the plane pitch are multiples of 4).
 __global__ void pack_kernel(const float* __restrict__ f, const float* __restrict__ g, float2* z, const Pad P, float p) {
     const int rows = P.ny * P.nz;
     for (int r = blockIdx.x; r < rows; r += gridDim.x) {
         const int j = r % P.ny, k = r / P.ny;
         const long long src = (long long)r * P.nx, dst = P.at(0, j, k);
-        for (int i = threadIdx.x; i < P.nx; i += blockDim.x)
-            z[dst + i] = make_float2(powered(__ldg(f + src + i), p), powered(__ldg(g + src + i), p));
+        if ((P.nx & 3) == 0) {
+            const float4* f4 = reinterpret_cast<const float4*>(f + src);
+            const float4* g4 = reinterpret_cast<const float4*>(g + src);
+            float4* z4 = reinterpret_cast<float4*>(z + dst);
+            for (int i = threadIdx.x; i < (P.nx >> 2); i += blockDim.x) {
+                const float4 a = __ldg(f4 + i), b = __ldg(g4 + i);
+                z4[2 * i] = make_float4(powered(a.x, p), powered(b.x, p), powered(a.y, p), powered(b.y, p));
+                z4[2 * i + 1] = make_float4(powered(a.z, p), powered(b.z, p), powered(a.w, p), powered(b.w, p));
+            }
+        } else {
+            for (int i = threadIdx.x; i < P.nx; i += blockDim.x)
+                z[dst + i] = make_float2(powered(__ldg(f + src + i), p), powered(__ldg(g + src + i), p));
+        }
     }
 }
 
@@ -275,36 +331,66 @@ int ilog2i(int v) {
     return l;
 }
 
-// nl lines of n per block; lines of the block are lstride apart, blocks nbi per outer index.
-cudaError_t fft_axis(float2* data, int n, int nl, int nbi, int nouter, long long outer_pitch, long long lstride,
-                     long long pstride, float sign, cudaStream_t s) {
-    if (n < 2) return cudaSuccess;
-    const size_t smem = (size_t)(n + nl * n) * sizeof(float2);
-    cudaError_t e = cudaFuncSetAttribute(fft_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+template <int LOG2N, bool kContig>
+cudaError_t launch_pass(float2* data, const Pass& P, cudaStream_t s) {
+    const size_t smem = ((size_t)(1 << LOG2N) + (size_t)tile_slots<LOG2N, kContig>(1 << P.log2nl)) * sizeof(float2);
+    auto k = fft_pass_kernel<LOG2N, kContig>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    fft_pass_kernel<<<nouter * nbi, kFftThreads, smem, s>>>(data, n, ilog2i(n), nl, nbi, outer_pitch, lstride, pstride,
-                                                           sign);
+    k<<<P.ntiles, kFftThreads, smem, s>>>(data, P);
     return cudaGetLastError();
 }
 
-// Lines per block for lines of n among `avail` neighbours: up to `want`, fewer when the axis
-// has fewer, and at most 8 kUnits kFftThreads / n so that a middle (shared-memory, in-place)
-// radix-8 stage has at most kUnits * kFftThreads units: all of its reads then happen before
-// its writes.  Strided passes take up to 64 columns (512-byte rows), so that each of the n
-// widely spaced rows a block visits is read in one long burst.
-int lines_per_block(int n, int avail, int want) {
-    int L = avail < want ? avail : want;
-    return L < 8 * kUnits * kFftThreads / n ? L : 8 * kUnits * kFftThreads / n;
+template <bool kContig>
+cudaError_t launch_pass_n(float2* data, int log2n, const Pass& P, cudaStream_t s) {
+    switch (log2n) {
+        case 1: return launch_pass<1, kContig>(data, P, s);
+        case 2: return launch_pass<2, kContig>(data, P, s);
+        case 3: return launch_pass<3, kContig>(data, P, s);
+        case 4: return launch_pass<4, kContig>(data, P, s);
+        case 5: return launch_pass<5, kContig>(data, P, s);
+        case 6: return launch_pass<6, kContig>(data, P, s);
+        case 7: return launch_pass<7, kContig>(data, P, s);
+        case 8: return launch_pass<8, kContig>(data, P, s);
+        case 9: return launch_pass<9, kContig>(data, P, s);
+        case 10: return launch_pass<10, kContig>(data, P, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// Tiles of nl lines of n; nbi tiles per outer index; rows along x (lines lstride apart) or columns
+// (elements pstride apart).
+cudaError_t fft_axis(float2* data, bool rows, int n, int nl, int nbi, int nouter, long long outer_pitch,
+                     long long stride, float sign, cudaStream_t s) {
+    if (n < 2) return cudaSuccess;
+    Pass P;
+    P.log2nl = ilog2i(nl);
+    P.nbi = nbi;
+    P.ntiles = nbi * nouter;
+    P.outer_pitch = outer_pitch;
+    P.stride = stride;
+    P.sign = sign;
+    return rows ? launch_pass_n<true>(data, ilog2i(n), P, s) : launch_pass_n<false>(data, ilog2i(n), P, s);
+}
+
+// Lines per tile for lines of n among `avail` neighbours: up to `want`, fewer when the axis
+// has fewer, and at most 8 U kFftThreads / n (U units per thread) so that a radix-8 stage that
+// writes shared memory (in place) has at most U kFftThreads units: all of its reads then happen
+// before its writes.
+int lines_per_block(int n, int avail, int want, int units) {
+    const int cap = 8 * units * kFftThreads / n;
+    const int L = avail < want ? avail : want;
+    return L < cap ? L : cap;
 }
 
 cudaError_t fft3(float2* data, const Pad& P, float sign, cudaStream_t s) {
     cudaError_t e;
-    int nl = lines_per_block(P.nx, P.ny, kLines);  // x: lines are rows j of a plane k
-    if ((e = fft_axis(data, P.nx, nl, P.ny / nl, P.nz, P.pz, P.px, 1, sign, s)) != cudaSuccess) return e;
-    nl = lines_per_block(P.ny, P.nx, kStridedLines);  // y: lines are columns i of a plane k
-    if ((e = fft_axis(data, P.ny, nl, P.nx / nl, P.nz, P.pz, 1, P.px, sign, s)) != cudaSuccess) return e;
-    nl = lines_per_block(P.nz, P.nx, kStridedLines);  // z: lines are columns i of a row j
-    return fft_axis(data, P.nz, nl, P.nx / nl, P.ny, P.px, 1, P.pz, sign, s);
+    int nl = lines_per_block(P.nx, P.ny, kLines, kUnits);  // x: lines are rows j of a plane k
+    if ((e = fft_axis(data, true, P.nx, nl, P.ny / nl, P.nz, P.pz, P.px, sign, s)) != cudaSuccess) return e;
+    nl = lines_per_block(P.ny, P.nx, kStridedLines, kUnits);  // y: lines are columns i of a plane k
+    if ((e = fft_axis(data, false, P.ny, nl, P.nx / nl, P.nz, P.pz, P.px, sign, s)) != cudaSuccess) return e;
+    nl = lines_per_block(P.nz, P.nx, kStridedLines, kUnits);  // z: lines are columns i of a row j
+    return fft_axis(data, false, P.nz, nl, P.nx / nl, P.ny, P.px, P.pz, sign, s);
 }
 
 }  // namespace

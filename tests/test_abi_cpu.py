@@ -140,6 +140,10 @@ def test_fft_correlate_validated_on_host(L):
     assert L.pp_fft_correlate(fake, fake, C.byref(g), C.c_float(1), C.c_float(1), 0, fake, fake, 100, None) == 4
     assert L.pp_fft_correlate(fake, fake, C.byref(g), C.c_float(1), C.c_float(0), 0, fake, fake, 1 << 20, None) == 1
     assert L.pp_fft_correlate(None, fake, C.byref(g), C.c_float(1), C.c_float(1), 0, fake, fake, 1 << 20, None) == 1
+    # the sample field is read 16 bytes at a time
+    assert L.pp_fft_correlate(C.c_void_p(20), fake, C.byref(g), C.c_float(1), C.c_float(1), 0, fake, fake, 1 << 20,
+                              None) == 1
+    assert b"aligned" in L.pp_last_error()
 
 
 def test_split_and_combine_are_validated_on_host(L):
