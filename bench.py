@@ -445,6 +445,52 @@ def measure_split(case, steps, warmup, flush, hbm_gbs):
             "split_ff_traffic": measured_traffic("ff_assemble_split"), "combine_traffic": measured_traffic("ff_combine")}
 
 
+IETS_BYTES_PER_POINT = 164  # position 12 + the cell's 8 corner float4 128 + eigenvalues and mode energies 24
+
+
+def measure_iets(case, steps, warmup, flush, hbm_gbs):
+    """IETS map (pp_iets) at the relaxed positions of the line's workload, on the trilinear force
+    grid and on the 0.1 A tricubic energy grid; CUDA events, L2 flushed before each."""
+    import torch
+
+    from paper_2401_14564_gb300 import afm, pp
+
+    out = []
+    for interp in (0, 1):
+        c = dict(case, grid=dict(case["grid"], interp=interp))
+        sim = afm.Simulator(c)
+        sim.run(afm.atoms_to_device(c["atoms"]))
+        s = c["scan"]
+        npts = s["nx"] * s["ny"] * s["nz"]
+        eig = torch.empty(3 * npts, device="cuda")
+        hw = torch.empty(3 * npts, device="cuda")
+
+        def go():
+            pp.pp_iets(sim.ff, sim.grid, sim.scan, sim.tip, sim.pos, 16.0, eig, hw)
+
+        for _ in range(max(warmup, 3)):
+            go()
+        stream = torch.cuda.current_stream()
+        ts = []
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            go()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ms = statistics.mean(ts)
+        entry = {"grid": "trilinear force grid" if interp == 0 else "tricubic energy grid", "ms": ms,
+                 "points_per_s": npts / (ms * 1e-3)}
+        if interp == 0:
+            gbs = IETS_BYTES_PER_POINT * npts / (ms * 1e-3) / 1e9
+            entry.update({"bytes_per_point": IETS_BYTES_PER_POINT, "gbs": gbs, "frac_of_hbm": gbs / hbm_gbs})
+        out.append(entry)
+        del sim, eig, hw
+    return {"workload": "flake60 relaxed positions, 2.62 M points, CO mass 16 amu", "points": out}
+
+
 FFT_BYTES_PER_NODE = 224  # one correlation: pack 16 + 3 forward passes 48 + spectral 32 + 6 inverse passes 96 + output 32
 FDBM_A, FDBM_BETA = 18.0, 1.0  # Pauli prefactor and exponent of the synthetic full-density workload
 
@@ -578,6 +624,7 @@ def main():
     ap.add_argument("--no-tricubic", action="store_true")
     ap.add_argument("--no-fdbm", action="store_true")
     ap.add_argument("--no-split", action="store_true")
+    ap.add_argument("--no-iets", action="store_true")
     ap.add_argument("--zpt", type=int, default=0, help="FF z-nodes per thread (skips the autotuner)")
     ap.add_argument("--brick", default="", help="bricked layout bx,by,bz for the scan (skips the autotuner)")
     ap.add_argument("--batch-mol", type=int, default=1024)
@@ -747,6 +794,8 @@ def main():
         line["quadrupole"] = measure_quadrupole(case, tuning, max(3, args.steps // 2), args.warmup, flush, alu_peak)
     if not args.no_split:
         line["split"] = measure_split(case, max(3, args.steps // 2), args.warmup, flush, peaks["hbm_gbs"])
+    if not args.no_iets:
+        line["iets"] = measure_iets(case, max(3, args.steps // 2), args.warmup, flush, peaks["hbm_gbs"])
     if not args.no_slab:
         line["slab"] = measure_slab(3, 1, flush)
     if not args.no_batch:

@@ -4,8 +4,9 @@
 // the stiffness K = -(J + J^T)/2, J = dG/dp = tip-spring Jacobian + exact
 // Jacobian of the trilinear force interpolant (the same J the adjoint uses),
 // or, on a tricubic energy grid, minus the Hessian of the energy interpolant,
-// and writes its three eigenvalues ascending (cyclic Jacobi rotations, FP32)
-// and the mode energies hbar sqrt(lambda/m).
+// and writes its three eigenvalues ascending (cyclic Jacobi rotations, FP32,
+// stopped once the off-diagonal part is below FP32 resolution) and the mode
+// energies hbar sqrt(lambda/m).
 #include "interp.cuh"
 
 namespace pp {
@@ -72,8 +73,14 @@ __global__ void __launch_bounds__(kThreads) iets_kernel(const IetsLaunch P) {
             a[m][n] = -0.5f * (J[m][n] + J[n][m]) - ((m == n ? ar : 0.f) + br * dd[m] * dd[n]);
     a[0][0] += P.kx;
     a[1][1] += P.ky;
-#pragma unroll
+    // cyclic sweeps until every off-diagonal element is below the FP32 resolution of the diagonal
+    // (the eigenvalue error is then a few ulps of |a|, also for a degenerate pair, where closed
+    // forms through acos lose half the digits); at most 5, the warp leaving together
+    const unsigned lanes = __activemask();
     for (int sweep = 0; sweep < 5; ++sweep) {
+        const float off = fmaf(a[0][1], a[0][1], fmaf(a[0][2], a[0][2], a[1][2] * a[1][2]));
+        const float diag = fmaf(a[0][0], a[0][0], fmaf(a[1][1], a[1][1], a[2][2] * a[2][2]));
+        if (__all_sync(lanes, off <= 3.5527137e-15f * diag)) break;  // (2^-24)^2
         jacobi_rotate(a, 0, 1);
         jacobi_rotate(a, 0, 2);
         jacobi_rotate(a, 1, 2);
