@@ -200,11 +200,25 @@ def cpu_baseline(case, target_s=12.0, chunk=8192, max_cols=None, full_ff=True):
     ff_desc = ("FF on all 256x256x200 nodes" if full_ff else "FF on nodes z 20..90 of 256x256x200, scaled by 200/71")
     scan_desc = (f"all {npix} pixel columns (the whole workload; median of {len(reps)} runs)" if done == npix
                  else f"{done} of {npix} seeded random pixel columns, scaled by {npix}/{done}")
-    return {"value": units / t_full, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+    # the same on one core, on a small sample: 2 of the 200 grid planes and 256 seeded columns
+    cores = oracle.max_threads()
+    t0 = time.perf_counter()
+    oracle.make_ff(case["atoms"], case["probe"], dict(g, nz=2), nthreads=1)
+    t1_ff = (time.perf_counter() - t0) * g["nz"] / 2
+    cols1 = np.sort(order[:256])
+    t0 = time.perf_counter()
+    r = oracle.relax_columns(ff, slab, None, None, s, case["tip"], case["fire"], cols1, polish_tol=0.0, nthreads=1)
+    oracle.fz_to_df(r["fz"].T, s["dz"], case["df"])
+    t1_rx = (time.perf_counter() - t0) * npix / len(cols1)
+    oracle.make_ff(case["atoms"], case["probe"], dict(g, nz=2), nthreads=cores)  # restores the thread count
+    return {"value": units / t_full, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": (f"{ff_desc} ({(k1 - k0) * 256 * 256 * 60 / 1e6:.0f} M pairs, FP64, OpenMP) + FIRE scan "
                        f"(no Newton polish) x 40 heights + df of {scan_desc}"),
             "sample_seconds": sum(reps) if len(reps) > 1 else t_ff + t_rx, "ff_seconds": t_ff, "scan_columns": done,
-            "repetitions": len(reps)}
+            "repetitions": len(reps),
+            "one_core": {"value": units / (t1_ff + t1_rx), "unit": UNIT, "cores": 1,
+                         "sample": "FF on 2 of the 200 grid planes scaled by 100, FIRE scan + df of 256 seeded "
+                                   "pixel columns scaled by 256"}}
 
 
 def run_reference(args, rank, world):
