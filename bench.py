@@ -221,6 +221,54 @@ def cpu_baseline(case, target_s=12.0, chunk=8192, max_cols=None, full_ff=True):
                                    "pixel columns scaled by 256"}}
 
 
+def cpu_baseline_other():
+    """FP64 oracle (all host cores) on stated samples of the batched and the slab workloads,
+    reported per unit and projected to the whole workload.
+
+    batch: the first 16 of the 1024 molecules, each FF grid + FIRE scan (no Newton polish) + df.
+    slab: a 32 x 32 pixel tile at the centre of the 512 x 512 scan, all 60 heights, relaxed on an
+    80 x 80 x 101 node window of the grid (2.4 A lateral margin, z 9 .. 19 A) built by direct
+    minimum-image sums; FF pairs/s and pixel-heights/s projected to the 512 x 512 x 250 grid
+    (1.65e11 pairs) and the 512 x 512 x 60 scan."""
+    import oracle
+
+    from paper_2401_14564_gb300 import synth
+
+    out = {"cores": oracle.max_threads()}
+    cases = synth.batch_cases(16)
+    t0 = time.perf_counter()
+    for c in cases:
+        ff, _ = oracle.make_ff(c["atoms"], c["probe"], c["grid"])
+        r = oracle.relax_scan(ff, c["grid"], c["atoms"], c["probe"], c["scan"], c["tip"], c["fire"], polish_tol=0.0)
+        oracle.fz_to_df(r["fz"], c["scan"]["dz"], c["df"])
+    t = time.perf_counter() - t0
+    out["batch"] = {"mol_per_s": len(cases) / t, "seconds": t,
+                    "sample": "molecules 1000..1015 of the 1024 (FF grid + FIRE scan + df each)"}
+    c = synth.slab_case()
+    g, s = c["grid"], c["scan"]
+    i0, n, m = 240, 32, 24
+    win = dict(g, nx=n + 2 * m, ny=n + 2 * m, nz=101, x0=g["x0"] + (i0 - m) * g["dx"],
+               y0=g["y0"] + (i0 - m) * g["dy"], z0=g["z0"] + 90 * g["dz"], periodic_xy=0,
+               Lx=g["nx"] * g["dx"], Ly=g["ny"] * g["dy"])
+    t0 = time.perf_counter()
+    ffw, _ = oracle.make_ff(c["atoms"], c["probe"], win)
+    t_ff = time.perf_counter() - t0
+    jj, ii = np.meshgrid(np.arange(i0, i0 + n), np.arange(i0, i0 + n), indexing="ij")
+    cols = (jj * s["nx"] + ii).ravel()
+    t0 = time.perf_counter()
+    r = oracle.relax_columns(ffw, win, None, None, s, c["tip"], c["fire"], cols, polish_tol=0.0)
+    oracle.fz_to_df(r["fz"].T, s["dz"], c["df"])
+    t_rx = time.perf_counter() - t0
+    natoms = len(c["atoms"]["x"])
+    pairs_rate = win["nx"] * win["ny"] * win["nz"] * natoms / t_ff
+    pz_rate = len(cols) * s["nz"] / t_rx
+    full = g["nx"] * g["ny"] * g["nz"] * natoms / pairs_rate + s["nx"] * s["ny"] * s["nz"] / pz_rate
+    out["slab"] = {"ff_pairs_per_s": pairs_rate, "pixel_z_per_s": pz_rate, "projected_forward_s": full,
+                   "sample": f"FF on an {win['nx']}x{win['ny']}x{win['nz']} node window, scan of a {n}x{n} px "
+                             "tile x 60 heights"}
+    return out
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -816,6 +864,7 @@ def main():
         line["batched"] = measure_batch(args.batch_mol, max(3, args.steps // 4), args.warmup, flush)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(case)
+        line["cpu_baseline"]["other_configs"] = cpu_baseline_other()
     if rank == 0:
         print(json.dumps(line))
     if dist is not None:
