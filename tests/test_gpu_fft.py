@@ -106,6 +106,19 @@ def test_spot_values_at_a_large_size(orc):
     assert np.abs(got[..., 3].reshape(-1)[nodes] - E).max() <= TOL * np.abs(got[..., 3]).max()
 
 
+@pytest.mark.parametrize("shape", [(1024, 4, 8), (8, 1024, 4), (4, 8, 1024)])
+def test_longest_axes(orc, shape):
+    # the longest supported axis (1024: three radix-8 stages and a radix-2 one, 4 lines per tile)
+    # along x, y and z; energies at seeded nodes against the direct sum
+    g = grid(*shape, d=(0.05, 0.07, 0.06))
+    f, tip = fields(g, sum(shape) + 1)
+    got = run(f, tip, g, scale=1.7)
+    nodes = np.random.default_rng(6).choice(f.size, 24, replace=False)
+    E = orc.correlate_nodes(f, tip, g, nodes, scale=1.7)
+    assert np.abs(got[..., 3].reshape(-1)[nodes] - E).max() <= TOL * np.abs(got[..., 3]).max()
+    assert np.isfinite(got).all()
+
+
 def test_fdbm_force_field_on_a_graphene_cell(orc):
     # the full-density model's two terms on a small periodic graphene cell: Hartree electrostatics
     # of the quadrupolar tip charge plus Pauli repulsion of the tip density, accumulated into one grid
