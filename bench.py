@@ -773,6 +773,9 @@ def main():
     iters = sim.iters.to(torch.int64)
     it_total = int(iters.sum().item())
     nonconv = float((sim.iters >= case["fire"]["max_iter"]).float().mean().item())
+    # FIRE position updates per pixel-height, binned in powers of two up to max_iter
+    edges = [0, 1, 2, 4, 8, 16, 32, 64, 128, case["fire"]["max_iter"], case["fire"]["max_iter"] + 1]
+    it_hist = [int(((iters >= a) & (iters < b)).sum().item()) for a, b in zip(edges[:-1], edges[1:])]
 
     # end to end through the public API: pinned host atoms in, host df image out.  Per step with a
     # synchronisation after each (run_host), and as a stream of steps whose device-to-host copies
@@ -806,6 +809,7 @@ def main():
                         "achieved_tflops": ff_tflops, "peak_tflops": alu_peak, "frac": ff_tflops / alu_peak},
         "relax_scan": {"ms": rx_ms, "share": rx_ms / (ff_ms + rx_ms), "pixel_z_per_s": units / (rx_ms * 1e-3),
                        "fire_iters_mean": it_total / units, "nonconverged_frac": nonconv,
+                       "fire_iters_hist": {"bin_lower_edges": edges[:-1], "counts": it_hist},
                        "gather_gbs": rx_gbs, "hbm_peak_gbs": peaks["hbm_gbs"], "frac_of_hbm": rx_gbs / peaks["hbm_gbs"]},
     }
     dom = "ff_assemble" if ff_ms >= rx_ms else "relax_scan"

@@ -412,6 +412,17 @@ PP_API size_t pp_fft_workspace(const pp_grid* grid);
 PP_API pp_status pp_fft_correlate(const float* f, const float* g, const pp_grid* grid, float scale, float power,
                                   int accumulate, float* ff, void* ws, size_t ws_bytes, pp_stream stream);
 
+/* Bounds-checked builds (libpp_checked.so, compiled with PP_CHECKED defined):
+ * every global gather and scatter index of the kernels is tested against
+ * the size of its array; an index outside it sets a bit and is replaced by
+ * 0 (the result is then wrong, never an out-of-bounds access).  Bits: 1 grid
+ * read, 2 grid write or grid-adjoint accumulation, 4 scan array read
+ * (positions, Fz, loss weights), 8 scan array write, 16 FFT arrays.
+ * pp_check_flags synchronises the device, stores the bits set since the last
+ * call in *flags and clears them.  In a normal build *flags = 0 and it
+ * returns PP_ERR_UNSUPPORTED. */
+PP_API pp_status pp_check_flags(unsigned int* flags);
+
 /* Message of the last failed call on this host thread ("" if none). */
 PP_API const char* pp_last_error(void);
 

@@ -1,5 +1,6 @@
 // C ABI of libpp: argument checks, unit conversion, launch.
 #include <math.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstring>
 #include <string>
@@ -10,6 +11,16 @@
 namespace pp {
 
 static thread_local std::string g_error;
+
+// NVTX range around an entry point's host side (validation and enqueue), named after the
+// entry point, so that a timeline tool shows which call issued which kernels.  Without an
+// attached tool a push or pop costs a branch.
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range&) = delete;
+    Range& operator=(const Range&) = delete;
+};
 
 void set_error(const std::string& msg) { g_error = msg; }
 
@@ -106,6 +117,17 @@ void df_stencil(double A_pp, double dz, double k, double f0, int m, float* coef)
     for (int s = -m; s <= m; ++s) coef[s + m] = (float)(pref * W[-s + m]);
 }
 
+#ifdef PP_CHECKED
+// flag readers of the kernel translation units (bounds-checked builds)
+unsigned int check_flags_ff_assemble();
+unsigned int check_flags_relax_scan();
+unsigned int check_flags_fz_to_df();
+unsigned int check_flags_backward();
+unsigned int check_flags_batch();
+unsigned int check_flags_iets();
+unsigned int check_flags_fft();
+#endif
+
 }  // namespace pp
 
 using namespace pp;
@@ -113,6 +135,22 @@ using namespace pp;
 extern "C" {
 
 const char* pp_last_error(void) { return g_error.c_str(); }
+
+pp_status pp_check_flags(unsigned int* flags) {
+    g_error.clear();
+    if (!flags) { set_error("pp_check_flags: NULL argument"); return PP_ERR_ARG; }
+    *flags = 0;
+#ifdef PP_CHECKED
+    pp_status st = cuda_status(cudaDeviceSynchronize(), "pp_check_flags sync");
+    if (st != PP_OK) return st;
+    *flags = check_flags_ff_assemble() | check_flags_relax_scan() | check_flags_fz_to_df() | check_flags_backward() |
+             check_flags_batch() | check_flags_iets() | check_flags_fft();
+    return PP_OK;
+#else
+    set_error("pp_check_flags: not a bounds-checked build (compile with -DPP_CHECKED)");
+    return PP_ERR_UNSUPPORTED;
+#endif
+}
 
 size_t pp_ff_floats(const pp_grid* grid) {
     GridMap m;
@@ -183,12 +221,14 @@ static pp_status make_ff_impl(const char* name, const pp_atoms* atoms, const pp_
 
 pp_status pp_make_ff(const pp_atoms* atoms, const pp_probe* probe, const pp_grid* grid, float* ff,
                      pp_stream stream) {
+    Range range("pp_make_ff");
     g_error.clear();
     return make_ff_impl("pp_make_ff", atoms, probe, grid, ff, nullptr, 8, stream);
 }
 
 pp_status pp_make_ff_tuned(const pp_atoms* atoms, const pp_probe* probe, const pp_grid* grid, float* ff,
                            const pp_tuning* tuning, pp_stream stream) {
+    Range range("pp_make_ff_tuned");
     g_error.clear();
     const int zpt = (tuning && tuning->ff_zpt) ? tuning->ff_zpt : 8;
     if (zpt != 4 && zpt != 8 && zpt != 16) { set_error("pp_make_ff_tuned: ff_zpt must be 4, 8 or 16"); return PP_ERR_ARG; }
@@ -197,6 +237,7 @@ pp_status pp_make_ff_tuned(const pp_atoms* atoms, const pp_probe* probe, const p
 
 pp_status pp_make_ff_split(const pp_atoms* atoms, const pp_probe* probe, const pp_grid* grid, float* ff,
                            float* ff_el, pp_stream stream) {
+    Range range("pp_make_ff_split");
     g_error.clear();
     if (!ff_el) { set_error("pp_make_ff_split: NULL ff_el"); return PP_ERR_ARG; }
     return make_ff_impl("pp_make_ff_split", atoms, probe, grid, ff, ff_el, 8, stream);
@@ -204,6 +245,7 @@ pp_status pp_make_ff_split(const pp_atoms* atoms, const pp_probe* probe, const p
 
 pp_status pp_ff_combine(const float* ff, const float* ff_el, float Q, const pp_grid* grid, float* out,
                         pp_stream stream) {
+    Range range("pp_ff_combine");
     g_error.clear();
     if (!ff || !ff_el || !grid || !out) { set_error("pp_ff_combine: NULL argument"); return PP_ERR_ARG; }
     if (!isfinite(Q)) { set_error("pp_ff_combine: Q must be finite"); return PP_ERR_ARG; }
@@ -237,6 +279,7 @@ static bool check_tip_fire(const pp_tip* tip, const pp_fire* fire, std::string* 
 pp_status pp_relax_scan(const float* ff, const pp_grid* grid, const pp_scan* scan, const pp_tip* tip,
                         const pp_fire* fire, float* pos, float* fz, int* iters, const pp_df* fused_df, float* df,
                         pp_stream stream) {
+    Range range("pp_relax_scan");
     g_error.clear();
     if (!ff || !grid || !scan || !tip || !fire || !fz) { set_error("pp_relax_scan: NULL argument"); return PP_ERR_ARG; }
     if (!aligned16(ff)) { set_error("pp_relax_scan: ff must be 16-byte aligned"); return PP_ERR_ARG; }
@@ -299,6 +342,7 @@ pp_status pp_relax_scan(const float* ff, const pp_grid* grid, const pp_scan* sca
 }
 
 pp_status pp_fz_to_df(const float* fz, int nz, int npix, float dz, const pp_df* dfp, float* df, pp_stream stream) {
+    Range range("pp_fz_to_df");
     g_error.clear();
     if (!dfp) { set_error("pp_fz_to_df: NULL argument"); return PP_ERR_ARG; }
     if (nz < 1 || npix < 0) { set_error("pp_fz_to_df: nz >= 1 and npix >= 0 required"); return PP_ERR_SHAPE; }
@@ -326,6 +370,7 @@ size_t pp_backward_workspace(const pp_grid* grid) {
 pp_status pp_backward(const pp_atoms* atoms, const pp_probe* probe, const pp_grid* grid, const float* ff,
                       const pp_scan* scan, const pp_tip* tip, const pp_df* dfp, const float* pos, const float* g_df,
                       const pp_grads* grads, void* ws, size_t ws_bytes, pp_stream stream) {
+    Range range("pp_backward");
     g_error.clear();
     if (!atoms || !probe || !grid || !ff || !scan || !tip || !dfp || !pos || !g_df || !grads || !ws) {
         set_error("pp_backward: NULL argument");
@@ -420,6 +465,7 @@ size_t pp_batch_workspace(int nmol) { return batch_workspace_bytes(nmol); }
 pp_status pp_batch_run(const pp_mol_desc* descs, int nmol, const pp_batch_params* bp, const pp_atoms* atoms,
                        float* ff, float* pos, float* fz, int* iters, float* df, void* ws, size_t ws_bytes,
                        pp_stream stream) {
+    Range range("pp_batch_run");
     g_error.clear();
     if (!descs || !bp || !atoms || !ff || !fz || !df || !ws) { set_error("pp_batch_run: NULL argument"); return PP_ERR_ARG; }
     if (nmol < 1 || nmol > (1 << 24)) { set_error("pp_batch_run: nmol must be in [1, 2^24]"); return PP_ERR_SHAPE; }
@@ -482,6 +528,7 @@ pp_status pp_batch_status(const void* ws, int* flags, pp_stream stream) {
 
 pp_status pp_iets(const float* ff, const pp_grid* grid, const pp_scan* scan, const pp_tip* tip, const float* pos,
                   float mass_amu, float* eig, float* hw, pp_stream stream) {
+    Range range("pp_iets");
     g_error.clear();
     if (!ff || !grid || !scan || !tip || !pos || !eig) { set_error("pp_iets: NULL argument"); return PP_ERR_ARG; }
     if (!aligned16(ff)) { set_error("pp_iets: ff must be 16-byte aligned"); return PP_ERR_ARG; }
@@ -525,6 +572,7 @@ pp_status pp_iets(const float* ff, const pp_grid* grid, const pp_scan* scan, con
 
 pp_status pp_ff_convert(const float* src, const pp_grid* src_grid, float* dst, const pp_grid* dst_grid,
                         pp_stream stream) {
+    Range range("pp_ff_convert");
     g_error.clear();
     if (!src || !dst || !src_grid || !dst_grid) { set_error("pp_ff_convert: NULL argument"); return PP_ERR_ARG; }
     if (!aligned16(src) || !aligned16(dst)) { set_error("pp_ff_convert: buffers must be 16-byte aligned"); return PP_ERR_ARG; }
@@ -574,6 +622,7 @@ size_t pp_fft_workspace(const pp_grid* grid) {
 
 pp_status pp_fft_correlate(const float* f, const float* g, const pp_grid* grid, float scale, float power,
                            int accumulate, float* ff, void* ws, size_t ws_bytes, pp_stream stream) {
+    Range range("pp_fft_correlate");
     g_error.clear();
     if (!f || !g || !grid || !ff || !ws) { set_error("pp_fft_correlate: NULL argument"); return PP_ERR_ARG; }
     if (!isfinite(scale) || !(power > 0.f) || !isfinite(power) || (accumulate != 0 && accumulate != 1)) {

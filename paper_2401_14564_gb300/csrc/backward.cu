@@ -62,14 +62,18 @@ __device__ __forceinline__ float df_transpose(const BwdLaunch& P, int k, int pix
 #pragma unroll
         for (int s = -M; s <= M; ++s) {
             const int c = k - M - s;
-            t[s + M] = (c >= 0 && c < P.nzo) ? __ldg(P.g_df + (int64_t)c * npix + pix) : 0.f;
+            t[s + M] = (c >= 0 && c < P.nzo)
+                           ? __ldg(P.g_df + checked((int64_t)c * npix + pix, (long long)P.nzo * npix, kChkScanRead))
+                           : 0.f;
         }
 #pragma unroll
         for (int s = -M; s <= M; ++s) gf = fmaf(P.coef[s + M], t[s + M], gf);
     } else {
         for (int s = -P.m; s <= P.m; ++s) {
             const int c = k - P.m - s;
-            if (c >= 0 && c < P.nzo) gf = fmaf(P.coef[s + P.m], __ldg(P.g_df + (int64_t)c * npix + pix), gf);
+            if (c >= 0 && c < P.nzo)
+                gf = fmaf(P.coef[s + P.m],
+                          __ldg(P.g_df + checked((int64_t)c * npix + pix, (long long)P.nzo * npix, kChkScanRead)), gf);
         }
     }
     return gf;
@@ -93,7 +97,8 @@ __global__ void __launch_bounds__(kAdjThreads) relax_adjoint_kernel(const BwdLau
          o += (int64_t)gridDim.x * kAdjThreads) {
         const int k = (int)(o / npix), pix = (int)(o - (int64_t)k * npix);
         // the relaxed position is loaded together with the g_df taps (one memory round trip)
-        const float px = __ldg(P.pos + 3 * o), py = __ldg(P.pos + 3 * o + 1), pz = __ldg(P.pos + 3 * o + 2);
+        const int64_t o3 = checked(3 * o, 3 * total, kChkScanRead);
+        const float px = __ldg(P.pos + o3), py = __ldg(P.pos + o3 + 1), pz = __ldg(P.pos + o3 + 2);
         const float gf = df_transpose<M>(P, k, pix, npix);
         if (gf != 0.f) {
             const int i = pix % P.snx, j = pix / P.snx;
@@ -168,7 +173,9 @@ __global__ void __launch_bounds__(kAdjThreads) relax_adjoint_kernel(const BwdLau
 #pragma unroll
                             for (int c = 0; c < 4; ++c) {
                                 const float v = fmaf(wz[c], pab, lzs * dwz[c] * qab);
-                                if (v != 0.f) atomicAdd(P.gbarE + zo[c] + yo[b] + xo[a], v);
+                                if (v != 0.f)
+                                    atomicAdd(P.gbarE + checked(zo[c] + yo[b] + xo[a], P.map.stored_nodes, kChkGridWrite),
+                                              v);
                             }
                         }
                     kmin = min(kmin, max(cl.z.i0 - 1, 0));
@@ -182,7 +189,8 @@ __global__ void __launch_bounds__(kAdjThreads) relax_adjoint_kernel(const BwdLau
 #pragma unroll
                     for (int c = 0; c < 8; ++c)
                         if (w[c] != 0.f)
-                            atomicAdd(P.gbar + idx[c], make_float4(-lx * w[c], -ly * w[c], -lz * w[c], 0.f));
+                            atomicAdd(P.gbar + checked(idx[c], P.map.stored_nodes, kChkGridWrite),
+                                      make_float4(-lx * w[c], -ly * w[c], -lz * w[c], 0.f));
                     kmin = min(kmin, cl.z.i0);
                     kmax = max(kmax, cl.z.i1);
                 }
@@ -261,7 +269,7 @@ __global__ void __launch_bounds__(kFFBThreads) ff_backward_kernel(const BwdLaunc
             const int64_t r = g - (int64_t)k * nxy;
             j = (int)(r / nx);
             i = (int)(r - (int64_t)j * nx);
-            a = P.gbar[node_index(P.map, i, j, k)];
+            a = P.gbar[checked(node_index(P.map, i, j, k), P.map.stored_nodes, kChkGridRead)];
             keep = (a.x != 0.f) || (a.y != 0.f) || (a.z != 0.f);
         }
         const unsigned mask = __ballot_sync(0xffffffffu, keep);
@@ -454,7 +462,7 @@ __global__ void __launch_bounds__(kFFBThreads) ff_backward_energy_kernel(const B
             const int64_t r = g - (int64_t)k * nxy;
             j = (int)(r / nx);
             i = (int)(r - (int64_t)j * nx);
-            e = P.gbarE[node_index(P.map, i, j, k)];
+            e = P.gbarE[checked(node_index(P.map, i, j, k), P.map.stored_nodes, kChkGridRead)];
             keep = e != 0.f;
         }
         const unsigned mask = __ballot_sync(0xffffffffu, keep);
@@ -678,5 +686,7 @@ cudaError_t launch_backward(const BwdLaunch& L, cudaStream_t s) {
     finalize_kernel<<<1, 256, 0, s>>>(L);
     return cudaGetLastError();
 }
+
+PP_CHECK_READER(check_flags_backward)
 
 }  // namespace pp

@@ -195,13 +195,14 @@ __device__ __forceinline__ void ff_tile(const BatchLaunch& B, const pp_mol_desc&
         ff_accumulate<ZP, kMinImage, kCutoff, kQuad>(s0, s1, s2, s3, cnt, cst, gx, gy, gz, fx, fy, fz, en);
     }
     if (i < D.nx && j < D.ny) {
-        float4* out = B.ff + D.ff_offset + (long long)j * D.nx + i;
+        const long long first = D.ff_offset + (long long)j * D.nx + i;
         const long long plane = (long long)D.nx * D.ny;
+        auto at = [&](int k) { return checked(first + k * plane, (long long)B.ff_cap, kChkGridWrite); };
 #pragma unroll
         for (int t = 0; t < ZP; ++t) {
             const int k = k0 + 2 * t;
-            if (k < D.nz) out[k * plane] = make_float4(fx[t].x, fy[t].x, fz[t].x, en[t].x);
-            if (k + 1 < D.nz) out[(k + 1) * plane] = make_float4(fx[t].y, fy[t].y, fz[t].y, en[t].y);
+            if (k < D.nz) B.ff[at(k)] = make_float4(fx[t].x, fy[t].x, fz[t].x, en[t].x);
+            if (k + 1 < D.nz) B.ff[at(k + 1)] = make_float4(fx[t].y, fy[t].y, fz[t].y, en[t].y);
         }
     }
 }
@@ -345,5 +346,7 @@ cudaError_t launch_batch(const BatchArgs& A, cudaStream_t s) {
     void* args[] = {&B};
     return cudaLaunchKernel(fn, dim3(ctas), dim3(kThreads), args, 0, s);
 }
+
+PP_CHECK_READER(check_flags_batch)
 
 }  // namespace pp

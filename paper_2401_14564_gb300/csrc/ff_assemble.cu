@@ -74,29 +74,30 @@ __global__ void __launch_bounds__(kThreads) ff_assemble_kernel(const FFLaunch P)
 
     if (i >= P.map.nx || j >= P.map.ny) return;
     const int base_xy = axis_off(P.map.ax, i) + axis_off(P.map.ay, j);
+    auto at = [&](int k) { return checked(base_xy + axis_off(P.map.az, k), P.map.stored_nodes, kChkGridWrite); };
     if constexpr (kEnergy) {
 #pragma unroll
         for (int t = 0; t < ZP; ++t) {
             const int k = k0 + 2 * t;
-            if (k < P.map.nz) P.ffE[base_xy + axis_off(P.map.az, k)] = en[t].x;
-            if (k + 1 < P.map.nz) P.ffE[base_xy + axis_off(P.map.az, k + 1)] = en[t].y;
+            if (k < P.map.nz) P.ffE[at(k)] = en[t].x;
+            if (k + 1 < P.map.nz) P.ffE[at(k + 1)] = en[t].y;
             if constexpr (kSplit) {
-                if (k < P.map.nz) P.ffelE[base_xy + axis_off(P.map.az, k)] = ene[t].x;
-                if (k + 1 < P.map.nz) P.ffelE[base_xy + axis_off(P.map.az, k + 1)] = ene[t].y;
+                if (k < P.map.nz) P.ffelE[at(k)] = ene[t].x;
+                if (k + 1 < P.map.nz) P.ffelE[at(k + 1)] = ene[t].y;
             }
         }
     } else {
 #pragma unroll
         for (int t = 0; t < ZP; ++t) {
             const int k = k0 + 2 * t;
-            if (k < P.map.nz) P.ff[base_xy + axis_off(P.map.az, k)] = make_float4(fx[t].x, fy[t].x, fz[t].x, en[t].x);
+            if (k < P.map.nz) P.ff[at(k)] = make_float4(fx[t].x, fy[t].x, fz[t].x, en[t].x);
             if (k + 1 < P.map.nz)
-                P.ff[base_xy + axis_off(P.map.az, k + 1)] = make_float4(fx[t].y, fy[t].y, fz[t].y, en[t].y);
+                P.ff[at(k + 1)] = make_float4(fx[t].y, fy[t].y, fz[t].y, en[t].y);
             if constexpr (kSplit) {
                 if (k < P.map.nz)
-                    P.ffel[base_xy + axis_off(P.map.az, k)] = make_float4(fxe[t].x, fye[t].x, fze[t].x, ene[t].x);
+                    P.ffel[at(k)] = make_float4(fxe[t].x, fye[t].x, fze[t].x, ene[t].x);
                 if (k + 1 < P.map.nz)
-                    P.ffel[base_xy + axis_off(P.map.az, k + 1)] = make_float4(fxe[t].y, fye[t].y, fze[t].y, ene[t].y);
+                    P.ffel[at(k + 1)] = make_float4(fxe[t].y, fye[t].y, fze[t].y, ene[t].y);
             }
         }
     }
@@ -171,5 +172,7 @@ cudaError_t launch_ff_assemble(const FFLaunch& L, cudaStream_t s) {
     if (L.zpt == 16) return launch_zpt<16>(L, s);
     return launch_zpt<8>(L, s);
 }
+
+PP_CHECK_READER(check_flags_ff_assemble)
 
 }  // namespace pp

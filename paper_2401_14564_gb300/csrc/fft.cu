@@ -90,15 +90,16 @@ __device__ __forceinline__ void dft<8>(float2 (&x)[8], float sign) {
 struct Pass {
     int log2nl, nbi, ntiles;
     long long outer_pitch, stride;  // stride: lstride for rows, pstride for columns
+    long long limit;                // complex values in the array (index bound)
     float sign;
 };
 
 template <int LOG2N, bool kContig>
 struct TileAt {
-    long long base, stride;
+    long long base, stride, limit;
     int log2nl;
     __device__ __forceinline__ long long at(int l, int p) const {
-        return kContig ? base + l * stride + p : base + l + p * stride;
+        return checked(kContig ? base + l * stride + p : base + l + p * stride, limit, kChkFft);
     }
     // slot of element p of line l in the layout written by the stage after radices L = 2^LOG2W
     template <int LOG2W>
@@ -212,6 +213,7 @@ __global__ void __launch_bounds__(kFftThreads, kFftBlocksPerSm) fft_pass_kernel(
     const int b = blockIdx.x;
     T.base = (long long)(b / P.nbi) * P.outer_pitch + ((long long)(b % P.nbi) << P.log2nl) * (kContig ? P.stride : 1);
     T.stride = P.stride;
+    T.limit = P.limit;
     T.log2nl = P.log2nl;
     __syncthreads();
     fft_tile<LOG2N, kContig>(data, T, x, tw, P.sign);
@@ -250,6 +252,9 @@ __global__ void pack_kernel(const float* __restrict__ f, const float* __restrict
     for (int r = blockIdx.x; r < rows; r += gridDim.x) {
         const int j = r % P.ny, k = r / P.ny;
         const long long src = (long long)r * P.nx, dst = P.at(0, j, k);
+        // the row's last complex value and last input float lie inside their arrays
+        checked(dst + P.nx - 1, (long long)P.nz * P.pz, kChkFft);
+        checked(src + P.nx - 1, (long long)P.nx * P.ny * P.nz, kChkFft);
         if ((P.nx & 3) == 0) {
             const float4* f4 = reinterpret_cast<const float4*>(f + src);
             const float4* g4 = reinterpret_cast<const float4*>(g + src);
@@ -287,7 +292,8 @@ __global__ void spectral_kernel(const SpecArgs A) {
         const int j = r % P.ny, k = r / P.ny;
         const int mj = j == 0 ? 0 : P.ny - j, mk = k == 0 ? 0 : P.nz - k;
         const float ky = wavenumber(j, P.ny, A.ky0), kz = wavenumber(k, P.nz, A.kz0);
-        const long long row = P.at(0, j, k), mrow = P.at(0, mj, mk);
+        const long long row = checked(P.at(0, j, k), (long long)P.nz * P.pz - P.nx + 1, kChkFft);
+        const long long mrow = checked(P.at(0, mj, mk), (long long)P.nz * P.pz - P.nx + 1, kChkFft);
         for (int i = threadIdx.x; i < P.nx; i += blockDim.x) {
             const int mi = i == 0 ? 0 : P.nx - i;
             const float2 zk = A.z[row + i];
@@ -312,7 +318,8 @@ __global__ void output_kernel(const float2* __restrict__ b1, const float2* __res
                               int accumulate) {
     const int rows = P.ny * P.nz;
     for (int r = blockIdx.x; r < rows; r += gridDim.x) {
-        const long long src = P.at(0, r % P.ny, r / P.ny), dst = (long long)r * P.nx;
+        const long long src = checked(P.at(0, r % P.ny, r / P.ny), (long long)P.nz * P.pz - P.nx + 1, kChkFft);
+        const long long dst = checked((long long)r * P.nx, (long long)P.nx * P.ny * P.nz - P.nx + 1, kChkFft);
         for (int i = threadIdx.x; i < P.nx; i += blockDim.x) {
             const float2 a = b1[src + i], b = b2[src + i];  // (E, Fx), (Fy, Fz)
             float4 v = make_float4(a.y, b.x, b.y, a.x);     // the spectra already hold -i k P: forces
@@ -360,8 +367,8 @@ cudaError_t launch_pass_n(float2* data, int log2n, const Pass& P, cudaStream_t s
 
 // Tiles of nl lines of n; nbi tiles per outer index; rows along x (lines lstride apart) or columns
 // (elements pstride apart).
-cudaError_t fft_axis(float2* data, bool rows, int n, int nl, int nbi, int nouter, long long outer_pitch,
-                     long long stride, float sign, cudaStream_t s) {
+cudaError_t fft_axis(float2* data, long long limit, bool rows, int n, int nl, int nbi, int nouter,
+                     long long outer_pitch, long long stride, float sign, cudaStream_t s) {
     if (n < 2) return cudaSuccess;
     Pass P;
     P.log2nl = ilog2i(nl);
@@ -369,6 +376,7 @@ cudaError_t fft_axis(float2* data, bool rows, int n, int nl, int nbi, int nouter
     P.ntiles = nbi * nouter;
     P.outer_pitch = outer_pitch;
     P.stride = stride;
+    P.limit = limit;
     P.sign = sign;
     return rows ? launch_pass_n<true>(data, ilog2i(n), P, s) : launch_pass_n<false>(data, ilog2i(n), P, s);
 }
@@ -386,11 +394,12 @@ int lines_per_block(int n, int avail, int want, int units) {
 cudaError_t fft3(float2* data, const Pad& P, float sign, cudaStream_t s) {
     cudaError_t e;
     int nl = lines_per_block(P.nx, P.ny, kLines, kUnits);  // x: lines are rows j of a plane k
-    if ((e = fft_axis(data, true, P.nx, nl, P.ny / nl, P.nz, P.pz, P.px, sign, s)) != cudaSuccess) return e;
+    const long long lim = (long long)P.nz * P.pz;
+    if ((e = fft_axis(data, lim, true, P.nx, nl, P.ny / nl, P.nz, P.pz, P.px, sign, s)) != cudaSuccess) return e;
     nl = lines_per_block(P.ny, P.nx, kStridedLines, kUnits);  // y: lines are columns i of a plane k
-    if ((e = fft_axis(data, false, P.ny, nl, P.nx / nl, P.nz, P.pz, P.px, sign, s)) != cudaSuccess) return e;
+    if ((e = fft_axis(data, lim, false, P.ny, nl, P.nx / nl, P.nz, P.pz, P.px, sign, s)) != cudaSuccess) return e;
     nl = lines_per_block(P.nz, P.nx, kStridedLines, kUnits);  // z: lines are columns i of a row j
-    return fft_axis(data, false, P.nz, nl, P.nx / nl, P.ny, P.px, P.pz, sign, s);
+    return fft_axis(data, lim, false, P.nz, nl, P.nx / nl, P.ny, P.px, P.pz, sign, s);
 }
 
 }  // namespace
@@ -429,5 +438,7 @@ cudaError_t launch_fft_correlate(const FftLaunch& L, cudaStream_t s) {
     output_kernel<<<blocks, threads, 0, s>>>(b1, b2, L.ff, P, L.accumulate);
     return cudaGetLastError();
 }
+
+PP_CHECK_READER(check_flags_fft)
 
 }  // namespace pp

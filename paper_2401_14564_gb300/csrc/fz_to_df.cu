@@ -22,9 +22,10 @@ __global__ void __launch_bounds__(kThreads) fz_to_df_kernel(const DfLaunch P) {
         const int c = (int)(o / P.npix) + P.m;
         const int64_t px = o - (int64_t)(c - P.m) * P.npix;
         float s = 0.f;
-        const float* col = P.fz + px;
-        for (int t = -P.m; t <= P.m; ++t) s = fmaf(P.coef[t + P.m], __ldg(col + (int64_t)(c + t) * P.npix), s);
-        P.df[o] = s;
+        for (int t = -P.m; t <= P.m; ++t)
+            s = fmaf(P.coef[t + P.m],
+                     __ldg(P.fz + checked((int64_t)(c + t) * P.npix + px, (long long)P.nz * P.npix, kChkScanRead)), s);
+        P.df[checked(o, total, kChkScanWrite)] = s;
     }
 }
 
@@ -36,7 +37,8 @@ __global__ void ff_convert_kernel(const float4* __restrict__ src, const GridMap 
         const int64_t r = g / dm.nx;
         const int j = (int)(r % dm.ny);
         const int k = (int)(r / dm.ny);
-        dst[node_index(dm, i, j, k)] = __ldg(src + node_index(sm, i, j, k));
+        dst[checked(node_index(dm, i, j, k), dm.stored_nodes, kChkGridWrite)] =
+            __ldg(src + checked(node_index(sm, i, j, k), sm.stored_nodes, kChkGridRead));
     }
 }
 
@@ -64,5 +66,7 @@ cudaError_t launch_ff_convert(const float4* src, const GridMap& sm, float4* dst,
     ff_convert_kernel<<<grid_blocks(n, 256), 256, 0, s>>>(src, sm, dst, dm);
     return cudaGetLastError();
 }
+
+PP_CHECK_READER(check_flags_fz_to_df)
 
 }  // namespace pp

@@ -43,7 +43,8 @@ __global__ void __launch_bounds__(kThreads) iets_kernel(const IetsLaunch P) {
     if (o >= total) return;
     const int k = (int)(o / npix), pix = (int)(o - (int64_t)k * npix);
     const int i = pix % P.snx, j = pix / P.snx;
-    const float px = __ldg(P.pos + 3 * o), py = __ldg(P.pos + 3 * o + 1), pz = __ldg(P.pos + 3 * o + 2);
+    const int64_t o3 = checked(3 * o, 3 * total, kChkScanRead);
+    const float px = __ldg(P.pos + o3), py = __ldg(P.pos + o3 + 1), pz = __ldg(P.pos + o3 + 2);
     const float dx = px - fmaf((float)i, P.spx, P.sx0), dy = py - fmaf((float)j, P.spy, P.sy0);
     const float dz = pz - (P.z_top - k * P.sdz);
     const float ex = dx - P.d0x, ey = dy - P.d0y, ez = dz - P.d0z;
@@ -89,13 +90,14 @@ __global__ void __launch_bounds__(kThreads) iets_kernel(const IetsLaunch P) {
     if (e0 > e1) { t = e0; e0 = e1; e1 = t; }
     if (e1 > e2) { t = e1; e1 = e2; e2 = t; }
     if (e0 > e1) { t = e0; e0 = e1; e1 = t; }
-    P.eig[3 * o] = e0;
-    P.eig[3 * o + 1] = e1;
-    P.eig[3 * o + 2] = e2;
+    const int64_t w3 = checked(3 * o, 3 * total, kChkScanWrite);
+    P.eig[w3] = e0;
+    P.eig[w3 + 1] = e1;
+    P.eig[w3 + 2] = e2;
     if (P.hw) {
-        P.hw[3 * o] = e0 > 0.f ? P.hw_unit * sqrtf(e0) : 0.f;
-        P.hw[3 * o + 1] = e1 > 0.f ? P.hw_unit * sqrtf(e1) : 0.f;
-        P.hw[3 * o + 2] = e2 > 0.f ? P.hw_unit * sqrtf(e2) : 0.f;
+        P.hw[w3] = e0 > 0.f ? P.hw_unit * sqrtf(e0) : 0.f;
+        P.hw[w3 + 1] = e1 > 0.f ? P.hw_unit * sqrtf(e1) : 0.f;
+        P.hw[w3 + 2] = e2 > 0.f ? P.hw_unit * sqrtf(e2) : 0.f;
     }
 }
 
@@ -109,5 +111,7 @@ cudaError_t launch_iets(const IetsLaunch& L, cudaStream_t s) {
     else iets_kernel<1, false><<<blocks, kThreads, 0, s>>>(L);
     return cudaGetLastError();
 }
+
+PP_CHECK_READER(check_flags_iets)
 
 }  // namespace pp

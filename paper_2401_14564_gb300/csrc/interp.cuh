@@ -124,7 +124,10 @@ __device__ __forceinline__ void load_corners(const float4* __restrict__ ff, cons
     int idx[8];
     corner_index<LAYOUT>(m, c, idx);
 #pragma unroll
-    for (int q = 0; q < 8; ++q) v[q] = kCoherent ? __ldca(ff + idx[q]) : __ldg(ff + idx[q]);
+    for (int q = 0; q < 8; ++q) {
+        const int i = checked(idx[q], m.stored_nodes, kChkGridRead);
+        v[q] = kCoherent ? __ldca(ff + i) : __ldg(ff + i);
+    }
 }
 
 // Trilinear interpolant of (Fx, Fy, Fz); (Fx, Fy) as packed pairs.
@@ -195,7 +198,8 @@ __device__ __forceinline__ void tricubic_load(const float* __restrict__ E, const
 #pragma unroll
         for (int b = 0; b < 4; ++b)
 #pragma unroll
-            for (int a = 0; a < 4; ++a) ec[(cz * 4 + b) * 4 + a] = __ldg(E + zo[cz] + yo[b] + xo[a]);
+            for (int a = 0; a < 4; ++a)
+                ec[(cz * 4 + b) * 4 + a] = __ldg(E + checked(zo[cz] + yo[b] + xo[a], m.stored_nodes, kChkGridRead));
 }
 
 // Second derivatives in t of the cubic convolution weights.

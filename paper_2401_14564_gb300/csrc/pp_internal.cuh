@@ -42,6 +42,41 @@ __host__ __device__ __forceinline__ int node_index(const GridMap& g, int i, int 
     return axis_off(g.ax, i) + axis_off(g.ay, j) + axis_off(g.az, k);
 }
 
+// Bounds-checked builds (-DPP_CHECKED: the library the bounds-check test loads, standing in for
+// a memory checker): every global gather and scatter index of the kernels goes through
+// checked(i, n, bit), which there records `bit` in this translation unit's flag word and
+// substitutes index 0 when i is outside [0, n); in a normal build it returns i unchanged.
+enum CheckBits : unsigned {
+    kChkGridRead = 1u,    // force-field / energy grid reads
+    kChkGridWrite = 2u,   // grid writes, grid-adjoint accumulation
+    kChkScanRead = 4u,    // relaxed positions, Fz, loss weights read back
+    kChkScanWrite = 8u,   // positions, Fz, iterations, df, eigenvalues written
+    kChkFft = 16u,        // FFT scratch and input arrays
+};
+#ifdef PP_CHECKED
+namespace {
+__device__ unsigned int g_check_flags;  // one per translation unit
+}
+template <class I>
+__device__ __forceinline__ I checked(I i, long long n, unsigned bit) {
+    if ((unsigned long long)(long long)i < (unsigned long long)n) return i;
+    atomicOr(&g_check_flags, bit);
+    return I(0);
+}
+// Host function `fn` returning and clearing this translation unit's flag word.
+#define PP_CHECK_READER(fn)                                           \
+    unsigned int fn() {                                               \
+        unsigned int v = 0, z = 0;                                    \
+        cudaMemcpyFromSymbol(&v, g_check_flags, sizeof(v));           \
+        cudaMemcpyToSymbol(g_check_flags, &z, sizeof(z));             \
+        return v;                                                     \
+    }
+#else
+template <class I>
+__device__ __forceinline__ I checked(I i, long long, unsigned) { return i; }
+#define PP_CHECK_READER(fn)
+#endif
+
 // Calls f(std::bool_constant<a>, std::bool_constant<b>, std::bool_constant<c>)
 // for the runtime flags a, b, c: one place that turns the pair-term options
 // (minimum image, Coulomb cutoff, tip quadrupole) into kernel template arguments.

@@ -92,7 +92,7 @@ __device__ __forceinline__ void relax_pixel(const G_t& P, const Q_t& Q, int i, i
         if (g2 < Q.ftol2 || it >= Q.max_iter) {
             // converged (or out of iterations) at height k: write, then go one height down
             // keeping the deflection e (the warm start p*(k-1) - dz z_hat)
-            const int o = k * npix + pix;
+            const int o = checked(k * npix + pix, (long long)npix * P.snz, kChkScanWrite);
             P.fz[o] = -s * (Q.d0z + e.z);  // kR (|d| - R0) d_z / |d|
             if (P.pos) {
                 P.pos[3 * o] = bx + e.x;
@@ -145,8 +145,10 @@ __device__ __forceinline__ void relax_pixel(const G_t& P, const Q_t& Q, int i, i
         const int m = Q.df_m;
         for (int c = m; c < P.snz - m; ++c) {
             float acc = 0.f;
-            for (int t = -m; t <= m; ++t) acc = fmaf(Q.coef[t + m], P.fz[(c + t) * npix + pix], acc);
-            P.df[(c - m) * npix + pix] = acc;
+            for (int t = -m; t <= m; ++t)
+                acc = fmaf(Q.coef[t + m], P.fz[checked((c + t) * npix + pix, (long long)npix * P.snz, kChkScanRead)],
+                           acc);
+            P.df[checked((c - m) * npix + pix, (long long)npix * (P.snz - 2 * m), kChkScanWrite)] = acc;
         }
     }
 }

@@ -93,4 +93,6 @@ cudaError_t launch_relax_scan(const RelaxLaunch& L, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+PP_CHECK_READER(check_flags_relax_scan)
+
 }  // namespace pp

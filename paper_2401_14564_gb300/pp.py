@@ -16,7 +16,8 @@ import torch
 
 PKG = os.path.dirname(os.path.abspath(__file__))
 HEADER = os.path.join(os.path.dirname(PKG), "include", "pp.h")
-LIB_PATH = os.path.join(PKG, "libpp.so")
+# PP_LIBRARY selects another build of the library (the bounds-checked libpp_checked.so)
+LIB_PATH = os.environ.get("PP_LIBRARY") or os.path.join(PKG, "libpp.so")
 
 STATUS = {0: "PP_OK", 1: "PP_ERR_ARG", 2: "PP_ERR_SHAPE", 3: "PP_ERR_CUDA", 4: "PP_ERR_CAPACITY",
           5: "PP_ERR_TIMEOUT", 6: "PP_ERR_UNSUPPORTED"}
@@ -153,6 +154,8 @@ def lib():
             L.pp_fft_correlate.argtypes = [vp, vp, C.POINTER(Grid), C.c_float, C.c_float, C.c_int, vp, vp,
                                            C.c_size_t, vp]
             L.pp_fft_correlate.restype = st
+            L.pp_check_flags.argtypes = [C.POINTER(C.c_uint)]
+            L.pp_check_flags.restype = st
             L.pp_last_error.argtypes = []
             L.pp_last_error.restype = C.c_char_p
             _lib = L
@@ -397,6 +400,14 @@ def pp_fft_correlate(f, g, grid: Grid, scale: float, power: float, ff, ws, accum
     _check(lib().pp_fft_correlate(_dev(f, "f"), _dev(g, "g"), C.byref(grid), float(scale), float(power),
                                   int(bool(accumulate)), _dev(ff, "ff"), _dev(ws, "ws", ws.dtype), nbytes,
                                   _stream(stream)))
+
+
+def pp_check_flags() -> int:
+    """Bits of the bounds checks hit since the last call (bounds-checked library only; raises
+    PPError with PP_ERR_UNSUPPORTED on a normal build)."""
+    flags = C.c_uint(0)
+    _check(lib().pp_check_flags(C.byref(flags)))
+    return flags.value
 
 
 def pp_last_error() -> str:

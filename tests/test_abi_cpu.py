@@ -164,3 +164,9 @@ def test_split_and_combine_are_validated_on_host(L):
     bad = pp.make_grid({"nx": 1, "ny": 6, "nz": 5, "x0": 0, "y0": 0, "z0": 0, "dx": 0.1, "dy": 0.1, "dz": 0.1,
                         "periodic_xy": 1})
     assert L.pp_ff_combine(fake, other, C.c_float(0.5), C.byref(bad), fake, None) == 2
+
+
+def test_check_flags_unsupported_in_a_normal_build(L):
+    flags = C.c_uint(7)
+    assert L.pp_check_flags(C.byref(flags)) == 6 and flags.value == 0
+    assert b"not a bounds-checked build" in L.pp_last_error()
