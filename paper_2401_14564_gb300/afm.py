@@ -177,6 +177,26 @@ class Simulator:
     def d2h_bytes(self):
         return self.df.numel() * 4
 
+    def save(self, path, grid=True):
+        """Write the last run's outputs (df, Fz, and the positions and iteration counts when kept;
+        the force-field grid too unless grid=False) to a NumPy .npz file, with the case's grid and
+        scan geometry.  The paper's CPU code keeps its grids on disk; here they are recomputed
+        faster than read back, so this is for inspection, not for resuming."""
+        torch.cuda.synchronize()
+        out = {"df": self.df.cpu().numpy(), "fz": self.fz.cpu().numpy()}
+        if self.pos is not None:
+            out["pos"] = self.pos.cpu().numpy()
+        if self.iters is not None:
+            out["iters"] = self.iters.cpu().numpy()
+        if grid:
+            out["ff"] = self.ff.cpu().numpy()
+        g, s = self.case["grid"], self.case["scan"]
+        out["grid_geometry"] = np.array([g["nx"], g["ny"], g["nz"], g["x0"], g["y0"], g["z0"], g["dx"], g["dy"],
+                                         g["dz"], g.get("interp", 0), self.grid.layout], dtype=np.float64)
+        out["scan_geometry"] = np.array([s["nx"], s["ny"], s["nz"], s["x0"], s["y0"], s["px"], s["py"], s["z_top"],
+                                         s["dz"]], dtype=np.float64)
+        np.savez(path, **out)
+
 
 class Pipeline:
     """Independent forward passes in flight `slots` at a time.

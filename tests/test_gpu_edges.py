@@ -109,3 +109,15 @@ def test_pipeline_items_equal_one_run_per_item():
         assert torch.equal(outs[k], one[k]), k
         assert torch.equal(host[k], one[k].cpu()), k
     assert not torch.equal(one[0], one[-1])
+
+
+def test_saved_outputs_round_trip(tmp_path):
+    c = case32(synth.small_case(seed=13, n_atoms=9, nxy=24, nz=30, scan_px=9, nz_scan=12))
+    sim = afm.Simulator(c)
+    sim.run(afm.atoms_to_device(c["atoms"]))
+    path = tmp_path / "run.npz"
+    sim.save(path)
+    z = np.load(path)
+    assert np.array_equal(z["df"], sim.df.cpu().numpy()) and np.array_equal(z["ff"], sim.ff.cpu().numpy())
+    assert np.array_equal(z["pos"], sim.pos.cpu().numpy()) and np.array_equal(z["iters"], sim.iters.cpu().numpy())
+    assert int(z["grid_geometry"][0]) == c["grid"]["nx"] and int(z["scan_geometry"][2]) == c["scan"]["nz"]
