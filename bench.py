@@ -32,6 +32,7 @@ METRIC = "relaxed pixel·z-steps/sec + FF grid·atom evals/sec vs roofline; batc
 UNIT = "pixel·z-steps/s"
 FLOPS_PER_PAIR = 30          # algorithmic FP32 flops per grid-node/atom pair (FMA = 2)
 FLOPS_PER_PAIR_QUAD = 45     # the same with the tip-quadrupole term (+15)
+FLOPS_PER_PAIR_FORCES = 26   # forces only: FLOPS_PER_PAIR without the 4 flops of the energy sum
 QZZ_CO = -0.05               # CO tip quadrupole of the paper's point-charge simulations, e*A^2
 BYTES_PER_FIRE_ITER = 96     # 8 corners x (Fx, Fy, Fz) FP32 per FIRE iteration
 SM_COUNT = 152
@@ -619,15 +620,16 @@ def measure_fdbm_sweep(reps, flush, sizes=((5, 3), (10, 6), (20, 12))):
             "fft_bytes_per_node": FFT_BYTES_PER_NODE, "points": out}
 
 
-def measure_batch(n_mol, steps, warmup, flush, seq_sample=64):
+def measure_batch(n_mol, steps, warmup, flush, seq_sample=64, ff_energy=False):
     """Batched molecules/s: pp_batch_run over n_mol seeded molecules replayed from a CUDA graph,
-    beside the same molecules run one by one through pp_make_ff + pp_relax_scan."""
+    beside the same molecules run one by one through pp_make_ff + pp_relax_scan (both with or
+    both without the grids' energy sums)."""
     import torch
 
     from paper_2401_14564_gb300 import afm, batch, synth
 
     cases = synth.batch_cases(n_mol)
-    b = batch.Batch(cases)
+    b = batch.Batch(cases, ff_energy=ff_energy)
     b.capture()
     for _ in range(max(warmup, 1)):
         b.replay()
@@ -645,7 +647,7 @@ def measure_batch(n_mol, steps, warmup, flush, seq_sample=64):
     st, flags = b.status()
     t = statistics.median(ts)
     # the same molecules one at a time (first seq_sample of them), per-molecule buffers preallocated
-    sims = [(afm.Simulator(c), afm.atoms_to_device(c["atoms"])) for c in cases[:seq_sample]]
+    sims = [(afm.Simulator(c, ff_energy=ff_energy), afm.atoms_to_device(c["atoms"])) for c in cases[:seq_sample]]
     for sim, at in sims:
         sim.run(at)
     torch.cuda.synchronize()
@@ -661,7 +663,7 @@ def measure_batch(n_mol, steps, warmup, flush, seq_sample=64):
     out = {"workload": f"{n_mol} seeded molecules of 10-80 H/C/N/O/F atoms (seeds 1000+i), grids 128-256^2 x 60 "
                        f"at 0.1 A, scans 128x128x20; one persistent launch in a CUDA graph",
            "mol_per_s": n_mol / (t * 1e-3), "ms_per_batch": t, "pixel_z_per_s": b.pixel_heights / (t * 1e-3),
-           "ff_pair_evals_per_s": b.pairs / (t * 1e-3), "status": st,
+           "ff_pair_evals_per_s": b.pairs / (t * 1e-3), "status": st, "ff_energy": bool(ff_energy),
            "single_path_mol_per_s": 1e3 / t_seq,
            "single_path_note": f"pp_make_ff + pp_relax_scan per molecule, mean over the first {seq_sample}",
            "gpu_launches_per_batch": 2}
@@ -687,6 +689,8 @@ def main():
     ap.add_argument("--no-fdbm", action="store_true")
     ap.add_argument("--no-split", action="store_true")
     ap.add_argument("--no-iets", action="store_true")
+    ap.add_argument("--ff-energy", action="store_true",
+                    help="assemble the grid's energies too (the scan reads only the forces; default: E slots 0)")
     ap.add_argument("--zpt", type=int, default=0, help="FF z-nodes per thread (skips the autotuner)")
     ap.add_argument("--brick", default="", help="bricked layout bx,by,bz for the scan (skips the autotuner)")
     ap.add_argument("--batch-mol", type=int, default=1024)
@@ -719,12 +723,12 @@ def main():
     elif not args.no_tune:
         from paper_2401_14564_gb300 import tune
 
-        tuning = tune.tune_case(case)
+        tuning = tune.tune_case(case, ff_energy=args.ff_energy)
     # four steps in flight, each slot with its own grid, outputs and stream: the next steps' force
     # fields and scans fill the issue slots a latency-bound scan leaves idle (measured on flake60:
     # 1.478 ms per step with one slot, 1.064 / 0.915 / 0.826 / 0.823 ms with 2 / 3 / 4 / 6);
     # slot 0 alone gives the isolated per-kernel timings
-    pipe = afm.Pipeline(case, slots=4, layout=args.layout, tuning=tuning)
+    pipe = afm.Pipeline(case, slots=4, layout=args.layout, tuning=tuning, ff_energy=args.ff_energy)
     sim = pipe.sims[0]
     atoms = afm.atoms_to_device(case["atoms"])
     stream = torch.cuda.current_stream()
@@ -801,11 +805,13 @@ def main():
     peaks, src = load_peaks()
     sm_max = peaks.get("sm_max_mhz", 2070.0)
     ff_ms, rx_ms = statistics.mean(t_ff), statistics.mean(t_rx)
-    ff_tflops = pairs * FLOPS_PER_PAIR / (ff_ms * 1e-3) / 1e12
+    flops_pair = FLOPS_PER_PAIR if args.ff_energy else FLOPS_PER_PAIR_FORCES
+    ff_tflops = pairs * flops_pair / (ff_ms * 1e-3) / 1e12
     alu_peak = fp32_peak_tflops(sm_max)
     rx_gbs = it_total * BYTES_PER_FIRE_ITER / (rx_ms * 1e-3) / 1e9
     kernels = {
         "ff_assemble": {"ms": ff_ms, "share": ff_ms / (ff_ms + rx_ms), "pair_evals_per_s": pairs / (ff_ms * 1e-3),
+                        "flops_per_pair": flops_pair, "energy": bool(args.ff_energy),
                         "achieved_tflops": ff_tflops, "peak_tflops": alu_peak, "frac": ff_tflops / alu_peak},
         "relax_scan": {"ms": rx_ms, "share": rx_ms / (ff_ms + rx_ms), "pixel_z_per_s": units / (rx_ms * 1e-3),
                        "fire_iters_mean": it_total / units, "nonconverged_frac": nonconv,
@@ -833,7 +839,9 @@ def main():
                                  "flushed), from which the per-kernel figures and the roofline are taken"},
             "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": workload_config(case),
+            "config": dict(workload_config(case),
+                           ff="forces and energies" if args.ff_energy else
+                              "forces only: E slots written as 0 (the scan reads only the forces; --ff-energy adds E)"),
             "ff_pair_evals_per_s": world * pairs / (ff_ms * 1e-3),
             "roofline": roof, "kernels": kernels,
             "e2e": {"value": world * units / (e2e_ms * 1e-3), "unit": UNIT,
@@ -865,7 +873,8 @@ def main():
     if not args.no_slab:
         line["slab"] = measure_slab(3, 1, flush)
     if not args.no_batch:
-        line["batched"] = measure_batch(args.batch_mol, max(3, args.steps // 4), args.warmup, flush)
+        line["batched"] = measure_batch(args.batch_mol, max(3, args.steps // 4), args.warmup, flush,
+                                        ff_energy=args.ff_energy)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(case)
         line["cpu_baseline"]["other_configs"] = cpu_baseline_other()

@@ -195,15 +195,22 @@ PP_API pp_status pp_make_ff_split(const pp_atoms* atoms, const pp_probe* probe, 
 PP_API pp_status pp_ff_combine(const float* ff, const float* ff_el, float Q, const pp_grid* grid, float* out,
                                pp_stream stream);
 
-/* Launch shape of pp_make_ff_tuned (picked by the autotuner): ff_zpt is the
- * number of consecutive z-nodes each thread accumulates, 4, 8 or 16; 0 = 8. */
+/* Options of pp_make_ff_tuned.  ff_zpt (the launch shape, picked by the
+ * autotuner) is the number of consecutive z-nodes each thread accumulates, 4,
+ * 8 or 16; 0 = 8.  ff_forces_only = 1 skips the energy sums of an interp = 0
+ * grid and writes 0 in every E slot: the scan reads only the forces (Sec.
+ * 5.1.1 step 2), and the forces are bit for bit those of ff_forces_only = 0
+ * (the default, E written). */
 typedef struct {
     int ff_zpt;
+    int ff_forces_only;
 } pp_tuning;
 
-/* pp_make_ff with an explicit launch shape; the values written are the same
- * sums (identical arithmetic per node).  Errors as pp_make_ff, plus
- * PP_ERR_ARG for an unsupported ff_zpt.  tuning may be NULL. */
+/* pp_make_ff with an explicit launch shape; the forces written are the same
+ * sums (identical arithmetic per node), and so are the energies unless
+ * ff_forces_only.  Errors as pp_make_ff, plus PP_ERR_ARG for an unsupported
+ * ff_zpt, an ff_forces_only other than 0 or 1, or ff_forces_only on an
+ * interp = 1 grid (which holds nothing but E).  tuning may be NULL. */
 PP_API pp_status pp_make_ff_tuned(const pp_atoms* atoms, const pp_probe* probe, const pp_grid* grid,
                                   float* ff, const pp_tuning* tuning, pp_stream stream);
 
@@ -277,6 +284,8 @@ typedef struct {
                                molecule's force field; 0 = 1<<23 (about one second)           */
     int wait_extra;         /* test hook, 0 in normal use: relax items wait for this many more
                                force-field tiles than exist, so every wait runs out            */
+    int ff_forces_only;     /* 1: every grid's E slots written as 0 and the energy sums skipped
+                               (the forces, and so all scan outputs, are unchanged); 0 or 1    */
 } pp_batch_params;
 
 /* Status bits reported by pp_batch_status. */
@@ -295,7 +304,8 @@ PP_API size_t pp_batch_workspace(int nmol);
  * molecule is done; items are handed out in list order, so the force field
  * it waits for is always being computed by running warps.  Writes, per
  * molecule, the force field, fz, df and (nullable) pos and iters exactly as
- * pp_make_ff + pp_relax_scan (fused df) on that molecule alone.  descs is a
+ * pp_make_ff + pp_relax_scan (fused df) on that molecule alone (the grid's E
+ * slots 0 when params->ff_forces_only).  descs is a
  * DEVICE array of nmol descriptors; atoms are packed device arrays; ws is
  * 16-byte aligned scratch of pp_batch_workspace(nmol) bytes.  Nothing is
  * synchronised: the launch can be captured in a CUDA graph and replayed.

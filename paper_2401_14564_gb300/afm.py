@@ -26,14 +26,21 @@ class Simulator:
     """Preallocated FF grid, positions, Fz, iteration counts and df for one case shape."""
 
     def __init__(self, case, layout=0, brick=(4, 4, 4), fire=None, device="cuda", fused_df=True,
-                 want_pos=True, want_iters=True, tuning=None):
-        """tuning: an autotuner result ({"ff_zpt", "layout", "brick"}) overriding layout and brick."""
+                 want_pos=True, want_iters=True, tuning=None, ff_energy=True):
+        """tuning: an autotuner result ({"ff_zpt", "layout", "brick"}) overriding layout and brick.
+        ff_energy=False: the grid's E slots are written as 0 and the energy sums skipped (the scan
+        reads only the forces, which are unchanged); trilinear force grids only."""
         self.case = case
         self.device = torch.device(device)
         if tuning is not None:
             layout = tuning["layout"]
             brick = tuple(tuning["brick"]) if tuning.get("brick") else brick
-        self.zpt = pp.Tuning(int(tuning["ff_zpt"])) if tuning is not None else None
+        if not ff_energy and case["grid"].get("interp", 0):
+            raise ValueError("ff_energy=False needs a force grid (interp 0)")
+        self.ff_energy = ff_energy
+        self.zpt = None
+        if tuning is not None or not ff_energy:
+            self.zpt = pp.Tuning(int(tuning["ff_zpt"]) if tuning is not None else 0, 0 if ff_energy else 1)
         self.grid = pp.make_grid(case["grid"], layout=layout, brick=brick)
         self.probe = pp.make_probe(case["probe"])
         self.scan = pp.make_scan(case["scan"])

@@ -21,7 +21,9 @@ ATOM_KEYS = ("x", "y", "z", "R", "eps", "q")
 
 class Batch:
     def __init__(self, cases, device="cuda", want_pos=False, want_iters=True, ctas=0, fire=None,
-                 spin_limit=0, wait_extra=0):
+                 spin_limit=0, wait_extra=0, ff_energy=True):
+        """ff_energy=False skips the energy sums of every molecule's grid (E slots 0; the scan
+        outputs are unchanged)."""
         if not cases:
             raise ValueError("empty batch")
         c0 = cases[0]
@@ -83,6 +85,7 @@ class Batch:
         bp.ctas = ctas
         bp.spin_limit = spin_limit
         bp.wait_extra = wait_extra
+        bp.ff_forces_only = 0 if ff_energy else 1
         self.params = bp
         self.graph = None
         self.pixel_heights = out_off

@@ -165,7 +165,7 @@ static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
 // Validation and launch shared by pp_make_ff, pp_make_ff_tuned and pp_make_ff_split.
 static pp_status make_ff_impl(const char* name, const pp_atoms* atoms, const pp_probe* probe, const pp_grid* grid,
-                              float* ff, float* ff_el, int zpt, pp_stream stream) {
+                              float* ff, float* ff_el, int zpt, int forces_only, pp_stream stream) {
     const std::string who(name);
     if (!atoms || !probe || !grid || !ff) { set_error(who + ": NULL argument"); return PP_ERR_ARG; }
     if (atoms->n < 0) { set_error(who + ": atoms->n < 0"); return PP_ERR_ARG; }
@@ -185,6 +185,7 @@ static pp_status make_ff_impl(const char* name, const pp_atoms* atoms, const pp_
     GridMap map;
     std::string why;
     if (!make_grid_map(grid, &map, &why)) { set_error(who + ": " + why); return PP_ERR_SHAPE; }
+    if (forces_only && map.interp) { set_error(who + ": ff_forces_only on an energy-only (interp = 1) grid"); return PP_ERR_ARG; }
     cudaStream_t s = (cudaStream_t)stream;
     if (map.stored_nodes > (int64_t)grid->nx * grid->ny * grid->nz) {
         for (float* g : {ff, ff_el}) {
@@ -213,6 +214,7 @@ static pp_status make_ff_impl(const char* name, const pp_atoms* atoms, const pp_
     L.ff = map.interp ? nullptr : reinterpret_cast<float4*>(ff);
     L.ffE = map.interp ? ff : nullptr;
     L.zpt = zpt;
+    L.forces_only = forces_only;
     L.split = ff_el != nullptr;
     L.ffel = (ff_el && !map.interp) ? reinterpret_cast<float4*>(ff_el) : nullptr;
     L.ffelE = (ff_el && map.interp) ? ff_el : nullptr;
@@ -223,7 +225,7 @@ pp_status pp_make_ff(const pp_atoms* atoms, const pp_probe* probe, const pp_grid
                      pp_stream stream) {
     Range range("pp_make_ff");
     g_error.clear();
-    return make_ff_impl("pp_make_ff", atoms, probe, grid, ff, nullptr, 8, stream);
+    return make_ff_impl("pp_make_ff", atoms, probe, grid, ff, nullptr, 8, 0, stream);
 }
 
 pp_status pp_make_ff_tuned(const pp_atoms* atoms, const pp_probe* probe, const pp_grid* grid, float* ff,
@@ -232,7 +234,9 @@ pp_status pp_make_ff_tuned(const pp_atoms* atoms, const pp_probe* probe, const p
     g_error.clear();
     const int zpt = (tuning && tuning->ff_zpt) ? tuning->ff_zpt : 8;
     if (zpt != 4 && zpt != 8 && zpt != 16) { set_error("pp_make_ff_tuned: ff_zpt must be 4, 8 or 16"); return PP_ERR_ARG; }
-    return make_ff_impl("pp_make_ff_tuned", atoms, probe, grid, ff, nullptr, zpt, stream);
+    const int forces_only = tuning ? tuning->ff_forces_only : 0;
+    if (forces_only != 0 && forces_only != 1) { set_error("pp_make_ff_tuned: ff_forces_only must be 0 or 1"); return PP_ERR_ARG; }
+    return make_ff_impl("pp_make_ff_tuned", atoms, probe, grid, ff, nullptr, zpt, forces_only, stream);
 }
 
 pp_status pp_make_ff_split(const pp_atoms* atoms, const pp_probe* probe, const pp_grid* grid, float* ff,
@@ -240,7 +244,7 @@ pp_status pp_make_ff_split(const pp_atoms* atoms, const pp_probe* probe, const p
     Range range("pp_make_ff_split");
     g_error.clear();
     if (!ff_el) { set_error("pp_make_ff_split: NULL ff_el"); return PP_ERR_ARG; }
-    return make_ff_impl("pp_make_ff_split", atoms, probe, grid, ff, ff_el, 8, stream);
+    return make_ff_impl("pp_make_ff_split", atoms, probe, grid, ff, ff_el, 8, 0, stream);
 }
 
 pp_status pp_ff_combine(const float* ff, const float* ff_el, float Q, const pp_grid* grid, float* out,
@@ -488,7 +492,8 @@ pp_status pp_batch_run(const pp_mol_desc* descs, int nmol, const pp_batch_params
         return PP_ERR_ARG;
     }
     if (bp->ff_capacity < 0 || bp->out_capacity < 0 || bp->df_capacity < 0 || bp->n_atoms_total < 0 ||
-        bp->n_atoms_total > atoms->n || bp->ctas < 0 || bp->spin_limit < 0 || bp->wait_extra < 0) {
+        bp->n_atoms_total > atoms->n || bp->ctas < 0 || bp->spin_limit < 0 || bp->wait_extra < 0 ||
+        (bp->ff_forces_only != 0 && bp->ff_forces_only != 1)) {
         set_error("pp_batch_run: invalid capacities or launch settings");
         return PP_ERR_ARG;
     }

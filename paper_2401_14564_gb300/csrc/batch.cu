@@ -55,6 +55,7 @@ struct BatchLaunch {
     float* coef_ws;
     long long spin_limit;
     int wait_extra;
+    int forces_only;  // E slots written as 0, energy sums skipped
     float coef_init[2 * kMaxDfHalfWidth + 1];
 };
 
@@ -165,7 +166,7 @@ __device__ __forceinline__ void add_release(int* p, int v) {
     asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-template <bool kMinImage, bool kCutoff, bool kQuad>
+template <bool kMinImage, bool kCutoff, bool kQuad, bool kForcesOnly>
 __device__ __forceinline__ void ff_tile(const BatchLaunch& B, const pp_mol_desc& D, long long tile, float4* s0,
                                         float4* s1, float4* s2, float4* s3, int lane) {
     constexpr int ZP = kZPT / 2;
@@ -201,13 +202,14 @@ __device__ __forceinline__ void ff_tile(const BatchLaunch& B, const pp_mol_desc&
 #pragma unroll
         for (int t = 0; t < ZP; ++t) {
             const int k = k0 + 2 * t;
-            if (k < D.nz) B.ff[at(k)] = make_float4(fx[t].x, fy[t].x, fz[t].x, en[t].x);
-            if (k + 1 < D.nz) B.ff[at(k + 1)] = make_float4(fx[t].y, fy[t].y, fz[t].y, en[t].y);
+            const float2 e = kForcesOnly ? make_float2(0.f, 0.f) : en[t];
+            if (k < D.nz) B.ff[at(k)] = make_float4(fx[t].x, fy[t].x, fz[t].x, e.x);
+            if (k + 1 < D.nz) B.ff[at(k + 1)] = make_float4(fx[t].y, fy[t].y, fz[t].y, e.y);
         }
     }
 }
 
-template <bool kMinImage, bool kCutoff, bool kQuad>
+template <bool kMinImage, bool kCutoff, bool kQuad, bool kForcesOnly>
 __global__ void __launch_bounds__(kThreads, kMinCtas) batch_kernel(const BatchLaunch B) {
     __shared__ float4 st[kWarps][4][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -230,7 +232,7 @@ __global__ void __launch_bounds__(kThreads, kMinCtas) batch_kernel(const BatchLa
         const long long tile = t - B.seg_start[lo];
         const pp_mol_desc D = B.descs[mol];
         if (ff) {
-            ff_tile<kMinImage, kCutoff, kQuad>(B, D, tile, st[warp][0], st[warp][1], st[warp][2], st[warp][3], lane);
+            ff_tile<kMinImage, kCutoff, kQuad, kForcesOnly>(B, D, tile, st[warp][0], st[warp][1], st[warp][2], st[warp][3], lane);
             __syncwarp();
             if (lane == 0) {
                 __threadfence();
@@ -330,10 +332,13 @@ cudaError_t launch_batch(const BatchArgs& A, cudaStream_t s) {
     B.done_ff = reinterpret_cast<int*>(w + 320 + 8 * (2 * (size_t)A.nmol + 1));
     B.spin_limit = P.spin_limit > 0 ? P.spin_limit : (1LL << 23);
     B.wait_extra = P.wait_extra;
+    B.forces_only = P.ff_forces_only;
 
     batch_plan_kernel<<<1, 1024, 0, s>>>(B);
-    const void* fn = with_flags(B.min_image != 0, B.coul_rc > 0.f, B.kQzz != 0.f, [](auto mi, auto cut, auto quad) {
-        return (const void*)batch_kernel<decltype(mi)::value, decltype(cut)::value, decltype(quad)::value>;
+    const bool fo = B.forces_only != 0;
+    const void* fn = with_flags(B.min_image != 0, B.coul_rc > 0.f, B.kQzz != 0.f, [fo](auto mi, auto cut, auto quad) {
+        constexpr bool MI = decltype(mi)::value, CUT = decltype(cut)::value, QUAD = decltype(quad)::value;
+        return fo ? (const void*)batch_kernel<MI, CUT, QUAD, true> : (const void*)batch_kernel<MI, CUT, QUAD, false>;
     });
     int ctas = P.ctas;
     if (ctas <= 0) {

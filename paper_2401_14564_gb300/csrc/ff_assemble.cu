@@ -35,7 +35,10 @@ constexpr int kChunk = 256;  // atoms staged per pass
 // are then never formed (the compiler drops them with their stores).
 // kSplit: the point-charge field per unit probe charge goes to a second grid
 // (ffel / ffelE), the rest (LJ and the tip quadrupole) to the first.
-template <int ZPT, bool kMinImage, bool kCutoff, bool kQuad, bool kEnergy = false, bool kSplit = false>
+// kForcesOnly: E slots written as 0; the energy sums are never formed (3 of
+// the 17 packed FP32 operations per node pair), the force sums are unchanged.
+template <int ZPT, bool kMinImage, bool kCutoff, bool kQuad, bool kEnergy = false, bool kSplit = false,
+          bool kForcesOnly = false>
 __global__ void __launch_bounds__(kThreads) ff_assemble_kernel(const FFLaunch P) {
     static_assert(ZPT % 2 == 0, "z-nodes come in packed pairs");
     constexpr int ZP = ZPT / 2;
@@ -90,9 +93,9 @@ __global__ void __launch_bounds__(kThreads) ff_assemble_kernel(const FFLaunch P)
 #pragma unroll
         for (int t = 0; t < ZP; ++t) {
             const int k = k0 + 2 * t;
-            if (k < P.map.nz) P.ff[at(k)] = make_float4(fx[t].x, fy[t].x, fz[t].x, en[t].x);
-            if (k + 1 < P.map.nz)
-                P.ff[at(k + 1)] = make_float4(fx[t].y, fy[t].y, fz[t].y, en[t].y);
+            const float2 e = kForcesOnly ? make_float2(0.f, 0.f) : en[t];
+            if (k < P.map.nz) P.ff[at(k)] = make_float4(fx[t].x, fy[t].x, fz[t].x, e.x);
+            if (k + 1 < P.map.nz) P.ff[at(k + 1)] = make_float4(fx[t].y, fy[t].y, fz[t].y, e.y);
             if constexpr (kSplit) {
                 if (k < P.map.nz)
                     P.ffel[at(k)] = make_float4(fxe[t].x, fye[t].x, fze[t].x, ene[t].x);
@@ -124,8 +127,9 @@ template <int ZPT>
 cudaError_t launch_zpt(const FFLaunch& L, cudaStream_t s) {
     dim3 grid((L.map.nx + kTileX - 1) / kTileX, (L.map.ny + kTileY - 1) / kTileY, (L.map.nz + ZPT - 1) / ZPT);
     with_flags(L.min_image != 0, L.coul_rc > 0.f, L.kQzz != 0.f, [&](auto mi, auto cut, auto quad) {
-        ff_assemble_kernel<ZPT, decltype(mi)::value, decltype(cut)::value, decltype(quad)::value>
-            <<<grid, kThreads, 0, s>>>(L);
+        constexpr bool MI = decltype(mi)::value, CUT = decltype(cut)::value, QUAD = decltype(quad)::value;
+        if (L.forces_only) ff_assemble_kernel<ZPT, MI, CUT, QUAD, false, false, true><<<grid, kThreads, 0, s>>>(L);
+        else ff_assemble_kernel<ZPT, MI, CUT, QUAD><<<grid, kThreads, 0, s>>>(L);
         return 0;
     });
     return cudaGetLastError();

@@ -114,6 +114,7 @@ struct FFLaunch {
     float4* ff;   // map.interp == 0
     float* ffE;   // map.interp == 1: energies only
     int zpt;  // z-nodes per thread: 4, 8 or 16
+    int forces_only;  // 1: no energy sums, E slots written as 0 (map.interp == 0, not split)
     int split;     // 1: point charges per unit probe charge into ffel / ffelE, the rest into ff / ffE
     float4* ffel;  // split, map.interp == 0
     float* ffelE;  // split, map.interp == 1

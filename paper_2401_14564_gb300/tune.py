@@ -44,8 +44,9 @@ def _time(fn, reps):
     return statistics.median(ts)
 
 
-def tune_case(case, reps=3, bricks=BRICKS, zpts=ZPTS):
-    """Time every FF launch shape and every grid layout for the relaxation; return the fastest."""
+def tune_case(case, reps=3, bricks=BRICKS, zpts=ZPTS, ff_energy=True):
+    """Time every FF launch shape and every grid layout for the relaxation; return the fastest.
+    ff_energy=False times the forces-only assembly (the one a Simulator with ff_energy=False runs)."""
     atoms_t = afm.atoms_to_device(case["atoms"])
     atoms = pp.make_atoms(atoms_t)
     probe = pp.make_probe(case["probe"])
@@ -53,7 +54,7 @@ def tune_case(case, reps=3, bricks=BRICKS, zpts=ZPTS):
     grid0 = pp.make_grid(case["grid"], 0)
     ff = torch.empty(pp.pp_ff_floats(grid0), dtype=torch.float32, device="cuda")
     for z in zpts:
-        t = pp.Tuning(z)
+        t = pp.Tuning(z, 0 if ff_energy or case["grid"].get("interp", 0) else 1)
         pp.pp_make_ff_tuned(atoms, probe, grid0, ff, t)
         ff_times[z] = _time(lambda: pp.pp_make_ff_tuned(atoms, probe, grid0, ff, t), reps)
     best_z = min(ff_times, key=ff_times.get)
@@ -93,7 +94,7 @@ def cached(case, path=None, **kw):
     if os.path.exists(path):
         with open(path) as f:
             db = json.load(f)
-    k = _key(case)
+    k = _key(case) + ("" if kw.get("ff_energy", True) else "|forces_only")
     if k not in db:
         r = tune_case(case, **kw)
         db[k] = {"ff_zpt": r["ff_zpt"], "layout": r["layout"], "brick": r["brick"],

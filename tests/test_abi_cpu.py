@@ -170,3 +170,18 @@ def test_check_flags_unsupported_in_a_normal_build(L):
     flags = C.c_uint(7)
     assert L.pp_check_flags(C.byref(flags)) == 6 and flags.value == 0
     assert b"not a bounds-checked build" in L.pp_last_error()
+
+
+def test_forces_only_option_is_validated_on_host(L):
+    fake = C.c_void_p(16)  # never dereferenced: the host checks fail first
+    atoms = pp.Atoms(0, None, None, None, None, None, None)
+    probe = pp.make_probe({"R_pp": 1.66, "eps_pp": 0.0091, "Q": -0.1, "coul_rc": 0.0, "min_image": 0,
+                           "core_frac": 0.5})
+    g = pp.make_grid({"nx": 10, "ny": 6, "nz": 5, "x0": 0, "y0": 0, "z0": 0, "dx": 0.1, "dy": 0.1, "dz": 0.1,
+                      "periodic_xy": 1})
+    assert L.pp_make_ff_tuned(C.byref(atoms), C.byref(probe), C.byref(g), fake, C.byref(pp.Tuning(8, 2)), None) == 1
+    assert b"ff_forces_only" in L.pp_last_error()
+    # an energy-only grid has nothing but E to write
+    g.interp = 1
+    assert L.pp_make_ff_tuned(C.byref(atoms), C.byref(probe), C.byref(g), fake, C.byref(pp.Tuning(0, 1)), None) == 1
+    assert b"interp = 1" in L.pp_last_error()

@@ -55,6 +55,22 @@ def test_batch_matches_single_molecule_path_bit_for_bit():
             assert np.array_equal(got[k], ref[k]), (n, k)
 
 
+def test_forces_only_batch_matches_the_full_one():
+    # ff_forces_only: the grids' forces and every scan output are bit for bit the full batch's,
+    # the E slots are 0
+    cs = cases(6, 3000)
+    full, fo = batch.Batch(cs, want_pos=True), batch.Batch(cs, want_pos=True, ff_energy=False)
+    full.run()
+    fo.run()
+    assert full.status() == (0, 0) and fo.status() == (0, 0)
+    for n in range(len(cs)):
+        a, b = full.molecule(n), fo.molecule(n)
+        for k in ("fz", "df", "iters", "pos"):
+            assert torch.equal(a[k], b[k]), (n, k)
+        assert torch.equal(a["ff"][..., :3], b["ff"][..., :3]), n
+        assert torch.count_nonzero(b["ff"][..., 3]).item() == 0, n
+
+
 def test_graph_replay_reproduces_the_eager_run():
     cs = cases(6, 2000)
     b = batch.Batch(cs)

@@ -118,3 +118,39 @@ def test_flake_full_size_sampled_nodes(orc):
     err = ff_rel_err(got, ref)[~core]
     assert err.max() <= TOL, err.max()
     assert torch.isfinite(F).all()
+
+
+@pytest.mark.parametrize("zpt", [4, 8, 16])
+@pytest.mark.parametrize("variant", ["plain", "min_image_cutoff", "quadrupole"])
+def test_forces_only_grid_has_the_same_forces_and_zero_energies(orc, zpt, variant):
+    # ff_forces_only drops the energy sums: every force component is bit for bit the full grid's,
+    # every E slot is 0, and the forces still meet the oracle bar
+    c = case32(synth.small_case(seed=6, n_atoms=14, nxy=34, nz=29))
+    if variant == "min_image_cutoff":
+        c["probe"] = dict(synth.default_probe(coul_rc=3.0, min_image=1), Q=c["probe"]["Q"])
+    elif variant == "quadrupole":
+        c["probe"] = dict(c["probe"], Qzz=-0.05)
+    c = case32(c)
+    grid = pp.make_grid(c["grid"], 0)
+    atoms, probe = pp.make_atoms(afm.atoms_to_device(c["atoms"])), pp.make_probe(c["probe"])
+    full = torch.full((pp.pp_ff_floats(grid),), float("nan"), dtype=torch.float32, device="cuda")
+    forces = torch.full_like(full, float("nan"))
+    pp.pp_make_ff_tuned(atoms, probe, grid, full, pp.Tuning(zpt, 0))
+    pp.pp_make_ff_tuned(atoms, probe, grid, forces, pp.Tuning(zpt, 1))
+    a, b = full.view(-1, 4), forces.view(-1, 4)
+    assert torch.equal(a[:, :3], b[:, :3])
+    assert torch.count_nonzero(b[:, 3]).item() == 0 and torch.count_nonzero(a[:, 3]).item() > 0
+    ref, core = orc.make_ff(c["atoms"], c["probe"], c["grid"])
+    F = linear_ff(forces.cpu().numpy(), c["grid"])
+    assert ff_rel_err(F, ref)[~core].max() <= TOL
+
+
+def test_forces_only_simulator_gives_the_same_images():
+    c = case32(synth.small_case(seed=7, n_atoms=11, nxy=32, nz=36, scan_px=10, nz_scan=14))
+    outs = []
+    for energy in (True, False):
+        sim = afm.Simulator(c, ff_energy=energy)
+        sim.run(afm.atoms_to_device(c["atoms"]))
+        outs.append((sim.df.clone(), sim.pos.clone(), sim.iters.clone()))
+    for u, v in zip(*outs):
+        assert torch.equal(u, v)
