@@ -17,10 +17,14 @@
 // all ZPT nodes.  The per-node arithmetic runs two z-nodes at a time on
 // Blackwell's packed f32x2 FMA/MUL/ADD (one issue slot for two lanes' worth
 // of FP32 work); only the core floor (no packed max) and the rsqrt stay
-// scalar.  Atoms are staged into shared memory in chunks, with the per-atom
-// mixing (R_iPP^2, 12 e_iPP, k_e Q q_i, floor radius^2, e_iPP) done while
-// staging, and each per-atom constant stored twice so that one 16-byte
-// broadcast load yields a ready packed operand.
+// scalar.  The Lennard-Jones terms are evaluated as polynomials in 1/r^6 with
+// per-atom coefficients (12 e R^12, 12 e R^6, e R^12, 2 e R^6 with the mixed
+// R = R_iPP, e = e_iPP), which takes 12 packed FP32 operations per pair of
+// nodes for the forces and 3 more for the energy.  Atoms are staged into
+// shared memory in chunks, with the mixing and these coefficients, k_e Q q_i
+// and the floor radius^2 formed while staging, and each per-atom constant
+// stored twice so that one 16-byte broadcast load yields a ready packed
+// operand.
 #include "ff_core.cuh"
 
 namespace pp {
@@ -36,7 +40,8 @@ constexpr int kChunk = 256;  // atoms staged per pass
 // kSplit: the point-charge field per unit probe charge goes to a second grid
 // (ffel / ffelE), the rest (LJ and the tip quadrupole) to the first.
 // kForcesOnly: E slots written as 0; the energy sums are never formed (3 of
-// the 17 packed FP32 operations per node pair), the force sums are unchanged.
+// the 15 packed FP32 operations per pair of nodes), the force sums are
+// unchanged.
 template <int ZPT, bool kMinImage, bool kCutoff, bool kQuad, bool kEnergy = false, bool kSplit = false,
           bool kForcesOnly = false>
 __global__ void __launch_bounds__(kThreads) ff_assemble_kernel(const FFLaunch P) {

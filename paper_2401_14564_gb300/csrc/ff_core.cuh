@@ -5,14 +5,17 @@
 // Atoms are staged as 64-byte records in shared memory, each per-atom
 // constant stored twice so that one 16-byte broadcast load yields a ready
 // packed f32x2 operand:
-//   s0 = (x, y, rmin^2, 0)     s1 = (-z, -z, R_iPP^2, R_iPP^2)
-//   s2 = (12 e, 12 e, kq, kq)  s3 = (e, e, kqq, kqq)
-// with R_iPP = R_i + R_PP, e = e_iPP = sqrt(e_i e_PP), kq = k_e Q q_i,
-// kqq = k_e Qzz q_i / 2 and rmin = core_frac R_iPP.  A thread accumulates ZP
-// packed pairs of z-nodes of one grid column: per node and atom, with
-// delta = r_node - r_atom and u3 = (R_iPP^2 / r^2)^3,
-//   F += [12 e (u3^2 - u3) / r^2 + kq / r^3] delta,
-//   E += e (u3^2 - 2 u3) + kq / r,
+//   s0 = (x, y, rmin^2, kqq)   s1 = (-z, -z, a, a)
+//   s2 = (-b, -b, kq, kq)      s3 = (c, c, -d, -d)
+// with R = R_iPP = R_i + R_PP, e = e_iPP = sqrt(e_i e_PP), a = 12 e R^12,
+// b = 12 e R^6, c = e R^12, d = 2 e R^6, kq = k_e Q q_i, kqq = k_e Qzz q_i / 2
+// and rmin = core_frac R.  With u3 = (R^2 / r^2)^3 the Lennard-Jones terms
+// are then polynomials in 1/r^6:
+//   12 e (u3^2 - u3) = (a / r^6 - b) / r^6,   e (u3^2 - 2 u3) = (c / r^6 - d) / r^6.
+// A thread accumulates ZP packed pairs of z-nodes of one grid column: per
+// node and atom, with delta = r_node - r_atom,
+//   F += [(a / r^6 - b) / r^8 + kq / r^3] delta,
+//   E += (c / r^6 - d) / r^6 + kq / r,
 // with r^2 floored at rmin^2 (shifted-force Coulomb when kCutoff), and with
 // the tip quadrupole (kQuad; cut off at coul_rc when kCutoff)
 //   F += kqq [(15 dz^2/r^2 - 3) delta - 6 dz z_hat] / r^5,
@@ -47,12 +50,15 @@ __device__ __forceinline__ void ff_stage_atom(const FFConst& c, float x, float y
     const float Rij = R + c.R_pp;
     const float eij = sqrtf(eps * c.eps_pp);
     const float rmin = c.core_frac * Rij;
+    const float R2 = Rij * Rij;
+    const float R6 = R2 * R2 * R2;
+    const float R12 = R6 * R6;
     const float kq = c.kQ * q;
     const float kqq = c.kQzz * q;
-    s0 = make_float4(x, y, rmin * rmin, 0.f);
-    s1 = make_float4(-z, -z, Rij * Rij, Rij * Rij);
-    s2 = make_float4(12.f * eij, 12.f * eij, kq, kq);
-    s3 = make_float4(eij, eij, kqq, kqq);
+    s0 = make_float4(x, y, rmin * rmin, kqq);
+    s1 = make_float4(-z, -z, 12.f * eij * R12, 12.f * eij * R12);
+    s2 = make_float4(-12.f * eij * R6, -12.f * eij * R6, kq, kq);
+    s3 = make_float4(eij * R12, eij * R12, -2.f * eij * R6, -2.f * eij * R6);
 }
 
 // kSplit: the point-charge terms go to (fxe, fye, fze, ene) instead (staged with kq = k_e q_i, i.e.
@@ -63,7 +69,6 @@ __device__ __forceinline__ void ff_accumulate_impl(const float4* s0, const float
                                                    const float2 (&gz)[ZP], float2 (&fx)[ZP], float2 (&fy)[ZP],
                                                    float2 (&fz)[ZP], float2 (&en)[ZP], float2 (&fxe)[ZP],
                                                    float2 (&fye)[ZP], float2 (&fze)[ZP], float2 (&ene)[ZP]) {
-    const float2 minus1 = make_float2(-1.f, -1.f);
     const float2 minus3 = make_float2(-3.f, -3.f), minus6 = make_float2(-6.f, -6.f);
     const float2 three = make_float2(3.f, 3.f), fifteen = make_float2(15.f, 15.f);
 #pragma unroll 1
@@ -77,9 +82,10 @@ __device__ __forceinline__ void ff_accumulate_impl(const float4* s0, const float
         }
         const float rxy2 = fmaf(rx, rx, ry * ry);
         const float2 RX = make_float2(rx, rx), RY = make_float2(ry, ry), RXY = make_float2(rxy2, rxy2);
-        const float2 NZ = make_float2(A1.x, A1.y), R2 = make_float2(A1.z, A1.w);
-        const float2 E12 = make_float2(A2.x, A2.y), KQ = make_float2(A2.z, A2.w);
-        const float2 EE = make_float2(A3.x, A3.y), KQQ = make_float2(A3.z, A3.w);
+        const float2 NZ = make_float2(A1.x, A1.y), LA = make_float2(A1.z, A1.w);
+        const float2 LB = make_float2(A2.x, A2.y), KQ = make_float2(A2.z, A2.w);
+        const float2 EC = make_float2(A3.x, A3.y), ED = make_float2(A3.z, A3.w);
+        const float2 KQQ = make_float2(A0.w, A0.w);
 #pragma unroll
         for (int t = 0; t < ZP; ++t) {
             const float2 rz = f2add(gz[t], NZ);
@@ -88,21 +94,22 @@ __device__ __forceinline__ void ff_accumulate_impl(const float4* s0, const float
             r2.y = fmaxf(r2.y, A0.z);
             const float2 rs = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
             const float2 ir2 = f2mul(rs, rs);
-            const float2 u = f2mul(R2, ir2);
-            const float2 u3 = f2mul(f2mul(u, u), u);
-            const float2 lj = f2mul(u3, f2add(u3, minus1));  // u6 - u3
-            float2 eel = f2mul(KQ, rs);                         // kq / r
-            float2 f;   // radial factor of every term (of the LJ and quadrupole terms when kSplit)
-            float2 fe;  // kSplit: radial factor of the point-charge term
+            const float2 ir4 = f2mul(ir2, ir2);
+            const float2 ir6 = f2mul(ir4, ir2);
+            const float2 lj = f2mul(f2fma(LA, ir6, LB), ir6);  // 12 e (u6 - u3)
+            float2 eel;  // kq / r (cut and shifted when kCutoff); formed when needed
+            float2 f;    // radial factor of every term (of the LJ and quadrupole terms when kSplit)
+            float2 fe;   // kSplit: radial factor of the point-charge term
             if (kCutoff) {
+                eel = f2mul(KQ, rs);
                 eel.x = (r2.x < c.rc2) ? eel.x : 0.f;
                 eel.y = (r2.y < c.rc2) ? eel.y : 0.f;
                 if (kSplit) {
                     fe = f2fma(eel, make_float2(-c.irc2, -c.irc2), f2mul(eel, ir2));  // kq (1/r^3 - 1/(r rc^2))
-                    f = f2mul(f2mul(E12, lj), ir2);
+                    f = f2mul(lj, ir2);
                 } else {
                     // kq (1/r^3 - 1/(r rc^2)) + 12 e (u6 - u3) / r^2
-                    f = f2fma(eel, make_float2(-c.irc2, -c.irc2), f2mul(f2fma(E12, lj, eel), ir2));
+                    f = f2fma(eel, make_float2(-c.irc2, -c.irc2), f2mul(f2add(lj, eel), ir2));
                 }
                 // shifted-force energy kq (1/r + r/rc^2 - 2/rc)
                 float2 ee = f2fma(eel, f2mul(r2, make_float2(c.irc2, c.irc2)), eel);
@@ -110,15 +117,17 @@ __device__ __forceinline__ void ff_accumulate_impl(const float4* s0, const float
                 ee.y -= (r2.y < c.rc2) ? KQ.y * c.two_irc : 0.f;
                 eel = ee;
             } else if (kSplit) {
+                eel = f2mul(KQ, rs);
                 fe = f2mul(eel, ir2);
-                f = f2mul(f2mul(E12, lj), ir2);
+                f = f2mul(lj, ir2);
             } else {
-                f = f2mul(f2fma(E12, lj, eel), ir2);  // (12 e (u6 - u3) + kq / r) / r^2
+                eel = f2mul(KQ, rs);                // formed only for the quadrupole's energy sum
+                f = f2mul(f2fma(KQ, rs, lj), ir2);  // (12 e (u6 - u3) + kq / r) / r^2
             }
             float2 fzf = f;
             float2 eq = make_float2(0.f, 0.f);  // quadrupole energy
             if (kQuad) {
-                float2 c5 = f2mul(KQQ, f2mul(f2mul(ir2, ir2), rs));  // kqq / r^5
+                float2 c5 = f2mul(KQQ, f2mul(ir4, rs));  // kqq / r^5
                 if (kCutoff) {
                     c5.x = (r2.x < c.rc2) ? c5.x : 0.f;
                     c5.y = (r2.y < c.rc2) ? c5.y : 0.f;
@@ -134,13 +143,15 @@ __device__ __forceinline__ void ff_accumulate_impl(const float4* s0, const float
             fy[t] = f2fma(f, RY, fy[t]);
             fz[t] = f2fma(fzf, rz, fz[t]);
             if (kSplit) {
-                en[t] = f2add(f2fma(EE, f2sub(lj, u3), en[t]), eq);  // e (u6 - 2 u3) + E_quad
+                en[t] = f2add(f2fma(f2fma(EC, ir6, ED), ir6, en[t]), eq);  // e (u6 - 2 u3) + E_quad
                 fxe[t] = f2fma(fe, RX, fxe[t]);
                 fye[t] = f2fma(fe, RY, fye[t]);
                 fze[t] = f2fma(fe, rz, fze[t]);
                 ene[t] = f2add(ene[t], eel);
+            } else if (kCutoff || kQuad) {
+                en[t] = f2add(f2fma(f2fma(EC, ir6, ED), ir6, en[t]), eel);  // e (u6 - 2 u3) + E_el (+ E_quad)
             } else {
-                en[t] = f2add(f2fma(EE, f2sub(lj, u3), en[t]), eel);  // e (u6 - 2 u3) + E_el
+                en[t] = f2fma(KQ, rs, f2fma(f2fma(EC, ir6, ED), ir6, en[t]));  // e (u6 - 2 u3) + kq / r
             }
         }
     }
