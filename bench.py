@@ -45,13 +45,13 @@ TRAFFIC = {
                    "files": ["relax_scan.cu", "relax_core.cuh", "interp.cuh"]},
     "relax_scan_tricubic": {"bytes": 22.30e6, "sha": "9c144ef97f440d45",
                             "files": ["relax_scan.cu", "relax_core.cuh", "interp.cuh"]},
-    "ff_assemble": {"bytes": 144.58e6, "sha": "88b70d6f9aa34036",
+    "ff_assemble": {"bytes": 144.63e6, "sha": "bba60445429332e1",
                     "files": ["ff_assemble.cu", "ff_core.cuh", "interp.cuh"]},
-    "ff_assemble_quad": {"bytes": 144.80e6, "sha": "88b70d6f9aa34036",
+    "ff_assemble_quad": {"bytes": 144.63e6, "sha": "bba60445429332e1",
                          "files": ["ff_assemble.cu", "ff_core.cuh", "interp.cuh"]},
-    "ff_assemble_split": {"bytes": 354.09e6, "sha": "88b70d6f9aa34036",
+    "ff_assemble_split": {"bytes": 354.30e6, "sha": "bba60445429332e1",
                           "files": ["ff_assemble.cu", "ff_core.cuh", "interp.cuh"]},
-    "ff_combine": {"bytes": 597.06e6, "sha": "88b70d6f9aa34036",
+    "ff_combine": {"bytes": 597.01e6, "sha": "bba60445429332e1",
                    "files": ["ff_assemble.cu", "ff_core.cuh", "interp.cuh"]},
 }
 
@@ -305,13 +305,14 @@ def workload_config(case):
                   "it back; per-kernel timings: 256 MiB write before every step"}
 
 
-def measure_bwd_fwd(case, steps, warmup, flush, tag):
-    """CUDA-event times of the forward (FF + relaxed scan + df) and of pp_backward on one workload."""
+def measure_bwd_fwd(case, steps, warmup, flush, tag, ff_energy=False):
+    """CUDA-event times of the forward (FF + relaxed scan + df) and of pp_backward on one workload
+    (the adjoint reads the grid's forces only, so the forward assembles them as the main step does)."""
     import torch
 
     from paper_2401_14564_gb300 import afm, pp
 
-    sim = afm.Simulator(case)
+    sim = afm.Simulator(case, ff_energy=ff_energy)
     atoms_t = afm.atoms_to_device(case["atoms"])
     n = len(case["atoms"]["x"])
     grads = {k: torch.empty(n, device="cuda") for k in ("x", "y", "z", "q", "R", "eps")}
@@ -344,12 +345,12 @@ def measure_bwd_fwd(case, steps, warmup, flush, tag):
         tf.append(e0.elapsed_time(e1))
         tb.append(e2a.elapsed_time(e2))
     f, b = statistics.mean(tf), statistics.mean(tb)
-    return {"workload": tag, "fwd_ms": f, "bwd_ms": b, "ratio": b / f,
+    return {"workload": tag, "fwd_ms": f, "bwd_ms": b, "ratio": b / f, "ff_energy": bool(ff_energy),
             "note": "forward = FF + relaxed scan + fused df; backward = pp_backward (df adjoint, 3x3 implicit solves, "
                     "grid-adjoint scatter, per-atom pair-derivative sums); L2 flushed before each"}
 
 
-def measure_slab(steps, warmup, flush):
+def measure_slab(steps, warmup, flush, ff_energy=False):
     """2516-atom periodic slab: 512x512x250 grid with minimum image and an 8 A shifted-force
     Coulomb cut, 512x512 px x 60 heights; forward and adjoint times."""
     import torch
@@ -357,7 +358,8 @@ def measure_slab(steps, warmup, flush):
     from paper_2401_14564_gb300 import synth
 
     case = synth.slab_case()
-    r = measure_bwd_fwd(case, steps, warmup, flush, "slab2016+mol500: 2516 atoms, grid 512x512x250, scan 512x512x60")
+    r = measure_bwd_fwd(case, steps, warmup, flush, "slab2016+mol500: 2516 atoms, grid 512x512x250, scan 512x512x60",
+                        ff_energy)
     g, s = case["grid"], case["scan"]
     pairs = g["nx"] * g["ny"] * g["nz"] * len(case["atoms"]["x"])
     r["pixel_z_per_s_fwd"] = s["nx"] * s["ny"] * s["nz"] / (r["fwd_ms"] * 1e-3)
@@ -812,11 +814,12 @@ def main():
     kernels = {
         "ff_assemble": {"ms": ff_ms, "share": ff_ms / (ff_ms + rx_ms), "pair_evals_per_s": pairs / (ff_ms * 1e-3),
                         "flops_per_pair": flops_pair, "energy": bool(args.ff_energy),
+                        "traffic": measured_traffic("ff_assemble") if not args.ff_energy else None,
                         "achieved_tflops": ff_tflops, "peak_tflops": alu_peak, "frac": ff_tflops / alu_peak},
         "relax_scan": {"ms": rx_ms, "share": rx_ms / (ff_ms + rx_ms), "pixel_z_per_s": units / (rx_ms * 1e-3),
                        "fire_iters_mean": it_total / units, "nonconverged_frac": nonconv,
                        "fire_iters_hist": {"bin_lower_edges": edges[:-1], "counts": it_hist},
-                       "gather_gbs": rx_gbs, "hbm_peak_gbs": peaks["hbm_gbs"], "frac_of_hbm": rx_gbs / peaks["hbm_gbs"]},
+                       "traffic": measured_traffic("relax_scan"), "gather_gbs": rx_gbs, "hbm_peak_gbs": peaks["hbm_gbs"], "frac_of_hbm": rx_gbs / peaks["hbm_gbs"]},
     }
     dom = "ff_assemble" if ff_ms >= rx_ms else "relax_scan"
     if dom == "ff_assemble":
@@ -857,8 +860,9 @@ def main():
     line["bwd_fwd"] = [] if args.no_bwdfwd else [
         measure_bwd_fwd(g4, max(3, args.steps // 2), args.warmup, flush,
                         "mol40 seed 4040: 40 atoms, grid %dx%dx%d, scan 128x128x20" % (
-                            g4["grid"]["nx"], g4["grid"]["ny"], g4["grid"]["nz"])),
-        measure_bwd_fwd(case, max(3, args.steps // 2), args.warmup, flush, "flake60 (this line's workload)"),
+                            g4["grid"]["nx"], g4["grid"]["ny"], g4["grid"]["nz"]), args.ff_energy),
+        measure_bwd_fwd(case, max(3, args.steps // 2), args.warmup, flush, "flake60 (this line's workload)",
+                        args.ff_energy),
     ]
     if not args.no_fdbm:
         line["fdbm_sweep"] = measure_fdbm_sweep(5, flush)
@@ -871,7 +875,7 @@ def main():
     if not args.no_iets:
         line["iets"] = measure_iets(case, max(3, args.steps // 2), args.warmup, flush, peaks["hbm_gbs"])
     if not args.no_slab:
-        line["slab"] = measure_slab(3, 1, flush)
+        line["slab"] = measure_slab(3, 1, flush, args.ff_energy)
     if not args.no_batch:
         line["batched"] = measure_batch(args.batch_mol, max(3, args.steps // 4), args.warmup, flush,
                                         ff_energy=args.ff_energy)
