@@ -42,3 +42,24 @@ def test_tuned_simulator_reproduces_default_images():
     b.run(at)
     torch.cuda.synchronize()
     assert torch.equal(a.df, b.df) and torch.equal(a.fz, b.fz)
+
+
+def test_forces_only_tuning_and_its_cache_entry(tmp_path):
+    # the tuner times the forces-only assembly when asked, caches it under its own key, and the
+    # tuned forces-only simulator reproduces the default images
+    c = case32(synth.benzene_case())
+    path = str(tmp_path / "tuning.json")
+    full = tune.cached(c, path=path, reps=1)
+    fo = tune.cached(c, path=path, reps=1, ff_energy=False)
+    import json
+    keys = sorted(json.load(open(path)))
+    assert len(keys) == 2 and keys[1] == keys[0] + "|forces_only"
+    assert fo["ff_zpt"] in (4, 8, 16) and full["ff_zpt"] in (4, 8, 16)
+    a = afm.Simulator(c)
+    b = afm.Simulator(c, tuning=fo, ff_energy=False)
+    at = afm.atoms_to_device(c["atoms"])
+    a.run(at)
+    b.run(at)
+    torch.cuda.synchronize()
+    assert torch.equal(a.df, b.df) and torch.equal(a.fz, b.fz)
+    assert torch.count_nonzero(b.ff.view(-1, 4)[:, 3]).item() == 0
