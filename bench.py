@@ -478,6 +478,39 @@ def measure_tricubic(case, steps, warmup, flush):
     return out
 
 
+def measure_df(case, steps, flush, hbm_gbs, shape=(60, 512, 512)):
+    """K3 alone (pp_fz_to_df) on a seeded Fz volume of the slab scan's shape (60 heights x 512 x 512
+    pixels) with the line's df parameters: algorithmic bytes = Fz read once + df written once;
+    CUDA events, L2 flushed before each."""
+    import torch
+
+    from paper_2401_14564_gb300 import pp
+
+    nz, ny, nx = shape
+    dfp = pp.make_df(case["df"])
+    dz = case["scan"]["dz"]
+    m = pp.pp_df_margin(dfp.A_pp, dz)
+    g = torch.Generator(device="cuda").manual_seed(11)
+    fz = torch.randn((nz, ny, nx), generator=g, device="cuda")
+    df = torch.empty((nz - 2 * m, ny, nx), device="cuda")
+    for _ in range(3):
+        pp.pp_fz_to_df(fz, nz, nx * ny, dz, dfp, df)
+    stream = torch.cuda.current_stream()
+    ts = []
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pp.pp_fz_to_df(fz, nz, nx * ny, dz, dfp, df)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ms = statistics.median(ts)
+    nbytes = 4 * (nz + (nz - 2 * m)) * nx * ny
+    return {"workload": f"Fz {nz} heights x {nx}x{ny} px (seeded), {2 * m + 1}-tap stencil", "ms": ms,
+            "bytes": nbytes, "gbs": nbytes / (ms * 1e-3) / 1e9, "frac_of_hbm": nbytes / (ms * 1e-3) / 1e9 / hbm_gbs}
+
+
 def measure_split(case, steps, warmup, flush, hbm_gbs):
     """The line's workload with the electrostatics kept apart (pp_make_ff_split: LJ grid + point-charge
     grid per unit probe charge) and recombined for the probe charge (pp_ff_combine, 12 bytes moved per
@@ -894,6 +927,7 @@ def main():
         line["split"] = measure_split(case, max(3, args.steps // 2), args.warmup, flush, peaks["hbm_gbs"])
     if not args.no_iets:
         line["iets"] = measure_iets(case, max(3, args.steps // 2), args.warmup, flush, peaks["hbm_gbs"])
+    line["df_standalone"] = measure_df(case, 20, flush, peaks["hbm_gbs"])
     if not args.no_slab:
         line["slab"] = measure_slab(3, 1, flush, args.ff_energy)
     if not args.no_batch:

@@ -5,14 +5,46 @@
 // whose weights come from integrating a piecewise-linear Fz exactly against
 // the Giessibl kernel u / sqrt(a^2 - u^2) over one peak-to-peak amplitude.
 // The stencil is HBM-bound streaming work: lanes run along the pixel axis
-// (contiguous), each thread produces one output, the 2m+1 taps of a column
-// are re-read from L1/L2 rather than from DRAM.
+// (contiguous loads and stores).  For half-widths m <= 8 (A_pp up to 16 dz)
+// each thread owns kRows consecutive outputs of one pixel: it loads the
+// kRows + 2m Fz values they need once into registers and forms the kRows sums
+// there, so every Fz value is read about (kRows + 2m) / kRows times instead of
+// 2m + 1.  Wider stencils take the generic kernel, one output per thread with
+// the taps re-read from L1/L2.  Both sum the taps in the same order, so the
+// results are identical.
 #include "pp_internal.cuh"
 
 namespace pp {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kRows = 32;      // consecutive df heights per thread (register path)
+constexpr int kMaxRegM = 8;    // largest half-width with a register path
+
+template <int M>
+__global__ void __launch_bounds__(kThreads) fz_to_df_rows_kernel(const DfLaunch P) {
+    constexpr int W = kRows + 2 * M;  // Fz heights behind kRows outputs
+    const int64_t px = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (px >= P.npix) return;
+    const int nout = P.nz - 2 * M;
+    const int o0 = blockIdx.y * kRows;  // first output height; it reads Fz heights o0 .. o0 + W - 1
+    float v[W];
+#pragma unroll
+    for (int t = 0; t < W; ++t) {
+        const int z = o0 + t;
+        v[t] = z < P.nz ? __ldg(P.fz + checked((int64_t)z * P.npix + px, (long long)P.nz * P.npix, kChkScanRead))
+                        : 0.f;
+    }
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+        if (o0 + r < nout) {
+            float s = 0.f;
+#pragma unroll
+            for (int t = 0; t <= 2 * M; ++t) s = fmaf(P.coef[t], v[r + t], s);
+            P.df[checked((int64_t)(o0 + r) * P.npix + px, (long long)nout * P.npix, kChkScanWrite)] = s;
+        }
+    }
+}
 
 __global__ void __launch_bounds__(kThreads) fz_to_df_kernel(const DfLaunch P) {
     const int nout = P.nz - 2 * P.m;
@@ -52,9 +84,30 @@ int grid_blocks(int64_t work, int threads) {
 
 }  // namespace
 
+template <int M>
+static void launch_rows(const DfLaunch& L, cudaStream_t s) {
+    const int nout = L.nz - 2 * M;
+    const dim3 grid((unsigned)((L.npix + kThreads - 1) / kThreads), (unsigned)((nout + kRows - 1) / kRows));
+    fz_to_df_rows_kernel<M><<<grid, kThreads, 0, s>>>(L);
+}
+
 cudaError_t launch_fz_to_df(const DfLaunch& L, cudaStream_t s) {
     const int64_t total = (int64_t)(L.nz - 2 * L.m) * L.npix;
     if (total <= 0) return cudaSuccess;
+    const int64_t row_blocks = ((int64_t)(L.nz - 2 * L.m) + kRows - 1) / kRows;
+    if (L.m >= 1 && L.m <= kMaxRegM && row_blocks <= 65535) {
+        switch (L.m) {
+            case 1: launch_rows<1>(L, s); break;
+            case 2: launch_rows<2>(L, s); break;
+            case 3: launch_rows<3>(L, s); break;
+            case 4: launch_rows<4>(L, s); break;
+            case 5: launch_rows<5>(L, s); break;
+            case 6: launch_rows<6>(L, s); break;
+            case 7: launch_rows<7>(L, s); break;
+            default: launch_rows<8>(L, s); break;
+        }
+        return cudaGetLastError();
+    }
     fz_to_df_kernel<<<grid_blocks(total, kThreads), kThreads, 0, s>>>(L);
     return cudaGetLastError();
 }

@@ -45,3 +45,21 @@ def test_linear_force_law(orc):
 def test_empty_pixel_axis():
     got = gpu_df(np.zeros((12, 0)), 0.1, {"A_pp": 1.0, "k": 1800.0, "f0": 30300.0})
     assert got.shape == (2, 0)
+
+
+@pytest.mark.parametrize("m", list(range(1, 10)))
+def test_every_half_width_matches_oracle(orc, m):
+    # half-widths 1..8 take the register-window kernel, 9 the generic one; heights and pixels
+    # ragged against the 8-height and 256-pixel blocks
+    dz = 0.1
+    A = 2 * m * dz - 0.01
+    nz, npix = 2 * m + 1 + 13, 523
+    rng = np.random.default_rng(100 + m)
+    fz = rng.standard_normal((nz, npix)).astype(np.float32) * 0.05
+    dfp = {"A_pp": A, "k": 1800.0, "f0": 30300.0}
+    assert pp.pp_df_margin(A, dz) == m
+    got = gpu_df(fz, dz, dfp)
+    ref = orc.fz_to_df(fz.astype(np.float64), float(np.float32(dz)), {"A_pp": float(np.float32(A)), "k": 1800.0,
+                                                                       "f0": 30300.0})
+    assert got.shape == ref.shape == (nz - 2 * m, npix)
+    assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max()

@@ -8,6 +8,8 @@ the symmetrised -J >= 0.01 eV/A^2) and that reached the same basin (|dp| <
 0.05 A); the excluded counts are bounded.  With the timed settings (ftol =
 1e-4) positions must stay inside the residual bound ftol/lambda_min.
 """
+import copy
+
 import numpy as np
 import pytest
 import torch
@@ -67,8 +69,13 @@ def test_bricked_grid_same_images(orc):
     assert np.array_equal(a["pos"], b["pos"]) and np.array_equal(a["df"], b["df"])
 
 
-def test_fused_df_equals_standalone_kernel():
-    c = case32(synth.benzene_case())
+@pytest.mark.parametrize("A", [1.0, 0.19, 0.79, 1.59, 1.79])
+def test_fused_df_equals_standalone_kernel(A):
+    # the standalone kernel (register window for half-widths 1..8, generic beyond) sums the taps in
+    # the fused epilogue's order: bit-identical images for m = 5, 1, 4, 8, 9
+    c = copy.deepcopy(synth.benzene_case())
+    c["df"] = dict(c["df"], A_pp=A)
+    c = case32(c)
     a = gpu_run(c, fused=True)
     b = gpu_run(c, fused=False)
     assert np.array_equal(a["fz"], b["fz"])
