@@ -63,3 +63,23 @@ def test_every_half_width_matches_oracle(orc, m):
                                                                        "f0": 30300.0})
     assert got.shape == ref.shape == (nz - 2 * m, npix)
     assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max()
+
+
+def test_slab_scan_shape_sampled_columns(orc):
+    # the standalone kernel at the 2516-atom slab's scan shape (60 heights x 512 x 512 px, the
+    # bench's df_standalone volume): 256 sampled pixel columns against the oracle
+    nz, ny, nx = 60, 512, 512
+    g = torch.Generator(device="cuda").manual_seed(11)
+    fz = torch.randn((nz, ny, nx), generator=g, device="cuda") * 0.05
+    dfp = {"A_pp": 1.0, "k": 1800.0, "f0": 30300.0}
+    m = pp.pp_df_margin(1.0, 0.1)
+    out = torch.empty((nz - 2 * m, ny, nx), device="cuda")
+    pp.pp_fz_to_df(fz, nz, nx * ny, 0.1, pp.make_df(dfp), out)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(5)
+    cols = rng.integers(0, nx * ny, 256)
+    f = fz.view(nz, -1)[:, cols].cpu().numpy().astype(np.float64)
+    got = out.view(nz - 2 * m, -1)[:, cols].cpu().numpy()
+    ref = orc.fz_to_df(f, float(np.float32(0.1)), dfp)
+    assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max()
+    assert torch.isfinite(out).all()
