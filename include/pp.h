@@ -98,8 +98,9 @@ typedef struct {
  * layout 1: bricks of bx*by*bz nodes (each a power of two, 1..16), bricks in
  *           x-fastest order, nodes x-fastest inside a brick; dimensions are
  *           padded up to whole bricks.  pp_ff_floats() gives the size.
- * interp 0: every node holds 4 floats (Fx, Fy, Fz, E) in eV/A and eV and the
- *           scan interpolates the forces trilinearly (Sec. 5.1.1 step 2).
+ * interp 0: every node holds 4 floats (Fx, Fy, Fz, E) in eV/A and eV (E = 0
+ *           when assembled with ff_forces_only) and the scan interpolates the
+ *           forces trilinearly (Sec. 5.1.1 step 2).
  * interp 1: every node holds the energy E only (eV), layout 0; the scan
  *           interpolates E tricubically (the paper's suggestion for larger
  *           spacings without stored forces) and takes F = -grad of the
