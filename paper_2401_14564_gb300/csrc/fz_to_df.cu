@@ -87,7 +87,7 @@ int grid_blocks(int64_t work, int threads) {
 template <int M>
 static void launch_rows(const DfLaunch& L, cudaStream_t s) {
     const int nout = L.nz - 2 * M;
-    const dim3 grid((unsigned)((L.npix + kThreads - 1) / kThreads), (unsigned)((nout + kRows - 1) / kRows));
+    const dim3 grid((unsigned)(((int64_t)L.npix + kThreads - 1) / kThreads), (unsigned)((nout + kRows - 1) / kRows));
     fz_to_df_rows_kernel<M><<<grid, kThreads, 0, s>>>(L);
 }
 
