@@ -6,6 +6,12 @@ independent units (molecules of a batch, pixel rows of a scan), and
 `max_over_ranks` / `sum_over_ranks` reduce a host scalar with whatever
 process group is initialised (NCCL on GPUs, gloo on CPU).  Without an
 initialised group they return their input.
+
+The one exchange a single large system needs is in the backward: the loss
+sum(w * df) is a sum over pixels, so when the ranks split the scan by pixel
+rows, each rank's gradient of its own rows' terms adds up to the whole
+image's gradient.  `reduce_grads` sums those per-atom and tip gradients over
+the ranks in one all-reduce of 6N + 5 values.
 """
 from __future__ import annotations
 
@@ -43,3 +49,32 @@ def sum_over_ranks(x: float, device=None) -> float:
     import torch.distributed as dist
 
     return _reduce(x, dist.ReduceOp.SUM, device)
+
+
+GRAD_KEYS = ("x", "y", "z", "q", "R", "eps")
+TIP_KEYS = ("kx", "ky", "kR", "Q", "Qzz")
+
+
+def reduce_grads(grads: dict, device=None) -> dict:
+    """Sum a gradient dict (per-atom arrays under GRAD_KEYS, scalars under TIP_KEYS; torch
+    tensors or numpy arrays) over all ranks with one all-reduce of a packed float64 buffer.
+    Returns a dict of the same keys (float64 torch tensors on the reduction device for the
+    per-atom entries, Python floats for the scalars); without an initialised group it returns
+    the input's values unchanged."""
+    import torch.distributed as dist
+
+    n = len(grads[GRAD_KEYS[0]])
+    grouped = dist.is_available() and dist.is_initialized()
+    if device is None:
+        device = "cuda" if grouped and dist.get_backend() == "nccl" else "cpu"
+    flat = torch.empty(6 * n + 5, dtype=torch.float64, device=device)
+    for r, k in enumerate(GRAD_KEYS):
+        v = grads[k]
+        flat[r * n:(r + 1) * n] = v.to(device=device, dtype=torch.float64) if torch.is_tensor(v) else \
+            torch.as_tensor(v, dtype=torch.float64, device=device)
+    flat[6 * n:] = torch.tensor([float(grads.get(k, 0.0)) for k in TIP_KEYS], dtype=torch.float64, device=device)
+    if grouped:
+        dist.all_reduce(flat, op=dist.ReduceOp.SUM)
+    out = {k: flat[r * n:(r + 1) * n] for r, k in enumerate(GRAD_KEYS)}
+    out.update({k: float(flat[6 * n + i].item()) for i, k in enumerate(TIP_KEYS)})
+    return out

@@ -1,12 +1,16 @@
-"""Multi-rank host logic on CPU (gloo, world size 2): work split and timing reductions."""
+"""Multi-rank host logic on CPU (gloo, world size 2): work split, timing reductions, and the
+one collective of a pixel-sharded backward (the per-atom and tip gradients summed over ranks)."""
 import os
 import socket
 
+import numpy as np
 import pytest
 import torch
 import torch.multiprocessing as mp
 
+from helpers import case32
 from paper_2401_14564_gb300 import dist as ppd
+from paper_2401_14564_gb300 import synth
 
 
 def test_shard_covers_every_unit_once():
@@ -64,3 +68,55 @@ def test_two_gloo_ranks_split_and_reduce():
         assert total == 1000
         assert slowest == 2.25
         assert value == pytest.approx(2 * 1000 / 2.25e-3)
+
+
+def _grad_case():
+    return case32(synth.small_case(seed=21, n_atoms=7, nxy=24, nz=30, scan_px=9, nz_scan=14))
+
+
+def _grad_worker(rank, world, port, q):
+    import torch.distributed as dist
+
+    import oracle as orc
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        c = _grad_case()
+        o = orc.forward(c, fire=synth.parity_fire())
+        w = np.random.default_rng(3).standard_normal(o["df"].shape)
+        j0, j1 = ppd.shard(c["scan"]["ny"], rank, world)  # this rank's pixel rows
+        wr = np.zeros_like(w)
+        wr[:, j0:j1, :] = w[:, j0:j1, :]
+        g = orc.backward(o["ff"], c["grid"], c["atoms"], c["probe"], c["scan"], c["tip"], c["df"], o["pos"], wr)
+        tot = ppd.reduce_grads(g)
+        q.put((rank, j1 - j0, {k: tot[k].numpy() for k in ppd.GRAD_KEYS}, {k: tot[k] for k in ppd.TIP_KEYS}))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_pixel_sharded_backward_reduces_to_the_whole_gradient(orc):
+    # two ranks, each the oracle's adjoint of its own pixel rows' df terms; one all-reduce of the
+    # 6N + 5 gradient values gives the gradient of the whole image's loss on every rank
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_grad_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted((q.get(timeout=300) for _ in procs), key=lambda r: r[0])
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    c = _grad_case()
+    o = orc.forward(c, fire=synth.parity_fire())
+    w = np.random.default_rng(3).standard_normal(o["df"].shape)
+    ref = orc.backward(o["ff"], c["grid"], c["atoms"], c["probe"], c["scan"], c["tip"], c["df"], o["pos"], w)
+    assert sum(r[1] for r in res) == c["scan"]["ny"] and min(r[1] for r in res) > 0
+    for _, _, per_atom, tip in res:
+        for k in ppd.GRAD_KEYS:
+            scale = np.abs(ref[k]).max()
+            assert scale > 0 and np.abs(per_atom[k] - ref[k]).max() <= 1e-10 * scale, k
+        for k in ("kx", "ky", "kR", "Q"):
+            assert tip[k] == pytest.approx(ref[k], rel=1e-10, abs=1e-14), k
