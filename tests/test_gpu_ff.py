@@ -154,3 +154,17 @@ def test_forces_only_simulator_gives_the_same_images():
         outs.append((sim.df.clone(), sim.pos.clone(), sim.iters.clone()))
     for u, v in zip(*outs):
         assert torch.equal(u, v)
+
+
+def test_forces_only_on_a_bricked_grid():
+    # the forces-only flag is independent of the storage layout: bricked grid, padding written
+    c = case32(synth.small_case(seed=8, n_atoms=10, nxy=26, nz=13))
+    g1 = pp.make_grid(c["grid"], 1, (4, 4, 4))
+    atoms, probe = pp.make_atoms(afm.atoms_to_device(c["atoms"])), pp.make_probe(c["probe"])
+    full = torch.full((pp.pp_ff_floats(g1),), float("nan"), dtype=torch.float32, device="cuda")
+    forces = torch.full_like(full, float("nan"))
+    pp.pp_make_ff_tuned(atoms, probe, g1, full, pp.Tuning(8, 0))
+    pp.pp_make_ff_tuned(atoms, probe, g1, forces, pp.Tuning(8, 1))
+    a, b = full.view(-1, 4), forces.view(-1, 4)
+    assert torch.isfinite(b).all()
+    assert torch.equal(a[:, :3], b[:, :3]) and torch.count_nonzero(b[:, 3]).item() == 0
