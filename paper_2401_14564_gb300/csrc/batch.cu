@@ -281,7 +281,7 @@ __global__ void __launch_bounds__(kThreads, kMinCtas) batch_kernel(const BatchLa
         G.df = B.df + D.df_offset;
         const int tiles_x = (D.snx + 7) / 8;
         const int ty = (int)(tile / tiles_x), tx = (int)(tile - (long long)ty * tiles_x);
-        relax_pixel<0, true>(G, B, tx * 8 + (lane & 7), ty * 4 + (lane >> 3));
+        relax_pixel<0, true, false, true>(G, B, tx * 8 + (lane & 7), ty * 4 + (lane >> 3));
     }
 }
 

@@ -3,7 +3,11 @@
 Choices it sweeps, each timed with CUDA events through the C ABI on the
 workload itself (inputs on the device, median of a few repetitions):
   - pp_make_ff_tuned: z-nodes per thread (4, 8, 16);
-  - pp_relax_scan: force-field layout, linear or bricked (several brick shapes);
+  - pp_relax_scan: force-field layout, linear or bricked (several brick shapes),
+    timed on the scan alone, or on whole steps several in flight (afm.Pipeline)
+    when the caller runs them that way: the two regimes can prefer different
+    layouts (a lone scan is bound by its slowest columns' dependency chains,
+    overlapped steps by issue slots and cache capacity);
   - pp_batch_run: persistent CTAs (multiples of the SM count).
 Every candidate computes the same values (the layout and the launch shape do
 not change the arithmetic per node or per pixel), so the pick is a pure
@@ -44,9 +48,11 @@ def _time(fn, reps):
     return statistics.median(ts)
 
 
-def tune_case(case, reps=3, bricks=BRICKS, zpts=ZPTS, ff_energy=True):
+def tune_case(case, reps=3, bricks=BRICKS, zpts=ZPTS, ff_energy=True, pipeline_slots=0):
     """Time every FF launch shape and every grid layout for the relaxation; return the fastest.
-    ff_energy=False times the forces-only assembly (the one a Simulator with ff_energy=False runs)."""
+    ff_energy=False times the forces-only assembly (the one a Simulator with ff_energy=False runs).
+    pipeline_slots > 0 times each layout on 4 x pipeline_slots whole steps through an
+    afm.Pipeline of that many slots (the regime of Pipeline.run_many) instead of the scan alone."""
     atoms_t = afm.atoms_to_device(case["atoms"])
     atoms = pp.make_atoms(atoms_t)
     probe = pp.make_probe(case["probe"])
@@ -62,6 +68,16 @@ def tune_case(case, reps=3, bricks=BRICKS, zpts=ZPTS, ff_energy=True):
         bricks = [(0, None)]  # tricubic energy grids are linear
     relax_times = {}
     for layout, brick in bricks:
+        if pipeline_slots > 0:
+            tun = {"ff_zpt": best_z, "layout": layout, "brick": list(brick) if brick else None}
+            pipe = afm.Pipeline(case, slots=pipeline_slots, tuning=tun,
+                                ff_energy=ff_energy or bool(case["grid"].get("interp", 0)))
+            items = [atoms_t] * (4 * pipeline_slots)
+            pipe.run_many(items)
+            relax_times[f"{layout}:{brick}"] = _time(lambda: pipe.run_many(items), reps) / len(items)
+            del pipe
+            torch.cuda.empty_cache()
+            continue
         sim = afm.Simulator(case, layout=layout, brick=brick or (4, 4, 4), want_pos=False, want_iters=False)
         sim.make_ff(atoms_t)
         sim.relax()
@@ -71,7 +87,9 @@ def tune_case(case, reps=3, bricks=BRICKS, zpts=ZPTS, ff_energy=True):
     layout, brick = best.split(":", 1)
     brick = None if brick == "None" else tuple(int(v) for v in brick.strip("()").split(","))
     return {"ff_zpt": best_z, "layout": int(layout), "brick": list(brick) if brick else None,
-            "ff_ms": ff_times, "relax_ms": relax_times}
+            "ff_ms": ff_times, "relax_ms": relax_times,
+            "layout_timing": "ms per step, whole steps %d in flight" % pipeline_slots if pipeline_slots > 0
+            else "ms per scan alone"}
 
 
 def tune_batch(batch_obj, reps=2, factors=(1, 2, 3, 4)):
@@ -94,7 +112,8 @@ def cached(case, path=None, **kw):
     if os.path.exists(path):
         with open(path) as f:
             db = json.load(f)
-    k = _key(case) + ("" if kw.get("ff_energy", True) else "|forces_only")
+    k = _key(case) + ("" if kw.get("ff_energy", True) else "|forces_only") + (
+        f"|pipeline{kw['pipeline_slots']}" if kw.get("pipeline_slots", 0) else "")
     if k not in db:
         r = tune_case(case, **kw)
         db[k] = {"ff_zpt": r["ff_zpt"], "layout": r["layout"], "brick": r["brick"],

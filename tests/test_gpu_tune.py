@@ -63,3 +63,21 @@ def test_forces_only_tuning_and_its_cache_entry(tmp_path):
     torch.cuda.synchronize()
     assert torch.equal(a.df, b.df) and torch.equal(a.fz, b.fz)
     assert torch.count_nonzero(b.ff.view(-1, 4)[:, 3]).item() == 0
+
+
+def test_pipeline_regime_tuning_reproduces_the_images():
+    # layouts timed on whole steps two in flight: the pick is one of the candidates and a pipeline
+    # built with it gives the default images, item by item
+    c = case32(synth.small_case(seed=13, n_atoms=9, nxy=32, nz=36, scan_px=10, nz_scan=12))
+    r = tune.tune_case(c, reps=1, pipeline_slots=2, ff_energy=False)
+    assert r["layout_timing"].startswith("ms per step")
+    assert f"{r['layout']}:{tuple(r['brick']) if r['brick'] else None}" in r["relax_ms"]
+    at = afm.atoms_to_device(c["atoms"])
+    ref = afm.Simulator(c)
+    ref.run(at)
+    pipe = afm.Pipeline(c, slots=2, tuning=r, ff_energy=False)
+    outs = [torch.empty_like(ref.df) for _ in range(3)]
+    pipe.run_many([at] * 3, outs)
+    torch.cuda.synchronize()
+    for o in outs:
+        assert torch.equal(o, ref.df)
