@@ -113,26 +113,26 @@ __device__ __forceinline__ void relax_pixel(const G_t& P, const Q_t& Q, int i, i
             it = 0;
             continue;
         }
-        if (it > 0) {
+        {
+            // FIRE velocity mixing, or the reset after an uphill step, as selects rather than
+            // branches (lanes disagree on pw > 0 at different iterations; a branch serialised both
+            // paths and added a reconvergence to every iteration's chain): the values taken are
+            // those of the branching form.  v = 0 on a height's first iteration, where v2 = 0 and
+            // the unused mixed velocity is NaN.
             const float pw = fmaf(G.x, v.x, fmaf(G.y, v.y, G.z * v.z));
-            if (pw > 0.f) {
-                const float v2 = fmaf(v.x, v.x, fmaf(v.y, v.y, v.z * v.z));
-                const float c = alpha * (v2 * rsqrtf(v2)) * rsqrtf(g2);  // alpha |v| / |G|
-                const float om = 1.f - alpha;
-                v.x = fmaf(om, v.x, c * G.x);
-                v.y = fmaf(om, v.y, c * G.y);
-                v.z = fmaf(om, v.z, c * G.z);
-                if (npos > Q.n_min) {
-                    dt = fminf(dt * Q.f_inc, Q.dt_max);
-                    alpha *= Q.f_alpha;
-                }
-                ++npos;
-            } else {
-                v = make_float3(0.f, 0.f, 0.f);
-                dt *= Q.f_dec;
-                alpha = Q.alpha0;
-                npos = 0;
-            }
+            const bool up = (it > 0) && (pw > 0.f);
+            const bool down = (it > 0) && !(pw > 0.f);
+            const float v2 = fmaf(v.x, v.x, fmaf(v.y, v.y, v.z * v.z));
+            const float c = alpha * (v2 * rsqrtf(v2)) * rsqrtf(g2);  // alpha |v| / |G|
+            const float om = 1.f - alpha;
+            const float mx = fmaf(om, v.x, c * G.x), my = fmaf(om, v.y, c * G.y), mz = fmaf(om, v.z, c * G.z);
+            const bool grow = up && (npos > Q.n_min);
+            v.x = up ? mx : (down ? 0.f : v.x);
+            v.y = up ? my : (down ? 0.f : v.y);
+            v.z = up ? mz : (down ? 0.f : v.z);
+            dt = grow ? fminf(dt * Q.f_inc, Q.dt_max) : (down ? dt * Q.f_dec : dt);
+            alpha = grow ? alpha * Q.f_alpha : (down ? Q.alpha0 : alpha);
+            npos = up ? npos + 1 : (down ? 0 : npos);
         }
         const float h = dt * Q.inv_mass;
         v.x = fmaf(h, G.x, v.x);
