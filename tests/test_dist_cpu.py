@@ -29,6 +29,18 @@ def test_reductions_without_a_group_are_identity():
     assert ppd.max_over_ranks(3.5) == 3.5 and ppd.sum_over_ranks(2.0) == 2.0
 
 
+def test_gradient_packing_without_a_group_is_identity():
+    # torch tensors and numpy arrays mix; absent tip entries read as 0; values come back unchanged
+    g = {k: (torch.arange(4, dtype=torch.float32) * (i + 1) if i % 2 else np.arange(4.0) - i)
+         for i, k in enumerate(ppd.GRAD_KEYS)}
+    g.update(kx=0.5, ky=-1.25, kR=3.0, Q=7.0)
+    r = ppd.reduce_grads(g)
+    for i, k in enumerate(ppd.GRAD_KEYS):
+        want = np.arange(4.0) * (i + 1) if i % 2 else np.arange(4.0) - i
+        assert r[k].dtype == torch.float64 and np.array_equal(r[k].numpy(), want)
+    assert (r["kx"], r["ky"], r["kR"], r["Q"], r["Qzz"]) == (0.5, -1.25, 3.0, 7.0, 0.0)
+
+
 def _free_port():
     with socket.socket() as s:
         s.bind(("127.0.0.1", 0))
