@@ -775,9 +775,10 @@ def main():
         # layouts timed the way the headline runs them: whole steps, four in flight
         tuning = tune.tune_case(case, ff_energy=args.ff_energy, pipeline_slots=4)
     # four steps in flight, each slot with its own grid, outputs and stream: the next steps' force
-    # fields and scans fill the issue slots a latency-bound scan leaves idle (measured on flake60:
-    # 1.478 ms per step with one slot, 1.064 / 0.915 / 0.826 / 0.823 ms with 2 / 3 / 4 / 6);
-    # slot 0 alone gives the isolated per-kernel timings
+    # fields and scans fill the issue slots a latency-bound scan leaves idle (measured on flake60
+    # with the forces-only grid: 0.821 / 0.730 / 0.729 / 0.728 / 0.727 ms per step with
+    # 3 / 4 / 5 / 6 / 8 slots, against about 1.3 ms one step at a time); slot 0 alone gives the
+    # isolated per-kernel timings
     pipe = afm.Pipeline(case, slots=4, layout=args.layout, tuning=tuning, ff_energy=args.ff_energy)
     sim = pipe.sims[0]
     atoms = afm.atoms_to_device(case["atoms"])
