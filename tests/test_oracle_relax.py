@@ -166,3 +166,47 @@ def test_grid_converges_to_grid_free_second_order(orc):
     # least-squares order of convergence over an 8x range of spacings: 2 for trilinear, 1 if broken
     order = np.polyfit(np.log(hs), np.log(errs), 1)[0]
     assert order > 1.7, (order, errs)
+
+
+@pytest.mark.parametrize("alpha,dt", [(1.0, 0.4), (1.0, 1.0), (0.0, 0.4), (0.0, 1.0)])
+def test_fire_special_cases_step_by_step(orc, alpha, dt):
+    # FIRE's velocity mixing v <- (1 - alpha) v + alpha |v| F/|F| has two limits with a simpler
+    # rule: alpha = 1 turns every downhill velocity onto the force direction at unchanged speed,
+    # alpha = 0 leaves it alone (plain semi-implicit Euler); an uphill step (F.v <= 0) stops the
+    # probe and scales the step by f_dec.  With f_alpha = 1 and the step growth held off, the
+    # first positions from rest under a constant sample force follow from those rules and the tip
+    # force law (Eq. F_tip) alone; dt = 1 overshoots, so the uphill reset is exercised too.
+    c = np.array([0.004, -0.003, -0.03])
+    grid, ff = flat_grid(tuple(c))
+    tip = synth.default_tip(d0x=0.2, d0y=-0.1)
+    kx, ky, kR, R0 = 0.25 * NM, 0.25 * NM, 20.0 * NM, 4.0
+    d0 = np.array([0.2, -0.1, -math.sqrt(R0**2 - 0.2**2 - 0.1**2)])
+
+    def force(d):
+        dn = np.linalg.norm(d)
+        return -kR * (dn - R0) / dn * d - np.array([kx, ky, 0.0]) * (d - d0) + c
+
+    fire = synth.default_fire(alpha0=alpha, f_alpha=1.0, n_min=10**6, dt0=dt, dt_max=dt, ftol=1e-12, mass=1.3)
+    s = scan3(1)
+    resets = 0
+    for n in range(1, 9):
+        d, v, h = d0.copy(), np.zeros(3), dt
+        for it in range(n):
+            F = force(d)
+            if it > 0:
+                if F @ v > 0.0:
+                    v = np.linalg.norm(v) * F / np.linalg.norm(F) if alpha == 1.0 else v
+                else:
+                    v = np.zeros(3)
+                    h *= fire["f_dec"]
+                    resets += n == 8
+            v = v + h * F / fire["mass"]
+            d = d + h * v
+        r = orc.relax_scan(ff, grid, None, None, s, tip, dict(fire, max_iter=n), polish_tol=0.0)
+        assert (r["iters"] == n).all()
+        for j in range(s["ny"]):
+            for i in range(s["nx"]):
+                anchor = np.array([s["x0"] + i * s["px"], s["y0"] + j * s["py"], s["z_top"]])
+                np.testing.assert_allclose(r["pos"][0, j, i] - anchor, d, atol=1e-12, rtol=0)
+    if dt == 1.0:
+        assert resets > 0  # the overshooting step size takes the uphill branch within 8 steps
