@@ -89,3 +89,31 @@ def test_single_atom_below_adds_its_curvature(orc):
         fp = (f(h + 1e-5) - f(h - 1e-5)) / 2e-5
         lat, ax = kx + sR - f(h) / h, kR - fp
         np.testing.assert_allclose(sorted(eig[k, 0, 0]), sorted([lat, lat, ax]), rtol=1e-6, atol=1e-9)
+
+
+def test_coupled_asymmetric_field_against_a_library_eigensolver(orc):
+    # a linear sample field F = A (p - p_ref) with a non-symmetric, strongly coupled A is
+    # interpolated exactly by the trilinear grid, so at the tip's rest offset (0, 0, -R0) the
+    # stiffness is K = diag(kx, ky, kR) - (A + A^T)/2 (the springs' part is the at-rest pin
+    # above); its eigenvalues come from numpy's symmetric eigensolver
+    A = np.array([[0.010, 0.021, -0.015], [-0.004, 0.008, 0.030], [0.012, -0.020, 0.050]])
+    g = {"nx": 8, "ny": 8, "nz": 8, "x0": -4.0, "y0": -4.0, "z0": 0.0, "dx": 1.0, "dy": 1.0, "dz": 1.0,
+         "periodic_xy": 0}
+    p_ref = np.array([0.3, -0.2, 2.5])
+    zz, yy, xx = np.meshgrid(g["z0"] + np.arange(8.0), g["y0"] + np.arange(8.0), g["x0"] + np.arange(8.0),
+                             indexing="ij")
+    nodes = np.stack([xx, yy, zz], -1)
+    ff = np.zeros((8, 8, 8, 4))
+    ff[..., :3] = (nodes - p_ref) @ A.T
+    tip = synth.default_tip()
+    s = scan1(nz=2)
+    pos = np.empty((s["nz"], s["ny"], s["nx"], 3))
+    for k in range(s["nz"]):
+        for i in range(s["nx"]):
+            pos[k, 0, i] = [s["x0"] + i * s["px"], s["y0"], s["z_top"] - k * s["dz"] - 4.0]
+    eig, _ = orc.iets(ff, g, None, None, s, tip, pos, mass_amu=16.0)
+    K = np.diag([0.25 * NM, 0.25 * NM, 20.0 * NM]) - 0.5 * (A + A.T)
+    want = np.linalg.eigvalsh(K)
+    assert abs(want[0] - want[1]) > 1e-3  # a genuinely coupled lateral pair
+    np.testing.assert_allclose(eig.reshape(-1, 3), np.broadcast_to(want, (eig.size // 3, 3)), rtol=1e-12,
+                               atol=1e-14)
