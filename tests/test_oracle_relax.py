@@ -210,3 +210,101 @@ def test_fire_special_cases_step_by_step(orc, alpha, dt):
                 np.testing.assert_allclose(r["pos"][0, j, i] - anchor, d, atol=1e-12, rtol=0)
     if dt == 1.0:
         assert resets > 0  # the overshooting step size takes the uphill branch within 8 steps
+
+
+def test_fire_step_growth_schedule_on_an_axial_force(orc):
+    # A sample force along z under a tip hanging straight down (d0 = (0, 0, -R0)) keeps the probe
+    # on the axis, where the tip force is linear in the deflection, F = c_z - kR e_z (Eq. F_tip with
+    # |d| = R0 - e_z).  The velocity then stays parallel to the force, FIRE's mixing leaves it
+    # unchanged, and while the probe has not yet passed the minimum every step is downhill.  The
+    # positions are those of semi-implicit Euler under the step schedule of Bitzek et al.: dt0 for
+    # the first n_min + 1 downhill steps after the first one, then growing by f_inc per step up to
+    # dt_max (n_min = 2, f_inc = 1.25 from 0.2 reaches the 0.5 cap at the ninth update).
+    cz = -0.03
+    kR = 1.0 * NM  # soft radial spring: a quarter period of 6.3 time units, past the 12 steps' 4.2
+    grid, ff = flat_grid((0.0, 0.0, cz))
+    tip = synth.default_tip(kR=1.0)
+    dt0, dt_max, f_inc, n_min, mass = 0.2, 0.5, 1.25, 2, 1.0
+    fire = synth.default_fire(dt0=dt0, dt_max=dt_max, f_inc=f_inc, n_min=n_min, f_alpha=0.9, alpha0=0.3,
+                              ftol=1e-12, mass=mass)
+    s = scan3(1)
+    for n in range(1, 13):
+        e, v = 0.0, 0.0
+        for it in range(n):
+            h = min(dt0 * f_inc ** max(0, it - n_min - 1), dt_max)
+            v += h * (cz - kR * e) / mass
+            e += h * v
+        assert e > cz / kR  # still above the minimum: every step was downhill
+        r = orc.relax_scan(ff, grid, None, None, s, tip, dict(fire, max_iter=n), polish_tol=0.0)
+        assert (r["iters"] == n).all()
+        for j in range(s["ny"]):
+            for i in range(s["nx"]):
+                anchor = np.array([s["x0"] + i * s["px"], s["y0"] + j * s["py"], s["z_top"]])
+                np.testing.assert_allclose(r["pos"][0, j, i] - anchor, [0.0, 0.0, -4.0 + e], atol=1e-12, rtol=0)
+    assert min(dt0 * f_inc ** max(0, 11 - n_min - 1), dt_max) == dt_max  # the cap was reached
+
+
+def fire_by_hand(force, d0, fire, n):
+    """Bitzek et al.'s FIRE written out for n position updates from rest (the deflection-free
+    start d0): returns the final d, the number of updates taken with a grown step, and the number
+    of those that followed an uphill reset."""
+    d, v = d0.copy(), np.zeros(3)
+    dt, alpha, npos, grown, regrown, reset = fire["dt0"], fire["alpha0"], 0, 0, 0, False
+    for it in range(n):
+        F = force(d)
+        if it > 0:
+            if F @ v > 0.0:
+                v = (1.0 - alpha) * v + alpha * np.linalg.norm(v) * F / np.linalg.norm(F)
+                if npos > fire["n_min"]:
+                    dt = min(dt * fire["f_inc"], fire["dt_max"])
+                    alpha *= fire["f_alpha"]
+                    grown += 1
+                    regrown += reset
+                npos += 1
+            else:
+                v = np.zeros(3)
+                dt *= fire["f_dec"]
+                alpha = fire["alpha0"]
+                npos = 0
+                reset = True
+        v = v + dt * F / fire["mass"]
+        d = d + dt * v
+    return d, grown, regrown
+
+
+@pytest.mark.parametrize("f_alpha,kR,dt0,n_min,steps", [(0.9, 1.0, 0.2, 2, 12), (0.99, 1.0, 0.2, 2, 12),
+                                                         (0.9, 20.0, 0.5, 1, 24)])
+def test_fire_growth_and_alpha_decay_step_by_step(orc, f_alpha, kR, dt0, n_min, steps):
+    # A lateral + vertical constant sample force under a tilted tip: the probe moves off the axis,
+    # so the velocity mixing acts on every downhill step, and after more than n_min downhill steps
+    # the step grows and alpha decays.  Positions after each number of updates against FIRE
+    # written out by hand (Bitzek et al. 2006) and Eq. F_tip, to 1e-12 A; the same run with alpha
+    # held (f_alpha = 1) ends elsewhere, so the decay is seen.  With the 20 N/m radial spring and
+    # dt0 = 0.5 the probe overshoots: the uphill reset is taken and the count of downhill steps
+    # starts again before the step grows anew.
+    c = np.array([0.012, -0.008, -0.03])
+    grid, ff = flat_grid(tuple(c))
+    tip = synth.default_tip(d0x=0.2, d0y=-0.1, kR=kR)
+    kx, ky, kRe, R0 = 0.25 * NM, 0.25 * NM, kR * NM, 4.0
+    d0 = np.array([0.2, -0.1, -math.sqrt(R0**2 - 0.2**2 - 0.1**2)])
+
+    def force(d):
+        dn = np.linalg.norm(d)
+        return -kRe * (dn - R0) / dn * d - np.array([kx, ky, 0.0]) * (d - d0) + c
+
+    fire = synth.default_fire(dt0=dt0, dt_max=2.5 * dt0, f_inc=1.25, n_min=n_min, f_alpha=f_alpha, alpha0=0.3,
+                              ftol=1e-12, mass=1.0)
+    s = scan3(1)
+    for n in range(1, steps + 1):
+        d, grown, regrown = fire_by_hand(force, d0, fire, n)
+        r = orc.relax_scan(ff, grid, None, None, s, tip, dict(fire, max_iter=n), polish_tol=0.0)
+        assert (r["iters"] == n).all()
+        for j in range(s["ny"]):
+            for i in range(s["nx"]):
+                anchor = np.array([s["x0"] + i * s["px"], s["y0"] + j * s["py"], s["z_top"]])
+                np.testing.assert_allclose(r["pos"][0, j, i] - anchor, d, atol=1e-12, rtol=0)
+    assert grown >= 6  # the growth branch was taken on many of the updates
+    if kR > 1.0:
+        assert regrown >= 2  # ... also after an uphill reset
+    held, _, _ = fire_by_hand(force, d0, dict(fire, f_alpha=1.0), steps)
+    assert np.linalg.norm(held - d) > 1e-6
