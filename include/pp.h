@@ -143,11 +143,18 @@ typedef struct {
  * iteration on, G.v > 0 mixes v <- (1-alpha) v + alpha |v| G/|G| and, after
  * more than n_min such steps in a row, sets dt <- min(dt*f_inc, dt_max),
  * alpha <- alpha*f_alpha; G.v <= 0 sets v = 0, dt <- dt*f_dec,
- * alpha <- alpha0.  Then v += dt G/mass, p += dt v. */
+ * alpha <- alpha0.  Then v += dt G/mass, p += dt v.
+ * polish (0..16, 0 = off) adds, at every height where FIRE stopped below
+ * ftol, up to that many Newton steps p <- p - J^{-1} G with the exact
+ * Jacobian J = dG/dp (tip springs + the interpolant's), each kept only if it
+ * lowers |G|: the relaxed point then sits at the equilibrium G = 0 to the
+ * FP32 resolution of G, as the implicit adjoint (pp_backward) assumes.  The
+ * iteration counts are FIRE's alone.  pp_batch_run requires polish = 0. */
 typedef struct {
     int max_iter;
     float ftol, dt0, dt_max, f_inc, f_dec, alpha0, f_alpha, mass;
     int n_min;
+    int polish;
 } pp_fire;
 
 /* Cantilever of Eq. df: A_pp is the PEAK-TO-PEAK amplitude (A), k the
@@ -370,9 +377,11 @@ PP_API pp_status pp_backward(const pp_atoms* atoms, const pp_probe* probe, const
  * 32 MiB array that every GPU loading this library holds until the process
  * exits; it allocates nothing itself.  Grids whose pp_backward_workspace()
  * exceeds pp_backward_noalloc_capacity() bytes (about 2.1 million stored
- * nodes) are rejected with PP_ERR_CAPACITY.  The first call on each device
- * looks up the array's device address (make that call before any stream
- * capture).  All calls share the one array and it keeps the last call's
+ * nodes) are rejected with PP_ERR_CAPACITY.  Every call looks up the
+ * array's device address on the current device (cudaGetSymbolAddress), so a
+ * device reset or a new context leaves later calls valid; the first call on a
+ * device may load the library's code there, so make it before any stream
+ * capture.  All calls share the one array and it keeps the last call's
  * contents (each call clears what must start at zero): calls that overlap on
  * the GPU -- on different streams, or from different threads -- race and
  * must be serialised by the caller.  Inputs, outputs and errors as

@@ -3,7 +3,9 @@
 Forward runs the three CUDA stages and saves the force-field grid and the
 relaxed positions; backward runs the implicit adjoint (pp_backward) and
 returns gradients for the atom arrays (x, y, z, q, R, eps) and the tip
-scalars (kx, ky, kR, Q, Qzz).  Only argument marshalling happens here.
+scalars (kx, ky, kR, Q, Qzz).  Only the df image is differentiable: Fz and
+the relaxed positions come back marked non-differentiable.  Only argument
+marshalling happens here.
 """
 from __future__ import annotations
 
@@ -38,14 +40,16 @@ class PPFunction(torch.autograd.Function):
         pp.pp_make_ff(atoms, pp_probe, grid, ff)
         pp.pp_relax_scan(ff, grid, scan, pp_tip, pp.make_fire(fire or case["fire"]), pos, fz, None, dfp, df)
         ctx.save_for_backward(*[atoms_t[k] for k in ATOM_KEYS], ff, pos)
-        ctx.meta = (probe, tip, grid, scan, dfp)
-        ctx.mark_non_differentiable(fz)
+        ctx.meta = (probe, tip, grid, scan, dfp, tuple(df.shape))
+        # Fz and the relaxed positions are returned for inspection only: the adjoint propagates the
+        # df image's gradient, so a loss on either must not pass through here silently
+        ctx.mark_non_differentiable(fz, pos)
         return df, fz, pos
 
     @staticmethod
     def backward(ctx, g_df, g_fz, g_pos):
         *atoms_l, ff, pos = ctx.saved_tensors
-        probe, tip, grid, scan, dfp = ctx.meta
+        probe, tip, grid, scan, dfp, df_shape = ctx.meta
         atoms_t = dict(zip(ATOM_KEYS, atoms_l))
         dev = ff.device
         n = atoms_t["x"].numel()
@@ -53,7 +57,7 @@ class PPFunction(torch.autograd.Function):
         grads["tip"] = torch.empty(5, dtype=torch.float32, device=dev)
         ws = torch.empty(pp.pp_backward_workspace(grid) // 4 + 4, dtype=torch.float32, device=dev)
         if g_df is None:
-            g_df = torch.zeros(1, dtype=torch.float32, device=dev)
+            g_df = torch.zeros(df_shape, dtype=torch.float32, device=dev)
         pp.pp_backward(pp.make_atoms(atoms_t), pp.make_probe(probe), grid, ff, scan, pp.make_tip(tip), dfp, pos,
                        g_df.contiguous().to(torch.float32), pp.make_grads(grads), ws)
         gt = grads["tip"].cpu()

@@ -273,7 +273,8 @@ static bool check_tip_fire(const pp_tip* tip, const pp_fire* fire, std::string* 
     if (!(tip->d0x * tip->d0x + tip->d0y * tip->d0y < tip->R0 * tip->R0)) { *why = "|(d0x, d0y)| must be < R0"; return false; }
     if (fire->max_iter < 0 || !(fire->ftol > 0.f) || !(fire->dt0 > 0.f) || !(fire->dt_max > 0.f) ||
         !(fire->f_inc >= 1.f) || !(fire->f_dec > 0.f && fire->f_dec <= 1.f) || !(fire->alpha0 >= 0.f && fire->alpha0 <= 1.f) ||
-        !(fire->f_alpha > 0.f && fire->f_alpha <= 1.f) || !(fire->mass > 0.f) || fire->n_min < 0) {
+        !(fire->f_alpha > 0.f && fire->f_alpha <= 1.f) || !(fire->mass > 0.f) || fire->n_min < 0 ||
+        fire->polish < 0 || fire->polish > 16) {
         *why = "invalid FIRE parameters";
         return false;
     }
@@ -329,6 +330,7 @@ pp_status pp_relax_scan(const float* ff, const pp_grid* grid, const pp_scan* sca
     L.ftol2 = fire->ftol * fire->ftol;
     L.dt0 = fire->dt0; L.dt_max = fire->dt_max; L.f_inc = fire->f_inc; L.f_dec = fire->f_dec;
     L.alpha0 = fire->alpha0; L.f_alpha = fire->f_alpha; L.inv_mass = 1.f / fire->mass;
+    L.polish = fire->polish;
     L.pos = pos; L.fz = fz; L.iters = iters;
     L.df_m = -1;
     L.df = nullptr;
@@ -371,51 +373,54 @@ size_t pp_backward_workspace(const pp_grid* grid) {
     return kBwdHeader + (size_t)m.stored_nodes * (m.interp ? 4 : 16);
 }
 
-pp_status pp_backward(const pp_atoms* atoms, const pp_probe* probe, const pp_grid* grid, const float* ff,
-                      const pp_scan* scan, const pp_tip* tip, const pp_df* dfp, const float* pos, const float* g_df,
-                      const pp_grads* grads, void* ws, size_t ws_bytes, pp_stream stream) {
-    Range range("pp_backward");
-    g_error.clear();
-    if (!atoms || !probe || !grid || !ff || !scan || !tip || !dfp || !pos || !g_df || !grads || !ws) {
-        set_error("pp_backward: NULL argument");
+}  // extern "C"
+
+namespace pp {
+
+// Every check of the adjoint's arguments except those of the workspace, in the order pp_backward
+// has always made them (so that pp_backward and pp_backward_noalloc return the same status for
+// the same arguments); on success fills *Lp (all but the workspace fields) and the grid adjoint's
+// byte count *adj_bytes.
+pp_status backward_prepare(const std::string& who, const pp_atoms* atoms, const pp_probe* probe, const pp_grid* grid,
+                           const float* ff, const pp_scan* scan, const pp_tip* tip, const pp_df* dfp,
+                           const float* pos, const float* g_df, const pp_grads* grads, BwdLaunch* Lp,
+                           size_t* adj_bytes_out) {
+    if (!atoms || !probe || !grid || !ff || !scan || !tip || !dfp || !pos || !g_df || !grads) {
+        set_error(who + ": NULL argument");
         return PP_ERR_ARG;
     }
-    if (atoms->n < 0) { set_error("pp_backward: atoms->n < 0"); return PP_ERR_ARG; }
+    if (atoms->n < 0) { set_error(who + ": atoms->n < 0"); return PP_ERR_ARG; }
     if (atoms->n > 0 && (!atoms->x || !atoms->y || !atoms->z || !atoms->R || !atoms->eps || !atoms->q ||
                          !grads->x || !grads->y || !grads->z || !grads->q || !grads->R || !grads->eps)) {
-        set_error("pp_backward: NULL atom or gradient array");
+        set_error(who + ": NULL atom or gradient array");
         return PP_ERR_ARG;
     }
-    if (!grads->tip) { set_error("pp_backward: NULL tip gradient"); return PP_ERR_ARG; }
-    if (!aligned16(ff) || !aligned16(ws)) { set_error("pp_backward: ff and ws must be 16-byte aligned"); return PP_ERR_ARG; }
+    if (!grads->tip) { set_error(who + ": NULL tip gradient"); return PP_ERR_ARG; }
+    if (!aligned16(ff)) { set_error(who + ": ff must be 16-byte aligned"); return PP_ERR_ARG; }
     if (!(probe->core_frac > 0.f && probe->core_frac < 1.f) || !(probe->eps_pp >= 0.f) || !(probe->coul_rc >= 0.f) ||
         (probe->min_image != 0 && probe->min_image != 1) || !isfinite(probe->Q) || !isfinite(probe->Qzz)) {
-        set_error("pp_backward: invalid probe parameters");
+        set_error(who + ": invalid probe parameters");
         return PP_ERR_ARG;
     }
     GridMap map;
     std::string why;
-    if (!make_grid_map(grid, &map, &why)) { set_error("pp_backward: " + why); return PP_ERR_SHAPE; }
+    if (!make_grid_map(grid, &map, &why)) { set_error(who + ": " + why); return PP_ERR_SHAPE; }
     if (scan->nx < 1 || scan->ny < 1 || scan->nz < 1 ||
         (int64_t)scan->nx * scan->ny * scan->nz * 3 >= (int64_t(1) << 31)) {
-        set_error("pp_backward: invalid scan size");
+        set_error(who + ": invalid scan size");
         return PP_ERR_SHAPE;
     }
-    if (!finite_pos(scan->dz)) { set_error("pp_backward: invalid scan geometry"); return PP_ERR_ARG; }
-    pp_fire dummy = {1, 1.f, 1.f, 1.f, 1.f, 1.f, 0.f, 1.f, 1.f, 0};
-    if (!check_tip_fire(tip, &dummy, &why)) { set_error("pp_backward: " + why); return PP_ERR_ARG; }
-    if (!finite_pos(dfp->k) || !isfinite(dfp->f0)) { set_error("pp_backward: invalid df parameters"); return PP_ERR_ARG; }
+    if (!finite_pos(scan->dz)) { set_error(who + ": invalid scan geometry"); return PP_ERR_ARG; }
+    pp_fire dummy = {1, 1.f, 1.f, 1.f, 1.f, 1.f, 0.f, 1.f, 1.f, 0, 0};
+    if (!check_tip_fire(tip, &dummy, &why)) { set_error(who + ": " + why); return PP_ERR_ARG; }
+    if (!finite_pos(dfp->k) || !isfinite(dfp->f0)) { set_error(who + ": invalid df parameters"); return PP_ERR_ARG; }
     const int m = df_half_width(dfp->A_pp, scan->dz);
-    if (m < 0) { set_error("pp_backward: invalid df amplitude"); return PP_ERR_ARG; }
-    if (m > kMaxDfHalfWidth) { set_error("pp_backward: df stencil wider than 63 taps"); return PP_ERR_UNSUPPORTED; }
-    if (scan->nz < 2 * m + 1) { set_error("pp_backward: fewer heights than the df stencil"); return PP_ERR_SHAPE; }
+    if (m < 0) { set_error(who + ": invalid df amplitude"); return PP_ERR_ARG; }
+    if (m > kMaxDfHalfWidth) { set_error(who + ": df stencil wider than 63 taps"); return PP_ERR_UNSUPPORTED; }
+    if (scan->nz < 2 * m + 1) { set_error(who + ": fewer heights than the df stencil"); return PP_ERR_SHAPE; }
     const size_t adj_bytes = (size_t)map.stored_nodes * (map.interp ? 4 : 16);
-    const size_t need = kBwdHeader + adj_bytes;
-    if (ws_bytes < need) {
-        set_error("pp_backward: workspace too small (need " + std::to_string(need) + " bytes)");
-        return PP_ERR_CAPACITY;
-    }
-    BwdLaunch L;
+    *adj_bytes_out = adj_bytes;
+    BwdLaunch& L = *Lp;
     std::memset(&L, 0, sizeof(L));
     L.ax = atoms->x; L.ay = atoms->y; L.az = atoms->z; L.aR = atoms->R; L.aeps = atoms->eps; L.aq = atoms->q;
     L.n = atoms->n;
@@ -452,16 +457,45 @@ pp_status pp_backward(const pp_atoms* atoms, const pp_probe* probe, const pp_gri
     L.g_df = g_df;
     L.gx = grads->x; L.gy = grads->y; L.gz = grads->z; L.gq = grads->q; L.gR = grads->R; L.geps = grads->eps;
     L.gtip = grads->tip;
+    return PP_OK;
+}
+
+// Points the prepared launch at the workspace ws (kBwdHeader + adj_bytes bytes, 16-byte aligned),
+// clears the grid adjoint and enqueues the adjoint kernels.
+pp_status backward_launch(const std::string& who, BwdLaunch& L, void* ws, size_t adj_bytes, cudaStream_t s) {
     L.slab = reinterpret_cast<int*>(ws);
     L.qsum = reinterpret_cast<float*>(reinterpret_cast<char*>(ws) + 16);
-    L.gbar = map.interp ? nullptr : reinterpret_cast<float4*>(reinterpret_cast<char*>(ws) + kBwdHeader);
-    L.gbarE = map.interp ? reinterpret_cast<float*>(reinterpret_cast<char*>(ws) + kBwdHeader) : nullptr;
+    L.gbar = L.map.interp ? nullptr : reinterpret_cast<float4*>(reinterpret_cast<char*>(ws) + kBwdHeader);
+    L.gbarE = L.map.interp ? reinterpret_cast<float*>(reinterpret_cast<char*>(ws) + kBwdHeader) : nullptr;
     L.qsumd = reinterpret_cast<double*>(reinterpret_cast<char*>(ws) + 32);
-    cudaStream_t s = (cudaStream_t)stream;
     pp_status st = cuda_status(cudaMemsetAsync(reinterpret_cast<char*>(ws) + kBwdHeader, 0, adj_bytes, s),
-                               "pp_backward memset");
+                               (who + " memset").c_str());
     if (st != PP_OK) return st;
-    return cuda_status(launch_backward(L, s), "pp_backward launch");
+    return cuda_status(launch_backward(L, s), (who + " launch").c_str());
+}
+
+}  // namespace pp
+
+extern "C" {
+
+pp_status pp_backward(const pp_atoms* atoms, const pp_probe* probe, const pp_grid* grid, const float* ff,
+                      const pp_scan* scan, const pp_tip* tip, const pp_df* dfp, const float* pos, const float* g_df,
+                      const pp_grads* grads, void* ws, size_t ws_bytes, pp_stream stream) {
+    Range range("pp_backward");
+    g_error.clear();
+    if (!ws) { set_error("pp_backward: NULL argument"); return PP_ERR_ARG; }
+    if (!aligned16(ws)) { set_error("pp_backward: ws must be 16-byte aligned"); return PP_ERR_ARG; }
+    BwdLaunch L;
+    size_t adj_bytes = 0;
+    const pp_status st = backward_prepare("pp_backward", atoms, probe, grid, ff, scan, tip, dfp, pos, g_df, grads, &L,
+                                          &adj_bytes);
+    if (st != PP_OK) return st;
+    const size_t need = kBwdHeader + adj_bytes;
+    if (ws_bytes < need) {
+        set_error("pp_backward: workspace too small (need " + std::to_string(need) + " bytes)");
+        return PP_ERR_CAPACITY;
+    }
+    return backward_launch("pp_backward", L, ws, adj_bytes, (cudaStream_t)stream);
 }
 
 size_t pp_batch_workspace(int nmol) { return batch_workspace_bytes(nmol); }
@@ -487,6 +521,7 @@ pp_status pp_batch_run(const pp_mol_desc* descs, int nmol, const pp_batch_params
     }
     std::string why;
     if (!check_tip_fire(&bp->tip, &bp->fire, &why)) { set_error("pp_batch_run: " + why); return PP_ERR_ARG; }
+    if (bp->fire.polish != 0) { set_error("pp_batch_run: the Newton polish is not available in batches"); return PP_ERR_UNSUPPORTED; }
     if (!finite_pos(bp->scan_dz) || (bp->periodic_xy != 0 && bp->periodic_xy != 1)) {
         set_error("pp_batch_run: invalid scan_dz or periodic_xy");
         return PP_ERR_ARG;
@@ -548,7 +583,7 @@ pp_status pp_iets(const float* ff, const pp_grid* grid, const pp_scan* scan, con
         return PP_ERR_SHAPE;
     }
     if (!finite_pos(scan->dz)) { set_error("pp_iets: invalid scan geometry"); return PP_ERR_ARG; }
-    pp_fire dummy = {1, 1.f, 1.f, 1.f, 1.f, 1.f, 0.f, 1.f, 1.f, 0};
+    pp_fire dummy = {1, 1.f, 1.f, 1.f, 1.f, 1.f, 0.f, 1.f, 1.f, 0, 0};
     if (!check_tip_fire(tip, &dummy, &why)) { set_error("pp_iets: " + why); return PP_ERR_ARG; }
     IetsLaunch L;
     std::memset(&L, 0, sizeof(L));

@@ -8,7 +8,6 @@
 // allocator of their own.  For them the scratch of the adjoint lives in the
 // file-scope array below: every GPU that loads this library holds those
 // bytes until the process exits.
-#include <mutex>
 #include <string>
 
 #include "pp_internal.cuh"
@@ -22,29 +21,16 @@ constexpr size_t kStaticScratchBytes = size_t(32) << 20;
 
 static __device__ __align__(256) unsigned char g_backward_scratch[kStaticScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_addr_mutex;
-void* g_addr[kMaxDevices] = {};
-
 // Device address of the array on the current device.  In host code the
-// array's name is only a host-side stand-in, so the address is looked up once
-// per device (with that device current) and cached.
+// array's name is only a host-side stand-in, so the address is looked up
+// with the device current, on every call: a cached address would outlive a
+// cudaDeviceReset or a new primary context, and the lookup costs nothing next
+// to the adjoint.
 pp_status scratch_address(void** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return cuda_status(e, "pp_backward_noalloc cudaGetDevice");
-    if (dev < 0 || dev >= kMaxDevices) {
-        set_error("pp_backward_noalloc: device ordinal " + std::to_string(dev) + " beyond 63");
-        return PP_ERR_UNSUPPORTED;
-    }
-    std::lock_guard<std::mutex> lock(g_addr_mutex);
-    if (!g_addr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_backward_scratch);
-        if (e != cudaSuccess) return cuda_status(e, "pp_backward_noalloc cudaGetSymbolAddress");
-        g_addr[dev] = p;
-    }
-    *out = g_addr[dev];
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_backward_scratch);
+    if (e != cudaSuccess) return cuda_status(e, "pp_backward_noalloc cudaGetSymbolAddress");
+    *out = p;
     return PP_OK;
 }
 
@@ -62,11 +48,13 @@ pp_status pp_backward_noalloc(const pp_atoms* atoms, const pp_probe* probe, cons
                               const pp_df* df_params, const float* pos, const float* g_df,
                               const pp_grads* grads, pp_stream stream) {
     set_error("");
-    const size_t need = pp_backward_workspace(grid);
-    if (need == 0) {
-        set_error("pp_backward_noalloc: invalid grid");
-        return PP_ERR_SHAPE;
-    }
+    // the same checks, in the same order and with the same status codes, as pp_backward
+    BwdLaunch L;
+    size_t adj_bytes = 0;
+    pp_status st = backward_prepare("pp_backward_noalloc", atoms, probe, grid, ff, scan, tip, df_params, pos, g_df,
+                                    grads, &L, &adj_bytes);
+    if (st != PP_OK) return st;
+    const size_t need = kBwdHeader + adj_bytes;
     if (need > kStaticScratchBytes) {
         set_error("pp_backward_noalloc: the grid needs " + std::to_string(need) +
                   " bytes of scratch but the library's static scratch holds " +
@@ -74,10 +62,9 @@ pp_status pp_backward_noalloc(const pp_atoms* atoms, const pp_probe* probe, cons
         return PP_ERR_CAPACITY;
     }
     void* ws = nullptr;
-    const pp_status st = scratch_address(&ws);
+    st = scratch_address(&ws);
     if (st != PP_OK) return st;
-    return pp_backward(atoms, probe, grid, ff, scan, tip, df_params, pos, g_df, grads, ws, kStaticScratchBytes,
-                       stream);
+    return backward_launch("pp_backward_noalloc", L, ws, adj_bytes, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -136,6 +136,7 @@ struct RelaxLaunch {
     float R0sq, c0;                       // R0^2 and |d0|^2 - R0^2 (rounding residue of d0)
     int max_iter, n_min;
     float ftol2, dt0, dt_max, f_inc, f_dec, alpha0, f_alpha, inv_mass;
+    int polish;  // Newton steps after FIRE stops below ftol (0: none)
     float* pos;
     float* fz;
     int* iters;
@@ -187,6 +188,13 @@ struct BwdLaunch {
     double* qsumd;  // the same sums on energy grids
 };
 cudaError_t launch_backward(const BwdLaunch& L, cudaStream_t s);
+// Host side of the adjoint entry points (api.cu): argument checks into a prepared launch, then the
+// launch on a workspace of kBwdHeader + adj_bytes bytes.  `who` prefixes the error messages.
+pp_status backward_prepare(const std::string& who, const pp_atoms* atoms, const pp_probe* probe, const pp_grid* grid,
+                           const float* ff, const pp_scan* scan, const pp_tip* tip, const pp_df* dfp,
+                           const float* pos, const float* g_df, const pp_grads* grads, BwdLaunch* L,
+                           size_t* adj_bytes);
+pp_status backward_launch(const std::string& who, BwdLaunch& L, void* ws, size_t adj_bytes, cudaStream_t s);
 
 struct BatchArgs {
     const pp_mol_desc* descs;

@@ -37,6 +37,37 @@ __device__ __forceinline__ float3 total_force_tip(const Q_t& P, float3 e, float 
     return G;
 }
 
+// Adds the tip springs' Jacobian dF_T/dp = s I - kR R0 d d^T / |d|^3 - diag(kx, ky, 0) (Eq. F_tip,
+// s = -kR (|d| - R0)/|d|, d = d0 + e) to J.
+template <class Q_t>
+__device__ __forceinline__ void add_spring_jacobian(const Q_t& P, float3 e, float s, float J[3][3]) {
+    const float q = fmaf(2.f * P.d0x + e.x, e.x, fmaf(2.f * P.d0y + e.y, e.y, fmaf(2.f * P.d0z + e.z, e.z, P.c0)));
+    const float rs = rsqrtf(P.R0sq + q);
+    const float br = -P.kR * P.R0 * rs * rs * rs;
+    const float d[3] = {P.d0x + e.x, P.d0y + e.y, P.d0z + e.z};
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) J[a][b] += (a == b ? s : 0.f) + br * d[a] * d[b];
+    J[0][0] -= P.kx;
+    J[1][1] -= P.ky;
+}
+
+// x = J^{-1} b by the adjugate; false when J is singular.
+__device__ __forceinline__ bool solve3(const float J[3][3], float3 b, float3& x) {
+    const float c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1], c01 = J[0][2] * J[2][1] - J[0][1] * J[2][2];
+    const float c02 = J[0][1] * J[1][2] - J[0][2] * J[1][1], c10 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+    const float c11 = J[0][0] * J[2][2] - J[0][2] * J[2][0], c12 = J[0][2] * J[1][0] - J[0][0] * J[1][2];
+    const float c20 = J[1][0] * J[2][1] - J[1][1] * J[2][0], c21 = J[0][1] * J[2][0] - J[0][0] * J[2][1];
+    const float c22 = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+    const float det = J[0][0] * c00 + J[0][1] * c10 + J[0][2] * c20;
+    if (!(det != 0.f) || !isfinite(det)) return false;
+    const float id = 1.f / det;
+    x = make_float3((c00 * b.x + c01 * b.y + c02 * b.z) * id, (c10 * b.x + c11 * b.y + c12 * b.z) * id,
+                    (c20 * b.x + c21 * b.y + c22 * b.z) * id);
+    return true;
+}
+
 // One lane's pixel column (i, j) of an 8x4 pixel tile: all heights, FIRE per
 // height, outputs, and the fused df epilogue.  Each lane loops until its own
 // column is done; the lanes of a warp still issue together while they are in
@@ -47,8 +78,12 @@ __device__ __forceinline__ float3 total_force_tip(const Q_t& P, float3 e, float 
 // selects plain cached loads of the force field instead of the read-only
 // path, for grids written earlier in the same kernel.  kTricubic takes F_S
 // from the tricubic energy grid P.ffE (linear layout) instead of the
-// trilinear force grid.
-template <int LAYOUT, bool kCoherent, bool kTricubic = false, bool kWarpVote = false, class G_t, class Q_t>
+// trilinear force grid.  kPolish adds, where FIRE stopped below ftol, up to
+// Q.polish Newton steps p <- p - J^{-1} G with the exact Jacobian (springs +
+// interpolant), each kept only if it lowers |G| (the equilibrium the implicit
+// adjoint differentiates, to the FP32 resolution of G).
+template <int LAYOUT, bool kCoherent, bool kTricubic = false, bool kWarpVote = false, bool kPolish = false,
+          class G_t, class Q_t>
 __device__ __forceinline__ void relax_pixel(const G_t& P, const Q_t& Q, int i, int j) {
     const bool valid = (i < P.snx) && (j < P.sny);
     const int npix = P.snx * P.sny;
@@ -96,8 +131,53 @@ __device__ __forceinline__ void relax_pixel(const G_t& P, const Q_t& Q, int i, i
         if (g2 < Q.ftol2 || it >= Q.max_iter) {
             // converged (or out of iterations) at height k: write, then go one height down
             // keeping the deflection e (the warm start p*(k-1) - dz z_hat)
+            float sw = s;
+            if constexpr (kPolish) {
+                if (it < Q.max_iter) {
+                    Cells cc = cl;
+                    float gc2 = g2;
+                    float3 Gc = G;
+                    for (int n = 0; n < Q.polish; ++n) {
+                        float J[3][3];
+                        if constexpr (kTricubic) tricubic_jacobian(ec, cc, P.inv_dx, P.inv_dy, P.inv_dz, J);
+                        else trilinear_jacobian(cv, cc, P.inv_dx, P.inv_dy, P.inv_dz, J);
+                        add_spring_jacobian(Q, e, sw, J);
+                        float3 dp;
+                        if (!solve3(J, make_float3(-Gc.x, -Gc.y, -Gc.z), dp)) break;
+                        const float3 et = make_float3(e.x + dp.x, e.y + dp.y, e.z + dp.z);
+                        const float st = radial_factor(Q, et);
+                        const Cells ct = locate(P, bx + et.x, by + et.y, (az + Q.d0z) + et.z);
+                        float3 Ft;
+                        if constexpr (kTricubic) {
+                            if (ct.x.i0 != cell_x || ct.y.i0 != cell_y || ct.z.i0 != cell_z) {
+                                tricubic_load(P.ffE, P.map, ct, P.periodic_xy, ec);
+                                cell_x = ct.x.i0;
+                                cell_y = ct.y.i0;
+                                cell_z = ct.z.i0;
+                            }
+                            Ft = tricubic_eval(ec, ct, P.inv_dx, P.inv_dy, P.inv_dz);
+                        } else {
+                            if (ct.x.i0 != cell_x || ct.y.i0 != cell_y || ct.z.i0 != cell_z) {
+                                load_corners<LAYOUT, kCoherent>(P.ff, P.map, ct, cv);
+                                cell_x = ct.x.i0;
+                                cell_y = ct.y.i0;
+                                cell_z = ct.z.i0;
+                            }
+                            Ft = trilinear(cv, ct);
+                        }
+                        const float3 Gt = total_force_tip(Q, et, st, Ft);
+                        const float gt2 = fmaf(Gt.x, Gt.x, fmaf(Gt.y, Gt.y, Gt.z * Gt.z));
+                        if (!(gt2 < gc2)) break;  // no progress: FP32 resolution of G reached
+                        e = et;
+                        sw = st;
+                        cc = ct;
+                        Gc = Gt;
+                        gc2 = gt2;
+                    }
+                }
+            }
             const int o = checked(k * npix + pix, (long long)npix * P.snz, kChkScanWrite);
-            P.fz[o] = -s * (Q.d0z + e.z);  // kR (|d| - R0) d_z / |d|
+            P.fz[o] = -sw * (Q.d0z + e.z);  // kR (|d| - R0) d_z / |d|
             if (P.pos) {
                 P.pos[3 * o] = bx + e.x;
                 P.pos[3 * o + 1] = by + e.y;

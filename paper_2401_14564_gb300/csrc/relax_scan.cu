@@ -71,25 +71,34 @@ __device__ __forceinline__ void prefetch_tile_slab(const RelaxLaunch& P, int tx,
     }
 }
 
-template <int LAYOUT>
+template <int LAYOUT, bool kPolish>
 __global__ void __launch_bounds__(kThreads) relax_scan_kernel(const RelaxLaunch P) {
     if (LAYOUT == 0) prefetch_tile_slab(P, blockIdx.x, blockIdx.y, threadIdx.x);
-    relax_pixel<LAYOUT, false>(P, P, blockIdx.x * kTileX + (threadIdx.x & 7), blockIdx.y * kTileY + (threadIdx.x >> 3));
+    relax_pixel<LAYOUT, false, false, false, kPolish>(P, P, blockIdx.x * kTileX + (threadIdx.x & 7),
+                                                      blockIdx.y * kTileY + (threadIdx.x >> 3));
 }
 
 // Tricubic energy grid (linear layout).
+template <bool kPolish>
 __global__ void __launch_bounds__(kThreads) relax_scan_tricubic_kernel(const RelaxLaunch P) {
     prefetch_tile_slab(P, blockIdx.x, blockIdx.y, threadIdx.x);
-    relax_pixel<0, false, true>(P, P, blockIdx.x * kTileX + (threadIdx.x & 7), blockIdx.y * kTileY + (threadIdx.x >> 3));
+    relax_pixel<0, false, true, false, kPolish>(P, P, blockIdx.x * kTileX + (threadIdx.x & 7),
+                                                blockIdx.y * kTileY + (threadIdx.x >> 3));
+}
+
+template <bool kPolish>
+void launch_relax_scan_t(const RelaxLaunch& L, dim3 grid, cudaStream_t s) {
+    if (L.map.interp == 1) relax_scan_tricubic_kernel<kPolish><<<grid, kThreads, 0, s>>>(L);
+    else if (L.layout == 0) relax_scan_kernel<0, kPolish><<<grid, kThreads, 0, s>>>(L);
+    else relax_scan_kernel<1, kPolish><<<grid, kThreads, 0, s>>>(L);
 }
 
 }  // namespace
 
 cudaError_t launch_relax_scan(const RelaxLaunch& L, cudaStream_t s) {
     dim3 grid((L.snx + kTileX - 1) / kTileX, (L.sny + kTileY - 1) / kTileY, 1);
-    if (L.map.interp == 1) relax_scan_tricubic_kernel<<<grid, kThreads, 0, s>>>(L);
-    else if (L.layout == 0) relax_scan_kernel<0><<<grid, kThreads, 0, s>>>(L);
-    else relax_scan_kernel<1><<<grid, kThreads, 0, s>>>(L);
+    if (L.polish > 0) launch_relax_scan_t<true>(L, grid, s);
+    else launch_relax_scan_t<false>(L, grid, s);
     return cudaGetLastError();
 }
 

@@ -59,7 +59,7 @@ class Scan(C.Structure):
 class Fire(C.Structure):
     _fields_ = [("max_iter", C.c_int)] + \
                [(k, C.c_float) for k in ("ftol", "dt0", "dt_max", "f_inc", "f_dec", "alpha0", "f_alpha", "mass")] + \
-               [("n_min", C.c_int)]
+               [("n_min", C.c_int), ("polish", C.c_int)]
 
 
 class DF(C.Structure):
@@ -212,7 +212,7 @@ def make_scan(s):
 
 def make_fire(f):
     return Fire(int(f["max_iter"]), f["ftol"], f["dt0"], f["dt_max"], f["f_inc"], f["f_dec"], f["alpha0"],
-                f["f_alpha"], f["mass"], int(f["n_min"]))
+                f["f_alpha"], f["mass"], int(f["n_min"]), int(f.get("polish", 0)))
 
 
 def make_df(d):

@@ -185,3 +185,58 @@ def test_forces_only_option_is_validated_on_host(L):
     g.interp = 1
     assert L.pp_make_ff_tuned(C.byref(atoms), C.byref(probe), C.byref(g), fake, C.byref(pp.Tuning(0, 1)), None) == 1
     assert b"interp = 1" in L.pp_last_error()
+
+
+def test_noalloc_adjoint_validates_like_pp_backward(L):
+    # pp_backward_noalloc makes pp_backward's checks in pp_backward's order (same status codes),
+    # then its own capacity check; none of these calls reaches the GPU
+    fake = C.c_void_p(256)  # never dereferenced: a check fails first
+    atoms = pp.Atoms(0, None, None, None, None, None, None)
+    probe = pp.make_probe({"R_pp": 1.66, "eps_pp": 0.0091, "Q": -0.1, "coul_rc": 0.0, "min_image": 0,
+                           "core_frac": 0.5})
+    scan = pp.make_scan({"nx": 4, "ny": 4, "nz": 12, "x0": 0.0, "y0": 0.0, "px": 0.1, "py": 0.1, "z_top": 0.3,
+                         "dz": 0.1})
+    tip = pp.make_tip({"kx": 0.25, "ky": 0.25, "kR": 20.0, "R0": 4.0, "d0x": 0.0, "d0y": 0.0})
+    dfp = pp.DF(1.0, 1800.0, 30300.0)
+    grads = pp.Grads(*([256] * 7))
+
+    def grid(n):
+        return pp.make_grid({"nx": n, "ny": n, "nz": 60, "x0": 0, "y0": 0, "z0": 0, "dx": 0.1, "dy": 0.1, "dz": 0.1,
+                             "periodic_xy": 1})
+
+    def both(g, pos=fake):
+        gp = C.byref(g) if g is not None else None
+        a = L.pp_backward(C.byref(atoms), C.byref(probe), gp, fake, C.byref(scan), C.byref(tip), C.byref(dfp), pos,
+                          fake, C.byref(grads), fake, 1 << 40, None)
+        b = L.pp_backward_noalloc(C.byref(atoms), C.byref(probe), gp, fake, C.byref(scan), C.byref(tip),
+                                  C.byref(dfp), pos, fake, C.byref(grads), None)
+        return a, b
+
+    assert both(None) == (1, 1)                  # NULL grid: PP_ERR_ARG from both
+    assert b"NULL" in L.pp_last_error()
+    assert both(grid(1)) == (2, 2)               # invalid grid: PP_ERR_SHAPE from both
+    big = grid(512)                              # 15.7 M nodes: beyond the static scratch
+    assert L.pp_backward_workspace(C.byref(big)) > L.pp_backward_noalloc_capacity()
+    assert both(big, pos=None) == (1, 1)         # a NULL argument wins over the capacity
+    tip_bad = pp.make_tip({"kx": -1.0, "ky": 0.25, "kR": 20.0, "R0": 4.0, "d0x": 0.0, "d0y": 0.0})
+    assert L.pp_backward_noalloc(C.byref(atoms), C.byref(probe), C.byref(big), fake, C.byref(scan),
+                                 C.byref(tip_bad), C.byref(dfp), fake, fake, C.byref(grads), None) == 1
+    assert L.pp_backward_noalloc(C.byref(atoms), C.byref(probe), C.byref(big), fake, C.byref(scan), C.byref(tip),
+                                 C.byref(dfp), fake, fake, C.byref(grads), None) == 4
+    assert b"static scratch" in L.pp_last_error()
+
+
+def test_fire_polish_is_validated_on_host(L):
+    fake = C.c_void_p(256)
+    g = pp.make_grid({"nx": 8, "ny": 8, "nz": 8, "x0": 0, "y0": 0, "z0": 0, "dx": 0.1, "dy": 0.1, "dz": 0.1,
+                      "periodic_xy": 1})
+    scan = pp.make_scan({"nx": 4, "ny": 4, "nz": 12, "x0": 0.0, "y0": 0.0, "px": 0.1, "py": 0.1, "z_top": 0.3,
+                         "dz": 0.1})
+    tip = pp.make_tip({"kx": 0.25, "ky": 0.25, "kR": 20.0, "R0": 4.0, "d0x": 0.0, "d0y": 0.0})
+    from paper_2401_14564_gb300 import synth
+
+    for bad in (-1, 17):
+        fire = pp.make_fire(synth.default_fire(polish=bad))
+        assert L.pp_relax_scan(fake, C.byref(g), C.byref(scan), C.byref(tip), C.byref(fire), fake, fake, fake, None,
+                               None, None) == 1
+        assert b"FIRE" in L.pp_last_error()

@@ -119,3 +119,36 @@ def test_invalid_descriptor_is_skipped_and_flagged():
     for n in (0, 1, 3):
         assert np.array_equal(b.molecule(n)["df"].cpu().numpy(), single(cs[n])["df"]), n
     assert (b.molecule(2)["df"].cpu().numpy() == 7.0).all()
+
+
+# Batch molecules with the extremes of the batched workload (seeds 1000 + i): the smallest grid
+# (128 x 128, 13 atoms), the largest (208 x 256, 62 atoms), the least planar (2.99 A of height
+# spread) and the one with the most fluorine atoms (14 of 74).
+ORACLE_MOLECULES = (67, 12, 83, 104)
+
+
+def test_batch_molecules_match_the_oracle(orc):
+    from helpers import df_keep, ill_conditioned_within_bound, relax_compare
+
+    cs = [case32(synth.batch_cases(1, 1000 + i)[0]) for i in ORACLE_MOLECULES]
+    g0 = [c["grid"] for c in cs]
+    assert min(g["nx"] * g["ny"] for g in g0) == 128 * 128 and max(g["nx"] * g["ny"] for g in g0) == 208 * 256
+    assert max(float(np.ptp(c["atoms"]["z"])) for c in cs) > 2.9
+    assert max(int(np.isclose(c["atoms"]["R"], 1.75).sum()) for c in cs) >= 10  # F atoms
+    fire = synth.parity_fire()
+    b = batch.Batch(cs, want_pos=True, fire=fire)
+    b.run()
+    assert b.status() == (0, 0)
+    for n, c in enumerate(cs):
+        got = {k: v.cpu().numpy().astype(np.float64) for k, v in b.molecule(n).items()}
+        o = orc.forward(c, fire=fire)
+        assert (got["iters"] < fire["max_iter"]).mean() > 0.999
+        dp, dfz, keep, n_ill, n_basin = relax_compare(got, o)
+        assert n_ill + n_basin <= 0.02 * keep.size, (n, n_ill, n_basin)
+        assert dp <= 1e-3, (n, dp)
+        n_sel, n_ok = ill_conditioned_within_bound(got["pos"], o, fire["ftol"])
+        assert n_ok == n_sel, (n, n_ok, n_sel)
+        m = (keep.shape[0] - got["df"].shape[0]) // 2
+        rng = o["df"].max() - o["df"].min()
+        ddf = np.abs(got["df"] - o["df"])[df_keep(keep, m)].max()
+        assert ddf <= 1e-3 * rng, (n, ddf, rng)

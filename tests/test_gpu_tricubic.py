@@ -92,9 +92,10 @@ def test_tricubic_fused_df_equals_standalone_kernel():
 # keep 1e-4.  The tip scalars sum lambda-weighted terms over every point and so pick up the least
 # stable points in full: on the oracle's own grid (rounded to FP32, so only the adjoint kernels'
 # arithmetic differs) they hold 5e-4 (measured <= 2.1e-4); on the GPU's grid, whose energies add
-# K1's rounding, 2e-3 (measured <= 6.2e-4); end to end, with each side's relaxed positions, 3e-3
-# as for the tip scalars of the trilinear gradient workload.
-TIP_ORACLE_GRID, TIP_OWN_GRID, TIP_E2E = 5e-4, 2e-3, 3e-3
+# K1's rounding, and end to end (each side's relaxed positions, the GPU's Newton-polished to the
+# equilibrium the adjoint differentiates) the gradient bar of 1e-3 (measured <= 6.2e-4 on the
+# GPU's grid).
+TIP_ORACLE_GRID, TIP_OWN_GRID, TIP_E2E = 5e-4, 1e-3, 1e-3
 
 
 @pytest.mark.parametrize("probe", [{}, dict(Qzz=-0.1), dict(coul_rc=3.0, min_image=1, Qzz=-0.1)])
