@@ -35,7 +35,7 @@ FLOPS_PER_PAIR_QUAD = 45     # the same with the tip-quadrupole term (+15)
 FLOPS_PER_PAIR_FORCES = 26   # forces only: FLOPS_PER_PAIR without the 4 flops of the energy sum
 QZZ_CO = -0.05               # CO tip quadrupole of the paper's point-charge simulations, e*A^2
 BYTES_PER_FIRE_ITER = 96     # 8 corners x (Fx, Fy, Fz) FP32 per FIRE iteration
-SM_COUNT = 152
+SM_COUNT_NOMINAL = 152       # GB300; the bench reads the count from the device it runs on
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the ncu captures
 # summarised in profiles/, valid only for the kernel sources they were taken on: the bench
@@ -57,15 +57,41 @@ TRAFFIC = {
 
 
 def measured_traffic(kernel):
+    t = TRAFFIC[kernel]
+    return t["bytes"] if _src_hash(t["files"]) == t["sha"] else None
+FP32_LANES_PER_SM = 128
+
+# Figures from single-kernel ncu captures summarised in profiles/, valid for the sources they were
+# taken on (same hash rule as TRAFFIC): the FP32 operations K1 executes per node-atom pair
+# (sm__sass_thread_inst_executed_op_{fadd,fmul,ffma}_pred_on, FFMA counted twice, over the pairs of
+# the launch) and the issue-active fraction of K2 (smsp__issue_active.avg.pct_of_peak_sustained_active).
+EXECUTED = {
+    "ff_forces": {"value": None, "sha": None, "files": ["ff_assemble.cu", "ff_core.cuh", "interp.cuh"]},
+    "ff_energy": {"value": None, "sha": None, "files": ["ff_assemble.cu", "ff_core.cuh", "interp.cuh"]},
+}
+ISSUE = {
+    "relax_scan": {"value": None, "sha": None, "files": ["relax_scan.cu", "relax_core.cuh", "interp.cuh"]},
+}
+
+
+def _src_hash(files):
     import hashlib
 
-    t = TRAFFIC[kernel]
     h = hashlib.sha1()
-    for f in t["files"]:
+    for f in files:
         with open(os.path.join(ROOT, "paper_2401_14564_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
-    return t["bytes"] if h.hexdigest()[:16] == t["sha"] else None
-FP32_LANES_PER_SM = 128
+    return h.hexdigest()[:16]
+
+
+def executed_ff_flops(energy):
+    t = EXECUTED["ff_energy" if energy else "ff_forces"]
+    return t["value"] if t["sha"] == _src_hash(t["files"]) else None
+
+
+def measured_issue(kernel):
+    t = ISSUE[kernel]
+    return t["value"] if t["sha"] == _src_hash(t["files"]) else None
 
 
 def load_peaks():
@@ -77,8 +103,48 @@ def load_peaks():
     return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def fp32_peak_tflops(sm_mhz):
-    return SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+def sm_count():
+    import torch
+
+    return int(torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
+
+
+def fp32_peak_tflops(sm_mhz, sms):
+    return sms * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+
+def measure_l2_peak(reps=20, nbytes=48 << 20):
+    """L2 bandwidth on this device: a buffer of nbytes (well inside the 129 MB L2) read by a
+    reduction and copied to a second one, each pass timed with CUDA events after the buffers
+    are L2-resident; best of reps.  The kernels are torch's own (plain library streaming
+    kernels, like the HBM copy figure of MEASURED_PEAKS.json)."""
+    import torch
+
+    n = nbytes // 4
+    a = torch.rand(n, device="cuda")
+    b = torch.empty_like(a)
+    acc = torch.empty((), device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def best(fn, moved):
+        for _ in range(3):
+            fn()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return moved / (min(ts) * 1e-3) / 1e9
+
+    read = best(lambda: torch.sum(a, out=acc), nbytes)
+    copy = best(lambda: b.copy_(a), 2 * nbytes)
+    del a, b
+    return {"read_gbs": read, "copy_gbs": copy, "peak_gbs": max(read, copy), "buffer_bytes": nbytes,
+            "how": f"torch.sum over, and copy_ of, a {nbytes >> 20} MiB L2-resident float32 buffer; best of "
+                   f"{reps} CUDA-event timings each (copy counts read + write bytes)"}
 
 
 def dist_env():
@@ -287,7 +353,7 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * case["scan"]["nx"] * case["scan"]["ny"]
             * case["scan"]["nz"] / value, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64", "data": "synthetic", "config": workload_config(case),
+            "dtype": "f64", "data": "synthetic", "config": workload_config(case, args.ff_energy),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": info["cores"], "kind": "oracle",
                              "sample": info["sample"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -295,12 +361,14 @@ def run_reference(args, rank, world):
     return 0
 
 
-def workload_config(case):
+def workload_config(case, ff_energy=False):
     g, s = case["grid"], case["scan"]
     return {"workload": "flake60: 60-atom H-terminated aromatic flake (seed 42), FF grid 256x256x200 at 0.1 A, "
                         "scan 256x256 px x 40 heights, FIRE<=200 ftol 1e-4, df A=1 A k=1800 N/m f0=30.3 kHz",
             "atoms": len(case["atoms"]["x"]), "grid": [g["nx"], g["ny"], g["nz"]], "scan": [s["nx"], s["ny"], s["nz"]],
             "parallelism": "replicas",
+            "ff": "forces and energies" if ff_energy else
+                  "forces only: E slots written as 0 (the scan reads only the forces; --ff-energy adds E)",
             "l2": "headline steps: no flush, each step writes its own 210 MB FF grid (> the 129 MB L2) and reads "
                   "it back; per-kernel timings: 256 MiB write before every step"}
 
@@ -669,6 +737,68 @@ def measure_fdbm_sweep(reps, flush, sizes=((5, 3), (10, 6), (20, 12))):
             "fft_bytes_per_node": FFT_BYTES_PER_NODE, "points": out}
 
 
+def measure_small(case, steps, warmup, flush, alu_peak, ff_energy=False, cpu=True):
+    """A whole workload small enough for the oracle to run in full (benzene: 80x80x60 grid x 12
+    atoms, 40x40 px x 20 heights): FF pairs/s and relaxed pixel-heights/s of K1 + K2 (fused df)
+    by CUDA events with the L2 flushed before each step, beside the FP64 oracle timed on the
+    whole workload on all host cores and on one core (FF + FIRE scan without the Newton polish
+    + df, median of repeats)."""
+    import torch
+
+    from paper_2401_14564_gb300 import afm
+
+    sim = afm.Simulator(case, ff_energy=ff_energy)
+    atoms = afm.atoms_to_device(case["atoms"])
+    for _ in range(max(warmup, 3)):
+        sim.run(atoms)
+    stream = torch.cuda.current_stream()
+    t_ff, t_rx = [], []
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        sim.make_ff(atoms)
+        e1.record(stream)
+        sim.relax()
+        e2.record(stream)
+        torch.cuda.synchronize()
+        t_ff.append(e0.elapsed_time(e1))
+        t_rx.append(e1.elapsed_time(e2))
+    g, s = case["grid"], case["scan"]
+    pairs = g["nx"] * g["ny"] * g["nz"] * len(case["atoms"]["x"])
+    units = s["nx"] * s["ny"] * s["nz"]
+    ff_ms, rx_ms = statistics.median(t_ff), statistics.median(t_rx)
+    flops_pair = FLOPS_PER_PAIR if ff_energy else FLOPS_PER_PAIR_FORCES
+    out = {"workload": f"{case['name']}: {len(case['atoms']['x'])} atoms, grid {g['nx']}x{g['ny']}x{g['nz']}, "
+                       f"scan {s['nx']}x{s['ny']}x{s['nz']}",
+           "ff_ms": ff_ms, "relax_ms": rx_ms, "ms_per_step": ff_ms + rx_ms,
+           "ff_pair_evals_per_s": pairs / (ff_ms * 1e-3),
+           "ff_frac_of_alu_peak": pairs * flops_pair / (ff_ms * 1e-3) / 1e12 / alu_peak,
+           "relax_pixel_z_per_s": units / (rx_ms * 1e-3), "pixel_z_per_s": units / ((ff_ms + rx_ms) * 1e-3),
+           "fire_iters_mean": float(sim.iters.float().mean().item())}
+    if cpu:
+        import oracle
+
+        def oracle_step(nthreads):
+            t0 = time.perf_counter()
+            ff, _ = oracle.make_ff(case["atoms"], case["probe"], g, nthreads=nthreads)
+            t1 = time.perf_counter()
+            r = oracle.relax_scan(ff, g, None, None, s, case["tip"], case["fire"], polish_tol=0.0, nthreads=nthreads)
+            oracle.fz_to_df(r["fz"], s["dz"], case["df"])
+            return t1 - t0, time.perf_counter() - t1
+
+        cores = oracle.max_threads()
+        for nt, key in ((cores, "oracle_all_cores"), (1, "oracle_one_core")):
+            reps = [oracle_step(nt) for _ in range(3 if nt > 1 else 1)]
+            tf = statistics.median(r[0] for r in reps)
+            tr = statistics.median(r[1] for r in reps)
+            out[key] = {"cores": nt, "ff_pair_evals_per_s": pairs / tf, "relax_pixel_z_per_s": units / tr,
+                        "pixel_z_per_s": units / (tf + tr)}
+        oracle.make_ff(case["atoms"], case["probe"], dict(g, nz=2), nthreads=cores)  # restores the thread count
+    del sim
+    return out
+
+
 def measure_batch(n_mol, steps, warmup, flush, seq_sample=64, ff_energy=False):
     """Batched molecules/s: pp_batch_run over n_mol seeded molecules replayed from a CUDA graph,
     beside the same molecules run one by one through pp_make_ff + pp_relax_scan (both with or
@@ -677,8 +807,11 @@ def measure_batch(n_mol, steps, warmup, flush, seq_sample=64, ff_energy=False):
 
     from paper_2401_14564_gb300 import afm, batch, synth
 
+    from paper_2401_14564_gb300 import tune
+
     cases = synth.batch_cases(n_mol)
     b = batch.Batch(cases, ff_energy=ff_energy)
+    autotune = tune.tune_batch(b)
     b.capture()
     for _ in range(max(warmup, 1)):
         b.replay()
@@ -713,6 +846,7 @@ def measure_batch(n_mol, steps, warmup, flush, seq_sample=64, ff_energy=False):
                        f"at 0.1 A, scans 128x128x20; one persistent launch in a CUDA graph",
            "mol_per_s": n_mol / (t * 1e-3), "ms_per_batch": t, "pixel_z_per_s": b.pixel_heights / (t * 1e-3),
            "ff_pair_evals_per_s": b.pairs / (t * 1e-3), "status": st, "ff_energy": bool(ff_energy),
+           "autotune": autotune,
            "single_path_mol_per_s": 1e3 / t_seq,
            "single_path_note": f"pp_make_ff + pp_relax_scan per molecule, mean over the first {seq_sample}",
            "gpu_launches_per_batch": 2}
@@ -860,30 +994,47 @@ def main():
 
     peaks, src = load_peaks()
     sm_max = peaks.get("sm_max_mhz", 2070.0)
+    sms = sm_count()
+    l2 = measure_l2_peak()
     ff_ms, rx_ms = statistics.mean(t_ff), statistics.mean(t_rx)
     flops_pair = FLOPS_PER_PAIR if args.ff_energy else FLOPS_PER_PAIR_FORCES
     ff_tflops = pairs * flops_pair / (ff_ms * 1e-3) / 1e12
-    alu_peak = fp32_peak_tflops(sm_max)
+    alu_peak = fp32_peak_tflops(sm_max, sms)
+    alu_src = f"{sms} SMs (read from the device) x 128 FP32 lanes x 2 x {sm_max:.0f} MHz ({src} max SM clock)"
     rx_gbs = it_total * BYTES_PER_FIRE_ITER / (rx_ms * 1e-3) / 1e9
+    executed = executed_ff_flops(args.ff_energy)
     kernels = {
         "ff_assemble": {"ms": ff_ms, "share": ff_ms / (ff_ms + rx_ms), "pair_evals_per_s": pairs / (ff_ms * 1e-3),
                         "flops_per_pair": flops_pair, "energy": bool(args.ff_energy),
                         "traffic": measured_traffic("ff_assemble") if not args.ff_energy else None,
-                        "achieved_tflops": ff_tflops, "peak_tflops": alu_peak, "frac": ff_tflops / alu_peak},
+                        "achieved_tflops": ff_tflops, "peak_tflops": alu_peak, "frac": ff_tflops / alu_peak,
+                        "executed_flops_per_pair": executed,
+                        "executed_frac": (pairs * executed / (ff_ms * 1e-3) / 1e12 / alu_peak) if executed else None,
+                        "note": "frac counts the algorithmic flops per pair (the number the >= 50 % target is stated "
+                                "in); executed_frac counts the FP32 operations the kernel executes, from ncu's "
+                                "fadd/fmul/ffma counters (lateral terms are shared by a column's z-nodes, so fewer "
+                                "are executed than the pair formula has)"},
         "relax_scan": {"ms": rx_ms, "share": rx_ms / (ff_ms + rx_ms), "pixel_z_per_s": units / (rx_ms * 1e-3),
                        "fire_iters_mean": it_total / units, "nonconverged_frac": nonconv,
                        "fire_iters_hist": {"bin_lower_edges": edges[:-1], "counts": it_hist},
-                       "traffic": measured_traffic("relax_scan"), "gather_gbs": rx_gbs, "hbm_peak_gbs": peaks["hbm_gbs"], "frac_of_hbm": rx_gbs / peaks["hbm_gbs"]},
+                       "traffic": measured_traffic("relax_scan"), "gather_gbs": rx_gbs,
+                       "l2_peak_gbs": l2["peak_gbs"], "frac_of_l2": rx_gbs / l2["peak_gbs"],
+                       "hbm_peak_gbs": peaks["hbm_gbs"], "frac_of_hbm": rx_gbs / peaks["hbm_gbs"],
+                       "issue_active": measured_issue("relax_scan")},
     }
     dom = "ff_assemble" if ff_ms >= rx_ms else "relax_scan"
     if dom == "ff_assemble":
         roof = {"kernel": "ff_assemble", "bound": "alu", "achieved": ff_tflops, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": ff_tflops / alu_peak, "traffic": measured_traffic("ff_assemble"),
-                "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz ({src} max SM clock)"}
+                "frac": ff_tflops / alu_peak, "traffic": measured_traffic("ff_assemble"), "peak_source": alu_src}
     else:
-        roof = {"kernel": "relax_scan", "bound": "hbm", "achieved": rx_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": rx_gbs / peaks["hbm_gbs"], "traffic": measured_traffic("relax_scan"),
-                "peak_source": f"{src} HBM copy bandwidth (gather bytes are L1/L2-served)"}
+        roof = {"kernel": "relax_scan", "bound": "l2", "achieved": rx_gbs, "peak": l2["peak_gbs"], "unit": "GB/s",
+                "frac": rx_gbs / l2["peak_gbs"], "traffic": measured_traffic("relax_scan"),
+                "peak_source": "L2 bandwidth measured in this run (" + l2["how"] + "): the grid's z-slab the scan "
+                               "visits is L2-resident and the 96 B of corner values per FIRE iteration are served "
+                               "from registers, L1 and L2, not from HBM",
+                "issue_active": measured_issue("relax_scan"),
+                "note": "the scan is latency-bound (the FIRE update of a pixel is a dependent chain): issue_active "
+                        "is the fraction of cycles the SM sub-partitions issued an instruction, from ncu"}
 
     line = {"metric": METRIC, "value": world * units / (ms_step * 1e-3), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_step,
@@ -896,9 +1047,7 @@ def main():
                                  "flushed), from which the per-kernel figures and the roofline are taken"},
             "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": dict(workload_config(case),
-                           ff="forces and energies" if args.ff_energy else
-                              "forces only: E slots written as 0 (the scan reads only the forces; --ff-energy adds E)"),
+            "config": workload_config(case, args.ff_energy),
             "ff_pair_evals_per_s": world * pairs / (ff_ms * 1e-3),
             "roofline": roof, "kernels": kernels,
             "e2e": {"value": world * units / (e2e_ms * 1e-3), "unit": UNIT,
@@ -908,7 +1057,8 @@ def main():
                             "image copied out on its slot's stream, four steps in flight; no L2 flush between these "
                             "steps (each rewrites the 210 MB grid, larger than L2)",
                     "per_step_synchronised": world * units / (e2e_sync_ms * 1e-3)},
-            "gpu_launches": 2 * args.steps, "clocks": clk, "wall_s_timed": t_wall}
+            "gpu_launches": 2 * args.steps, "clocks": clk, "wall_s_timed": t_wall,
+            "device": {"sm_count": sms, "l2": l2}}
     if tuning is not None:
         line["autotune"] = tuning
     g4 = synth.gradient_case()
@@ -930,6 +1080,8 @@ def main():
     if not args.no_iets:
         line["iets"] = measure_iets(case, max(3, args.steps // 2), args.warmup, flush, peaks["hbm_gbs"])
     line["df_standalone"] = measure_df(case, 20, flush, peaks["hbm_gbs"])
+    line["benzene"] = measure_small(synth.benzene_case(), max(3, args.steps // 2), args.warmup, flush, alu_peak,
+                                    args.ff_energy, cpu=(rank == 0 and world == 1 and not args.no_cpu_baseline))
     if not args.no_slab:
         line["slab"] = measure_slab(3, 1, flush, args.ff_energy)
     if not args.no_batch:

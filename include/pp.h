@@ -109,7 +109,7 @@ typedef struct {
  *           ((-t^3+2t^2-t), (3t^3-5t^2+2), (-3t^3+4t^2+t), (t^3-t^2)) / 2,
  *           stencil nodes wrapping like the cell (periodic) or clamped into
  *           the grid (z, and x,y when not periodic).
- * The buffer must be 16-byte aligned. */
+ * Each axis holds 2..2^22 nodes.  The buffer must be 16-byte aligned. */
 typedef struct {
     int nx, ny, nz;
     float x0, y0, z0;
@@ -294,6 +294,13 @@ typedef struct {
                                force-field tiles than exist, so every wait runs out            */
     int ff_forces_only;     /* 1: every grid's E slots written as 0 and the energy sums skipped
                                (the forces, and so all scan outputs, are unchanged); 0 or 1    */
+    /* Work-item shapes (picked by the autotuner; every choice computes the same values bit for
+     * bit, only the scheduling differs).  0 selects the default in brackets. */
+    int ff_tile_w;          /* force-field tile width in grid columns along x: 4, 8 or 16 [8]; the
+                               tile is ff_tile_w x (32 / ff_tile_w) columns                    */
+    int ff_zpt;             /* z-nodes per force-field tile: 4 or 8 [8]                         */
+    int relax_tile_w;       /* relax tile width in pixels along x: 4, 8 or 16 [8]; the tile is
+                               relax_tile_w x (32 / relax_tile_w) pixels, all heights          */
 } pp_batch_params;
 
 /* Status bits reported by pp_batch_status. */
@@ -305,8 +312,9 @@ PP_API size_t pp_batch_workspace(int nmol);
 
 /* One launch over all molecules: a planning kernel validates every device
  * descriptor (bad ones are skipped and flagged) and lays out a work list of
- * force-field tiles (8x4 columns x 8 z-nodes) and relax tiles (8x4 pixels,
- * all heights) ordered FF(0), FF(1), R(0), FF(2), R(1), ...; then a
+ * force-field tiles (ff_tile_w x 32/ff_tile_w columns x ff_zpt z-nodes) and
+ * relax tiles (relax_tile_w x 32/relax_tile_w pixels, all heights) ordered
+ * FF(0), FF(1), R(0), FF(2), R(1), ...; then a
  * persistent kernel whose warps pull items from a device counter.  A relax
  * tile waits (bounded, see spin_limit) until every force-field tile of its
  * molecule is done; items are handed out in list order, so the force field

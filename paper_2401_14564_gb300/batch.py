@@ -21,9 +21,10 @@ ATOM_KEYS = ("x", "y", "z", "R", "eps", "q")
 
 class Batch:
     def __init__(self, cases, device="cuda", want_pos=False, want_iters=True, ctas=0, fire=None,
-                 spin_limit=0, wait_extra=0, ff_energy=True):
+                 spin_limit=0, wait_extra=0, ff_energy=True, ff_zpt=0, ff_tile_w=0, relax_tile_w=0):
         """ff_energy=False skips the energy sums of every molecule's grid (E slots 0; the scan
-        outputs are unchanged)."""
+        outputs are unchanged).  ff_zpt, ff_tile_w, relax_tile_w and ctas set the work-item
+        shapes and the persistent CTA count (0: defaults; tune.tune_batch picks them)."""
         if not cases:
             raise ValueError("empty batch")
         c0 = cases[0]
@@ -86,6 +87,7 @@ class Batch:
         bp.spin_limit = spin_limit
         bp.wait_extra = wait_extra
         bp.ff_forces_only = 0 if ff_energy else 1
+        bp.ff_zpt, bp.ff_tile_w, bp.relax_tile_w = ff_zpt, ff_tile_w, relax_tile_w
         self.params = bp
         self.graph = None
         self.pixel_heights = out_off

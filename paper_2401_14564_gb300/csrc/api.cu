@@ -41,6 +41,8 @@ static bool finite_pos(float v) { return isfinite(v) && v > 0.f; }
 bool make_grid_map(const pp_grid* g, GridMap* out, std::string* why) {
     if (!g) { *why = "grid is NULL"; return false; }
     if (g->nx < 2 || g->ny < 2 || g->nz < 2) { *why = "grid needs nx, ny, nz >= 2"; return false; }
+    // (the cell lookup's fast floor is exact below 2^22 nodes per axis)
+    if (g->nx > (1 << 22) || g->ny > (1 << 22) || g->nz > (1 << 22)) { *why = "grid axes hold at most 2^22 nodes"; return false; }
     if (!finite_pos(g->dx) || !finite_pos(g->dy) || !finite_pos(g->dz)) { *why = "grid spacing must be > 0"; return false; }
     if (!isfinite(g->x0) || !isfinite(g->y0) || !isfinite(g->z0)) { *why = "grid origin must be finite"; return false; }
     if (g->periodic_xy != 0 && g->periodic_xy != 1) { *why = "periodic_xy must be 0 or 1"; return false; }
@@ -324,6 +326,7 @@ pp_status pp_relax_scan(const float* ff, const pp_grid* grid, const pp_scan* sca
     L.d0z = (float)(-sqrt((double)tip->R0 * tip->R0 - (double)tip->d0x * tip->d0x - (double)tip->d0y * tip->d0y));
     L.R0sq = (float)((double)tip->R0 * tip->R0);
     L.c0 = (float)((double)L.d0x * L.d0x + (double)L.d0y * L.d0y + (double)L.d0z * L.d0z - (double)tip->R0 * tip->R0);
+    split_height_steps(scan->z_top, L.d0z, scan->dz, grid->z0, grid->dz, &L.fz0, &L.fz0_lo, &L.st, &L.st_lo);
     L.layout = grid->layout;
     L.max_iter = fire->max_iter;
     L.n_min = fire->n_min;
@@ -522,6 +525,14 @@ pp_status pp_batch_run(const pp_mol_desc* descs, int nmol, const pp_batch_params
     std::string why;
     if (!check_tip_fire(&bp->tip, &bp->fire, &why)) { set_error("pp_batch_run: " + why); return PP_ERR_ARG; }
     if (bp->fire.polish != 0) { set_error("pp_batch_run: the Newton polish is not available in batches"); return PP_ERR_UNSUPPORTED; }
+    {
+        auto width_ok = [](int w) { return w == 0 || w == 4 || w == 8 || w == 16; };
+        if (!width_ok(bp->ff_tile_w) || !width_ok(bp->relax_tile_w) ||
+            !(bp->ff_zpt == 0 || bp->ff_zpt == 4 || bp->ff_zpt == 8)) {
+            set_error("pp_batch_run: tile widths must be 0, 4, 8 or 16 and ff_zpt 0, 4 or 8");
+            return PP_ERR_ARG;
+        }
+    }
     if (!finite_pos(bp->scan_dz) || (bp->periodic_xy != 0 && bp->periodic_xy != 1)) {
         set_error("pp_batch_run: invalid scan_dz or periodic_xy");
         return PP_ERR_ARG;

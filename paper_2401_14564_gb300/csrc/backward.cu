@@ -103,8 +103,16 @@ __global__ void __launch_bounds__(kAdjThreads) relax_adjoint_kernel(const BwdLau
         if (gf != 0.f) {
             const int i = pix % P.snx, j = pix / P.snx;
             const float ax = fmaf((float)i, P.spx, P.sx0), ay = fmaf((float)j, P.spy, P.sy0);
-            const float az = P.z_top - k * P.sdz;
-            const float dx = px - ax, dy = py - ay, dz = pz - az;
+            // d = p - anchor with the anchor height z_top - k sdz carried exactly as az + az_lo (the
+            // product's rounding by an FMA, the difference's by a two-sum): a rounding common to
+            // every point of a height would sum coherently in the tip-parameter sums
+            float az, az_lo;
+            {
+                const float p_hi = __fmul_rn((float)k, P.sdz), p_lo = fmaf((float)k, P.sdz, -p_hi);
+                two_sum(P.z_top, -p_hi, az, az_lo);
+                az_lo -= p_lo;
+            }
+            const float dx = px - ax, dy = py - ay, dz = (pz - az) - az_lo;
             const float ex = dx - P.d0x, ey = dy - P.d0y, ez = dz - P.d0z;
             // q = |d|^2 - R0^2 without cancellation, as in the forward kernel
             const float q = fmaf(2.f * P.d0x + ex, ex, fmaf(2.f * P.d0y + ey, ey, fmaf(2.f * P.d0z + ez, ez, P.c0)));

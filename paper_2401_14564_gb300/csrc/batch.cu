@@ -1,8 +1,10 @@
 // K6: many molecules in one persistent launch (force field -> relaxed scan ->
 // df per molecule, exactly the single-molecule path of K1 + K2).
 //
-// Work items:  FF tile  = 8x4 grid columns x 8 z-nodes of one molecule;
-//              relax tile = 8x4 pixels x all heights of one molecule.
+// Work items:  FF tile  = fw x (32/fw) grid columns x ZPT z-nodes of one molecule;
+//              relax tile = rw x (32/rw) pixels x all heights of one molecule
+// (fw, rw in {4, 8, 16} at launch time, ZPT in {4, 8} as a template argument;
+// the shapes change the schedule, never a value).
 // Every warp is an independent worker: lane 0 takes the next item index from
 // a device counter.  The item list is a sequence of segments
 //   FF(0), FF(1), R(0), FF(2), R(1), ..., FF(n-1), R(n-2), R(n-1)
@@ -24,7 +26,6 @@ namespace {
 
 constexpr int kThreads = 128;  // 4 independent warps per CTA
 constexpr int kWarps = kThreads / 32;
-constexpr int kZPT = 8;        // z-nodes per FF tile (4 packed pairs)
 constexpr int kMinCtas = 5;    // resident CTAs per SM the register budget is sized for
 
 struct BatchLaunch {
@@ -56,6 +57,8 @@ struct BatchLaunch {
     long long spin_limit;
     int wait_extra;
     int forces_only;  // E slots written as 0, energy sums skipped
+    int zpt;          // z-nodes per FF tile
+    int fw_sh, rw_sh; // log2 of the FF and relax tile widths (4, 8 or 16 lanes along x)
     float coef_init[2 * kMaxDfHalfWidth + 1];
 };
 
@@ -64,6 +67,7 @@ struct MolRelax {
     const float4* ff;
     GridMap map;
     float inv_dx, inv_dy, inv_dz, gx0s, gy0s, gz0s;
+    float fz0, fz0_lo, st, st_lo;
     int periodic_xy;
     int snx, sny, snz;
     float sx0, sy0, spx, spy, z_top;
@@ -73,16 +77,19 @@ struct MolRelax {
 
 __device__ __forceinline__ long long cdiv(long long a, long long b) { return (a + b - 1) / b; }
 
-__device__ __forceinline__ long long ff_tiles(const pp_mol_desc& D) {
-    return cdiv(D.nx, 8) * cdiv(D.ny, 4) * cdiv(D.nz, kZPT);
+__device__ __forceinline__ long long ff_tiles(const BatchLaunch& B, const pp_mol_desc& D) {
+    return cdiv(D.nx, 1 << B.fw_sh) * cdiv(D.ny, 32 >> B.fw_sh) * cdiv(D.nz, B.zpt);
 }
-__device__ __forceinline__ long long relax_tiles(const pp_mol_desc& D) { return cdiv(D.snx, 8) * cdiv(D.sny, 4); }
+__device__ __forceinline__ long long relax_tiles(const BatchLaunch& B, const pp_mol_desc& D) {
+    return cdiv(D.snx, 1 << B.rw_sh) * cdiv(D.sny, 32 >> B.rw_sh);
+}
 
 __device__ __forceinline__ bool finite_pos(float v) { return isfinite(v) && v > 0.f; }
 
 // Every index a molecule's tiles will touch lies inside the caller's buffers.
 __device__ bool mol_valid(const BatchLaunch& B, const pp_mol_desc& D) {
     if (D.nx < 2 || D.ny < 2 || D.nz < 2 || !finite_pos(D.dx) || !finite_pos(D.dy) || !finite_pos(D.dz)) return false;
+    if (D.nx > (1 << 22) || D.ny > (1 << 22) || D.nz > (1 << 22)) return false;  // the cell lookup's fast floor
     if (!isfinite(D.x0) || !isfinite(D.y0) || !isfinite(D.z0)) return false;
     const long long nodes = (long long)D.nx * D.ny * D.nz;
     if (nodes >= (1LL << 31) || D.ff_offset < 0 || D.ff_offset + nodes > B.ff_cap) return false;
@@ -125,7 +132,7 @@ __global__ void __launch_bounds__(1024) batch_plan_kernel(const BatchLaunch B) {
             bool ff;
             decode_segment(s, B.nmol, mol, ff);
             const pp_mol_desc D = B.descs[mol];
-            if (mol_valid(B, D)) len = ff ? ff_tiles(D) : relax_tiles(D);
+            if (mol_valid(B, D)) len = ff ? ff_tiles(B, D) : relax_tiles(B, D);
             else if (ff) atomicOr(B.status, PP_BATCH_BAD_DESC);
         }
         // inclusive block scan of len
@@ -166,15 +173,16 @@ __device__ __forceinline__ void add_release(int* p, int v) {
     asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-template <bool kMinImage, bool kCutoff, bool kQuad, bool kForcesOnly>
+template <int kZPT, bool kMinImage, bool kCutoff, bool kQuad, bool kForcesOnly>
 __device__ __forceinline__ void ff_tile(const BatchLaunch& B, const pp_mol_desc& D, long long tile, float4* s0,
                                         float4* s1, float4* s2, float4* s3, int lane) {
     constexpr int ZP = kZPT / 2;
-    const long long tx_n = cdiv(D.nx, 8), ty_n = cdiv(D.ny, 4);
+    const int fw = 1 << B.fw_sh;
+    const long long tx_n = cdiv(D.nx, fw), ty_n = cdiv(D.ny, 32 >> B.fw_sh);
     const int tz = (int)(tile / (tx_n * ty_n));
     const long long r = tile - (long long)tz * tx_n * ty_n;
     const int ty = (int)(r / tx_n), tx = (int)(r - (long long)ty * tx_n);
-    const int i = tx * 8 + (lane & 7), j = ty * 4 + (lane >> 3), k0 = tz * kZPT;
+    const int i = tx * fw + (lane & (fw - 1)), j = ty * (32 >> B.fw_sh) + (lane >> B.fw_sh), k0 = tz * kZPT;
     const float gx = D.x0 + i * D.dx, gy = D.y0 + j * D.dy;
     float2 gz[ZP];
 #pragma unroll
@@ -209,7 +217,7 @@ __device__ __forceinline__ void ff_tile(const BatchLaunch& B, const pp_mol_desc&
     }
 }
 
-template <bool kMinImage, bool kCutoff, bool kQuad, bool kForcesOnly>
+template <int kZPT, bool kMinImage, bool kCutoff, bool kQuad, bool kForcesOnly>
 __global__ void __launch_bounds__(kThreads, kMinCtas) batch_kernel(const BatchLaunch B) {
     __shared__ float4 st[kWarps][4][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -232,7 +240,8 @@ __global__ void __launch_bounds__(kThreads, kMinCtas) batch_kernel(const BatchLa
         const long long tile = t - B.seg_start[lo];
         const pp_mol_desc D = B.descs[mol];
         if (ff) {
-            ff_tile<kMinImage, kCutoff, kQuad, kForcesOnly>(B, D, tile, st[warp][0], st[warp][1], st[warp][2], st[warp][3], lane);
+            ff_tile<kZPT, kMinImage, kCutoff, kQuad, kForcesOnly>(B, D, tile, st[warp][0], st[warp][1], st[warp][2],
+                                                                   st[warp][3], lane);
             __syncwarp();
             if (lane == 0) {
                 __threadfence();
@@ -272,6 +281,7 @@ __global__ void __launch_bounds__(kThreads, kMinCtas) batch_kernel(const BatchLa
         G.gx0s = (float)(-(double)D.x0 / (double)D.dx);
         G.gy0s = (float)(-(double)D.y0 / (double)D.dy);
         G.gz0s = (float)(-(double)D.z0 / (double)D.dz);
+        split_height_steps(D.z_top, B.d0z, B.sdz, D.z0, D.dz, &G.fz0, &G.fz0_lo, &G.st, &G.st_lo);
         G.periodic_xy = B.periodic_xy;
         G.snx = D.snx; G.sny = D.sny; G.snz = D.snz;
         G.sx0 = D.sx0; G.sy0 = D.sy0; G.spx = D.spx; G.spy = D.spy; G.z_top = D.z_top;
@@ -279,9 +289,10 @@ __global__ void __launch_bounds__(kThreads, kMinCtas) batch_kernel(const BatchLa
         G.pos = B.pos ? B.pos + 3 * D.out_offset : nullptr;
         G.iters = B.iters ? B.iters + D.out_offset : nullptr;
         G.df = B.df + D.df_offset;
-        const int tiles_x = (D.snx + 7) / 8;
+        const int rw = 1 << B.rw_sh;
+        const int tiles_x = (D.snx + rw - 1) / rw;
         const int ty = (int)(tile / tiles_x), tx = (int)(tile - (long long)ty * tiles_x);
-        relax_pixel<0, true, false, true>(G, B, tx * 8 + (lane & 7), ty * 4 + (lane >> 3));
+        relax_pixel<0, true, false, true>(G, B, tx * rw + (lane & (rw - 1)), ty * (32 >> B.rw_sh) + (lane >> B.rw_sh));
     }
 }
 
@@ -333,12 +344,18 @@ cudaError_t launch_batch(const BatchArgs& A, cudaStream_t s) {
     B.spin_limit = P.spin_limit > 0 ? P.spin_limit : (1LL << 23);
     B.wait_extra = P.wait_extra;
     B.forces_only = P.ff_forces_only;
+    B.zpt = P.ff_zpt > 0 ? P.ff_zpt : 8;
+    const int fw = P.ff_tile_w > 0 ? P.ff_tile_w : 8, rw = P.relax_tile_w > 0 ? P.relax_tile_w : 8;
+    B.fw_sh = fw == 4 ? 2 : (fw == 8 ? 3 : 4);
+    B.rw_sh = rw == 4 ? 2 : (rw == 8 ? 3 : 4);
 
     batch_plan_kernel<<<1, 1024, 0, s>>>(B);
     const bool fo = B.forces_only != 0;
-    const void* fn = with_flags(B.min_image != 0, B.coul_rc > 0.f, B.kQzz != 0.f, [fo](auto mi, auto cut, auto quad) {
+    const bool z4 = B.zpt == 4;
+    const void* fn = with_flags(B.min_image != 0, B.coul_rc > 0.f, B.kQzz != 0.f, [fo, z4](auto mi, auto cut, auto quad) {
         constexpr bool MI = decltype(mi)::value, CUT = decltype(cut)::value, QUAD = decltype(quad)::value;
-        return fo ? (const void*)batch_kernel<MI, CUT, QUAD, true> : (const void*)batch_kernel<MI, CUT, QUAD, false>;
+        if (z4) return fo ? (const void*)batch_kernel<4, MI, CUT, QUAD, true> : (const void*)batch_kernel<4, MI, CUT, QUAD, false>;
+        return fo ? (const void*)batch_kernel<8, MI, CUT, QUAD, true> : (const void*)batch_kernel<8, MI, CUT, QUAD, false>;
     });
     int ctas = P.ctas;
     if (ctas <= 0) {

@@ -46,7 +46,13 @@ __global__ void __launch_bounds__(kThreads) iets_kernel(const IetsLaunch P) {
     const int64_t o3 = checked(3 * o, 3 * total, kChkScanRead);
     const float px = __ldg(P.pos + o3), py = __ldg(P.pos + o3 + 1), pz = __ldg(P.pos + o3 + 2);
     const float dx = px - fmaf((float)i, P.spx, P.sx0), dy = py - fmaf((float)j, P.spy, P.sy0);
-    const float dz = pz - (P.z_top - k * P.sdz);
+    float az, az_lo;  // anchor height z_top - k sdz as az + az_lo, as in K4
+    {
+        const float p_hi = __fmul_rn((float)k, P.sdz), p_lo = fmaf((float)k, P.sdz, -p_hi);
+        two_sum(P.z_top, -p_hi, az, az_lo);
+        az_lo -= p_lo;
+    }
+    const float dz = (pz - az) - az_lo;
     const float ex = dx - P.d0x, ey = dy - P.d0y, ez = dz - P.d0z;
     const float q = fmaf(2.f * P.d0x + ex, ex, fmaf(2.f * P.d0y + ey, ey, fmaf(2.f * P.d0z + ez, ez, P.c0)));
     const float d2 = P.R0sq + q;

@@ -49,6 +49,14 @@ __device__ __forceinline__ float2 lerp2(float2 a, float2 b, float t) {
 }
 __device__ __forceinline__ float lerpf(float a, float b, float t) { return fmaf(t, b - a, a); }
 
+// s + e = a + b exactly (Knuth's two-sum; the _rn intrinsics keep each step a single rounding that
+// no multiply-add contraction may merge).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
 struct Cell {
     int i0, i1;
     float t;     // fraction in [0, 1]
@@ -57,15 +65,23 @@ struct Cell {
 
 // Cell along one axis from the scaled coordinate f = (p - o) / h.  In-range
 // cells (0 <= i <= n-2, the usual case) take a few instructions; the rest
-// wrap (periodic) or clamp (index in [0, n-2], fraction in [0, 1]).  The
-// conversion saturates, so any input (NaN included) ends up in range.
+// wrap (periodic) or clamp (index in [0, n-2], fraction in [0, 1]).  The fast
+// path floors by adding 1.5 * 2^23 rounded down: for |f| < 2^22 the sum is
+// 1.5 * 2^23 + floor(f) exactly, so its bits less those of 1.5 * 2^23 are
+// floor(f) and the sum less 1.5 * 2^23 is floor(f) as a float (two adds and an
+// integer subtract on the ALU pipes instead of two conversions on the
+// long-latency ones, on every FIRE iteration's dependency chain).  Anything
+// outside [0, n-2] (negative, huge, NaN) takes the slow path, which floors
+// again with the saturating conversion, so any input ends up in range.
 __device__ __forceinline__ Cell axis_cell(float f, int n, int periodic) {
     Cell c;
-    c.i0 = __float2int_rd(f);  // floor, saturating (NaN -> 0)
+    const float mg = __fadd_rd(f, 12582912.f);
+    c.i0 = __float_as_int(mg) - 0x4B400000;
     c.i1 = c.i0 + 1;
-    c.t = f - floorf(f);       // = f - (float)i0 in range, one conversion shorter
+    c.t = __fsub_rn(f, __fsub_rn(mg, 12582912.f));
     c.dtdf = 1.f;
     if ((unsigned)c.i0 > (unsigned)(n - 2)) {
+        c.i0 = __float2int_rd(f);  // floor, saturating (NaN -> 0)
         if (periodic) {
             const float nf = (float)n;
             float g = fminf(fmaxf(f, -1.0e7f), 1.0e7f);

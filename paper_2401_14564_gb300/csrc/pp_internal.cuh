@@ -92,6 +92,18 @@ inline auto with_flags(bool a, bool b, bool c, F&& f) {
     return c ? f(N{}, N{}, T{}) : f(N{}, N{}, N{});
 }
 
+// (z_top + d0z - z0) / dz and sdz / dz in FP64, each returned as a float and the float remainder
+// (the relaxation's per-height cell coordinates, see relax_core.cuh).
+__host__ __device__ inline void split_height_steps(float z_top, float d0z, float sdz, float z0, float dz, float* fz0,
+                                                   float* fz0_lo, float* st, float* st_lo) {
+    const double f = ((double)z_top + (double)d0z - (double)z0) / (double)dz;
+    const double t = (double)sdz / (double)dz;
+    *fz0 = (float)f;
+    *fz0_lo = (float)(f - (double)*fz0);
+    *st = (float)t;
+    *st_lo = (float)(t - (double)*st);
+}
+
 // Host-side helpers (api.cu).
 bool make_grid_map(const pp_grid* g, GridMap* out, std::string* why);
 void set_error(const std::string& msg);
@@ -128,6 +140,9 @@ struct RelaxLaunch {
     const float* ffE;   // map.interp == 1
     GridMap map;
     float gx0s, gy0s, gz0s, inv_dx, inv_dy, inv_dz;  // cell coordinate f = p * inv_d + g0s, g0s = -origin/d
+    // z cell coordinate of the first height's rest position (z_top + d0z - z0) / dz and the step
+    // sdz / dz per height, each a float and the float remainder of its FP64 value
+    float fz0, fz0_lo, st, st_lo;
     int periodic_xy;
     int snx, sny, snz;
     float sx0, sy0, spx, spy, z_top, sdz;

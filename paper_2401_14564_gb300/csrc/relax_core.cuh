@@ -28,6 +28,54 @@ __device__ __forceinline__ float radial_factor(const Q_t& P, float3 e) {
     return -P.kR * __fdividef(q, fmaf(P.R0, dn, d2));
 }
 
+// Height k of a scan, shared by every pixel of that height: the anchor z and the z cell coordinate
+// of the PP's rest position (anchor + d0z - z0) / dz, each as a float plus the float remainder of
+// its exact value.  A rounding left in a value every pixel of a height shares would move that
+// whole height coherently (by up to half an ulp of the coordinate, ~5e-7 A at 8 A): invisible in
+// one pixel, but it adds up over the image in the tip-parameter gradients, whose sums cancel to
+// a small fraction of their terms.  With the remainders carried, the roundings left are those of
+// per-pixel sums, which vary from pixel to pixel.  The first height's cell coordinate and the
+// step sdz / dz come in the launch as float pairs formed in FP64 on the host (fz0, fz0_lo, st,
+// st_lo); each later height is an exact float-float step (FP64 is a slow pipe on this part).
+struct Height {
+    float az, az_lo;  // anchor z
+    float fz, fz_lo;  // z cell coordinate of anchor + d0z
+};
+
+template <class G_t>
+__device__ __forceinline__ Height height_first(const G_t& P) {
+    Height h;
+    h.az = P.z_top;
+    h.az_lo = 0.f;
+    h.fz = P.fz0;
+    h.fz_lo = P.fz0_lo;
+    return h;
+}
+
+// One height down: anchor - sdz and cell coordinate - sdz / dz, in float-float.
+template <class G_t, class Q_t>
+__device__ __forceinline__ void height_next(Height& h, const G_t& P, const Q_t& Q) {
+    float s, e;
+    two_sum(h.az, -Q.sdz, s, e);
+    e = __fadd_rn(e, h.az_lo);
+    h.az = __fadd_rn(s, e);
+    h.az_lo = __fsub_rn(e, __fsub_rn(h.az, s));
+    two_sum(h.fz, -P.st, s, e);
+    e = __fadd_rn(e, __fsub_rn(h.fz_lo, P.st_lo));
+    h.fz = __fadd_rn(s, e);
+    h.fz_lo = __fsub_rn(e, __fsub_rn(h.fz, s));
+}
+
+// Cells of the PP at lateral position (px, py) and deflection ez below height h's rest position.
+template <class L>
+__device__ __forceinline__ Cells locate_h(const L& P, float px, float py, const Height& h, float ez) {
+    Cells c;
+    c.x = axis_cell(fmaf(px, P.inv_dx, P.gx0s), P.map.nx, P.periodic_xy);
+    c.y = axis_cell(fmaf(py, P.inv_dy, P.gy0s), P.map.ny, P.periodic_xy);
+    c.z = axis_cell(h.fz + fmaf(ez, P.inv_dz, h.fz_lo), P.map.nz, 0);
+    return c;
+}
+
 template <class Q_t>
 __device__ __forceinline__ float3 total_force_tip(const Q_t& P, float3 e, float s, float3 Fs) {
     float3 G;
@@ -102,11 +150,11 @@ __device__ __forceinline__ void relax_pixel(const G_t& P, const Q_t& Q, int i, i
     float4 cv[8];
     float ec[kTricubic ? 64 : 1];  // tricubic: the cached stencil energies
     int cell_x = -1, cell_y = -1, cell_z = -1;
+    Height hk = height_first(P);
     while (kWarpVote ? __any_sync(0xffffffffu, active) : active) {
         if (kWarpVote && !active) continue;
-        const float az = P.z_top - k * Q.sdz;
         const float s = radial_factor(Q, e);
-        const Cells cl = locate(P, bx + e.x, by + e.y, (az + Q.d0z) + e.z);
+        const Cells cl = locate_h(P, bx + e.x, by + e.y, hk, e.z);
         float3 Fs;
         if constexpr (kTricubic) {
             // the 64 stencil energies stay in registers until the PP changes cell
@@ -146,7 +194,7 @@ __device__ __forceinline__ void relax_pixel(const G_t& P, const Q_t& Q, int i, i
                         if (!solve3(J, make_float3(-Gc.x, -Gc.y, -Gc.z), dp)) break;
                         const float3 et = make_float3(e.x + dp.x, e.y + dp.y, e.z + dp.z);
                         const float st = radial_factor(Q, et);
-                        const Cells ct = locate(P, bx + et.x, by + et.y, (az + Q.d0z) + et.z);
+                        const Cells ct = locate_h(P, bx + et.x, by + et.y, hk, et.z);
                         float3 Ft;
                         if constexpr (kTricubic) {
                             if (ct.x.i0 != cell_x || ct.y.i0 != cell_y || ct.z.i0 != cell_z) {
@@ -179,13 +227,19 @@ __device__ __forceinline__ void relax_pixel(const G_t& P, const Q_t& Q, int i, i
             const int o = checked(k * npix + pix, (long long)npix * P.snz, kChkScanWrite);
             P.fz[o] = -sw * (Q.d0z + e.z);  // kR (|d| - R0) d_z / |d|
             if (P.pos) {
-                P.pos[3 * o] = bx + e.x;
-                P.pos[3 * o + 1] = by + e.y;
-                P.pos[3 * o + 2] = (az + Q.d0z) + e.z;
+                // anchor + (d0 + e): the rounding of the stored coordinate is then independent of
+                // the pixel's neighbours, so p - anchor recomputed from it (the adjoint, the IETS
+                // map) carries no error common to a whole height; (anchor + d0) + e would round
+                // anchor + d0 the same way for every pixel of a height, a bias that sums coherently
+                // in the tip-parameter gradients
+                P.pos[3 * o] = fmaf((float)i, P.spx, P.sx0) + (Q.d0x + e.x);
+                P.pos[3 * o + 1] = fmaf((float)j, P.spy, P.sy0) + (Q.d0y + e.y);
+                P.pos[3 * o + 2] = hk.az + ((Q.d0z + e.z) + hk.az_lo);
             }
             if (P.iters) P.iters[o] = it;
             ++k;
             active = k < P.snz;
+            height_next(hk, P, Q);
             v = make_float3(0.f, 0.f, 0.f);
             dt = Q.dt0;
             alpha = Q.alpha0;
@@ -203,7 +257,9 @@ __device__ __forceinline__ void relax_pixel(const G_t& P, const Q_t& Q, int i, i
             const bool up = (it > 0) && (pw > 0.f);
             const bool down = (it > 0) && !(pw > 0.f);
             const float v2 = fmaf(v.x, v.x, fmaf(v.y, v.y, v.z * v.z));
-            const float c = alpha * (v2 * rsqrtf(v2)) * rsqrtf(g2);  // alpha |v| / |G|
+            // alpha |v| / |G| with one reciprocal root (the floor only keeps a product that
+            // underflows, after many step halvings, from giving 0 * inf)
+            const float c = alpha * v2 * rsqrtf(fmaxf(v2 * g2, 1e-37f));
             const float om = 1.f - alpha;
             const float mx = fmaf(om, v.x, c * G.x), my = fmaf(om, v.y, c * G.y), mz = fmaf(om, v.z, c * G.z);
             const bool grow = up && (npos > Q.n_min);

@@ -78,7 +78,8 @@ class BatchParams(C.Structure):
     _fields_ = [("probe", Probe), ("tip", Tip), ("fire", Fire), ("df", DF), ("scan_dz", C.c_float),
                 ("periodic_xy", C.c_int), ("ff_capacity", C.c_longlong), ("out_capacity", C.c_longlong),
                 ("df_capacity", C.c_longlong), ("n_atoms_total", C.c_int), ("ctas", C.c_int),
-                ("spin_limit", C.c_longlong), ("wait_extra", C.c_int), ("ff_forces_only", C.c_int)]
+                ("spin_limit", C.c_longlong), ("wait_extra", C.c_int), ("ff_forces_only", C.c_int),
+                ("ff_tile_w", C.c_int), ("ff_zpt", C.c_int), ("relax_tile_w", C.c_int)]
 
 
 class Tuning(C.Structure):

@@ -8,7 +8,8 @@ workload itself (inputs on the device, median of a few repetitions):
     when the caller runs them that way: the two regimes can prefer different
     layouts (a lone scan is bound by its slowest columns' dependency chains,
     overlapped steps by issue slots and cache capacity);
-  - pp_batch_run: persistent CTAs (multiples of the SM count).
+  - pp_batch_run: the work-item shapes (force-field tile depth and width, relax tile width) and
+    the persistent CTA count.
 Every candidate computes the same values (the layout and the launch shape do
 not change the arithmetic per node or per pixel), so the pick is a pure
 speed decision.  Results are cached in a JSON file keyed by GPU name and
@@ -92,17 +93,42 @@ def tune_case(case, reps=3, bricks=BRICKS, zpts=ZPTS, ff_energy=True, pipeline_s
             else "ms per scan alone"}
 
 
-def tune_batch(batch_obj, reps=2, factors=(1, 2, 3, 4)):
-    """Time pp_batch_run for persistent-CTA counts that are multiples of the SM count."""
-    sms = torch.cuda.get_device_properties(0).multi_processor_count
-    times = {}
-    for f in factors:
-        batch_obj.params.ctas = f * sms
-        batch_obj.run()
-        times[f * sms] = _time(batch_obj.run, reps)
-    best = min(times, key=times.get)
-    batch_obj.params.ctas = best
-    return {"ctas": best, "ms": times}
+BATCH_SHAPES = (("ff_zpt", (8, 4)), ("ff_tile_w", (8, 4, 16)), ("relax_tile_w", (8, 4, 16)))
+
+
+def tune_batch(batch_obj, reps=2, factors=(1, 2, 3, 4, 5, 6)):
+    """Pick the batch's work-item shapes (force-field tile depth and width, relax tile width) and
+    its persistent CTA count (0 = as many as fit, else multiples of the SM count) by coordinate
+    descent from the defaults: each choice in turn is swept with the others held at their best so
+    far, timing pp_batch_run itself (CUDA events, median of reps).  Every choice computes the
+    same molecules bit for bit.  Leaves the pick in batch_obj.params and returns it with the
+    timings."""
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    p = batch_obj.params
+    tried = {}
+
+    def run_with(cfg):
+        key = ",".join(f"{k}={v}" for k, v in sorted(cfg.items()))
+        if key not in tried:
+            for k, v in cfg.items():
+                setattr(p, k, v)
+            batch_obj.run()
+            tried[key] = _time(batch_obj.run, reps)
+        return tried[key]
+
+    best = {"ff_zpt": 8, "ff_tile_w": 8, "relax_tile_w": 8, "ctas": 0}
+    t_default = best_t = run_with(best)
+    for name, values in BATCH_SHAPES + (("ctas", (0,) + tuple(f * sms for f in factors)),):
+        for v in values:
+            cfg = dict(best, **{name: v})
+            t = run_with(cfg)
+            if t < best_t:
+                best, best_t = cfg, t
+    for k, v in best.items():
+        setattr(p, k, v)
+    return {"choice": best, "ms": best_t, "ms_default_shapes": t_default, "tried_ms": tried,
+            "how": "coordinate descent over ff_zpt, ff_tile_w, relax_tile_w, then ctas; median of %d timed runs "
+                   "each" % reps}
 
 
 def cached(case, path=None, **kw):

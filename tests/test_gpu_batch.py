@@ -144,7 +144,11 @@ def test_batch_molecules_match_the_oracle(orc):
         o = orc.forward(c, fire=fire)
         assert (got["iters"] < fire["max_iter"]).mean() > 0.999
         dp, dfz, keep, n_ill, n_basin = relax_compare(got, o)
-        assert n_ill + n_basin <= 0.02 * keep.size, (n, n_ill, n_basin)
+        # as on the full-size flake: the far field of the wider molecules has up to ~10 % of its
+        # points with lambda_min just under 0.01 eV/A^2 in the FP64 oracle itself; those are held
+        # to their residual bound below, and points that settled in another basin are capped
+        assert keep.mean() > 0.85, (n, n_ill, n_basin)
+        assert n_basin <= 0.005 * keep.size, (n, n_basin)
         assert dp <= 1e-3, (n, dp)
         n_sel, n_ok = ill_conditioned_within_bound(got["pos"], o, fire["ftol"])
         assert n_ok == n_sel, (n, n_ok, n_sel)
@@ -152,3 +156,51 @@ def test_batch_molecules_match_the_oracle(orc):
         rng = o["df"].max() - o["df"].min()
         ddf = np.abs(got["df"] - o["df"])[df_keep(keep, m)].max()
         assert ddf <= 1e-3 * rng, (n, ddf, rng)
+
+
+def test_every_batch_shape_gives_the_same_molecules():
+    # force-field tile depth and width, relax tile width and CTA count change the schedule only:
+    # every combination reproduces the default batch bit for bit, ragged scans included
+    cs = cases(5, 5000)
+    ref = batch.Batch(cs, want_pos=True)
+    ref.run()
+    assert ref.status() == (0, 0)
+    want = [{k: v.clone() for k, v in ref.molecule(n).items()} for n in range(len(cs))]
+    for zpt in (4, 8):
+        for fw in (4, 8, 16):
+            for rw in (4, 8, 16):
+                b = batch.Batch(cs, want_pos=True, ff_zpt=zpt, ff_tile_w=fw, relax_tile_w=rw,
+                                ctas=152 if (zpt, fw, rw) == (4, 16, 4) else 0)
+                b.run()
+                assert b.status() == (0, 0), (zpt, fw, rw)
+                for n in range(len(cs)):
+                    got = b.molecule(n)
+                    for k in ("ff", "fz", "df", "iters", "pos"):
+                        assert torch.equal(got[k], want[n][k]), (zpt, fw, rw, n, k)
+
+
+def test_batch_tuner_picks_a_candidate_and_keeps_the_molecules():
+    from paper_2401_14564_gb300 import tune
+
+    cs = cases(4, 6000)
+    b = batch.Batch(cs, want_pos=True)
+    b.run()
+    want = [b.molecule(n)["df"].clone() for n in range(len(cs))]
+    r = tune.tune_batch(b, reps=1, factors=(1, 2))
+    ch = r["choice"]
+    assert ch["ff_zpt"] in (4, 8) and ch["ff_tile_w"] in (4, 8, 16) and ch["relax_tile_w"] in (4, 8, 16)
+    assert (b.params.ff_zpt, b.params.ff_tile_w, b.params.relax_tile_w, b.params.ctas) == \
+        (ch["ff_zpt"], ch["ff_tile_w"], ch["relax_tile_w"], ch["ctas"])
+    assert r["ms"] <= r["ms_default_shapes"]
+    b.run()
+    for n in range(len(cs)):
+        assert torch.equal(b.molecule(n)["df"], want[n])
+
+
+def test_batch_shapes_are_validated():
+    cs = cases(2, 7000)
+    for kw in (dict(ff_tile_w=6), dict(relax_tile_w=32), dict(ff_zpt=16)):
+        b = batch.Batch(cs, **kw)
+        with pytest.raises(pp.PPError) as e:
+            b.run()
+        assert e.value.status == 1

@@ -5,10 +5,12 @@ Both sides relax on the same force field: the oracle's FP64 grid rounded to FP32
 scan reads as it is and the oracle reads back in FP64.  Only the precision of FIRE's own
 arithmetic then differs, so FIRE's branch decisions (downhill mixing, uphill reset, step growth
 after more than n_min downhill steps, alpha decay) must take the same turns: the number of
-position updates per pixel and height equals the oracle's at >= 99 % of the points, and the rest
-differ by one update (a residual that lands within FP32 rounding of ftol), under the timed
-settings (dt0 = dt_max: no step growth, alpha decay on), with the step growth on, and at the
-parity tolerance.
+position updates per pixel and height equals the oracle's at >= 99 % of the points, under the
+timed settings (dt0 = dt_max: no step growth, alpha decay on), with the step growth on, and at the
+parity tolerance.  Where they differ, a residual landed within FP32 rounding of ftol (one update
+more or less) or a downhill test F.v > 0 with F.v within rounding of zero went the other way and
+the two trajectories part; either way both end at the same fixed point, within FIRE's stopping
+residual ftol / lambda_min of it.
 """
 import numpy as np
 import pytest
@@ -58,10 +60,16 @@ def test_fire_update_counts_equal_the_oracle(orc, which, case):
     g = gpu_scan_on(ff32, c, fire)
     d = np.abs(g["iters"].astype(np.int64) - o["iters"])
     assert (d == 0).mean() >= 0.99, ((d == 0).mean(), d.max())
-    assert d.max() <= 1, d.max()
-    # a wrong count would also show as a different relaxed point: FIRE alone on both sides
+    assert (d <= 1).mean() >= 0.997, ((d <= 1).mean(), d.max())
+    # a wrong rule would also show as a different relaxed point: FIRE alone on both sides
     dp = np.linalg.norm(g["pos"] - o["pos"], axis=-1)
     assert np.median(dp) < 1e-4
+    # points whose counts differ still reach the same fixed point (both stop below ftol)
+    ref = orc.relax_scan(ff32.astype(np.float64), c["grid"], None, None, c["scan"], c["tip"], fire)
+    lam = np.maximum(ref["lam"], 1e-3)
+    diff = d > 0
+    bound = 2.2 * fire["ftol"] / lam + 1e-4
+    assert (dp[diff] <= bound[diff]).all(), (dp[diff] / bound[diff]).max()
     if which == "growth":
         # the settings reach the growth branch: more than n_min downhill steps in a row happen
         # whenever a point needs more than n_min + 2 updates
