@@ -113,38 +113,38 @@ def fp32_peak_tflops(sm_mhz, sms):
     return sms * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
 
 
-def measure_l2_peak(reps=20, nbytes=48 << 20):
-    """L2 bandwidth on this device: a buffer of nbytes (well inside the 129 MB L2) read by a
-    reduction and copied to a second one, each pass timed with CUDA events after the buffers
-    are L2-resident; best of reps.  The kernels are torch's own (plain library streaming
-    kernels, like the HBM copy figure of MEASURED_PEAKS.json)."""
+def measure_l2_peak(reps=10, sizes_mib=(8, 16, 32, 48)):
+    """L2 read bandwidth of this device: pp_read_probe (16-byte loads that bypass L1, every
+    resident thread of a full-GPU grid) over buffers well inside the 129 MB L2, each read 20
+    times per launch once resident; best of reps CUDA-event timings per size, the best size
+    kept."""
     import torch
 
-    n = nbytes // 4
-    a = torch.rand(n, device="cuda")
-    b = torch.empty_like(a)
-    acc = torch.empty((), device="cuda")
-    stream = torch.cuda.current_stream()
+    from paper_2401_14564_gb300 import pp
 
-    def best(fn, moved):
+    sink = torch.zeros(1, device="cuda")
+    stream = torch.cuda.current_stream()
+    per_size = {}
+    for mib in sizes_mib:
+        buf = torch.rand(mib * (1 << 20) // 4, device="cuda")
+        passes = 20
         for _ in range(3):
-            fn()
+            pp.pp_read_probe(buf, passes, sink)
         ts = []
         for _ in range(reps):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            fn()
+            pp.pp_read_probe(buf, passes, sink)
             e1.record(stream)
             torch.cuda.synchronize()
             ts.append(e0.elapsed_time(e1))
-        return moved / (min(ts) * 1e-3) / 1e9
-
-    read = best(lambda: torch.sum(a, out=acc), nbytes)
-    copy = best(lambda: b.copy_(a), 2 * nbytes)
-    del a, b
-    return {"read_gbs": read, "copy_gbs": copy, "peak_gbs": max(read, copy), "buffer_bytes": nbytes,
-            "how": f"torch.sum over, and copy_ of, a {nbytes >> 20} MiB L2-resident float32 buffer; best of "
-                   f"{reps} CUDA-event timings each (copy counts read + write bytes)"}
+        per_size[mib] = passes * buf.numel() * 4 / (min(ts) * 1e-3) / 1e9
+        del buf
+    best = max(per_size, key=per_size.get)
+    return {"peak_gbs": per_size[best], "read_gbs_by_mib": per_size, "buffer_mib": best,
+            "how": "pp_read_probe (16-byte L1-bypassing loads from every resident thread) reading an L2-resident "
+                   f"buffer of {best} MiB 20 times per launch; best of {reps} CUDA-event timings, best of "
+                   f"{', '.join(str(m) for m in sizes_mib)} MiB"}
 
 
 def dist_env():

@@ -451,6 +451,16 @@ PP_API pp_status pp_fft_correlate(const float* f, const float* g, const pp_grid*
  * returns PP_ERR_UNSUPPORTED. */
 PP_API pp_status pp_check_flags(unsigned int* flags);
 
+/* Read-bandwidth probe (a measurement aid of the benchmark; the paper has no
+ * counterpart): reads the nfloats floats of buf `passes` times with 16-byte
+ * loads that bypass L1, from every resident thread of a full-GPU grid, and
+ * writes nothing but (never, in practice) one float to *sink.  Timing it on a
+ * buffer well inside the L2 gives the L2 read bandwidth the relaxed scan's
+ * roofline is stated against.  buf: device, 16-byte aligned, nfloats a
+ * positive multiple of 4; sink: one device float.  Errors: PP_ERR_ARG,
+ * PP_ERR_CUDA. */
+PP_API pp_status pp_read_probe(const float* buf, size_t nfloats, int passes, float* sink, pp_stream stream);
+
 /* Message of the last failed call on this host thread ("" if none). */
 PP_API const char* pp_last_error(void);
 

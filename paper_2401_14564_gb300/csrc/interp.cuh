@@ -63,6 +63,17 @@ struct Cell {
     float dtdf;  // d t / d f: 1 inside, 0 where the fraction is clamped
 };
 
+// The in-range part of axis_cell alone (the caller checks the range).
+__device__ __forceinline__ Cell axis_fast(float f) {
+    Cell c;
+    const float mg = __fadd_rd(f, 12582912.f);
+    c.i0 = __float_as_int(mg) - 0x4B400000;
+    c.i1 = c.i0 + 1;
+    c.t = __fsub_rn(f, __fsub_rn(mg, 12582912.f));
+    c.dtdf = 1.f;
+    return c;
+}
+
 // Cell along one axis from the scaled coordinate f = (p - o) / h.  In-range
 // cells (0 <= i <= n-2, the usual case) take a few instructions; the rest
 // wrap (periodic) or clamp (index in [0, n-2], fraction in [0, 1]).  The fast
@@ -74,12 +85,7 @@ struct Cell {
 // outside [0, n-2] (negative, huge, NaN) takes the slow path, which floors
 // again with the saturating conversion, so any input ends up in range.
 __device__ __forceinline__ Cell axis_cell(float f, int n, int periodic) {
-    Cell c;
-    const float mg = __fadd_rd(f, 12582912.f);
-    c.i0 = __float_as_int(mg) - 0x4B400000;
-    c.i1 = c.i0 + 1;
-    c.t = __fsub_rn(f, __fsub_rn(mg, 12582912.f));
-    c.dtdf = 1.f;
+    Cell c = axis_fast(f);
     if ((unsigned)c.i0 > (unsigned)(n - 2)) {
         c.i0 = __float2int_rd(f);  // floor, saturating (NaN -> 0)
         if (periodic) {
@@ -105,12 +111,22 @@ struct Cells {
     Cell x, y, z;
 };
 
+
+// Cells of the point (px, py, pz): the three in-range paths, then one range test for all axes
+// (a branch per axis costs more than the arithmetic on a dependency chain).
 template <class L>
 __device__ __forceinline__ Cells locate(const L& P, float px, float py, float pz) {
+    const float fx = fmaf(px, P.inv_dx, P.gx0s), fy = fmaf(py, P.inv_dy, P.gy0s), fz = fmaf(pz, P.inv_dz, P.gz0s);
     Cells c;
-    c.x = axis_cell(fmaf(px, P.inv_dx, P.gx0s), P.map.nx, P.periodic_xy);
-    c.y = axis_cell(fmaf(py, P.inv_dy, P.gy0s), P.map.ny, P.periodic_xy);
-    c.z = axis_cell(fmaf(pz, P.inv_dz, P.gz0s), P.map.nz, 0);
+    c.x = axis_fast(fx);
+    c.y = axis_fast(fy);
+    c.z = axis_fast(fz);
+    if (((unsigned)c.x.i0 > (unsigned)(P.map.nx - 2)) | ((unsigned)c.y.i0 > (unsigned)(P.map.ny - 2)) |
+        ((unsigned)c.z.i0 > (unsigned)(P.map.nz - 2))) {
+        c.x = axis_cell(fx, P.map.nx, P.periodic_xy);
+        c.y = axis_cell(fy, P.map.ny, P.periodic_xy);
+        c.z = axis_cell(fz, P.map.nz, 0);
+    }
     return c;
 }
 

@@ -67,12 +67,23 @@ __device__ __forceinline__ void height_next(Height& h, const G_t& P, const Q_t& 
 }
 
 // Cells of the PP at lateral position (px, py) and deflection ez below height h's rest position.
+// The three axes take the in-range path together and share one range test: a branch per axis
+// on every FIRE iteration's dependency chain cost more than the arithmetic (the slowest pixel
+// column alone went from 650 to 494 cycles per iteration; identical cells).
 template <class L>
 __device__ __forceinline__ Cells locate_h(const L& P, float px, float py, const Height& h, float ez) {
+    const float fx = fmaf(px, P.inv_dx, P.gx0s), fy = fmaf(py, P.inv_dy, P.gy0s);
+    const float fz = h.fz + fmaf(ez, P.inv_dz, h.fz_lo);
     Cells c;
-    c.x = axis_cell(fmaf(px, P.inv_dx, P.gx0s), P.map.nx, P.periodic_xy);
-    c.y = axis_cell(fmaf(py, P.inv_dy, P.gy0s), P.map.ny, P.periodic_xy);
-    c.z = axis_cell(h.fz + fmaf(ez, P.inv_dz, h.fz_lo), P.map.nz, 0);
+    c.x = axis_fast(fx);
+    c.y = axis_fast(fy);
+    c.z = axis_fast(fz);
+    if (((unsigned)c.x.i0 > (unsigned)(P.map.nx - 2)) | ((unsigned)c.y.i0 > (unsigned)(P.map.ny - 2)) |
+        ((unsigned)c.z.i0 > (unsigned)(P.map.nz - 2))) {
+        c.x = axis_cell(fx, P.map.nx, P.periodic_xy);
+        c.y = axis_cell(fy, P.map.ny, P.periodic_xy);
+        c.z = axis_cell(fz, P.map.nz, 0);
+    }
     return c;
 }
 

@@ -157,6 +157,8 @@ def lib():
             L.pp_fft_correlate.restype = st
             L.pp_check_flags.argtypes = [C.POINTER(C.c_uint)]
             L.pp_check_flags.restype = st
+            L.pp_read_probe.argtypes = [vp, C.c_size_t, C.c_int, vp, vp]
+            L.pp_read_probe.restype = st
             L.pp_last_error.argtypes = []
             L.pp_last_error.restype = C.c_char_p
             _lib = L
@@ -409,6 +411,11 @@ def pp_check_flags() -> int:
     flags = C.c_uint(0)
     _check(lib().pp_check_flags(C.byref(flags)))
     return flags.value
+
+
+def pp_read_probe(buf, passes, sink, stream=None):
+    """Read the float32 CUDA tensor buf `passes` times (L2 read-bandwidth probe); sink: one float."""
+    _check(lib().pp_read_probe(_dev(buf, "buf"), buf.numel(), int(passes), _dev(sink, "sink"), _stream(stream)))
 
 
 def pp_last_error() -> str:

@@ -240,3 +240,11 @@ def test_fire_polish_is_validated_on_host(L):
         assert L.pp_relax_scan(fake, C.byref(g), C.byref(scan), C.byref(tip), C.byref(fire), fake, fake, fake, None,
                                None, None) == 1
         assert b"FIRE" in L.pp_last_error()
+
+
+def test_read_probe_validated_on_host(L):
+    fake = C.c_void_p(256)
+    assert L.pp_read_probe(None, 16, 1, fake, None) == 1
+    assert L.pp_read_probe(C.c_void_p(8), 16, 1, fake, None) == 1      # not 16-byte aligned
+    assert L.pp_read_probe(fake, 10, 1, fake, None) == 1               # not a multiple of 4 floats
+    assert L.pp_read_probe(fake, 16, 0, fake, None) == 1               # no pass

@@ -121,3 +121,12 @@ def test_saved_outputs_round_trip(tmp_path):
     assert np.array_equal(z["df"], sim.df.cpu().numpy()) and np.array_equal(z["ff"], sim.ff.cpu().numpy())
     assert np.array_equal(z["pos"], sim.pos.cpu().numpy()) and np.array_equal(z["iters"], sim.iters.cpu().numpy())
     assert int(z["grid_geometry"][0]) == c["grid"]["nx"] and int(z["scan_geometry"][2]) == c["scan"]["nz"]
+
+
+def test_read_probe_runs_and_writes_nothing():
+    # the benchmark's L2 read-bandwidth probe: reads the buffer, leaves the sink alone
+    buf = torch.rand(1 << 20, device="cuda")
+    sink = torch.full((1,), 7.0, device="cuda")
+    pp.pp_read_probe(buf, 3, sink)
+    torch.cuda.synchronize()
+    assert sink.item() == 7.0
