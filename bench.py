@@ -41,11 +41,11 @@ SM_COUNT_NOMINAL = 152       # GB300; the bench reads the count from the device 
 # summarised in profiles/, valid only for the kernel sources they were taken on: the bench
 # reports them when the sources still hash the same, else traffic is null.
 TRAFFIC = {
-    "relax_scan": {"bytes": 63.44e6, "sha": "98811a7a8f79d820",
+    "relax_scan": {"bytes": 67.92e6, "sha": "cae5f9f37181365e",
                    "files": ["relax_scan.cu", "relax_core.cuh", "interp.cuh"]},
     "relax_scan_tricubic": {"bytes": 21.29e6, "sha": "98811a7a8f79d820",
                             "files": ["relax_scan.cu", "relax_core.cuh", "interp.cuh"]},
-    "ff_assemble": {"bytes": 144.63e6, "sha": "bba60445429332e1",
+    "ff_assemble": {"bytes": 148.04e6, "sha": "8bd463bd812f7566",
                     "files": ["ff_assemble.cu", "ff_core.cuh", "interp.cuh"]},
     "ff_assemble_quad": {"bytes": 144.63e6, "sha": "bba60445429332e1",
                          "files": ["ff_assemble.cu", "ff_core.cuh", "interp.cuh"]},
@@ -66,11 +66,11 @@ FP32_LANES_PER_SM = 128
 # (sm__sass_thread_inst_executed_op_{fadd,fmul,ffma}_pred_on, FFMA counted twice, over the pairs of
 # the launch) and the issue-active fraction of K2 (smsp__issue_active.avg.pct_of_peak_sustained_active).
 EXECUTED = {
-    "ff_forces": {"value": None, "sha": None, "files": ["ff_assemble.cu", "ff_core.cuh", "interp.cuh"]},
+    "ff_forces": {"value": 18.69, "sha": "8bd463bd812f7566", "files": ["ff_assemble.cu", "ff_core.cuh", "interp.cuh"]},
     "ff_energy": {"value": None, "sha": None, "files": ["ff_assemble.cu", "ff_core.cuh", "interp.cuh"]},
 }
 ISSUE = {
-    "relax_scan": {"value": None, "sha": None, "files": ["relax_scan.cu", "relax_core.cuh", "interp.cuh"]},
+    "relax_scan": {"value": 0.573, "sha": "cae5f9f37181365e", "files": ["relax_scan.cu", "relax_core.cuh", "interp.cuh"]},
 }
 
 

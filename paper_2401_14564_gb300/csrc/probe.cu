@@ -15,21 +15,37 @@ constexpr int kProbeThreads = 256;
 
 __global__ void __launch_bounds__(kProbeThreads) read_probe_kernel(const float4* __restrict__ buf, long long n4,
                                                                    int passes, float* sink) {
-    float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+    // passes x n4 loads in all, taken as one sequence that wraps around the buffer: each thread
+    // issues kInFlight independent loads before it adds any of them, so a buffer smaller than
+    // (threads x kInFlight x 16 B) still keeps enough bytes in flight to cover the L2 latency
+    constexpr int kInFlight = 8;
     const long long stride = (long long)gridDim.x * kProbeThreads;
-    for (int p = 0; p < passes; ++p) {
-        long long i = (long long)blockIdx.x * kProbeThreads + threadIdx.x;
-        for (; i + stride < n4; i += 2 * stride) {  // two independent loads in flight per thread
-            const float4 u = __ldcg(buf + i), w = __ldcg(buf + i + stride);
-            a.x += u.x; a.y += u.y; a.z += u.z; a.w += u.w;
-            b.x += w.x; b.y += w.y; b.z += w.z; b.w += w.w;
+    const long long total = (long long)passes * n4;
+    const long long step = stride % n4;
+    long long j = (long long)blockIdx.x * kProbeThreads + threadIdx.x;
+    long long i = j % n4;
+    float4 acc[2] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
+    for (; j + (kInFlight - 1) * stride < total; j += kInFlight * stride) {
+        float4 u[kInFlight];
+#pragma unroll
+        for (int q = 0; q < kInFlight; ++q) {
+            u[q] = __ldcg(buf + i);
+            i += step;
+            if (i >= n4) i -= n4;
         }
-        if (i < n4) {
-            const float4 u = __ldcg(buf + i);
-            a.x += u.x; a.y += u.y; a.z += u.z; a.w += u.w;
+#pragma unroll
+        for (int q = 0; q < kInFlight; ++q) {
+            float4& a = acc[q & 1];
+            a.x += u[q].x; a.y += u[q].y; a.z += u[q].z; a.w += u[q].w;
         }
     }
-    const float s = (a.x + a.y) + (a.z + a.w) + (b.x + b.y) + (b.z + b.w);
+    for (; j < total; j += stride) {
+        const float4 u = __ldcg(buf + i);
+        acc[0].x += u.x; acc[0].y += u.y; acc[0].z += u.z; acc[0].w += u.w;
+        i += step;
+        if (i >= n4) i -= n4;
+    }
+    const float s = (acc[0].x + acc[0].y) + (acc[0].z + acc[0].w) + (acc[1].x + acc[1].y) + (acc[1].z + acc[1].w);
     if (s == -1.2345678e-30f) *sink = s;  // keeps the sums (and so the loads) alive
 }
 
