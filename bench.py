@@ -37,21 +37,21 @@ QZZ_CO = -0.05               # CO tip quadrupole of the paper's point-charge sim
 BYTES_PER_FIRE_ITER = 96     # 8 corners x (Fx, Fy, Fz) FP32 per FIRE iteration
 SM_COUNT_NOMINAL = 152       # GB300; the bench reads the count from the device it runs on
 
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the ncu captures
-# summarised in profiles/, valid only for the kernel sources they were taken on: the bench
-# reports them when the sources still hash the same, else traffic is null.
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from single-launch ncu
+# captures summarised in profiles/, valid only for the kernel sources they were taken on: the
+# bench reports them when the sources still hash the same, else traffic is null.
 TRAFFIC = {
     "relax_scan": {"bytes": 67.92e6, "sha": "cae5f9f37181365e",
                    "files": ["relax_scan.cu", "relax_core.cuh", "interp.cuh"]},
-    "relax_scan_tricubic": {"bytes": 21.29e6, "sha": "98811a7a8f79d820",
+    "relax_scan_tricubic": {"bytes": 23.03e6, "sha": "cae5f9f37181365e",
                             "files": ["relax_scan.cu", "relax_core.cuh", "interp.cuh"]},
     "ff_assemble": {"bytes": 148.04e6, "sha": "8bd463bd812f7566",
                     "files": ["ff_assemble.cu", "ff_core.cuh", "interp.cuh"]},
-    "ff_assemble_quad": {"bytes": 144.63e6, "sha": "bba60445429332e1",
+    "ff_assemble_quad": {"bytes": 147.27e6, "sha": "8bd463bd812f7566",
                          "files": ["ff_assemble.cu", "ff_core.cuh", "interp.cuh"]},
-    "ff_assemble_split": {"bytes": 354.30e6, "sha": "bba60445429332e1",
+    "ff_assemble_split": {"bytes": 356.94e6, "sha": "8bd463bd812f7566",
                           "files": ["ff_assemble.cu", "ff_core.cuh", "interp.cuh"]},
-    "ff_combine": {"bytes": 597.01e6, "sha": "bba60445429332e1",
+    "ff_combine": {"bytes": 600.95e6, "sha": "8bd463bd812f7566",
                    "files": ["ff_assemble.cu", "ff_core.cuh", "interp.cuh"]},
 }
 
@@ -113,10 +113,11 @@ def fp32_peak_tflops(sm_mhz, sms):
     return sms * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
 
 
-def measure_l2_peak(reps=10, sizes_mib=(8, 16, 32, 48)):
+def measure_l2_peak(reps=10, sizes_mib=(8, 16, 32, 48), bytes_per_launch=8 << 30):
     """L2 read bandwidth of this device: pp_read_probe (16-byte loads that bypass L1, every
-    resident thread of a full-GPU grid) over buffers well inside the 129 MB L2, each read 20
-    times per launch once resident; best of reps CUDA-event timings per size, the best size
+    resident thread of a full-GPU grid) over buffers well inside the 129 MB L2, each launch
+    reading about bytes_per_launch (several hundred microseconds, so that clocks and caches are in
+    their steady state) once resident; best of reps CUDA-event timings per size, the best size
     kept."""
     import torch
 
@@ -127,7 +128,7 @@ def measure_l2_peak(reps=10, sizes_mib=(8, 16, 32, 48)):
     per_size = {}
     for mib in sizes_mib:
         buf = torch.rand(mib * (1 << 20) // 4, device="cuda")
-        passes = 20
+        passes = max(1, bytes_per_launch // (mib << 20))
         for _ in range(3):
             pp.pp_read_probe(buf, passes, sink)
         ts = []
@@ -143,8 +144,8 @@ def measure_l2_peak(reps=10, sizes_mib=(8, 16, 32, 48)):
     best = max(per_size, key=per_size.get)
     return {"peak_gbs": per_size[best], "read_gbs_by_mib": per_size, "buffer_mib": best,
             "how": "pp_read_probe (16-byte L1-bypassing loads from every resident thread) reading an L2-resident "
-                   f"buffer of {best} MiB 20 times per launch; best of {reps} CUDA-event timings, best of "
-                   f"{', '.join(str(m) for m in sizes_mib)} MiB"}
+                   f"buffer of {best} MiB {max(1, bytes_per_launch // (best << 20))} times per launch; best of {reps} "
+                   f"CUDA-event timings, best of {', '.join(str(m) for m in sizes_mib)} MiB"}
 
 
 def dist_env():

@@ -6,7 +6,8 @@ Covered: the flake60 step (K1, K2 with fused df, K9, K3/K4/K5 adjoint) on the fo
 a 0.2 A tricubic energy grid; a bricked-layout case with the layout converter and the
 standalone df kernel; the quadrupole with minimum image and a Coulomb cutoff; the split force
 field and its recombination; FFT correlations with a ragged shape and a 1024-long axis; a
-batched launch of ragged molecules.  The library is loaded in a child process (PP_LIBRARY).
+batched launch of ragged molecules, also with other work-item shapes; the scan with the Newton
+polish on a force grid and on an energy grid.  The library is loaded in a child process (PP_LIBRARY).
 """
 import os
 import subprocess
@@ -82,6 +83,11 @@ r["scan"] = dict(r["scan"], nx=13, ny=7)
 cs.append(r)
 b = batch.Batch(cs)
 b.run()
+for zpt, fw, rw in ((4, 16, 4), (8, 4, 16)):
+    batch.Batch(cs, ff_zpt=zpt, ff_tile_w=fw, relax_tile_w=rw).run()
+# the Newton polish after FIRE, on the force and on the energy grid
+step(small, fire=synth.parity_fire(polish=4))
+step(dict(small, grid=dict(small["grid"], interp=1)), fire=synth.parity_fire(polish=4))
 torch.cuda.synchronize()
 print("FLAGS", pp.pp_check_flags())
 """
