@@ -248,3 +248,13 @@ def test_read_probe_validated_on_host(L):
     assert L.pp_read_probe(C.c_void_p(8), 16, 1, fake, None) == 1      # not 16-byte aligned
     assert L.pp_read_probe(fake, 10, 1, fake, None) == 1               # not a multiple of 4 floats
     assert L.pp_read_probe(fake, 16, 0, fake, None) == 1               # no pass
+
+
+def test_grid_axis_limit(L):
+    # the cell lookup's add-based floor is exact below 2^22 nodes per axis: longer axes are refused
+    ok = pp.make_grid({"nx": 1 << 22, "ny": 2, "nz": 2, "x0": 0, "y0": 0, "z0": 0, "dx": 0.1, "dy": 0.1, "dz": 0.1,
+                       "periodic_xy": 1})
+    assert pp.pp_ff_floats(ok) == 4 * (1 << 22) * 4
+    bad = pp.make_grid({"nx": (1 << 22) + 1, "ny": 2, "nz": 2, "x0": 0, "y0": 0, "z0": 0, "dx": 0.1, "dy": 0.1,
+                        "dz": 0.1, "periodic_xy": 1})
+    assert pp.pp_ff_floats(bad) == 0
