@@ -473,7 +473,7 @@ def measure_quadrupole(case, tuning, steps, warmup, flush, alu_peak):
             "ff_traffic": measured_traffic("ff_assemble_quad")}
 
 
-def measure_tricubic(case, steps, warmup, flush):
+def measure_tricubic(case, steps, warmup, flush, spacings=(0.1, 0.2)):
     """The line's workload on tricubic energy grids (one float per node, F = -grad of the tricubic
     interpolant): at the same 0.1 A spacing and at 0.2 A (8x fewer nodes); FF, relaxed scan
     (fused df) and adjoint (pp_backward) times by CUDA events, L2 flushed, grid bytes."""
@@ -483,7 +483,7 @@ def measure_tricubic(case, steps, warmup, flush):
 
     out = []
     g0 = case["grid"]
-    for h in (0.1, 0.2):
+    for h in spacings:
         f = round(h / g0["dx"])
         g = dict(g0, nx=g0["nx"] // f, ny=g0["ny"] // f, nz=(g0["nz"] - 1) // f + 1, dx=h, dy=h, dz=h, interp=1)
         tcase = dict(case, grid=g)
@@ -878,6 +878,7 @@ def main():
     ap.add_argument("--zpt", type=int, default=0, help="FF z-nodes per thread (skips the autotuner)")
     ap.add_argument("--brick", default="", help="bricked layout bx,by,bz for the scan (skips the autotuner)")
     ap.add_argument("--batch-mol", type=int, default=1024)
+    ap.add_argument("--tricubic-spacings", default="0.1,0.2", help="grid spacings (A) of the tricubic leg")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
@@ -1073,7 +1074,8 @@ def main():
     if not args.no_fdbm:
         line["fdbm_sweep"] = measure_fdbm_sweep(5, flush)
     if not args.no_tricubic:
-        line["tricubic"] = measure_tricubic(case, max(3, args.steps // 2), args.warmup, flush)
+        line["tricubic"] = measure_tricubic(case, max(3, args.steps // 2), args.warmup, flush,
+                                            tuple(float(v) for v in args.tricubic_spacings.split(",")))
     if not args.no_quad:
         line["quadrupole"] = measure_quadrupole(case, tuning, max(3, args.steps // 2), args.warmup, flush, alu_peak)
     if not args.no_split:
