@@ -35,8 +35,9 @@ __device__ __forceinline__ float radial_factor(const Q_t& P, float3 e) {
 // one pixel, but it adds up over the image in the tip-parameter gradients, whose sums cancel to
 // a small fraction of their terms.  With the remainders carried, the roundings left are those of
 // per-pixel sums, which vary from pixel to pixel.  The first height's cell coordinate and the
-// step sdz / dz come in the launch as float pairs formed in FP64 on the host (fz0, fz0_lo, st,
-// st_lo); each later height is an exact float-float step (FP64 is a slow pipe on this part).
+// step sdz / dz come as float pairs formed in FP64 once per launch (the single scan, on the host)
+// or once per work item (the batch) (fz0, fz0_lo, st, st_lo); each later height is an exact
+// float-float step (FP64 is a slow pipe on this part).
 struct Height {
     float az, az_lo;  // anchor z
     float fz, fz_lo;  // z cell coordinate of anchor + d0z
