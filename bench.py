@@ -41,9 +41,9 @@ SM_COUNT_NOMINAL = 152       # GB300; the bench reads the count from the device 
 # captures summarised in profiles/, valid only for the kernel sources they were taken on: the
 # bench reports them when the sources still hash the same, else traffic is null.
 TRAFFIC = {
-    "relax_scan": {"bytes": 67.92e6, "sha": "cae5f9f37181365e",
+    "relax_scan": {"bytes": 67.92e6, "sha": "bfc8c80d70d2f9d2",
                    "files": ["relax_scan.cu", "relax_core.cuh", "interp.cuh"]},
-    "relax_scan_tricubic": {"bytes": 23.03e6, "sha": "cae5f9f37181365e",
+    "relax_scan_tricubic": {"bytes": 23.03e6, "sha": "bfc8c80d70d2f9d2",
                             "files": ["relax_scan.cu", "relax_core.cuh", "interp.cuh"]},
     "ff_assemble": {"bytes": 148.04e6, "sha": "8bd463bd812f7566",
                     "files": ["ff_assemble.cu", "ff_core.cuh", "interp.cuh"]},
@@ -70,7 +70,7 @@ EXECUTED = {
     "ff_energy": {"value": None, "sha": None, "files": ["ff_assemble.cu", "ff_core.cuh", "interp.cuh"]},
 }
 ISSUE = {
-    "relax_scan": {"value": 0.573, "sha": "cae5f9f37181365e", "files": ["relax_scan.cu", "relax_core.cuh", "interp.cuh"]},
+    "relax_scan": {"value": 0.573, "sha": "bfc8c80d70d2f9d2", "files": ["relax_scan.cu", "relax_core.cuh", "interp.cuh"]},
 }
 
 
