@@ -193,3 +193,40 @@ def test_asymmetric_tip_on_a_clamped_grid_parity(orc):
     c["tip"] = synth.default_tip(kx=0.35, ky=0.28, d0x=0.35, d0y=-0.25)
     c["grid"] = dict(c["grid"], periodic_xy=0)
     check_parity(orc, c)
+
+
+def test_benzene_mirror_symmetry_on_the_gpu(orc):
+    # benzene is symmetric under x -> -x and y -> -y; the periodic 80 x 80 grid from -8 A at 0.2 A
+    # maps node i to node (80 - i) mod 80, and the 40 x 40 scan from -5.85 A at 0.3 A maps pixel i
+    # to 39 - i.  The GPU's force field and image keep the symmetry to FP32 rounding (the oracle's
+    # FP64 grid keeps it to 1e-12, tests/test_oracle_ff.py)
+    c = case32(synth.benzene_case())
+    g = gpu_run(c, synth.parity_fire())
+    F = np.asarray(g["ff"].view(c["grid"]["nz"], c["grid"]["ny"], c["grid"]["nx"], 4).cpu().numpy(), np.float64)
+    # node 0 (x = -8 A) would mirror onto x = +8 A, outside the grid (the field is summed over the
+    # atoms alone, without periodic images), so the comparison runs over nodes 1..79; core nodes
+    # (floored pairs, forces of hundreds of eV/A) are left out as in the parity tests
+    _, core = orc.make_ff(c["atoms"], c["probe"], c["grid"])
+    inner = ~core
+    inner[:, 0, :] = False
+    inner[:, :, 0] = False
+    mx = np.roll(F[:, :, ::-1], 1, axis=2)[..., :3] * np.array([-1.0, 1.0, 1.0])  # node i -> 80 - i
+    my = np.roll(F[:, ::-1, :], 1, axis=1)[..., :3] * np.array([1.0, -1.0, 1.0])  # node j -> 80 - j
+    norm = np.maximum(np.linalg.norm(F[..., :3], axis=-1), 1e-3)
+    assert (np.linalg.norm(mx - F[..., :3], axis=-1) / norm)[inner].max() <= 1e-4
+    assert (np.linalg.norm(my - F[..., :3], axis=-1) / norm)[inner].max() <= 1e-4
+    # the relaxed image: pixels mirrored into each other relax into mirrored basins (a bistable point
+    # may fall either way under FP32 rounding: those are counted, not compared), and df agrees
+    o = orc.forward(c, fire=synth.parity_fire())
+    pos = g["pos"]
+    px = pos[:, :, ::-1].copy()
+    px[..., 0] = -px[..., 0]
+    dpx = np.linalg.norm(px - pos, axis=-1)
+    well = (o["lam"] >= 0.01) & (o["lam"][:, :, ::-1] >= 0.01)
+    same = dpx < 0.05
+    assert (well & ~same).mean() <= 0.01
+    assert dpx[well & same].max() <= 2e-3
+    keep = well & same
+    kd = df_keep(keep, (keep.shape[0] - g["df"].shape[0]) // 2)
+    rng = g["df"].max() - g["df"].min()
+    assert np.abs(g["df"][:, :, ::-1] - g["df"])[kd].max() <= 1e-3 * rng
