@@ -829,6 +829,16 @@ def measure_batch(n_mol, steps, warmup, flush, seq_sample=64, ff_energy=False):
         ts.append(e0.elapsed_time(e1))
     st, flags = b.status()
     t = statistics.median(ts)
+    # end to end: the packed host atoms in, the batch's graph, every molecule's df image back to
+    # pinned host memory, synchronised, wall clock (median of 5 calls)
+    b.pack_atoms(cases)
+    b.run_host()
+    t_e2e = []
+    for _ in range(5):
+        t0 = time.perf_counter()
+        b.run_host()
+        t_e2e.append(time.perf_counter() - t0)
+    e2e_ms = 1e3 * statistics.median(t_e2e)
     # the same molecules one at a time (first seq_sample of them), per-molecule buffers preallocated
     sims = [(afm.Simulator(c, ff_energy=ff_energy), afm.atoms_to_device(c["atoms"])) for c in cases[:seq_sample]]
     for sim, at in sims:
@@ -848,6 +858,10 @@ def measure_batch(n_mol, steps, warmup, flush, seq_sample=64, ff_energy=False):
            "mol_per_s": n_mol / (t * 1e-3), "ms_per_batch": t, "pixel_z_per_s": b.pixel_heights / (t * 1e-3),
            "ff_pair_evals_per_s": b.pairs / (t * 1e-3), "status": st, "ff_energy": bool(ff_energy),
            "autotune": autotune,
+           "e2e": {"mol_per_s": n_mol / (e2e_ms * 1e-3), "ms_per_batch": e2e_ms, "h2d_bytes": b.h2d_bytes(),
+                   "d2h_bytes": b.d2h_bytes(),
+                   "note": "Batch.run_host: packed host atoms in, the graph replayed, all df images out to pinned "
+                           "host memory, synchronised; wall clock, median of 5"},
            "single_path_mol_per_s": 1e3 / t_seq,
            "single_path_note": f"pp_make_ff + pp_relax_scan per molecule, mean over the first {seq_sample}",
            "gpu_launches_per_batch": 2}

@@ -204,3 +204,23 @@ def test_batch_shapes_are_validated():
         with pytest.raises(pp.PPError) as e:
             b.run()
         assert e.value.status == 1
+
+
+def test_batch_from_host_memory():
+    # run_host: the same atoms give the device run's images bit for bit; moved atoms give what a batch
+    # built from the moved molecules (on the same grids and scans) computes
+    cs = cases(4, 8000)
+    b = batch.Batch(cs)
+    b.run()
+    want = b.df.clone()
+    b.capture()
+    got = b.run_host(b.pack_atoms(cs)).clone()
+    assert torch.equal(got.cuda(), want)
+    moved = copy.deepcopy(cs)
+    for c in moved:
+        c["atoms"]["x"] = (np.asarray(c["atoms"]["x"], np.float32) + np.float32(0.037)).astype(np.float64)
+    ref = batch.Batch(moved)
+    ref.run()
+    got = b.run_host(b.pack_atoms(moved)).clone()
+    assert torch.equal(got.cuda(), ref.df)
+    assert b.status() == (0, 0)
