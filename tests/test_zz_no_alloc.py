@@ -21,8 +21,9 @@ pytestmark = pytest.mark.gpu
 KEYS = ("x", "y", "z", "q", "R", "eps")
 
 
-def setup_case():
+def setup_case(interp=0):
     c = case32(synth.small_case(seed=9, n_atoms=8, nxy=40, nz=36, scan_px=9, nz_scan=14, d=0.15))
+    c["grid"] = dict(c["grid"], interp=interp)
     sim = afm.Simulator(c, fire=synth.parity_fire())
     atoms_t = afm.atoms_to_device(c["atoms"])
     sim.run(atoms_t)
@@ -39,8 +40,11 @@ def flat(g):
     return np.concatenate([g[k].cpu().numpy() for k in KEYS + ("tip",)]).astype(np.float64)
 
 
-def test_noalloc_matches_workspace_entry_point_twice():
-    c, sim, atoms_t = setup_case()
+@pytest.mark.parametrize("interp", [0, 1])
+def test_noalloc_matches_workspace_entry_point_twice(interp):
+    # on a force grid (a float4 grid adjoint per node) and on a tricubic energy grid (one float per
+    # node) the scratch is laid out differently; both must match pp_backward
+    c, sim, atoms_t = setup_case(interp)
     n = len(c["atoms"]["x"])
     atoms = pp.make_atoms(atoms_t)
     ws = torch.empty(pp.pp_backward_workspace(sim.grid) // 4 + 1, dtype=torch.float32, device="cuda")
