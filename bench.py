@@ -800,7 +800,7 @@ def measure_small(case, steps, warmup, flush, alu_peak, ff_energy=False, cpu=Tru
     return out
 
 
-def measure_batch(n_mol, steps, warmup, flush, seq_sample=64, ff_energy=False):
+def measure_batch(n_mol, steps, warmup, flush, seq_sample=64, ff_energy=False, autotune=True):
     """Batched molecules/s: pp_batch_run over n_mol seeded molecules replayed from a CUDA graph,
     beside the same molecules run one by one through pp_make_ff + pp_relax_scan (both with or
     both without the grids' energy sums)."""
@@ -812,7 +812,7 @@ def measure_batch(n_mol, steps, warmup, flush, seq_sample=64, ff_energy=False):
 
     cases = synth.batch_cases(n_mol)
     b = batch.Batch(cases, ff_energy=ff_energy)
-    autotune = tune.tune_batch(b)
+    autotune = tune.tune_batch(b) if autotune else None
     b.capture()
     for _ in range(max(warmup, 1)):
         b.replay()
@@ -893,6 +893,7 @@ def main():
     ap.add_argument("--brick", default="", help="bricked layout bx,by,bz for the scan (skips the autotuner)")
     ap.add_argument("--batch-mol", type=int, default=1024)
     ap.add_argument("--tricubic-spacings", default="0.1,0.2", help="grid spacings (A) of the tricubic leg")
+    ap.add_argument("--no-batch-tune", action="store_true", help="batched leg on the default work-item shapes")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
@@ -1103,7 +1104,7 @@ def main():
         line["slab"] = measure_slab(3, 1, flush, args.ff_energy)
     if not args.no_batch:
         line["batched"] = measure_batch(args.batch_mol, max(3, args.steps // 4), args.warmup, flush,
-                                        ff_energy=args.ff_energy)
+                                        ff_energy=args.ff_energy, autotune=not args.no_batch_tune)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(case)
         line["cpu_baseline"]["other_configs"] = cpu_baseline_other()
