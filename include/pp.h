@@ -222,6 +222,19 @@ typedef struct {
 PP_API pp_status pp_make_ff_tuned(const pp_atoms* atoms, const pp_probe* probe, const pp_grid* grid,
                                   float* ff, const pp_tuning* tuning, pp_stream stream);
 
+/* pp_make_ff_tuned restricted to the node layers k_begin <= k < k_end (every
+ * x and y): those nodes get exactly the values pp_make_ff_tuned writes there
+ * (each node's sums do not depend on which nodes share its launch); every
+ * other node of ff, and the padding nodes of a bricked layout (which
+ * pp_make_ff zeroes), are left as they are.  The paper has no counterpart: it
+ * lets a caller assemble the layers a scan reads first and the rest on
+ * another stream while the scan runs (the grid is still complete when both
+ * have finished).  tuning may be NULL.  Errors as pp_make_ff_tuned, plus
+ * PP_ERR_ARG unless 0 <= k_begin < k_end <= nz. */
+PP_API pp_status pp_make_ff_layers(const pp_atoms* atoms, const pp_probe* probe, const pp_grid* grid,
+                                   float* ff, const pp_tuning* tuning, int k_begin, int k_end,
+                                   pp_stream stream);
+
 /* Relaxed tip scan (Sec. 5.1.1 step 2; Eqs. F_PP, F_tip; Sec. 2.1 readout).
  * F_S comes from the grid by trilinear force interpolation, or by the
  * gradient of the tricubic energy interpolant when grid->interp = 1.
@@ -240,6 +253,22 @@ PP_API pp_status pp_relax_scan(const float* ff, const pp_grid* grid, const pp_sc
                         const pp_tip* tip, const pp_fire* fire,
                         float* pos, float* fz, int* iters,
                         const pp_df* fused_df, float* df, pp_stream stream);
+
+/* pp_relax_scan (the same outputs, bit for bit) that also reports which node
+ * layers of the grid its interpolations read: zspan (DEVICE, two ints,
+ * 4-byte aligned, caller-owned) receives the lowest and highest layer index k,
+ * over every FIRE iteration and Newton step of every pixel (trilinear: the
+ * two layers of each cell used; tricubic: the four stencil layers, clamped to
+ * the grid).  The call initialises zspan on the stream itself.  So a scan
+ * whose layers lie inside those already assembled read nothing else: the
+ * check a caller makes after overlapping the scan with pp_make_ff_layers of
+ * the other layers (and, if it fails, runs the scan again on the complete
+ * grid).  The paper has no counterpart.  Errors as pp_relax_scan, plus
+ * PP_ERR_ARG for a NULL or unaligned zspan. */
+PP_API pp_status pp_relax_scan_zspan(const float* ff, const pp_grid* grid, const pp_scan* scan,
+                                     const pp_tip* tip, const pp_fire* fire,
+                                     float* pos, float* fz, int* iters,
+                                     const pp_df* fused_df, float* df, int* zspan, pp_stream stream);
 
 /* Frequency shift of Eq. df.  fz[k*npix + p] holds Fz (eV/A) at tip heights
  * z_k = z_top - k*dz; df[c*npix + p] (Hz), c = 0..nz-2m-1, is centred at

@@ -26,10 +26,12 @@ class Simulator:
     """Preallocated FF grid, positions, Fz, iteration counts and df for one case shape."""
 
     def __init__(self, case, layout=0, brick=(4, 4, 4), fire=None, device="cuda", fused_df=True,
-                 want_pos=True, want_iters=True, tuning=None, ff_energy=True):
+                 want_pos=True, want_iters=True, tuning=None, ff_energy=True, overlap_ff=True):
         """tuning: an autotuner result ({"ff_zpt", "layout", "brick"}) overriding layout and brick.
         ff_energy=False: the grid's E slots are written as 0 and the energy sums skipped (the scan
-        reads only the forces, which are unchanged); trilinear force grids only."""
+        reads only the forces, which are unchanged); trilinear force grids only.
+        overlap_ff: run_host assembles the node layers the scan will read first and the others on a
+        second stream while the scan runs (see run_overlapped); False: one stage after the other."""
         self.case = case
         self.device = torch.device(device)
         if tuning is not None:
@@ -53,12 +55,19 @@ class Simulator:
         if self.m < 0 or s["nz"] < 2 * self.m + 1:
             raise ValueError("scan has fewer heights than the df stencil needs")
         nz, ny, nx = s["nz"], s["ny"], s["nx"]
-        self.ff = torch.empty(pp.pp_ff_floats(self.grid), dtype=torch.float32, device=self.device)
+        # zeroed once: a bricked layout's padding nodes, which only the whole-grid call writes
+        self.ff = torch.zeros(pp.pp_ff_floats(self.grid), dtype=torch.float32, device=self.device)
         self.pos = torch.empty((nz, ny, nx, 3), dtype=torch.float32, device=self.device) if want_pos else None
         self.fz = torch.empty((nz, ny, nx), dtype=torch.float32, device=self.device)
         self.iters = torch.empty((nz, ny, nx), dtype=torch.int32, device=self.device) if want_iters else None
         self.df = torch.empty((nz - 2 * self.m, ny, nx), dtype=torch.float32, device=self.device)
         self._host = None
+        self.overlap_ff = overlap_ff
+        self.reruns = 0      # scans run again because they read a layer outside the first part
+        self._span = None    # node layers the last overlapped scan read
+        self._side = None    # second stream of the overlapped forward
+        self._zspan_d = None
+        self._zspan_h = None
 
     def make_ff(self, atoms_dev, stream=None):
         if self.zpt is not None:
@@ -82,6 +91,70 @@ class Simulator:
         self.make_ff(atoms_dev, stream)
         self.relax(stream, df)
         return self.df if df is None else df
+
+    # ---- force field of the scan's layers first, the rest beside the scan
+    def first_layers(self):
+        """Node layers [k0, k1) assembled before the scan: those the last overlapped scan read, with
+        two layers of margin on either side; before any, the layers within R0 + 1 A of the anchor
+        heights (a PP hangs R0 from its anchor; the springs hold it near that sphere)."""
+        g, s = self.case["grid"], self.case["scan"]
+        nz = int(g["nz"])
+        if self._span is not None:
+            lo, hi = self._span[0] - 2, self._span[1] + 3
+        else:
+            reach = float(self.case["tip"]["R0"]) + 1.0
+            zbot = s["z_top"] - (s["nz"] - 1) * s["dz"]
+            lo = int(np.floor((zbot - reach - g["z0"]) / g["dz"]))
+            hi = int(np.floor((s["z_top"] + reach - g["z0"]) / g["dz"])) + 2
+        k0, k1 = min(max(lo, 0), nz - 1), min(max(hi, 1), nz)
+        return (k0, k1) if k1 > k0 else (0, nz)
+
+    def _ff_layers(self, atoms, k0, k1, stream):
+        pp.pp_make_ff_layers(atoms, self.probe, self.grid, self.ff, k0, k1, self.zpt, stream)
+
+    def run_overlapped(self, atoms_dev, stream=None):
+        """Forward pass with the force field in two parts: layers [k0, k1) = first_layers() on
+        `stream`, then the scan on `stream` (reporting the layers it read) while the other layers
+        are assembled on a second stream; `stream` waits for both.  Returns (k0, k1).  The result
+        stands only if the scan read nothing outside [k0, k1): check it with overlap_held() after
+        synchronising (run_host does, and runs the scan again on the complete grid if not)."""
+        st = stream or torch.cuda.current_stream()
+        nz = int(self.case["grid"]["nz"])
+        if self._side is None:
+            self._side = torch.cuda.Stream(device=self.device)
+            self._zspan_d = torch.empty(2, dtype=torch.int32, device=self.device)
+            self._zspan_h = torch.empty(2, dtype=torch.int32, pin_memory=torch.cuda.is_available())
+        k0, k1 = self.first_layers()
+        atoms = pp.make_atoms(atoms_dev)
+        self._ff_layers(atoms, k0, k1, st)
+        first = torch.cuda.Event()
+        first.record(st)
+        self._side.wait_event(first)
+        if k1 < nz:
+            self._ff_layers(atoms, k1, nz, self._side)
+        if k0 > 0:
+            self._ff_layers(atoms, 0, k0, self._side)
+        pp.pp_relax_scan(self.ff, self.grid, self.scan, self.tip, self.fire, self.pos, self.fz, self.iters,
+                         self.dfp if self.fused_df else None, self.df if self.fused_df else None, st,
+                         zspan=self._zspan_d)
+        if not self.fused_df:
+            pp.pp_fz_to_df(self.fz, self.scan.nz, self.scan.nx * self.scan.ny, self.scan.dz, self.dfp, self.df, st)
+        with torch.cuda.stream(st):
+            self._zspan_h.copy_(self._zspan_d, non_blocking=True)
+        rest = torch.cuda.Event()
+        rest.record(self._side)
+        st.wait_event(rest)
+        self._first = (k0, k1)
+        return k0, k1
+
+    def overlap_held(self):
+        """After run_overlapped and a synchronise: True when the scan read only layers of the first
+        part (its result is then that of run()); remembers the layers read for first_layers()."""
+        lo, hi = int(self._zspan_h[0]), int(self._zspan_h[1])
+        if lo > hi:  # nothing read (no pixel)
+            return True
+        self._span = (lo, hi)
+        return self._first[0] <= lo and hi < self._first[1]
 
     # ---- end to end from host memory
     def _host_buffers(self, n_atoms):
@@ -109,9 +182,19 @@ class Simulator:
         with torch.cuda.stream(st):
             hb["atoms_d"].copy_(hb["atoms_h"], non_blocking=True)
             dev = {k: hb["atoms_d"][r] for r, k in enumerate(ATOM_KEYS)}
-            self.run(dev, st)
+            if self.overlap_ff:
+                self.run_overlapped(dev, st)
+            else:
+                self.run(dev, st)
             hb["df_h"].copy_(self.df, non_blocking=True)
         st.synchronize()
+        if self.overlap_ff and not self.overlap_held():
+            # the scan left the first part: run it again on the grid, complete by now
+            self.reruns += 1
+            with torch.cuda.stream(st):
+                self.relax(st)
+                hb["df_h"].copy_(self.df, non_blocking=True)
+            st.synchronize()
         if out is not None:
             out.copy_(hb["df_h"])
             return out

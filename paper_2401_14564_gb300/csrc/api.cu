@@ -166,8 +166,10 @@ int pp_df_margin(float A_pp, float dz) { return df_half_width(A_pp, dz); }
 static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
 // Validation and launch shared by pp_make_ff, pp_make_ff_tuned and pp_make_ff_split.
+// layers: NULL for the whole grid (padding zeroed), else the node layers [layers[0], layers[1]) to write.
 static pp_status make_ff_impl(const char* name, const pp_atoms* atoms, const pp_probe* probe, const pp_grid* grid,
-                              float* ff, float* ff_el, int zpt, int forces_only, pp_stream stream) {
+                              float* ff, float* ff_el, int zpt, int forces_only, pp_stream stream,
+                              const int* layers = nullptr) {
     const std::string who(name);
     if (!atoms || !probe || !grid || !ff) { set_error(who + ": NULL argument"); return PP_ERR_ARG; }
     if (atoms->n < 0) { set_error(who + ": atoms->n < 0"); return PP_ERR_ARG; }
@@ -188,8 +190,13 @@ static pp_status make_ff_impl(const char* name, const pp_atoms* atoms, const pp_
     std::string why;
     if (!make_grid_map(grid, &map, &why)) { set_error(who + ": " + why); return PP_ERR_SHAPE; }
     if (forces_only && map.interp) { set_error(who + ": ff_forces_only on an energy-only (interp = 1) grid"); return PP_ERR_ARG; }
+    const int kbeg = layers ? layers[0] : 0, kend = layers ? layers[1] : grid->nz;
+    if (kbeg < 0 || kend <= kbeg || kend > grid->nz) {
+        set_error(who + ": node layers must satisfy 0 <= k_begin < k_end <= nz");
+        return PP_ERR_ARG;
+    }
     cudaStream_t s = (cudaStream_t)stream;
-    if (map.stored_nodes > (int64_t)grid->nx * grid->ny * grid->nz) {
+    if (!layers && map.stored_nodes > (int64_t)grid->nx * grid->ny * grid->nz) {
         for (float* g : {ff, ff_el}) {
             if (!g) continue;
             pp_status st = cuda_status(cudaMemsetAsync(g, 0, (size_t)map.stored_nodes * 16, s), (who + " memset").c_str());
@@ -220,6 +227,8 @@ static pp_status make_ff_impl(const char* name, const pp_atoms* atoms, const pp_
     L.split = ff_el != nullptr;
     L.ffel = (ff_el && !map.interp) ? reinterpret_cast<float4*>(ff_el) : nullptr;
     L.ffelE = (ff_el && map.interp) ? ff_el : nullptr;
+    L.kbeg = kbeg;
+    L.kend = kend;
     return cuda_status(launch_ff_assemble(L, s), (who + " launch").c_str());
 }
 
@@ -239,6 +248,18 @@ pp_status pp_make_ff_tuned(const pp_atoms* atoms, const pp_probe* probe, const p
     const int forces_only = tuning ? tuning->ff_forces_only : 0;
     if (forces_only != 0 && forces_only != 1) { set_error("pp_make_ff_tuned: ff_forces_only must be 0 or 1"); return PP_ERR_ARG; }
     return make_ff_impl("pp_make_ff_tuned", atoms, probe, grid, ff, nullptr, zpt, forces_only, stream);
+}
+
+pp_status pp_make_ff_layers(const pp_atoms* atoms, const pp_probe* probe, const pp_grid* grid, float* ff,
+                            const pp_tuning* tuning, int k_begin, int k_end, pp_stream stream) {
+    Range range("pp_make_ff_layers");
+    g_error.clear();
+    const int zpt = (tuning && tuning->ff_zpt) ? tuning->ff_zpt : 8;
+    if (zpt != 4 && zpt != 8 && zpt != 16) { set_error("pp_make_ff_layers: ff_zpt must be 4, 8 or 16"); return PP_ERR_ARG; }
+    const int forces_only = tuning ? tuning->ff_forces_only : 0;
+    if (forces_only != 0 && forces_only != 1) { set_error("pp_make_ff_layers: ff_forces_only must be 0 or 1"); return PP_ERR_ARG; }
+    const int layers[2] = {k_begin, k_end};
+    return make_ff_impl("pp_make_ff_layers", atoms, probe, grid, ff, nullptr, zpt, forces_only, stream, layers);
 }
 
 pp_status pp_make_ff_split(const pp_atoms* atoms, const pp_probe* probe, const pp_grid* grid, float* ff,
@@ -283,27 +304,27 @@ static bool check_tip_fire(const pp_tip* tip, const pp_fire* fire, std::string* 
     return true;
 }
 
-pp_status pp_relax_scan(const float* ff, const pp_grid* grid, const pp_scan* scan, const pp_tip* tip,
-                        const pp_fire* fire, float* pos, float* fz, int* iters, const pp_df* fused_df, float* df,
-                        pp_stream stream) {
-    Range range("pp_relax_scan");
-    g_error.clear();
-    if (!ff || !grid || !scan || !tip || !fire || !fz) { set_error("pp_relax_scan: NULL argument"); return PP_ERR_ARG; }
-    if (!aligned16(ff)) { set_error("pp_relax_scan: ff must be 16-byte aligned"); return PP_ERR_ARG; }
+// pp_relax_scan, and pp_relax_scan_zspan when zspan is given (checked by the caller).
+static pp_status relax_scan_impl(const char* name, const float* ff, const pp_grid* grid, const pp_scan* scan,
+                                 const pp_tip* tip, const pp_fire* fire, float* pos, float* fz, int* iters,
+                                 const pp_df* fused_df, float* df, int* zspan, pp_stream stream) {
+    const std::string who(name);
+    if (!ff || !grid || !scan || !tip || !fire || !fz) { set_error(who + ": NULL argument"); return PP_ERR_ARG; }
+    if (!aligned16(ff)) { set_error(who + ": ff must be 16-byte aligned"); return PP_ERR_ARG; }
     GridMap map;
     std::string why;
-    if (!make_grid_map(grid, &map, &why)) { set_error("pp_relax_scan: " + why); return PP_ERR_SHAPE; }
-    if (scan->nx < 1 || scan->ny < 1 || scan->nz < 1) { set_error("pp_relax_scan: scan sizes must be >= 1"); return PP_ERR_SHAPE; }
+    if (!make_grid_map(grid, &map, &why)) { set_error(who + ": " + why); return PP_ERR_SHAPE; }
+    if (scan->nx < 1 || scan->ny < 1 || scan->nz < 1) { set_error(who + ": scan sizes must be >= 1"); return PP_ERR_SHAPE; }
     if ((int64_t)scan->nx * scan->ny * scan->nz * 3 >= (int64_t(1) << 31)) {
-        set_error("pp_relax_scan: scan too large for one call");
+        set_error(who + ": scan too large for one call");
         return PP_ERR_SHAPE;
     }
     if (!isfinite(scan->x0) || !isfinite(scan->y0) || !isfinite(scan->px) || !isfinite(scan->py) ||
         !isfinite(scan->z_top) || !finite_pos(scan->dz)) {
-        set_error("pp_relax_scan: invalid scan geometry");
+        set_error(who + ": invalid scan geometry");
         return PP_ERR_ARG;
     }
-    if (!check_tip_fire(tip, fire, &why)) { set_error("pp_relax_scan: " + why); return PP_ERR_ARG; }
+    if (!check_tip_fire(tip, fire, &why)) { set_error(who + ": " + why); return PP_ERR_ARG; }
     RelaxLaunch L;
     std::memset(&L, 0, sizeof(L));
     L.ff = map.interp ? nullptr : reinterpret_cast<const float4*>(ff);
@@ -338,16 +359,44 @@ pp_status pp_relax_scan(const float* ff, const pp_grid* grid, const pp_scan* sca
     L.df_m = -1;
     L.df = nullptr;
     if (fused_df && df) {
-        if (!finite_pos(fused_df->k) || !isfinite(fused_df->f0)) { set_error("pp_relax_scan: invalid df parameters"); return PP_ERR_ARG; }
+        if (!finite_pos(fused_df->k) || !isfinite(fused_df->f0)) { set_error(who + ": invalid df parameters"); return PP_ERR_ARG; }
         const int m = df_half_width(fused_df->A_pp, scan->dz);
-        if (m < 0) { set_error("pp_relax_scan: invalid df amplitude"); return PP_ERR_ARG; }
-        if (m > kMaxDfHalfWidth) { set_error("pp_relax_scan: df stencil wider than 63 taps"); return PP_ERR_UNSUPPORTED; }
-        if (scan->nz < 2 * m + 1) { set_error("pp_relax_scan: fewer heights than the df stencil"); return PP_ERR_SHAPE; }
+        if (m < 0) { set_error(who + ": invalid df amplitude"); return PP_ERR_ARG; }
+        if (m > kMaxDfHalfWidth) { set_error(who + ": df stencil wider than 63 taps"); return PP_ERR_UNSUPPORTED; }
+        if (scan->nz < 2 * m + 1) { set_error(who + ": fewer heights than the df stencil"); return PP_ERR_SHAPE; }
         L.df_m = m;
         L.df = df;
         df_stencil(fused_df->A_pp, scan->dz, fused_df->k, fused_df->f0, m, L.coef);
     }
-    return cuda_status(launch_relax_scan(L, (cudaStream_t)stream), "pp_relax_scan launch");
+    L.zspan = zspan;
+    if (zspan) {
+        // (INT_MAX, INT_MIN) before the scan folds its lanes' layers in by atomic min / max
+        for (int h = 0; h < 2; ++h) {
+            const pp_status st = cuda_status(cudaMemsetAsync(zspan + h, h ? 0x80 : 0x7f, sizeof(int),
+                                                             (cudaStream_t)stream), (who + " memset").c_str());
+            if (st != PP_OK) return st;
+        }
+    }
+    return cuda_status(launch_relax_scan(L, (cudaStream_t)stream), (who + " launch").c_str());
+}
+
+pp_status pp_relax_scan(const float* ff, const pp_grid* grid, const pp_scan* scan, const pp_tip* tip,
+                        const pp_fire* fire, float* pos, float* fz, int* iters, const pp_df* fused_df, float* df,
+                        pp_stream stream) {
+    Range range("pp_relax_scan");
+    g_error.clear();
+    return relax_scan_impl("pp_relax_scan", ff, grid, scan, tip, fire, pos, fz, iters, fused_df, df, nullptr, stream);
+}
+
+pp_status pp_relax_scan_zspan(const float* ff, const pp_grid* grid, const pp_scan* scan, const pp_tip* tip,
+                              const pp_fire* fire, float* pos, float* fz, int* iters, const pp_df* fused_df,
+                              float* df, int* zspan, pp_stream stream) {
+    Range range("pp_relax_scan_zspan");
+    g_error.clear();
+    if (!zspan) { set_error("pp_relax_scan_zspan: NULL zspan"); return PP_ERR_ARG; }
+    if (((uintptr_t)zspan & 3u) != 0) { set_error("pp_relax_scan_zspan: zspan must be 4-byte aligned"); return PP_ERR_ARG; }
+    return relax_scan_impl("pp_relax_scan_zspan", ff, grid, scan, tip, fire, pos, fz, iters, fused_df, df, zspan,
+                           stream);
 }
 
 pp_status pp_fz_to_df(const float* fz, int nz, int npix, float dz, const pp_df* dfp, float* df, pp_stream stream) {

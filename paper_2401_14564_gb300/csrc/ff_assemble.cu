@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(kThreads) ff_assemble_kernel(const FFLaunch P)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int i = blockIdx.x * kTileX + (warp & 1) * 8 + (lane & 7);
     const int j = blockIdx.y * kTileY + (warp >> 1) * 4 + (lane >> 3);
-    const int k0 = blockIdx.z * ZPT;
+    const int k0 = P.kbeg + blockIdx.z * ZPT;
 
     const float gx = P.x0 + i * P.dx;
     const float gy = P.y0 + j * P.dy;
@@ -87,11 +87,11 @@ __global__ void __launch_bounds__(kThreads) ff_assemble_kernel(const FFLaunch P)
 #pragma unroll
         for (int t = 0; t < ZP; ++t) {
             const int k = k0 + 2 * t;
-            if (k < P.map.nz) P.ffE[at(k)] = en[t].x;
-            if (k + 1 < P.map.nz) P.ffE[at(k + 1)] = en[t].y;
+            if (k < P.kend) P.ffE[at(k)] = en[t].x;
+            if (k + 1 < P.kend) P.ffE[at(k + 1)] = en[t].y;
             if constexpr (kSplit) {
-                if (k < P.map.nz) P.ffelE[at(k)] = ene[t].x;
-                if (k + 1 < P.map.nz) P.ffelE[at(k + 1)] = ene[t].y;
+                if (k < P.kend) P.ffelE[at(k)] = ene[t].x;
+                if (k + 1 < P.kend) P.ffelE[at(k + 1)] = ene[t].y;
             }
         }
     } else {
@@ -99,12 +99,12 @@ __global__ void __launch_bounds__(kThreads) ff_assemble_kernel(const FFLaunch P)
         for (int t = 0; t < ZP; ++t) {
             const int k = k0 + 2 * t;
             const float2 e = kForcesOnly ? make_float2(0.f, 0.f) : en[t];
-            if (k < P.map.nz) P.ff[at(k)] = make_float4(fx[t].x, fy[t].x, fz[t].x, e.x);
-            if (k + 1 < P.map.nz) P.ff[at(k + 1)] = make_float4(fx[t].y, fy[t].y, fz[t].y, e.y);
+            if (k < P.kend) P.ff[at(k)] = make_float4(fx[t].x, fy[t].x, fz[t].x, e.x);
+            if (k + 1 < P.kend) P.ff[at(k + 1)] = make_float4(fx[t].y, fy[t].y, fz[t].y, e.y);
             if constexpr (kSplit) {
-                if (k < P.map.nz)
+                if (k < P.kend)
                     P.ffel[at(k)] = make_float4(fxe[t].x, fye[t].x, fze[t].x, ene[t].x);
-                if (k + 1 < P.map.nz)
+                if (k + 1 < P.kend)
                     P.ffel[at(k + 1)] = make_float4(fxe[t].y, fye[t].y, fze[t].y, ene[t].y);
             }
         }
@@ -130,7 +130,7 @@ __global__ void ff_combine_kernel(const float* a, const float* __restrict__ b, f
 
 template <int ZPT>
 cudaError_t launch_zpt(const FFLaunch& L, cudaStream_t s) {
-    dim3 grid((L.map.nx + kTileX - 1) / kTileX, (L.map.ny + kTileY - 1) / kTileY, (L.map.nz + ZPT - 1) / ZPT);
+    dim3 grid((L.map.nx + kTileX - 1) / kTileX, (L.map.ny + kTileY - 1) / kTileY, (L.kend - L.kbeg + ZPT - 1) / ZPT);
     with_flags(L.min_image != 0, L.coul_rc > 0.f, L.kQzz != 0.f, [&](auto mi, auto cut, auto quad) {
         constexpr bool MI = decltype(mi)::value, CUT = decltype(cut)::value, QUAD = decltype(quad)::value;
         if (L.forces_only) ff_assemble_kernel<ZPT, MI, CUT, QUAD, false, false, true><<<grid, kThreads, 0, s>>>(L);
@@ -155,10 +155,10 @@ cudaError_t launch_ff_combine(const float* a, const float* b, float Q, float* ou
 }
 
 cudaError_t launch_ff_assemble(const FFLaunch& L, cudaStream_t s) {
-    if (L.map.nx <= 0 || L.map.ny <= 0 || L.map.nz <= 0) return cudaSuccess;
+    if (L.map.nx <= 0 || L.map.ny <= 0 || L.kend <= L.kbeg) return cudaSuccess;
     if (L.split) {  // one launch shape: 8 z-nodes per thread
         constexpr int ZPT = 8;
-        dim3 grid((L.map.nx + kTileX - 1) / kTileX, (L.map.ny + kTileY - 1) / kTileY, (L.map.nz + ZPT - 1) / ZPT);
+        dim3 grid((L.map.nx + kTileX - 1) / kTileX, (L.map.ny + kTileY - 1) / kTileY, (L.kend - L.kbeg + ZPT - 1) / ZPT);
         with_flags(L.min_image != 0, L.coul_rc > 0.f, L.kQzz != 0.f, [&](auto mi, auto cut, auto quad) {
             constexpr bool MI = decltype(mi)::value, CUT = decltype(cut)::value, QUAD = decltype(quad)::value;
             if (L.map.interp == 1) ff_assemble_kernel<ZPT, MI, CUT, QUAD, true, true><<<grid, kThreads, 0, s>>>(L);
@@ -169,7 +169,7 @@ cudaError_t launch_ff_assemble(const FFLaunch& L, cudaStream_t s) {
     }
     if (L.map.interp == 1) {
         constexpr int ZPT = 8;
-        dim3 grid((L.map.nx + kTileX - 1) / kTileX, (L.map.ny + kTileY - 1) / kTileY, (L.map.nz + ZPT - 1) / ZPT);
+        dim3 grid((L.map.nx + kTileX - 1) / kTileX, (L.map.ny + kTileY - 1) / kTileY, (L.kend - L.kbeg + ZPT - 1) / ZPT);
         with_flags(L.min_image != 0, L.coul_rc > 0.f, L.kQzz != 0.f, [&](auto mi, auto cut, auto quad) {
             ff_assemble_kernel<ZPT, decltype(mi)::value, decltype(cut)::value, decltype(quad)::value, true>
                 <<<grid, kThreads, 0, s>>>(L);

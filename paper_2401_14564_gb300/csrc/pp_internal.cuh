@@ -130,6 +130,7 @@ struct FFLaunch {
     int split;     // 1: point charges per unit probe charge into ffel / ffelE, the rest into ff / ffE
     float4* ffel;  // split, map.interp == 0
     float* ffelE;  // split, map.interp == 1
+    int kbeg, kend;  // node layers written: z index in [kbeg, kend) (0, nz for the whole grid)
 };
 cudaError_t launch_ff_assemble(const FFLaunch& L, cudaStream_t s);
 // out = a + Q b over nfloats floats (16-byte aligned buffers; out may alias a)
@@ -157,6 +158,7 @@ struct RelaxLaunch {
     int* iters;
     int df_m;      // -1: no fused df
     float* df;
+    int* zspan;    // nullable: [0] lowest, [1] highest node layer an interpolation read (atomic min / max)
     float coef[2 * kMaxDfHalfWidth + 1];
 };
 cudaError_t launch_relax_scan(const RelaxLaunch& L, cudaStream_t s);

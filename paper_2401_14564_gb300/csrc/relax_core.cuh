@@ -128,6 +128,14 @@ __device__ __forceinline__ bool solve3(const float J[3][3], float3 b, float3& x)
     return true;
 }
 
+// Widens [lo, hi] to the node layers a lookup in cell c reads: the cell's two layers (trilinear), or
+// the four of its stencil, clamped into the grid (tricubic).
+template <bool kTricubic>
+__device__ __forceinline__ void note_layers(const Cells& c, int nz, int& lo, int& hi) {
+    lo = min(lo, kTricubic ? max(c.z.i0 - 1, 0) : c.z.i0);
+    hi = max(hi, kTricubic ? min(c.z.i1 + 1, nz - 1) : c.z.i1);
+}
+
 // One lane's pixel column (i, j) of an 8x4 pixel tile: all heights, FIRE per
 // height, outputs, and the fused df epilogue.  Each lane loops until its own
 // column is done; the lanes of a warp still issue together while they are in
@@ -141,10 +149,12 @@ __device__ __forceinline__ bool solve3(const float J[3][3], float3 b, float3& x)
 // trilinear force grid.  kPolish adds, where FIRE stopped below ftol, up to
 // Q.polish Newton steps p <- p - J^{-1} G with the exact Jacobian (springs +
 // interpolant), each kept only if it lowers |G| (the equilibrium the implicit
-// adjoint differentiates, to the FP32 resolution of G).
+// adjoint differentiates, to the FP32 resolution of G).  kSpan: returns the lowest and highest node
+// layer this lane's lookups read ((INT_MAX, INT_MIN) for a lane outside the scan, and always without
+// kSpan).
 template <int LAYOUT, bool kCoherent, bool kTricubic = false, bool kWarpVote = false, bool kPolish = false,
-          class G_t, class Q_t>
-__device__ __forceinline__ void relax_pixel(const G_t& P, const Q_t& Q, int i, int j) {
+          bool kSpan = false, class G_t, class Q_t>
+__device__ __forceinline__ int2 relax_pixel(const G_t& P, const Q_t& Q, int i, int j) {
     const bool valid = (i < P.snx) && (j < P.sny);
     const int npix = P.snx * P.sny;
     const int pix = j * P.snx + i;
@@ -162,6 +172,7 @@ __device__ __forceinline__ void relax_pixel(const G_t& P, const Q_t& Q, int i, i
     float4 cv[8];
     float ec[kTricubic ? 64 : 1];  // tricubic: the cached stencil energies
     int cell_x = -1, cell_y = -1, cell_z = -1;
+    int zlo = 0x7fffffff, zhi = -0x7fffffff - 1;
     Height hk = height_first(P);
     while (kWarpVote ? __any_sync(0xffffffffu, active) : active) {
         if (kWarpVote && !active) continue;
@@ -172,6 +183,7 @@ __device__ __forceinline__ void relax_pixel(const G_t& P, const Q_t& Q, int i, i
             // the 64 stencil energies stay in registers until the PP changes cell
             if (cl.x.i0 != cell_x || cl.y.i0 != cell_y || cl.z.i0 != cell_z) {
                 tricubic_load(P.ffE, P.map, cl, P.periodic_xy, ec);
+                if constexpr (kSpan) note_layers<true>(cl, P.map.nz, zlo, zhi);
                 cell_x = cl.x.i0;
                 cell_y = cl.y.i0;
                 cell_z = cl.z.i0;
@@ -180,6 +192,7 @@ __device__ __forceinline__ void relax_pixel(const G_t& P, const Q_t& Q, int i, i
         } else {
             if (cl.x.i0 != cell_x || cl.y.i0 != cell_y || cl.z.i0 != cell_z) {
                 load_corners<LAYOUT, kCoherent>(P.ff, P.map, cl, cv);
+                if constexpr (kSpan) note_layers<false>(cl, P.map.nz, zlo, zhi);
                 cell_x = cl.x.i0;
                 cell_y = cl.y.i0;
                 cell_z = cl.z.i0;
@@ -211,6 +224,7 @@ __device__ __forceinline__ void relax_pixel(const G_t& P, const Q_t& Q, int i, i
                         if constexpr (kTricubic) {
                             if (ct.x.i0 != cell_x || ct.y.i0 != cell_y || ct.z.i0 != cell_z) {
                                 tricubic_load(P.ffE, P.map, ct, P.periodic_xy, ec);
+                                if constexpr (kSpan) note_layers<true>(ct, P.map.nz, zlo, zhi);
                                 cell_x = ct.x.i0;
                                 cell_y = ct.y.i0;
                                 cell_z = ct.z.i0;
@@ -219,6 +233,7 @@ __device__ __forceinline__ void relax_pixel(const G_t& P, const Q_t& Q, int i, i
                         } else {
                             if (ct.x.i0 != cell_x || ct.y.i0 != cell_y || ct.z.i0 != cell_z) {
                                 load_corners<LAYOUT, kCoherent>(P.ff, P.map, ct, cv);
+                                if constexpr (kSpan) note_layers<false>(ct, P.map.nz, zlo, zhi);
                                 cell_x = ct.x.i0;
                                 cell_y = ct.y.i0;
                                 cell_z = ct.z.i0;
@@ -303,6 +318,7 @@ __device__ __forceinline__ void relax_pixel(const G_t& P, const Q_t& Q, int i, i
             P.df[checked((c - m) * npix + pix, (long long)npix * (P.snz - 2 * m), kChkScanWrite)] = acc;
         }
     }
+    return make_int2(zlo, zhi);
 }
 
 

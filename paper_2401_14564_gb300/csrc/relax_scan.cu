@@ -71,34 +71,48 @@ __device__ __forceinline__ void prefetch_tile_slab(const RelaxLaunch& P, int tx,
     }
 }
 
-template <int LAYOUT, bool kPolish>
+// The warp's lowest and highest node layer read, folded into P.zspan by lane 0 (all 32 lanes call).
+__device__ __forceinline__ void record_zspan(const RelaxLaunch& P, int2 span) {
+    const int lo = __reduce_min_sync(0xffffffffu, span.x);
+    const int hi = __reduce_max_sync(0xffffffffu, span.y);
+    if (threadIdx.x == 0) {
+        atomicMin(P.zspan, lo);
+        atomicMax(P.zspan + 1, hi);
+    }
+}
+
+// kSpan: P.zspan is set and receives the node layers the lookups read.
+template <int LAYOUT, bool kPolish, bool kSpan>
 __global__ void __launch_bounds__(kThreads) relax_scan_kernel(const RelaxLaunch P) {
     if (LAYOUT == 0) prefetch_tile_slab(P, blockIdx.x, blockIdx.y, threadIdx.x);
-    relax_pixel<LAYOUT, false, false, false, kPolish>(P, P, blockIdx.x * kTileX + (threadIdx.x & 7),
-                                                      blockIdx.y * kTileY + (threadIdx.x >> 3));
+    const int2 span = relax_pixel<LAYOUT, false, false, false, kPolish, kSpan>(
+        P, P, blockIdx.x * kTileX + (threadIdx.x & 7), blockIdx.y * kTileY + (threadIdx.x >> 3));
+    if constexpr (kSpan) record_zspan(P, span);
 }
 
 // Tricubic energy grid (linear layout).
-template <bool kPolish>
+template <bool kPolish, bool kSpan>
 __global__ void __launch_bounds__(kThreads) relax_scan_tricubic_kernel(const RelaxLaunch P) {
     prefetch_tile_slab(P, blockIdx.x, blockIdx.y, threadIdx.x);
-    relax_pixel<0, false, true, false, kPolish>(P, P, blockIdx.x * kTileX + (threadIdx.x & 7),
-                                                blockIdx.y * kTileY + (threadIdx.x >> 3));
+    const int2 span = relax_pixel<0, false, true, false, kPolish, kSpan>(
+        P, P, blockIdx.x * kTileX + (threadIdx.x & 7), blockIdx.y * kTileY + (threadIdx.x >> 3));
+    if constexpr (kSpan) record_zspan(P, span);
 }
 
-template <bool kPolish>
+template <bool kPolish, bool kSpan>
 void launch_relax_scan_t(const RelaxLaunch& L, dim3 grid, cudaStream_t s) {
-    if (L.map.interp == 1) relax_scan_tricubic_kernel<kPolish><<<grid, kThreads, 0, s>>>(L);
-    else if (L.layout == 0) relax_scan_kernel<0, kPolish><<<grid, kThreads, 0, s>>>(L);
-    else relax_scan_kernel<1, kPolish><<<grid, kThreads, 0, s>>>(L);
+    if (L.map.interp == 1) relax_scan_tricubic_kernel<kPolish, kSpan><<<grid, kThreads, 0, s>>>(L);
+    else if (L.layout == 0) relax_scan_kernel<0, kPolish, kSpan><<<grid, kThreads, 0, s>>>(L);
+    else relax_scan_kernel<1, kPolish, kSpan><<<grid, kThreads, 0, s>>>(L);
 }
 
 }  // namespace
 
 cudaError_t launch_relax_scan(const RelaxLaunch& L, cudaStream_t s) {
     dim3 grid((L.snx + kTileX - 1) / kTileX, (L.sny + kTileY - 1) / kTileY, 1);
-    if (L.polish > 0) launch_relax_scan_t<true>(L, grid, s);
-    else launch_relax_scan_t<false>(L, grid, s);
+    const bool span = L.zspan != nullptr;
+    if (L.polish > 0) span ? launch_relax_scan_t<true, true>(L, grid, s) : launch_relax_scan_t<true, false>(L, grid, s);
+    else span ? launch_relax_scan_t<false, true>(L, grid, s) : launch_relax_scan_t<false, false>(L, grid, s);
     return cudaGetLastError();
 }
 

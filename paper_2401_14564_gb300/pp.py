@@ -119,6 +119,9 @@ def lib():
             L.pp_make_ff_tuned.argtypes = [C.POINTER(Atoms), C.POINTER(Probe), C.POINTER(Grid), vp,
                                            C.POINTER(Tuning), vp]
             L.pp_make_ff_tuned.restype = st
+            L.pp_make_ff_layers.argtypes = [C.POINTER(Atoms), C.POINTER(Probe), C.POINTER(Grid), vp,
+                                            C.POINTER(Tuning), C.c_int, C.c_int, vp]
+            L.pp_make_ff_layers.restype = st
             L.pp_make_ff_split.argtypes = [C.POINTER(Atoms), C.POINTER(Probe), C.POINTER(Grid), vp, vp, vp]
             L.pp_make_ff_split.restype = st
             L.pp_ff_combine.argtypes = [vp, vp, C.c_float, C.POINTER(Grid), vp, vp]
@@ -126,6 +129,9 @@ def lib():
             L.pp_relax_scan.argtypes = [vp, C.POINTER(Grid), C.POINTER(Scan), C.POINTER(Tip), C.POINTER(Fire),
                                         vp, vp, vp, C.POINTER(DF), vp, vp]
             L.pp_relax_scan.restype = st
+            L.pp_relax_scan_zspan.argtypes = [vp, C.POINTER(Grid), C.POINTER(Scan), C.POINTER(Tip), C.POINTER(Fire),
+                                              vp, vp, vp, C.POINTER(DF), vp, vp, vp]
+            L.pp_relax_scan_zspan.restype = st
             L.pp_fz_to_df.argtypes = [vp, C.c_int, C.c_int, C.c_float, C.POINTER(DF), vp, vp]
             L.pp_fz_to_df.restype = st
             L.pp_ff_convert.argtypes = [vp, C.POINTER(Grid), vp, C.POINTER(Grid), vp]
@@ -260,6 +266,16 @@ def pp_make_ff_tuned(atoms: Atoms, probe: Probe, grid: Grid, ff: torch.Tensor, t
                                   C.byref(tuning) if tuning is not None else None, _stream(stream)))
 
 
+def pp_make_ff_layers(atoms: Atoms, probe: Probe, grid: Grid, ff: torch.Tensor, k_begin: int, k_end: int,
+                      tuning=None, stream=None):
+    """Node layers k_begin <= k < k_end of the grid (the values pp_make_ff_tuned writes there)."""
+    if ff.numel() < pp_ff_floats(grid):
+        raise ValueError("ff buffer smaller than pp_ff_floats(grid)")
+    _check(lib().pp_make_ff_layers(C.byref(atoms), C.byref(probe), C.byref(grid), _dev(ff, "ff"),
+                                   C.byref(tuning) if tuning is not None else None, int(k_begin), int(k_end),
+                                   _stream(stream)))
+
+
 def pp_make_ff_split(atoms: Atoms, probe: Probe, grid: Grid, ff: torch.Tensor, ff_el: torch.Tensor, stream=None):
     """LJ (+ quadrupole) into ff, point-charge electrostatics per unit probe charge into ff_el."""
     n = pp_ff_floats(grid)
@@ -279,7 +295,9 @@ def pp_ff_combine(ff: torch.Tensor, ff_el: torch.Tensor, Q: float, grid: Grid, o
 
 
 def pp_relax_scan(ff, grid: Grid, scan: Scan, tip: Tip, fire: Fire, pos, fz, iters, fused_df=None, df=None,
-                  stream=None):
+                  stream=None, zspan=None):
+    """zspan: a device int32 tensor of 2 elements to receive the lowest and highest node layer the scan's
+    interpolations read (pp_relax_scan_zspan), else None (pp_relax_scan)."""
     npx = scan.nx * scan.ny * scan.nz
     if fz.numel() < npx or (pos is not None and pos.numel() < 3 * npx) or (iters is not None and iters.numel() < npx):
         raise ValueError("output buffer too small for the scan")
@@ -289,11 +307,15 @@ def pp_relax_scan(ff, grid: Grid, scan: Scan, tip: Tip, fire: Fire, pos, fz, ite
         m = pp_df_margin(fused_df.A_pp, scan.dz)
         if m >= 0 and df.numel() < (scan.nz - 2 * m) * scan.nx * scan.ny:
             raise ValueError("df buffer too small")
-    _check(lib().pp_relax_scan(_dev(ff, "ff"), C.byref(grid), C.byref(scan), C.byref(tip), C.byref(fire),
-                               _dev(pos, "pos", allow_none=True), _dev(fz, "fz"),
-                               _dev(iters, "iters", torch.int32, allow_none=True),
-                               C.byref(fused_df) if fused_df is not None else None,
-                               _dev(df, "df", allow_none=True), _stream(stream)))
+    args = (_dev(ff, "ff"), C.byref(grid), C.byref(scan), C.byref(tip), C.byref(fire),
+            _dev(pos, "pos", allow_none=True), _dev(fz, "fz"), _dev(iters, "iters", torch.int32, allow_none=True),
+            C.byref(fused_df) if fused_df is not None else None, _dev(df, "df", allow_none=True))
+    if zspan is None:
+        _check(lib().pp_relax_scan(*args, _stream(stream)))
+    else:
+        if zspan.numel() < 2:
+            raise ValueError("zspan needs two ints")
+        _check(lib().pp_relax_scan_zspan(*args, _dev(zspan, "zspan", torch.int32), _stream(stream)))
 
 
 def pp_fz_to_df(fz, nz: int, npix: int, dz: float, df_params: DF, df, stream=None):

@@ -258,3 +258,38 @@ def test_grid_axis_limit(L):
     bad = pp.make_grid({"nx": (1 << 22) + 1, "ny": 2, "nz": 2, "x0": 0, "y0": 0, "z0": 0, "dx": 0.1, "dy": 0.1,
                         "dz": 0.1, "periodic_xy": 1})
     assert pp.pp_ff_floats(bad) == 0
+
+
+def test_ff_layers_and_zspan_validated_on_host(L):
+    fake = C.c_void_p(256)  # never dereferenced: a host check fails first
+    atoms = pp.Atoms(0, None, None, None, None, None, None)
+    probe = pp.make_probe({"R_pp": 1.66, "eps_pp": 0.0091, "Q": -0.1, "coul_rc": 0.0, "min_image": 0,
+                           "core_frac": 0.5})
+    g = pp.make_grid({"nx": 10, "ny": 6, "nz": 5, "x0": 0, "y0": 0, "z0": 0, "dx": 0.1, "dy": 0.1, "dz": 0.1,
+                      "periodic_xy": 1})
+    for k0, k1 in ((-1, 3), (2, 2), (3, 2), (0, 6)):
+        assert L.pp_make_ff_layers(C.byref(atoms), C.byref(probe), C.byref(g), fake, None, k0, k1, None) == 1
+        assert b"k_begin" in L.pp_last_error()
+    assert L.pp_make_ff_layers(None, C.byref(probe), C.byref(g), fake, None, 0, 2, None) == 1
+    assert b"NULL" in L.pp_last_error()
+    assert L.pp_make_ff_layers(C.byref(atoms), C.byref(probe), C.byref(g), fake, C.byref(pp.Tuning(5, 0)), 0, 2,
+                               None) == 1
+    bad = pp.make_grid({"nx": 1, "ny": 6, "nz": 5, "x0": 0, "y0": 0, "z0": 0, "dx": 0.1, "dy": 0.1, "dz": 0.1,
+                        "periodic_xy": 1})
+    assert L.pp_make_ff_layers(C.byref(atoms), C.byref(probe), C.byref(bad), fake, None, 0, 2, None) == 2
+
+    scan = pp.make_scan({"nx": 4, "ny": 4, "nz": 12, "x0": 0.0, "y0": 0.0, "px": 0.1, "py": 0.1, "z_top": 0.3,
+                         "dz": 0.1})
+    tip = pp.make_tip({"kx": 0.25, "ky": 0.25, "kR": 20.0, "R0": 4.0, "d0x": 0.0, "d0y": 0.0})
+    from paper_2401_14564_gb300 import synth
+
+    fire = pp.make_fire(synth.default_fire())
+    args = (fake, C.byref(g), C.byref(scan), C.byref(tip), C.byref(fire), fake, fake, fake, None, None)
+    assert L.pp_relax_scan_zspan(*args, None, None) == 1
+    assert b"zspan" in L.pp_last_error()
+    assert L.pp_relax_scan_zspan(*args, C.c_void_p(258), None) == 1     # not 4-byte aligned
+    assert b"aligned" in L.pp_last_error()
+    fire_bad = pp.make_fire(synth.default_fire(polish=-1))
+    assert L.pp_relax_scan_zspan(fake, C.byref(g), C.byref(scan), C.byref(tip), C.byref(fire_bad), fake, fake, fake,
+                                 None, None, fake, None) == 1            # pp_relax_scan's own checks follow
+    assert b"pp_relax_scan_zspan: invalid FIRE" in L.pp_last_error()
