@@ -2,8 +2,9 @@
 workload family runs on libpp_checked.so, whose kernels test each global gather and scatter
 index against the size of its array and record a bit when one falls outside; none may fire.
 
-Covered: the flake60 step (K1, K2 with fused df, K9, K3/K4/K5 adjoint) on the force grid and on
-a 0.2 A tricubic energy grid; a bricked-layout case with the layout converter and the
+Covered: the flake60 step (K1, K2 with fused df, K9, K3/K4/K5 adjoint, and the host-array call
+with K1 on node-layer ranges beside the layer-reporting K2) on the force grid and on a 0.2 A
+tricubic energy grid; a bricked-layout case with the layout converter and the
 standalone df kernel; the quadrupole with minimum image and a Coulomb cutoff; the split force
 field and its recombination; FFT correlations with a ragged shape and a 1024-long axis; a
 batched launch of ragged molecules, also with other work-item shapes; the scan with the Newton
@@ -49,6 +50,7 @@ def step(c, **kw):
     sim.run(at)
     iets(sim)
     backward(c, sim, at)
+    sim.run_host(c["atoms"])  # the force field in parts beside the layer-reporting scan
     return sim
 
 flake = synth.flake_case()
