@@ -110,8 +110,10 @@ def test_zspan_covers_every_layer_the_scan_reads(interp, polish):
         assert torch.equal(a, b)
 
 
-def test_run_host_overlapped_equals_one_stage_path():
+@pytest.mark.parametrize("interp", [0, 1])
+def test_run_host_overlapped_equals_one_stage_path(interp):
     c = tall_case(seed=9)
+    c["grid"] = dict(c["grid"], interp=interp)
     items = []
     for t in range(4):
         a = copy.deepcopy(c["atoms"])
