@@ -362,6 +362,22 @@ def run_reference(args, rank, world):
     return 0
 
 
+PLAN_FRAC, PLAN_LANES = 0.025, 4  # the scan plan's share of pixel columns and lanes per warp
+
+
+def neighbour_case(case, seed=77, shift=0.05, dq=0.1):
+    """The case with every atom moved by up to `shift` A per axis and every charge scaled by up to
+    1 +- dq (seeded): the input the scan's pixel-to-warp plan is built from."""
+    rng = np.random.default_rng(seed)
+    atoms = dict(case["atoms"])
+    for k in ("x", "y", "z"):
+        v = np.asarray(atoms[k], dtype=np.float64)
+        atoms[k] = v + rng.uniform(-shift, shift, size=v.shape)
+    q = np.asarray(atoms["q"], dtype=np.float64)
+    atoms["q"] = q * (1.0 + rng.uniform(-dq, dq, size=q.shape))
+    return dict(case, atoms=atoms)
+
+
 def workload_config(case, ff_energy=False):
     g, s = case["grid"], case["scan"]
     return {"workload": "flake60: 60-atom H-terminated aromatic flake (seed 42), FF grid 256x256x200 at 0.1 A, "
@@ -901,7 +917,7 @@ def main():
 
     import torch
 
-    from paper_2401_14564_gb300 import afm, synth
+    from paper_2401_14564_gb300 import afm, pp, synth
     from paper_2401_14564_gb300 import dist as ppd
 
     torch.cuda.set_device(local)
@@ -933,6 +949,14 @@ def main():
     pipe = afm.Pipeline(case, slots=4, layout=args.layout, tuning=tuning, ff_energy=args.ff_energy)
     sim = pipe.sims[0]
     atoms = afm.atoms_to_device(case["atoms"])
+    # iteration counts of a neighbouring input, for the scan's pixel-to-warp plan timed below (the
+    # headline steps run without a plan: with several steps in flight the issue slots, not the
+    # slowest tile, bound the step, and a plan's narrow warps cost more slots than they save)
+    plan_src = neighbour_case(case)
+    nsim = afm.Simulator(plan_src, layout=args.layout, tuning=tuning, ff_energy=args.ff_energy, plan_frac=0.0)
+    nsim.run(afm.atoms_to_device(plan_src["atoms"]))
+    neighbour_iters = nsim.iters
+    torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB
     s = case["scan"]
@@ -995,6 +1019,55 @@ def main():
             t += a.elapsed_time(b)
         ov_ms.append(t)
     ms_step_ov = ppd.max_over_ranks(statistics.mean(ov_ms))
+
+    # K2 alone on the same grid under three schedules: 8x4 tiles only (the steps above), a plan
+    # built from the neighbouring input's scan, and one from this very input's earlier scan
+    def time_relax(reps=20):
+        for _ in range(3):
+            sim.relax(stream)
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            sim.relax(stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    relax_sched = {"no_plan": time_relax()}
+    sim.plan_frac, sim.plan_lanes, sim.auto_plan = PLAN_FRAC, PLAN_LANES, False
+    sim.plan_from(neighbour_iters, stream)
+    relax_sched["neighbour_plan"] = time_relax()
+    sim.plan_from(sim.iters, stream)
+    relax_sched["own_plan"] = time_relax()
+    plan_cols = sim._plan_k
+    sim.drop_plan()
+    # a series of scans of one grid for five lateral tip stiffnesses (the force field is not rebuilt):
+    # with auto_plan each scan runs on the plan of the previous stiffness's scan
+    tip0 = sim.tip
+    series = {}
+    for planned in (False, True):
+        sim.plan_frac, sim.auto_plan = (PLAN_FRAC if planned else 0.0), planned
+        sim.drop_plan()
+        ts = []
+        for rep in range(2):
+            for kxy in (0.20, 0.225, 0.25, 0.275, 0.30):
+                sim.tip = pp.make_tip(dict(case["tip"], kx=kxy, ky=kxy))
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                sim.relax(stream)
+                b.record(stream)
+                torch.cuda.synchronize()
+                if rep == 1:
+                    ts.append(a.elapsed_time(b))
+        series["planned" if planned else "no_plan"] = statistics.mean(ts)
+    sim.tip = tip0
+    sim.drop_plan()
+    sim.plan_frac, sim.auto_plan = 0.0, True
+    torch.cuda.synchronize()
     clocks.end()
     barrier()
     clk = clocks.stop()
@@ -1063,7 +1136,17 @@ def main():
                        "traffic": measured_traffic("relax_scan"), "gather_gbs": rx_gbs,
                        "l2_peak_gbs": l2["peak_gbs"], "frac_of_l2": rx_gbs / l2["peak_gbs"],
                        "hbm_peak_gbs": peaks["hbm_gbs"], "frac_of_hbm": rx_gbs / peaks["hbm_gbs"],
-                       "issue_active": measured_issue("relax_scan")},
+                       "issue_active": measured_issue("relax_scan"),
+                       "schedules_ms": relax_sched,
+                       "stiffness_series_ms": dict(series, note="mean scan time over kx = ky = 0.20 .. 0.30 N/m on "
+                                                   "one grid (second pass); planned: each scan on the plan its "
+                                                   "predecessor (another stiffness) built, plan time included"),
+                       "plan": {"columns": plan_cols, "lanes": PLAN_LANES,
+                                "neighbour": "the flake with its atoms moved by up to 0.05 A and its charges "
+                                             "scaled by up to 1 +- 0.1 (seeded)",
+                                "note": "ms and the roofline are the headline's schedule (no plan); a plan moves "
+                                        "the costliest pixel columns of an earlier scan into 4-lane warps, which "
+                                        "shortens a scan run alone but costs issue slots when steps overlap"}},
     }
     dom = "ff_assemble" if ff_ms >= rx_ms else "relax_scan"
     if dom == "ff_assemble":

@@ -254,21 +254,55 @@ PP_API pp_status pp_relax_scan(const float* ff, const pp_grid* grid, const pp_sc
                         float* pos, float* fz, int* iters,
                         const pp_df* fused_df, float* df, pp_stream stream);
 
-/* pp_relax_scan (the same outputs, bit for bit) that also reports which node
- * layers of the grid its interpolations read: zspan (DEVICE, two ints,
- * 4-byte aligned, caller-owned) receives the lowest and highest layer index k,
- * over every FIRE iteration and Newton step of every pixel (trilinear: the
- * two layers of each cell used; tricubic: the four stencil layers, clamped to
- * the grid).  The call initialises zspan on the stream itself.  So a scan
- * whose layers lie inside those already assembled read nothing else: the
- * check a caller makes after overlapping the scan with pp_make_ff_layers of
- * the other layers (and, if it fails, runs the scan again on the complete
- * grid).  The paper has no counterpart.  Errors as pp_relax_scan, plus
- * PP_ERR_ARG for a NULL or unaligned zspan. */
-PP_API pp_status pp_relax_scan_zspan(const float* ff, const pp_grid* grid, const pp_scan* scan,
-                                     const pp_tip* tip, const pp_fire* fire,
-                                     float* pos, float* fz, int* iters,
-                                     const pp_df* fused_df, float* df, int* zspan, pp_stream stream);
+/* Options of pp_relax_scan_ex (neither changes an output bit; the paper has
+ * no counterpart to either).
+ *   zspan  DEVICE int[2] (4-byte aligned, caller-owned) or NULL: receives the
+ *          lowest and highest node layer k the scan's interpolations read,
+ *          over every FIRE iteration and Newton step of every pixel
+ *          (trilinear: the two layers of each cell used; tricubic: the four
+ *          stencil layers, clamped to the grid); the call initialises it on
+ *          the stream.  A scan whose layers lie inside those already assembled
+ *          read nothing else: the check a caller makes after overlapping the
+ *          scan with pp_make_ff_layers of the other layers (and, if it fails,
+ *          runs the scan again on the complete grid).
+ *   plan   DEVICE pixel-to-warp plan from pp_relax_plan for a scan of the same
+ *          nx and ny, built with plan_k and plan_lanes, or NULL: the plan's
+ *          pixels run in warps of plan_lanes lanes ahead of the 8x4 pixel
+ *          tiles, which skip them.  A stale plan (another image's) costs time,
+ *          never correctness. */
+typedef struct {
+    int* zspan;
+    const int* plan;
+    int plan_k;
+    int plan_lanes;
+} pp_scan_opts;
+
+/* pp_relax_scan with the options above: the same outputs, bit for bit.
+ * Errors as pp_relax_scan, plus PP_ERR_ARG for a NULL opts, an unaligned
+ * zspan or plan, plan_k outside [1, nx*ny] or plan_lanes outside [1, 32]. */
+PP_API pp_status pp_relax_scan_ex(const float* ff, const pp_grid* grid, const pp_scan* scan,
+                                  const pp_tip* tip, const pp_fire* fire,
+                                  float* pos, float* fz, int* iters,
+                                  const pp_df* fused_df, float* df, const pp_scan_opts* opts,
+                                  pp_stream stream);
+
+/* Bytes of a pixel-to-warp plan for a scan of nx x ny pixels (any nz): 0 when
+ * k is outside [1, nx*ny], lanes outside [1, 32] or the scan invalid. */
+PP_API size_t pp_relax_plan_size(const pp_scan* scan, int k, int lanes);
+
+/* Builds a plan in `plan` (DEVICE, 4-byte aligned, pp_relax_plan_size bytes)
+ * from an earlier scan's iteration counts iters[k][j][i] (DEVICE, the layout
+ * pp_relax_scan writes, nz heights; max_iter the FIRE limit it ran with): the
+ * cost of pixel column (i, j) is its FIRE updates summed over the heights,
+ * and the plan lists the k costliest columns (among equal costs at the
+ * boundary, any), to run `lanes` to a warp.  A K2 warp runs 32 columns until
+ * its slowest is done, and the other lanes' height changes and cell reloads
+ * hold that column up; columns of similar cost in narrow warps finish
+ * sooner.  Nothing of the paper's method changes: which warp computes a pixel
+ * never changes its value.  Errors: PP_ERR_ARG (NULL, unaligned, k, lanes or
+ * max_iter invalid), PP_ERR_SHAPE (scan sizes), PP_ERR_CUDA. */
+PP_API pp_status pp_relax_plan(const int* iters, const pp_scan* scan, int max_iter, int k, int lanes,
+                               void* plan, pp_stream stream);
 
 /* Frequency shift of Eq. df.  fz[k*npix + p] holds Fz (eV/A) at tip heights
  * z_k = z_top - k*dz; df[c*npix + p] (Hz), c = 0..nz-2m-1, is centred at

@@ -26,12 +26,16 @@ class Simulator:
     """Preallocated FF grid, positions, Fz, iteration counts and df for one case shape."""
 
     def __init__(self, case, layout=0, brick=(4, 4, 4), fire=None, device="cuda", fused_df=True,
-                 want_pos=True, want_iters=True, tuning=None, ff_energy=True, overlap_ff=True):
+                 want_pos=True, want_iters=True, tuning=None, ff_energy=True, overlap_ff=True, plan_frac=0.025,
+                 plan_lanes=4, auto_plan=True):
         """tuning: an autotuner result ({"ff_zpt", "layout", "brick"}) overriding layout and brick.
         ff_energy=False: the grid's E slots are written as 0 and the energy sums skipped (the scan
         reads only the forces, which are unchanged); trilinear force grids only.
         overlap_ff: run_host assembles the node layers the scan will read first and the others on a
-        second stream while the scan runs (see run_overlapped); False: one stage after the other."""
+        second stream while the scan runs (see run_overlapped); False: one stage after the other.
+        plan_frac, plan_lanes: the pixel-to-warp plan of the scan (plan_from): that fraction of the
+        pixel columns, the costliest in an earlier scan, runs plan_lanes to a warp; 0 = never.
+        auto_plan: every scan builds the plan for the next from its own iteration counts."""
         self.case = case
         self.device = torch.device(device)
         if tuning is not None:
@@ -68,6 +72,12 @@ class Simulator:
         self._side = None    # second stream of the overlapped forward
         self._zspan_d = None
         self._zspan_h = None
+        self.plan_frac = float(plan_frac)
+        self.plan_lanes = int(plan_lanes)
+        self.auto_plan = bool(auto_plan)
+        self._plan = None
+        self._plan_k = 0
+        self._plan_ready = False
 
     def make_ff(self, atoms_dev, stream=None):
         if self.zpt is not None:
@@ -75,16 +85,38 @@ class Simulator:
         else:
             pp.pp_make_ff(pp.make_atoms(atoms_dev), self.probe, self.grid, self.ff, stream)
 
-    def relax(self, stream=None, df=None):
-        """Relaxed scan and df image (into `df`, default self.df)."""
+    def relax(self, stream=None, df=None, zspan=None):
+        """Relaxed scan and df image (into `df`, default self.df), with the pixel-to-warp plan when one
+        is held (see plan_from); with auto_plan, the plan for the next call is then built from this
+        scan's iteration counts."""
         out = self.df if df is None else df
-        if self.fused_df:
-            pp.pp_relax_scan(self.ff, self.grid, self.scan, self.tip, self.fire, self.pos, self.fz, self.iters,
-                             self.dfp, out, stream)
-        else:
-            pp.pp_relax_scan(self.ff, self.grid, self.scan, self.tip, self.fire, self.pos, self.fz, self.iters,
-                             None, None, stream)
+        plan = (self._plan, self._plan_k, self.plan_lanes) if self._plan_ready else None
+        pp.pp_relax_scan(self.ff, self.grid, self.scan, self.tip, self.fire, self.pos, self.fz, self.iters,
+                         self.dfp if self.fused_df else None, out if self.fused_df else None, stream,
+                         zspan=zspan, plan=plan)
+        if not self.fused_df:
             pp.pp_fz_to_df(self.fz, self.scan.nz, self.scan.nx * self.scan.ny, self.scan.dz, self.dfp, out, stream)
+        if self.auto_plan and self.iters is not None:
+            self.plan_from(self.iters, stream)
+
+    # ---- pixel-to-warp plan of the scan
+    def plan_from(self, iters, stream=None):
+        """Builds the plan the next scans use from iteration counts of an earlier scan of this shape
+        (this simulator's own, or another image's, e.g. a neighbouring geometry): the plan_frac
+        costliest pixel columns run plan_lanes to a warp.  Outputs never depend on it."""
+        if self.plan_frac <= 0:
+            return
+        if self._plan is None:
+            npix = self.scan.nx * self.scan.ny
+            self._plan_k = max(1, min(npix, int(round(self.plan_frac * npix))))
+            n = pp.pp_relax_plan_size(self.scan, self._plan_k, self.plan_lanes)
+            self._plan = torch.empty((n + 3) // 4, dtype=torch.int32, device=self.device)
+        pp.pp_relax_plan(iters, self.scan, self.fire.max_iter, self._plan_k, self.plan_lanes, self._plan, stream)
+        self._plan_ready = True
+
+    def drop_plan(self):
+        """Scans go back to 8x4 pixel tiles alone (until the next plan_from)."""
+        self._plan_ready = False
 
     def run(self, atoms_dev, stream=None, df=None):
         """Device-resident forward pass; returns the df tensor (device)."""
@@ -134,11 +166,7 @@ class Simulator:
             self._ff_layers(atoms, k1, nz, self._side)
         if k0 > 0:
             self._ff_layers(atoms, 0, k0, self._side)
-        pp.pp_relax_scan(self.ff, self.grid, self.scan, self.tip, self.fire, self.pos, self.fz, self.iters,
-                         self.dfp if self.fused_df else None, self.df if self.fused_df else None, st,
-                         zspan=self._zspan_d)
-        if not self.fused_df:
-            pp.pp_fz_to_df(self.fz, self.scan.nz, self.scan.nx * self.scan.ny, self.scan.dz, self.dfp, self.df, st)
+        self.relax(st, zspan=self._zspan_d)
         with torch.cuda.stream(st):
             self._zspan_h.copy_(self._zspan_d, non_blocking=True)
         rest = torch.cuda.Event()
@@ -302,6 +330,10 @@ class Pipeline:
     def __init__(self, case, slots=4, **sim_kwargs):
         if slots < 1:
             raise ValueError("Pipeline needs at least one slot")
+        # no scan plan unless asked: with items in flight the issue slots bound a step, and a plan's
+        # narrow warps cost more of them than the shorter slowest tile saves (flake60, 4 slots:
+        # 0.739 ms per step without, 0.757-0.809 ms with plans of 1-5 % of the columns, 4-16 lanes)
+        sim_kwargs.setdefault("plan_frac", 0.0)
         self.sims = [Simulator(case, **sim_kwargs) for _ in range(slots)]
         self.streams = [torch.cuda.Stream() for _ in range(slots)]
         self._host = None

@@ -304,10 +304,11 @@ static bool check_tip_fire(const pp_tip* tip, const pp_fire* fire, std::string* 
     return true;
 }
 
-// pp_relax_scan, and pp_relax_scan_zspan when zspan is given (checked by the caller).
+// pp_relax_scan, and pp_relax_scan_ex with its options (checked by the caller).
 static pp_status relax_scan_impl(const char* name, const float* ff, const pp_grid* grid, const pp_scan* scan,
                                  const pp_tip* tip, const pp_fire* fire, float* pos, float* fz, int* iters,
-                                 const pp_df* fused_df, float* df, int* zspan, pp_stream stream) {
+                                 const pp_df* fused_df, float* df, int* zspan, const pp_scan_opts* opts,
+                                 pp_stream stream) {
     const std::string who(name);
     if (!ff || !grid || !scan || !tip || !fire || !fz) { set_error(who + ": NULL argument"); return PP_ERR_ARG; }
     if (!aligned16(ff)) { set_error(who + ": ff must be 16-byte aligned"); return PP_ERR_ARG; }
@@ -369,6 +370,14 @@ static pp_status relax_scan_impl(const char* name, const float* ff, const pp_gri
         df_stencil(fused_df->A_pp, scan->dz, fused_df->k, fused_df->f0, m, L.coef);
     }
     L.zspan = zspan;
+    if (opts && opts->plan) {
+        const int npix = scan->nx * scan->ny;
+        const int* plan = static_cast<const int*>(opts->plan);
+        L.plan_list = plan + relax_plan_list_offset(npix);
+        L.plan_mask = reinterpret_cast<const unsigned*>(plan + relax_plan_mask_offset(npix, opts->plan_k, opts->plan_lanes));
+        L.plan_lanes = opts->plan_lanes;
+        L.plan_hblocks = (opts->plan_k + opts->plan_lanes - 1) / opts->plan_lanes;
+    }
     if (zspan) {
         // (INT_MAX, INT_MIN) before the scan folds its lanes' layers in by atomic min / max
         for (int h = 0; h < 2; ++h) {
@@ -385,18 +394,61 @@ pp_status pp_relax_scan(const float* ff, const pp_grid* grid, const pp_scan* sca
                         pp_stream stream) {
     Range range("pp_relax_scan");
     g_error.clear();
-    return relax_scan_impl("pp_relax_scan", ff, grid, scan, tip, fire, pos, fz, iters, fused_df, df, nullptr, stream);
+    return relax_scan_impl("pp_relax_scan", ff, grid, scan, tip, fire, pos, fz, iters, fused_df, df, nullptr, nullptr,
+                           stream);
 }
 
-pp_status pp_relax_scan_zspan(const float* ff, const pp_grid* grid, const pp_scan* scan, const pp_tip* tip,
-                              const pp_fire* fire, float* pos, float* fz, int* iters, const pp_df* fused_df,
-                              float* df, int* zspan, pp_stream stream) {
-    Range range("pp_relax_scan_zspan");
+pp_status pp_relax_scan_ex(const float* ff, const pp_grid* grid, const pp_scan* scan, const pp_tip* tip,
+                           const pp_fire* fire, float* pos, float* fz, int* iters, const pp_df* fused_df, float* df,
+                           const pp_scan_opts* opts, pp_stream stream) {
+    Range range("pp_relax_scan_ex");
     g_error.clear();
-    if (!zspan) { set_error("pp_relax_scan_zspan: NULL zspan"); return PP_ERR_ARG; }
-    if (((uintptr_t)zspan & 3u) != 0) { set_error("pp_relax_scan_zspan: zspan must be 4-byte aligned"); return PP_ERR_ARG; }
-    return relax_scan_impl("pp_relax_scan_zspan", ff, grid, scan, tip, fire, pos, fz, iters, fused_df, df, zspan,
-                           stream);
+    const char* who = "pp_relax_scan_ex";
+    if (!opts) { set_error("pp_relax_scan_ex: NULL opts"); return PP_ERR_ARG; }
+    if (opts->zspan && ((uintptr_t)opts->zspan & 3u) != 0) {
+        set_error("pp_relax_scan_ex: zspan must be 4-byte aligned");
+        return PP_ERR_ARG;
+    }
+    if (opts->plan) {
+        if (((uintptr_t)opts->plan & 3u) != 0) { set_error("pp_relax_scan_ex: plan must be 4-byte aligned"); return PP_ERR_ARG; }
+        if (opts->plan_k < 1 || opts->plan_lanes < 1 || opts->plan_lanes > 32 || !scan ||
+            (int64_t)opts->plan_k > (int64_t)scan->nx * scan->ny) {
+            set_error("pp_relax_scan_ex: plan_k must be in [1, nx*ny] and plan_lanes in [1, 32]");
+            return PP_ERR_ARG;
+        }
+    }
+    return relax_scan_impl(who, ff, grid, scan, tip, fire, pos, fz, iters, fused_df, df, opts->zspan, opts, stream);
+}
+
+size_t pp_relax_plan_size(const pp_scan* scan, int k, int lanes) {
+    if (!scan || scan->nx < 1 || scan->ny < 1 || lanes < 1 || lanes > 32 || k < 1 ||
+        (int64_t)scan->nx * scan->ny >= (int64_t(1) << 30) || (int64_t)k > (int64_t)scan->nx * scan->ny)
+        return 0;
+    return relax_plan_words(scan->nx * scan->ny, k, lanes) * sizeof(int);
+}
+
+pp_status pp_relax_plan(const int* iters, const pp_scan* scan, int max_iter, int k, int lanes, void* plan,
+                        pp_stream stream) {
+    Range range("pp_relax_plan");
+    g_error.clear();
+    if (!iters || !scan || !plan) { set_error("pp_relax_plan: NULL argument"); return PP_ERR_ARG; }
+    if (((uintptr_t)plan & 3u) != 0 || ((uintptr_t)iters & 3u) != 0) {
+        set_error("pp_relax_plan: iters and plan must be 4-byte aligned");
+        return PP_ERR_ARG;
+    }
+    if (scan->nx < 1 || scan->ny < 1 || scan->nz < 1 ||
+        (int64_t)scan->nx * scan->ny * scan->nz * 3 >= (int64_t(1) << 31)) {
+        set_error("pp_relax_plan: invalid scan size");
+        return PP_ERR_SHAPE;
+    }
+    if (max_iter < 0) { set_error("pp_relax_plan: max_iter < 0"); return PP_ERR_ARG; }
+    if (pp_relax_plan_size(scan, k, lanes) == 0) {
+        set_error("pp_relax_plan: k must be in [1, nx*ny] and lanes in [1, 32]");
+        return PP_ERR_ARG;
+    }
+    return cuda_status(launch_relax_plan(iters, scan->nz, scan->nx * scan->ny, max_iter, k, lanes,
+                                         static_cast<int*>(plan), (cudaStream_t)stream),
+                       "pp_relax_plan launch");
 }
 
 pp_status pp_fz_to_df(const float* fz, int nz, int npix, float dz, const pp_df* dfp, float* df, pp_stream stream) {

@@ -159,6 +159,11 @@ struct RelaxLaunch {
     int df_m;      // -1: no fused df
     float* df;
     int* zspan;    // nullable: [0] lowest, [1] highest node layer an interpolation read (atomic min / max)
+    // nullable: a pixel-to-warp plan (relax_plan.cu): warps 0..plan_hblocks-1 run the listed pixels,
+    // plan_lanes lanes each; the tiles after them skip the pixels whose mask bit is set
+    const int* plan_list;
+    const unsigned* plan_mask;
+    int plan_hblocks, plan_lanes;
     float coef[2 * kMaxDfHalfWidth + 1];
 };
 cudaError_t launch_relax_scan(const RelaxLaunch& L, cudaStream_t s);
@@ -170,6 +175,16 @@ struct DfLaunch {
     float coef[2 * kMaxDfHalfWidth + 1];
 };
 cudaError_t launch_fz_to_df(const DfLaunch& L, cudaStream_t s);
+// Pixel-to-warp plan of the scan from an earlier scan's iteration counts (relax_plan.cu): buffer size in
+// int32 words, and its build on the stream (k heaviest columns, `lanes` per warp).
+size_t relax_plan_words(int npix, int k, int lanes);
+cudaError_t launch_relax_plan(const int* iters, int nz, int npix, int max_iter, int k, int lanes, int* plan,
+                              cudaStream_t s);
+// Offsets of the plan's pixel list and mask inside the buffer (int32 words).
+inline size_t relax_plan_list_offset(int npix) { return 8 + 2048 + (size_t)npix; }
+inline size_t relax_plan_mask_offset(int npix, int k, int lanes) {
+    return relax_plan_list_offset(npix) + (size_t)((k + lanes - 1) / lanes) * lanes;
+}
 
 struct BwdLaunch {
     // atoms and probe

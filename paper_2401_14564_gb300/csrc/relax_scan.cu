@@ -81,21 +81,58 @@ __device__ __forceinline__ void record_zspan(const RelaxLaunch& P, int2 span) {
     }
 }
 
+// This warp's pixel (i, j); i = snx marks an idle lane.  Without a plan: lane l of the 8x4 tile
+// (blockIdx.x, blockIdx.y).  With one (a 1-D grid): the first plan_hblocks warps take the plan's
+// listed pixels, plan_lanes lanes each (-1 or anything outside the scan: idle), and warp
+// plan_hblocks + t takes tile t less the listed pixels.  *tx < 0: no tile (no slab prefetch).
+__device__ __forceinline__ void scan_pixel(const RelaxLaunch& P, int& i, int& j, int& tx, int& ty) {
+    const int lane = threadIdx.x;
+    if (!P.plan_list) {
+        tx = blockIdx.x;
+        ty = blockIdx.y;
+        i = tx * kTileX + (lane & 7);
+        j = ty * kTileY + (lane >> 3);
+        return;
+    }
+    const int npix = P.snx * P.sny;
+    const int b = blockIdx.x;
+    if (b < P.plan_hblocks) {
+        tx = ty = -1;
+        int p = -1;
+        if (lane < P.plan_lanes) p = P.plan_list[b * P.plan_lanes + lane];
+        const bool ok = p >= 0 && p < npix;
+        i = ok ? p % P.snx : P.snx;
+        j = ok ? p / P.snx : P.sny;
+        return;
+    }
+    const int ntx = (P.snx + kTileX - 1) / kTileX, t = b - P.plan_hblocks;
+    tx = t % ntx;
+    ty = t / ntx;
+    i = tx * kTileX + (lane & 7);
+    j = ty * kTileY + (lane >> 3);
+    if (i < P.snx && j < P.sny) {
+        const int p = j * P.snx + i;
+        if ((P.plan_mask[p >> 5] >> (p & 31)) & 1u) i = P.snx;  // run by a plan warp
+    }
+}
+
 // kSpan: P.zspan is set and receives the node layers the lookups read.
 template <int LAYOUT, bool kPolish, bool kSpan>
 __global__ void __launch_bounds__(kThreads) relax_scan_kernel(const RelaxLaunch P) {
-    if (LAYOUT == 0) prefetch_tile_slab(P, blockIdx.x, blockIdx.y, threadIdx.x);
-    const int2 span = relax_pixel<LAYOUT, false, false, false, kPolish, kSpan>(
-        P, P, blockIdx.x * kTileX + (threadIdx.x & 7), blockIdx.y * kTileY + (threadIdx.x >> 3));
+    int i, j, tx, ty;
+    scan_pixel(P, i, j, tx, ty);
+    if (LAYOUT == 0 && tx >= 0) prefetch_tile_slab(P, tx, ty, threadIdx.x);
+    const int2 span = relax_pixel<LAYOUT, false, false, false, kPolish, kSpan>(P, P, i, j);
     if constexpr (kSpan) record_zspan(P, span);
 }
 
 // Tricubic energy grid (linear layout).
 template <bool kPolish, bool kSpan>
 __global__ void __launch_bounds__(kThreads) relax_scan_tricubic_kernel(const RelaxLaunch P) {
-    prefetch_tile_slab(P, blockIdx.x, blockIdx.y, threadIdx.x);
-    const int2 span = relax_pixel<0, false, true, false, kPolish, kSpan>(
-        P, P, blockIdx.x * kTileX + (threadIdx.x & 7), blockIdx.y * kTileY + (threadIdx.x >> 3));
+    int i, j, tx, ty;
+    scan_pixel(P, i, j, tx, ty);
+    if (tx >= 0) prefetch_tile_slab(P, tx, ty, threadIdx.x);
+    const int2 span = relax_pixel<0, false, true, false, kPolish, kSpan>(P, P, i, j);
     if constexpr (kSpan) record_zspan(P, span);
 }
 
@@ -110,6 +147,7 @@ void launch_relax_scan_t(const RelaxLaunch& L, dim3 grid, cudaStream_t s) {
 
 cudaError_t launch_relax_scan(const RelaxLaunch& L, cudaStream_t s) {
     dim3 grid((L.snx + kTileX - 1) / kTileX, (L.sny + kTileY - 1) / kTileY, 1);
+    if (L.plan_list) grid = dim3(L.plan_hblocks + grid.x * grid.y, 1, 1);
     const bool span = L.zspan != nullptr;
     if (L.polish > 0) span ? launch_relax_scan_t<true, true>(L, grid, s) : launch_relax_scan_t<true, false>(L, grid, s);
     else span ? launch_relax_scan_t<false, true>(L, grid, s) : launch_relax_scan_t<false, false>(L, grid, s);

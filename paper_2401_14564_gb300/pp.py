@@ -86,6 +86,10 @@ class Tuning(C.Structure):
     _fields_ = [("ff_zpt", C.c_int), ("ff_forces_only", C.c_int)]
 
 
+class ScanOpts(C.Structure):
+    _fields_ = [("zspan", C.c_void_p), ("plan", C.c_void_p), ("plan_k", C.c_int), ("plan_lanes", C.c_int)]
+
+
 class Grads(C.Structure):
     _fields_ = [(k, C.c_void_p) for k in ("x", "y", "z", "q", "R", "eps", "tip")]
 
@@ -129,9 +133,13 @@ def lib():
             L.pp_relax_scan.argtypes = [vp, C.POINTER(Grid), C.POINTER(Scan), C.POINTER(Tip), C.POINTER(Fire),
                                         vp, vp, vp, C.POINTER(DF), vp, vp]
             L.pp_relax_scan.restype = st
-            L.pp_relax_scan_zspan.argtypes = [vp, C.POINTER(Grid), C.POINTER(Scan), C.POINTER(Tip), C.POINTER(Fire),
-                                              vp, vp, vp, C.POINTER(DF), vp, vp, vp]
-            L.pp_relax_scan_zspan.restype = st
+            L.pp_relax_scan_ex.argtypes = [vp, C.POINTER(Grid), C.POINTER(Scan), C.POINTER(Tip), C.POINTER(Fire),
+                                           vp, vp, vp, C.POINTER(DF), vp, C.POINTER(ScanOpts), vp]
+            L.pp_relax_scan_ex.restype = st
+            L.pp_relax_plan_size.argtypes = [C.POINTER(Scan), C.c_int, C.c_int]
+            L.pp_relax_plan_size.restype = C.c_size_t
+            L.pp_relax_plan.argtypes = [vp, C.POINTER(Scan), C.c_int, C.c_int, C.c_int, vp, vp]
+            L.pp_relax_plan.restype = st
             L.pp_fz_to_df.argtypes = [vp, C.c_int, C.c_int, C.c_float, C.POINTER(DF), vp, vp]
             L.pp_fz_to_df.restype = st
             L.pp_ff_convert.argtypes = [vp, C.POINTER(Grid), vp, C.POINTER(Grid), vp]
@@ -295,9 +303,9 @@ def pp_ff_combine(ff: torch.Tensor, ff_el: torch.Tensor, Q: float, grid: Grid, o
 
 
 def pp_relax_scan(ff, grid: Grid, scan: Scan, tip: Tip, fire: Fire, pos, fz, iters, fused_df=None, df=None,
-                  stream=None, zspan=None):
+                  stream=None, zspan=None, plan=None):
     """zspan: a device int32 tensor of 2 elements to receive the lowest and highest node layer the scan's
-    interpolations read (pp_relax_scan_zspan), else None (pp_relax_scan)."""
+    interpolations read; plan: (buffer, k, lanes) from pp_relax_plan.  With either, pp_relax_scan_ex."""
     npx = scan.nx * scan.ny * scan.nz
     if fz.numel() < npx or (pos is not None and pos.numel() < 3 * npx) or (iters is not None and iters.numel() < npx):
         raise ValueError("output buffer too small for the scan")
@@ -310,12 +318,35 @@ def pp_relax_scan(ff, grid: Grid, scan: Scan, tip: Tip, fire: Fire, pos, fz, ite
     args = (_dev(ff, "ff"), C.byref(grid), C.byref(scan), C.byref(tip), C.byref(fire),
             _dev(pos, "pos", allow_none=True), _dev(fz, "fz"), _dev(iters, "iters", torch.int32, allow_none=True),
             C.byref(fused_df) if fused_df is not None else None, _dev(df, "df", allow_none=True))
-    if zspan is None:
+    if zspan is None and plan is None:
         _check(lib().pp_relax_scan(*args, _stream(stream)))
-    else:
+        return
+    opts = ScanOpts(None, None, 0, 0)
+    if zspan is not None:
         if zspan.numel() < 2:
             raise ValueError("zspan needs two ints")
-        _check(lib().pp_relax_scan_zspan(*args, _dev(zspan, "zspan", torch.int32), _stream(stream)))
+        opts.zspan = _dev(zspan, "zspan", torch.int32)
+    if plan is not None:
+        buf, k, lanes = plan
+        if buf.numel() * buf.element_size() < pp_relax_plan_size(scan, k, lanes):
+            raise ValueError("plan buffer smaller than pp_relax_plan_size")
+        opts.plan, opts.plan_k, opts.plan_lanes = _dev(buf, "plan", torch.int32), int(k), int(lanes)
+    _check(lib().pp_relax_scan_ex(*args, C.byref(opts), _stream(stream)))
+
+
+def pp_relax_plan_size(scan: Scan, k: int, lanes: int) -> int:
+    return int(lib().pp_relax_plan_size(C.byref(scan), int(k), int(lanes)))
+
+
+def pp_relax_plan(iters, scan: Scan, max_iter: int, k: int, lanes: int, plan, stream=None):
+    """Pixel-to-warp plan (an int32 device tensor of pp_relax_plan_size bytes) from an earlier scan's iters."""
+    n = pp_relax_plan_size(scan, k, lanes)
+    if n and plan.numel() * plan.element_size() < n:
+        raise ValueError("plan buffer smaller than pp_relax_plan_size")
+    if iters.numel() < scan.nx * scan.ny * scan.nz:
+        raise ValueError("iters smaller than the scan")
+    _check(lib().pp_relax_plan(_dev(iters, "iters", torch.int32), C.byref(scan), int(max_iter), int(k), int(lanes),
+                               _dev(plan, "plan", torch.int32), _stream(stream)))
 
 
 def pp_fz_to_df(fz, nz: int, npix: int, dz: float, df_params: DF, df, stream=None):

@@ -285,11 +285,35 @@ def test_ff_layers_and_zspan_validated_on_host(L):
 
     fire = pp.make_fire(synth.default_fire())
     args = (fake, C.byref(g), C.byref(scan), C.byref(tip), C.byref(fire), fake, fake, fake, None, None)
-    assert L.pp_relax_scan_zspan(*args, None, None) == 1
-    assert b"zspan" in L.pp_last_error()
-    assert L.pp_relax_scan_zspan(*args, C.c_void_p(258), None) == 1     # not 4-byte aligned
+    assert L.pp_relax_scan_ex(*args, None, None) == 1
+    assert b"opts" in L.pp_last_error()
+    opts = pp.ScanOpts(258, None, 0, 0)                                  # zspan not 4-byte aligned
+    assert L.pp_relax_scan_ex(*args, C.byref(opts), None) == 1
     assert b"aligned" in L.pp_last_error()
+    for k, lanes in ((0, 4), (4 * 4 + 1, 4), (8, 0), (8, 33)):          # the scan has 4 x 4 pixels
+        opts = pp.ScanOpts(None, 256, k, lanes)
+        assert L.pp_relax_scan_ex(*args, C.byref(opts), None) == 1
+        assert b"plan_k" in L.pp_last_error()
     fire_bad = pp.make_fire(synth.default_fire(polish=-1))
-    assert L.pp_relax_scan_zspan(fake, C.byref(g), C.byref(scan), C.byref(tip), C.byref(fire_bad), fake, fake, fake,
-                                 None, None, fake, None) == 1            # pp_relax_scan's own checks follow
-    assert b"pp_relax_scan_zspan: invalid FIRE" in L.pp_last_error()
+    opts = pp.ScanOpts(256, None, 0, 0)
+    assert L.pp_relax_scan_ex(fake, C.byref(g), C.byref(scan), C.byref(tip), C.byref(fire_bad), fake, fake, fake,
+                              None, None, C.byref(opts), None) == 1     # pp_relax_scan's own checks follow
+    assert b"pp_relax_scan_ex: invalid FIRE" in L.pp_last_error()
+
+
+def test_relax_plan_validated_on_host(L):
+    fake = C.c_void_p(256)
+    scan = pp.make_scan({"nx": 10, "ny": 7, "nz": 12, "x0": 0.0, "y0": 0.0, "px": 0.1, "py": 0.1, "z_top": 0.3,
+                         "dz": 0.1})
+    n = L.pp_relax_plan_size(C.byref(scan), 5, 4)
+    # header 8 + histogram 2048 + cost 70 + list ceil(5/4)*4 + mask ceil(70/32) int32 words
+    assert n == 4 * (8 + 2048 + 70 + 8 + 3)
+    for k, lanes in ((0, 4), (71, 4), (5, 0), (5, 33)):
+        assert L.pp_relax_plan_size(C.byref(scan), k, lanes) == 0
+        assert L.pp_relax_plan(fake, C.byref(scan), 200, k, lanes, fake, None) == 1
+    assert L.pp_relax_plan(None, C.byref(scan), 200, 5, 4, fake, None) == 1
+    assert L.pp_relax_plan(fake, C.byref(scan), 200, 5, 4, C.c_void_p(258), None) == 1
+    assert L.pp_relax_plan(fake, C.byref(scan), -1, 5, 4, fake, None) == 1
+    bad = pp.make_scan({"nx": 0, "ny": 7, "nz": 12, "x0": 0.0, "y0": 0.0, "px": 0.1, "py": 0.1, "z_top": 0.3,
+                        "dz": 0.1})
+    assert L.pp_relax_plan(fake, C.byref(bad), 200, 5, 4, fake, None) == 2
