@@ -1,5 +1,5 @@
 """The force field in two parts beside the scan: pp_make_ff_layers writes exactly
-the nodes of its layers, pp_relax_scan_zspan reports every layer the scan read
+the nodes of its layers, pp_relax_scan_ex reports every layer the scan read
 (and its outputs are pp_relax_scan's), and Simulator.run_host with the
 overlapped force field returns, call after call, the images of the one-stage
 path, also when the scan leaves the first part and is run again."""
