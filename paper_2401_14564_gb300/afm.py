@@ -27,7 +27,7 @@ class Simulator:
 
     def __init__(self, case, layout=0, brick=(4, 4, 4), fire=None, device="cuda", fused_df=True,
                  want_pos=True, want_iters=True, tuning=None, ff_energy=True, overlap_ff=True, plan_frac=0.025,
-                 plan_lanes=4, auto_plan=True):
+                 plan_lanes=4, auto_plan=True, plan_min_tiles=None):
         """tuning: an autotuner result ({"ff_zpt", "layout", "brick"}) overriding layout and brick.
         ff_energy=False: the grid's E slots are written as 0 and the energy sums skipped (the scan
         reads only the forces, which are unchanged); trilinear force grids only.
@@ -35,7 +35,8 @@ class Simulator:
         second stream while the scan runs (see run_overlapped); False: one stage after the other.
         plan_frac, plan_lanes: the pixel-to-warp plan of the scan (plan_from): that fraction of the
         pixel columns, the costliest in an earlier scan, runs plan_lanes to a warp; 0 = never.
-        auto_plan: every scan builds the plan for the next from its own iteration counts."""
+        auto_plan: every scan builds the plan for the next from its own iteration counts.
+        plan_min_tiles: scans of fewer 8x4 pixel tiles get no plan (None: the GPU's SM count)."""
         self.case = case
         self.device = torch.device(device)
         if tuning is not None:
@@ -75,6 +76,7 @@ class Simulator:
         self.plan_frac = float(plan_frac)
         self.plan_lanes = int(plan_lanes)
         self.auto_plan = bool(auto_plan)
+        self.plan_min_tiles = plan_min_tiles
         self._plan = None
         self._plan_k = 0
         self._plan_ready = False
@@ -105,6 +107,14 @@ class Simulator:
         (this simulator's own, or another image's, e.g. a neighbouring geometry): the plan_frac
         costliest pixel columns run plan_lanes to a warp.  Outputs never depend on it."""
         if self.plan_frac <= 0:
+            return
+        tiles = ((self.scan.nx + 7) // 8) * ((self.scan.ny + 3) // 4)
+        least = self.plan_min_tiles
+        if least is None:
+            least = torch.cuda.get_device_properties(self.device).multi_processor_count
+        if tiles < least:
+            # fewer 8x4 tiles than SMs: no tile shares an SM, and building the plan costs more than it
+            # saves (benzene, 50 tiles: 0.163 against 0.149 ms per forward pass)
             return
         if self._plan is None:
             npix = self.scan.nx * self.scan.ny

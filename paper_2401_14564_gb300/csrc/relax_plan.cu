@@ -27,10 +27,15 @@ namespace {
 constexpr int kBins = 2048;
 constexpr int kHdr = 8;
 
+// Also clears the list (-1) and the mask for plan_select_kernel, which runs after it.
 __global__ void __launch_bounds__(256) plan_cost_kernel(const int* __restrict__ iters, int nz, int npix, int shift,
-                                                        int* hist, int* cost) {
+                                                        int* hist, int* cost, int* list, int nlist, unsigned* mask,
+                                                        int nmask) {
     __shared__ int sh[kBins];
     for (int b = threadIdx.x; b < kBins; b += blockDim.x) sh[b] = 0;
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+    for (int q = gt; q < nlist; q += gs) list[q] = -1;
+    for (int q = gt; q < nmask; q += gs) mask[q] = 0u;
     __syncthreads();
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npix; p += gridDim.x * blockDim.x) {
         long long c = 0;
@@ -44,19 +49,47 @@ __global__ void __launch_bounds__(256) plan_cost_kernel(const int* __restrict__ 
         if (sh[b]) atomicAdd(hist + b, sh[b]);
 }
 
-// The bin T with (columns above T) < k <= (columns at or above T); T = 0 when fewer than k columns
-// exist.  One thread: 2048 steps.
-__global__ void plan_threshold_kernel(int* hdr, const int* hist, int k) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    int above = 0, t = 0;
-    for (int b = kBins - 1; b >= 0; --b) {
-        if (above + hist[b] >= k) { t = b; break; }
-        above += hist[b];
+// The bin T with (columns above T) < k <= (columns at or above T), and the count above it; T = 0
+// when fewer than k columns exist.  One block of 1024 threads: thread t holds the bins 2047 - 2t and
+// 2046 - 2t, and a scan over the threads (costliest bins first) finds the one bin where the running
+// count reaches k.
+__global__ void __launch_bounds__(1024) plan_threshold_kernel(int* hdr, const int* hist, int k) {
+    static_assert(kBins == 2 * 1024, "two bins per thread");
+    __shared__ int wsum[32];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const int h0 = hist[kBins - 1 - 2 * t], h1 = hist[kBins - 2 - 2 * t];
+    int v = h0 + h1;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int n = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += n;
     }
-    hdr[1] = t;
-    hdr[2] = above;
-    hdr[3] = 0;
-    hdr[4] = 0;
+    if (lane == 31) wsum[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        int x = wsum[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            const int n = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += n;
+        }
+        wsum[lane] = x;
+    }
+    __syncthreads();
+    const int before = (w ? wsum[w - 1] : 0) + v - (h0 + h1);  // columns in costlier bins
+    const int incl0 = before + h0, incl1 = incl0 + h1;
+    if (incl0 >= k && before < k) {
+        hdr[1] = kBins - 1 - 2 * t;
+        hdr[2] = before;
+    } else if (incl1 >= k && incl0 < k) {
+        hdr[1] = kBins - 2 - 2 * t;
+        hdr[2] = incl0;
+    } else if (t == 1023 && incl1 < k) {  // fewer than k columns: every one is taken
+        hdr[1] = 0;
+        hdr[2] = incl1 - h1;
+    }
+    if (t == 0) {
+        hdr[3] = 0;
+        hdr[4] = 0;
+    }
 }
 
 __global__ void __launch_bounds__(256) plan_select_kernel(int* hdr, const int* __restrict__ cost, int npix, int shift,
@@ -94,16 +127,15 @@ cudaError_t launch_relax_plan(const int* iters, int nz, int npix, int max_iter, 
     int* cost = hist + kBins;
     int* list = plan + relax_plan_list_offset(npix);
     unsigned* mask = reinterpret_cast<unsigned*>(plan + relax_plan_mask_offset(npix, k, lanes));
-    cudaError_t e = cudaMemsetAsync(hdr, 0, (size_t)(kHdr + kBins) * sizeof(int), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(list, 0xff, (size_t)(hb * lanes) * sizeof(int), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(mask, 0, (size_t)((npix + 31) / 32) * sizeof(unsigned), s);
+    const cudaError_t e = cudaMemsetAsync(hdr, 0, (size_t)(kHdr + kBins) * sizeof(int), s);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int blocks = (int)std::min<long long>(((long long)npix + 255) / 256, 2LL * sms);
-    plan_cost_kernel<<<blocks, 256, 0, s>>>(iters, nz, npix, shift, hist, cost);
-    plan_threshold_kernel<<<1, 32, 0, s>>>(hdr, hist, k);
+    plan_cost_kernel<<<blocks, 256, 0, s>>>(iters, nz, npix, shift, hist, cost, list, (int)(hb * lanes), mask,
+                                            (npix + 31) / 32);
+    plan_threshold_kernel<<<1, 1024, 0, s>>>(hdr, hist, k);
     plan_select_kernel<<<blocks, 256, 0, s>>>(hdr, cost, npix, shift, k, list, mask);
     return cudaGetLastError();
 }

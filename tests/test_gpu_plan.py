@@ -76,7 +76,8 @@ def test_planned_scan_writes_the_same_bits(variant):
     s = c["scan"]
     npix = s["nx"] * s["ny"]
     for frac, lanes in ((1.0 / npix, 1), (0.05, 4), (0.3, 8), (1.0, 32), (1.0, 1)):
-        sim = afm.Simulator(c, fire=fire, plan_frac=frac, plan_lanes=lanes, auto_plan=False, **kw)
+        sim = afm.Simulator(c, fire=fire, plan_frac=frac, plan_lanes=lanes, auto_plan=False, plan_min_tiles=0,
+                            **kw)
         sim.make_ff(atoms)
         sim.plan_from(ref.iters)
         zs = torch.empty(2, dtype=torch.int32, device="cuda") if variant == "zspan" else None
@@ -99,7 +100,7 @@ def test_another_images_plan_changes_nothing():
     ref = afm.Simulator(c, plan_frac=0.0)
     ref.run(atoms)
     want = outputs(ref)
-    sim = afm.Simulator(c, plan_frac=0.1, auto_plan=False)
+    sim = afm.Simulator(c, plan_frac=0.1, auto_plan=False, plan_min_tiles=0)
     sim.plan_from(a_sim.iters)
     sim.run(atoms)
     torch.cuda.synchronize()
@@ -109,7 +110,7 @@ def test_another_images_plan_changes_nothing():
 
 def test_auto_plan_over_a_sequence_of_images():
     c = case32(synth.small_case(seed=24, n_atoms=10, nxy=36, nz=40, scan_px=15, nz_scan=13))
-    auto = afm.Simulator(c)  # each scan plans the next
+    auto = afm.Simulator(c, plan_min_tiles=0)  # each scan plans the next
     plain = afm.Simulator(c, plan_frac=0.0)
     for t in range(3):
         a = copy.deepcopy(c["atoms"])
@@ -121,3 +122,27 @@ def test_auto_plan_over_a_sequence_of_images():
         assert auto._plan_ready
         for x, y in zip(outputs(auto), outputs(plain)):
             assert torch.equal(x, y), t
+
+
+def test_small_scans_get_no_plan():
+    # benzene's 40 x 40 pixels are 50 tiles, fewer than the SMs: no plan is built
+    c = case32(synth.benzene_case())
+    sim = afm.Simulator(c)
+    sim.run(afm.atoms_to_device(c["atoms"]))
+    sim.run(afm.atoms_to_device(c["atoms"]))
+    assert not sim._plan_ready
+
+
+def test_flake_scan_on_its_own_plan():
+    # the full-size scan with the default plan (2.5 % of the columns, 4 lanes), built by the first call
+    c = synth.flake_case()
+    at = afm.atoms_to_device(c["atoms"])
+    plain = afm.Simulator(c, ff_energy=False, plan_frac=0.0)
+    plain.run(at)
+    sim = afm.Simulator(c, ff_energy=False)
+    sim.run(at)
+    sim.run(at)
+    torch.cuda.synchronize()
+    assert sim._plan_ready and sim._plan_k == round(0.025 * 256 * 256)
+    for x, y in zip(outputs(sim), outputs(plain)):
+        assert torch.equal(x, y)
