@@ -397,7 +397,7 @@ def measure_bwd_fwd(case, steps, warmup, flush, tag, ff_energy=False):
 
     from paper_2401_14564_gb300 import afm, pp
 
-    sim = afm.Simulator(case, ff_energy=ff_energy)
+    sim = afm.Simulator(case, ff_energy=ff_energy, plan_frac=0.0)
     atoms_t = afm.atoms_to_device(case["atoms"])
     n = len(case["atoms"]["x"])
     grads = {k: torch.empty(n, device="cuda") for k in ("x", "y", "z", "q", "R", "eps")}
@@ -461,7 +461,7 @@ def measure_quadrupole(case, tuning, steps, warmup, flush, alu_peak):
     from paper_2401_14564_gb300 import afm
 
     qcase = dict(case, probe=dict(case["probe"], Qzz=QZZ_CO))
-    sim = afm.Simulator(qcase, tuning=tuning)
+    sim = afm.Simulator(qcase, tuning=tuning, plan_frac=0.0)
     atoms = afm.atoms_to_device(qcase["atoms"])
     for _ in range(max(warmup, 3)):
         sim.run(atoms)
@@ -503,7 +503,7 @@ def measure_tricubic(case, steps, warmup, flush, spacings=(0.1, 0.2)):
         f = round(h / g0["dx"])
         g = dict(g0, nx=g0["nx"] // f, ny=g0["ny"] // f, nz=(g0["nz"] - 1) // f + 1, dx=h, dy=h, dz=h, interp=1)
         tcase = dict(case, grid=g)
-        sim = afm.Simulator(tcase)
+        sim = afm.Simulator(tcase, plan_frac=0.0)
         atoms = afm.atoms_to_device(tcase["atoms"])
         n = len(tcase["atoms"]["x"])
         grads = {k: torch.empty(n, device="cuda") for k in ("x", "y", "z", "q", "R", "eps")}
@@ -655,7 +655,7 @@ def measure_iets(case, steps, warmup, flush, hbm_gbs):
     out = []
     for interp in (0, 1):
         c = dict(case, grid=dict(case["grid"], interp=interp))
-        sim = afm.Simulator(c)
+        sim = afm.Simulator(c, plan_frac=0.0)
         sim.run(afm.atoms_to_device(c["atoms"]))
         s = c["scan"]
         npts = s["nx"] * s["ny"] * s["nz"]
@@ -764,7 +764,7 @@ def measure_small(case, steps, warmup, flush, alu_peak, ff_energy=False, cpu=Tru
 
     from paper_2401_14564_gb300 import afm
 
-    sim = afm.Simulator(case, ff_energy=ff_energy)
+    sim = afm.Simulator(case, ff_energy=ff_energy, plan_frac=0.0)
     atoms = afm.atoms_to_device(case["atoms"])
     for _ in range(max(warmup, 3)):
         sim.run(atoms)
@@ -856,7 +856,8 @@ def measure_batch(n_mol, steps, warmup, flush, seq_sample=64, ff_energy=False, a
         t_e2e.append(time.perf_counter() - t0)
     e2e_ms = 1e3 * statistics.median(t_e2e)
     # the same molecules one at a time (first seq_sample of them), per-molecule buffers preallocated
-    sims = [(afm.Simulator(c, ff_energy=ff_energy), afm.atoms_to_device(c["atoms"])) for c in cases[:seq_sample]]
+    sims = [(afm.Simulator(c, ff_energy=ff_energy, plan_frac=0.0), afm.atoms_to_device(c["atoms"]))
+            for c in cases[:seq_sample]]
     for sim, at in sims:
         sim.run(at)
     torch.cuda.synchronize()
