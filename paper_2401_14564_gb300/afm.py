@@ -82,7 +82,8 @@ class Simulator:
         self.auto_plan = bool(auto_plan)
         self.plan_min_tiles = plan_min_tiles
         self._plan = None
-        self._plan_k = 0
+        self._plan_k = 0       # k and lanes the held plan was built with
+        self._plan_lanes = 0
         self._plan_ready = False
 
     def make_ff(self, atoms_dev, stream=None):
@@ -96,7 +97,7 @@ class Simulator:
         is held (see plan_from); with auto_plan, the plan for the next call is then built from this
         scan's iteration counts."""
         out = self.df if df is None else df
-        plan = (self._plan, self._plan_k, self.plan_lanes) if self._plan_ready else None
+        plan = (self._plan, self._plan_k, self._plan_lanes) if self._plan_ready else None
         pp.pp_relax_scan(self.ff, self.grid, self.scan, self.tip, self.fire, self.pos, self.fz, self.iters,
                          self.dfp if self.fused_df else None, out if self.fused_df else None, stream,
                          zspan=zspan, plan=plan)
@@ -120,12 +121,14 @@ class Simulator:
             # fewer 8x4 tiles than SMs: no tile shares an SM, and building the plan costs more than it
             # saves (benzene, 50 tiles: 0.163 against 0.149 ms per forward pass)
             return
-        if self._plan is None:
-            npix = self.scan.nx * self.scan.ny
-            self._plan_k = max(1, min(npix, int(round(self.plan_frac * npix))))
-            n = pp.pp_relax_plan_size(self.scan, self._plan_k, self.plan_lanes)
+        npix = self.scan.nx * self.scan.ny
+        k = max(1, min(npix, int(round(self.plan_frac * npix))))
+        if self._plan is None or (k, self.plan_lanes) != (self._plan_k, self._plan_lanes):
+            # the plan's layout depends on k and the lanes: a new shape gets a new buffer
+            n = pp.pp_relax_plan_size(self.scan, k, self.plan_lanes)
             self._plan = torch.empty((n + 3) // 4, dtype=torch.int32, device=self.device)
-        pp.pp_relax_plan(iters, self.scan, self.fire.max_iter, self._plan_k, self.plan_lanes, self._plan, stream)
+            self._plan_k, self._plan_lanes = k, self.plan_lanes
+        pp.pp_relax_plan(iters, self.scan, self.fire.max_iter, self._plan_k, self._plan_lanes, self._plan, stream)
         self._plan_ready = True
 
     def drop_plan(self):

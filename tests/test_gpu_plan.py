@@ -112,10 +112,14 @@ def test_auto_plan_over_a_sequence_of_images():
     c = case32(synth.small_case(seed=24, n_atoms=10, nxy=36, nz=40, scan_px=15, nz_scan=13))
     auto = afm.Simulator(c, plan_min_tiles=0)  # each scan plans the next
     plain = afm.Simulator(c, plan_frac=0.0)
-    for t in range(3):
+    for t in range(4):
         a = copy.deepcopy(c["atoms"])
         a["y"] = a["y"] - 0.04 * t
         at = afm.atoms_to_device(a)
+        if t == 2:
+            auto.plan_lanes = 8   # the plan held was built for 4 lanes: it is used as built, the next is for 8
+        if t == 3:
+            auto.plan_frac = 0.2
         auto.run(at)
         plain.run(at)
         torch.cuda.synchronize()
