@@ -430,9 +430,30 @@ def measure_bwd_fwd(case, steps, warmup, flush, tag, ff_energy=False):
         tf.append(e0.elapsed_time(e1))
         tb.append(e2a.elapsed_time(e2))
     f, b = statistics.mean(tf), statistics.mean(tb)
+    # the same forward with the force field in two parts beside the scan (Simulator.run_overlapped;
+    # the first call learns the layers the scan reads, untimed)
+    sim.run_overlapped(atoms_t, stream)
+    torch.cuda.synchronize()
+    sim.overlap_held()
+    to, held = [], 0
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
+        e0.record(stream)
+        first = sim.run_overlapped(atoms_t, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        held += bool(sim.overlap_held())
+        to.append(e0.elapsed_time(e1))
     return {"workload": tag, "fwd_ms": f, "bwd_ms": b, "ratio": b / f, "ff_energy": bool(ff_energy),
+            "fwd_overlapped_ms": statistics.mean(to), "overlap": {"first_layers": list(first),
+                                                                 "grid_layers": case["grid"]["nz"],
+                                                                 "steps_held": held, "steps": steps},
             "note": "forward = FF + relaxed scan + fused df; backward = pp_backward (df adjoint, 3x3 implicit solves, "
-                    "grid-adjoint scatter, per-atom pair-derivative sums); L2 flushed before each"}
+                    "grid-adjoint scatter, per-atom pair-derivative sums); L2 flushed before each; "
+                    "fwd_overlapped_ms: the force field of the layers the scan reads first, the rest beside "
+                    "the scan (a step that left the first part would need its scan again: steps_held counts "
+                    "those that did not)"}
 
 
 def measure_slab(steps, warmup, flush, ff_energy=False):
