@@ -31,8 +31,9 @@ class Simulator:
         """tuning: an autotuner result ({"ff_zpt", "layout", "brick"}) overriding layout and brick.
         ff_energy=False: the grid's E slots are written as 0 and the energy sums skipped (the scan
         reads only the forces, which are unchanged); trilinear force grids only.
-        overlap_ff: run_host assembles the node layers the scan will read first and the others on a
-        second stream while the scan runs (see run_overlapped); False: one stage after the other.
+        overlap_ff: run_host may assemble the node layers the scan will read first and the others on
+        a second stream while the scan runs (see run_overlapped): its first calls time that and the
+        one-stage forward in turn and keep the faster; False: one stage after the other.
         plan_frac, plan_lanes: the pixel-to-warp plan of the scan (plan_from): that fraction of the
         pixel columns, the costliest in an earlier scan, runs plan_lanes to a warp; 0 = never; None =
         0.025 on a force grid and 0 on a tricubic energy grid, whose scan is bound by issue slots rather
@@ -70,6 +71,9 @@ class Simulator:
         self.df = torch.empty((nz - 2 * self.m, ny, nx), dtype=torch.float32, device=self.device)
         self._host = None
         self.overlap_ff = overlap_ff
+        self._mode = None      # run_host's schedule once its trial calls have picked one
+        self._trial = {"overlap": [], "plain": []}
+        self._trial_warm = False
         self.reruns = 0      # scans run again because they read a layer outside the first part
         self._span = None    # node layers the last overlapped scan read
         self._side = None    # second stream of the overlapped forward
@@ -224,26 +228,63 @@ class Simulator:
         for r, k in enumerate(ATOM_KEYS):
             hb["atoms_h"][r].copy_(torch.from_numpy(np.asarray(atoms_host[k], dtype=np.float32)))
         st = stream or torch.cuda.current_stream()
+        overlap = self._forward_mode() == "overlap"
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         with torch.cuda.stream(st):
             hb["atoms_d"].copy_(hb["atoms_h"], non_blocking=True)
             dev = {k: hb["atoms_d"][r] for r, k in enumerate(ATOM_KEYS)}
-            if self.overlap_ff:
+            e0.record(st)
+            if overlap:
                 self.run_overlapped(dev, st)
             else:
                 self.run(dev, st)
+            e1.record(st)
             hb["df_h"].copy_(self.df, non_blocking=True)
         st.synchronize()
-        if self.overlap_ff and not self.overlap_held():
+        ms = e0.elapsed_time(e1)
+        if overlap and not self.overlap_held():
             # the scan left the first part: run it again on the grid, complete by now
             self.reruns += 1
             with torch.cuda.stream(st):
+                e0.record(st)
                 self.relax(st)
+                e1.record(st)
                 hb["df_h"].copy_(self.df, non_blocking=True)
             st.synchronize()
+            ms += e0.elapsed_time(e1)
+        self._note_forward(overlap, ms)
         if out is not None:
             out.copy_(hb["df_h"])
             return out
         return hb["df_h"]
+
+    # run_host's schedule: with overlap_ff, its first calls time the overlapped and the one-stage
+    # forward in turn and keep the faster (the overlap pays on flake60, 0.99 against 1.16 ms, and
+    # loses where the scan is short or the grid far larger than L2: the 2516-atom slab, 107.5
+    # against 103.9 ms, whose other layers' writes evict the scan's cells from L2)
+    _TRIALS = 3  # timed calls of each schedule
+
+    def _forward_mode(self):
+        if not self.overlap_ff:
+            return "plain"
+        if self._mode is not None:
+            return self._mode
+        n_ov, n_pl = len(self._trial["overlap"]), len(self._trial["plain"])
+        # the first overlapped call (on the anchors' reach, not yet the band a scan read) is not counted
+        if not self._trial_warm:
+            return "overlap"
+        return "overlap" if n_ov <= n_pl else "plain"
+
+    def _note_forward(self, overlap, ms):
+        if not self.overlap_ff or self._mode is not None:
+            return
+        if overlap and not self._trial_warm:
+            self._trial_warm = True
+            return
+        self._trial["overlap" if overlap else "plain"].append(ms)
+        if min(len(v) for v in self._trial.values()) >= self._TRIALS:
+            med = {k: sorted(v)[len(v) // 2] for k, v in self._trial.items()}
+            self._mode = "overlap" if med["overlap"] < med["plain"] else "plain"
 
     def host_outputs(self, n_items):
         """n_items pinned host tensors shaped like the df image, for run_host_many(outs=...)."""
