@@ -1212,8 +1212,9 @@ def main():
                             "image copied out on its slot's stream, four steps in flight; no L2 flush between these "
                             "steps (each rewrites the 210 MB grid, larger than L2)",
                     "per_step_synchronised": world * units / (e2e_sync_ms * 1e-3),
-                    "per_step_synchronised_note": "Simulator.run_host, one image at a time with the overlapped "
-                                                  "force field (ms_per_step_overlapped), host-timed"},
+                    "per_step_synchronised_note": "Simulator.run_host, one image at a time, host-timed, on the "
+                                                  "schedule its first calls picked (run_host_schedule)",
+                    "run_host_schedule": sim._mode},
             "gpu_launches": 2 * args.steps, "clocks": clk, "wall_s_timed": t_wall,
             "device": {"sm_count": sms, "l2": l2}}
     if tuning is not None:
