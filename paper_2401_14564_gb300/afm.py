@@ -260,8 +260,8 @@ class Simulator:
 
     # run_host's schedule: with overlap_ff, its first calls time the overlapped and the one-stage
     # forward in turn and keep the faster (the overlap pays on flake60, 0.99 against 1.16 ms, and
-    # loses where the scan is short or the grid far larger than L2: the 2516-atom slab, 107.5
-    # against 103.9 ms, whose other layers' writes evict the scan's cells from L2)
+    # loses where the force field dominates the pass: the 2516-atom slab, 107.5 against 103.9 ms,
+    # whose K1 gets too few CTAs per SM beside the scan's resident warps)
     _TRIALS = 3  # timed calls of each schedule
 
     def _forward_mode(self):
