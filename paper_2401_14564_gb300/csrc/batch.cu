@@ -201,7 +201,7 @@ __device__ __forceinline__ void ff_tile(const BatchLaunch& B, const pp_mol_desc&
                           s3[lane]);
         }
         __syncwarp();
-        ff_accumulate<ZP, kMinImage, kCutoff, kQuad>(s0, s1, s2, s3, cnt, cst, gx, gy, gz, fx, fy, fz, en);
+        ff_accumulate<ZP, kMinImage, kCutoff, kQuad, true>(s0, s1, s2, s3, cnt, cst, gx, gy, gz, fx, fy, fz, en);
     }
     if (i < D.nx && j < D.ny) {
         const long long first = D.ff_offset + (long long)j * D.nx + i;

@@ -76,7 +76,8 @@ __global__ void __launch_bounds__(kThreads) ff_assemble_kernel(const FFLaunch P)
             ff_stage_atom(cst, P.x[g], P.y[g], P.z[g], P.R[g], P.eps[g], P.q[g], s0[a], s1[a], s2[a], s3[a]);
         }
         __syncthreads();
-        ff_accumulate_impl<ZP, kMinImage, kCutoff, kQuad, kSplit>(s0, s1, s2, s3, cnt, cst, gx, gy, gz, fx, fy, fz, en,
+        // every thread of the block runs this (out-of-grid columns return only after it): the warp vote is safe
+        ff_accumulate_impl<ZP, kMinImage, kCutoff, kQuad, kSplit, true>(s0, s1, s2, s3, cnt, cst, gx, gy, gz, fx, fy, fz, en,
                                                                   fxe, fye, fze, ene);
     }
 

@@ -63,7 +63,12 @@ __device__ __forceinline__ void ff_stage_atom(const FFConst& c, float x, float y
 
 // kSplit: the point-charge terms go to (fxe, fye, fze, ene) instead (staged with kq = k_e q_i, i.e.
 // per unit probe charge), the LJ and quadrupole terms stay in (fx, fy, fz, en).
-template <int ZP, bool kMinImage, bool kCutoff, bool kQuad, bool kSplit>
+// kFloorVote (all 32 lanes of the warp call): r^2 = rxy^2 + rz^2 >= rxy^2, so where every lane's
+// column passes the atom laterally at or beyond the core radius the floor max(r^2, floor^2) is r^2
+// for all its nodes; the warp votes once per atom and then skips the two scalar max per node pair
+// (the same bits; the floor binds only for columns within the core radius of an atom, a few % of
+// the warp-atom pairs).
+template <int ZP, bool kMinImage, bool kCutoff, bool kQuad, bool kSplit, bool kFloorVote = false>
 __device__ __forceinline__ void ff_accumulate_impl(const float4* s0, const float4* s1, const float4* s2,
                                                    const float4* s3, int cnt, const FFConst& c, float gx, float gy,
                                                    const float2 (&gz)[ZP], float2 (&fx)[ZP], float2 (&fy)[ZP],
@@ -86,83 +91,90 @@ __device__ __forceinline__ void ff_accumulate_impl(const float4* s0, const float
         const float2 LB = make_float2(A2.x, A2.y), KQ = make_float2(A2.z, A2.w);
         const float2 EC = make_float2(A3.x, A3.y), ED = make_float2(A3.z, A3.w);
         const float2 KQQ = make_float2(A0.w, A0.w);
+        auto body = [&](auto floor_t) {
+            constexpr bool kFloor = decltype(floor_t)::value;
 #pragma unroll
-        for (int t = 0; t < ZP; ++t) {
-            const float2 rz = f2add(gz[t], NZ);
-            float2 r2 = f2fma(rz, rz, RXY);
-            r2.x = fmaxf(r2.x, A0.z);
-            r2.y = fmaxf(r2.y, A0.z);
-            const float2 rs = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
-            const float2 ir2 = f2mul(rs, rs);
-            const float2 ir4 = f2mul(ir2, ir2);
-            const float2 ir6 = f2mul(ir4, ir2);
-            const float2 lj = f2mul(f2fma(LA, ir6, LB), ir6);  // 12 e (u6 - u3)
-            float2 eel;  // kq / r (cut and shifted when kCutoff); formed when needed
-            float2 f;    // radial factor of every term (of the LJ and quadrupole terms when kSplit)
-            float2 fe;   // kSplit: radial factor of the point-charge term
-            if (kCutoff) {
-                eel = f2mul(KQ, rs);
-                eel.x = (r2.x < c.rc2) ? eel.x : 0.f;
-                eel.y = (r2.y < c.rc2) ? eel.y : 0.f;
-                if (kSplit) {
-                    fe = f2fma(eel, make_float2(-c.irc2, -c.irc2), f2mul(eel, ir2));  // kq (1/r^3 - 1/(r rc^2))
+            for (int t = 0; t < ZP; ++t) {
+                const float2 rz = f2add(gz[t], NZ);
+                float2 r2 = f2fma(rz, rz, RXY);
+                if (kFloor) {
+                    r2.x = fmaxf(r2.x, A0.z);
+                    r2.y = fmaxf(r2.y, A0.z);
+                }
+                const float2 rs = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+                const float2 ir2 = f2mul(rs, rs);
+                const float2 ir4 = f2mul(ir2, ir2);
+                const float2 ir6 = f2mul(ir4, ir2);
+                const float2 lj = f2mul(f2fma(LA, ir6, LB), ir6);  // 12 e (u6 - u3)
+                float2 eel;  // kq / r (cut and shifted when kCutoff); formed when needed
+                float2 f;    // radial factor of every term (of the LJ and quadrupole terms when kSplit)
+                float2 fe;   // kSplit: radial factor of the point-charge term
+                if (kCutoff) {
+                    eel = f2mul(KQ, rs);
+                    eel.x = (r2.x < c.rc2) ? eel.x : 0.f;
+                    eel.y = (r2.y < c.rc2) ? eel.y : 0.f;
+                    if (kSplit) {
+                        fe = f2fma(eel, make_float2(-c.irc2, -c.irc2), f2mul(eel, ir2));  // kq (1/r^3 - 1/(r rc^2))
+                        f = f2mul(lj, ir2);
+                    } else {
+                        // kq (1/r^3 - 1/(r rc^2)) + 12 e (u6 - u3) / r^2
+                        f = f2fma(eel, make_float2(-c.irc2, -c.irc2), f2mul(f2add(lj, eel), ir2));
+                    }
+                    // shifted-force energy kq (1/r + r/rc^2 - 2/rc)
+                    float2 ee = f2fma(eel, f2mul(r2, make_float2(c.irc2, c.irc2)), eel);
+                    ee.x -= (r2.x < c.rc2) ? KQ.x * c.two_irc : 0.f;
+                    ee.y -= (r2.y < c.rc2) ? KQ.y * c.two_irc : 0.f;
+                    eel = ee;
+                } else if (kSplit) {
+                    eel = f2mul(KQ, rs);
+                    fe = f2mul(eel, ir2);
                     f = f2mul(lj, ir2);
                 } else {
-                    // kq (1/r^3 - 1/(r rc^2)) + 12 e (u6 - u3) / r^2
-                    f = f2fma(eel, make_float2(-c.irc2, -c.irc2), f2mul(f2add(lj, eel), ir2));
+                    eel = f2mul(KQ, rs);                // formed only for the quadrupole's energy sum
+                    f = f2mul(f2fma(KQ, rs, lj), ir2);  // (12 e (u6 - u3) + kq / r) / r^2
                 }
-                // shifted-force energy kq (1/r + r/rc^2 - 2/rc)
-                float2 ee = f2fma(eel, f2mul(r2, make_float2(c.irc2, c.irc2)), eel);
-                ee.x -= (r2.x < c.rc2) ? KQ.x * c.two_irc : 0.f;
-                ee.y -= (r2.y < c.rc2) ? KQ.y * c.two_irc : 0.f;
-                eel = ee;
-            } else if (kSplit) {
-                eel = f2mul(KQ, rs);
-                fe = f2mul(eel, ir2);
-                f = f2mul(lj, ir2);
-            } else {
-                eel = f2mul(KQ, rs);                // formed only for the quadrupole's energy sum
-                f = f2mul(f2fma(KQ, rs, lj), ir2);  // (12 e (u6 - u3) + kq / r) / r^2
-            }
-            float2 fzf = f;
-            float2 eq = make_float2(0.f, 0.f);  // quadrupole energy
-            if (kQuad) {
-                float2 c5 = f2mul(KQQ, f2mul(ir4, rs));  // kqq / r^5
-                if (kCutoff) {
-                    c5.x = (r2.x < c.rc2) ? c5.x : 0.f;
-                    c5.y = (r2.y < c.rc2) ? c5.y : 0.f;
+                float2 fzf = f;
+                float2 eq = make_float2(0.f, 0.f);  // quadrupole energy
+                if (kQuad) {
+                    float2 c5 = f2mul(KQQ, f2mul(ir4, rs));  // kqq / r^5
+                    if (kCutoff) {
+                        c5.x = (r2.x < c.rc2) ? c5.x : 0.f;
+                        c5.y = (r2.y < c.rc2) ? c5.y : 0.f;
+                    }
+                    const float2 rz2 = f2mul(rz, rz);
+                    f = f2fma(c5, f2fma(f2mul(rz2, ir2), fifteen, minus3), f);  // + kqq (15 dz^2/r^2 - 3) / r^5
+                    fzf = f2fma(c5, minus6, f);                                 // axial -6 kqq dz / r^5
+                    // + kqq (3 dz^2 - r^2) / r^5
+                    if (kSplit) eq = f2mul(c5, f2sub(f2mul(rz2, three), r2));
+                    else eel = f2fma(c5, f2sub(f2mul(rz2, three), r2), eel);
                 }
-                const float2 rz2 = f2mul(rz, rz);
-                f = f2fma(c5, f2fma(f2mul(rz2, ir2), fifteen, minus3), f);  // + kqq (15 dz^2/r^2 - 3) / r^5
-                fzf = f2fma(c5, minus6, f);                                 // axial -6 kqq dz / r^5
-                // + kqq (3 dz^2 - r^2) / r^5
-                if (kSplit) eq = f2mul(c5, f2sub(f2mul(rz2, three), r2));
-                else eel = f2fma(c5, f2sub(f2mul(rz2, three), r2), eel);
+                fx[t] = f2fma(f, RX, fx[t]);
+                fy[t] = f2fma(f, RY, fy[t]);
+                fz[t] = f2fma(fzf, rz, fz[t]);
+                if (kSplit) {
+                    en[t] = f2add(f2fma(f2fma(EC, ir6, ED), ir6, en[t]), eq);  // e (u6 - 2 u3) + E_quad
+                    fxe[t] = f2fma(fe, RX, fxe[t]);
+                    fye[t] = f2fma(fe, RY, fye[t]);
+                    fze[t] = f2fma(fe, rz, fze[t]);
+                    ene[t] = f2add(ene[t], eel);
+                } else if (kCutoff || kQuad) {
+                    en[t] = f2add(f2fma(f2fma(EC, ir6, ED), ir6, en[t]), eel);  // e (u6 - 2 u3) + E_el (+ E_quad)
+                } else {
+                    en[t] = f2fma(KQ, rs, f2fma(f2fma(EC, ir6, ED), ir6, en[t]));  // e (u6 - 2 u3) + kq / r
+                }
             }
-            fx[t] = f2fma(f, RX, fx[t]);
-            fy[t] = f2fma(f, RY, fy[t]);
-            fz[t] = f2fma(fzf, rz, fz[t]);
-            if (kSplit) {
-                en[t] = f2add(f2fma(f2fma(EC, ir6, ED), ir6, en[t]), eq);  // e (u6 - 2 u3) + E_quad
-                fxe[t] = f2fma(fe, RX, fxe[t]);
-                fye[t] = f2fma(fe, RY, fye[t]);
-                fze[t] = f2fma(fe, rz, fze[t]);
-                ene[t] = f2add(ene[t], eel);
-            } else if (kCutoff || kQuad) {
-                en[t] = f2add(f2fma(f2fma(EC, ir6, ED), ir6, en[t]), eel);  // e (u6 - 2 u3) + E_el (+ E_quad)
-            } else {
-                en[t] = f2fma(KQ, rs, f2fma(f2fma(EC, ir6, ED), ir6, en[t]));  // e (u6 - 2 u3) + kq / r
-            }
-        }
+        };
+        if (kFloorVote && __all_sync(0xffffffffu, rxy2 >= A0.z)) body(std::false_type{});
+        else body(std::true_type{});
     }
 }
 
-template <int ZP, bool kMinImage, bool kCutoff, bool kQuad>
+template <int ZP, bool kMinImage, bool kCutoff, bool kQuad, bool kFloorVote = false>
 __device__ __forceinline__ void ff_accumulate(const float4* s0, const float4* s1, const float4* s2, const float4* s3,
                                               int cnt, const FFConst& c, float gx, float gy, const float2 (&gz)[ZP],
                                               float2 (&fx)[ZP], float2 (&fy)[ZP], float2 (&fz)[ZP], float2 (&en)[ZP]) {
-    ff_accumulate_impl<ZP, kMinImage, kCutoff, kQuad, false>(s0, s1, s2, s3, cnt, c, gx, gy, gz, fx, fy, fz, en, fx,
-                                                             fy, fz, en);
+    ff_accumulate_impl<ZP, kMinImage, kCutoff, kQuad, false, kFloorVote>(s0, s1, s2, s3, cnt, c, gx, gy, gz, fx, fy,
+                                                                         fz, en, fx, fy, fz, en);
 }
 
 }  // namespace pp
