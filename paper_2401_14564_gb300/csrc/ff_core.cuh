@@ -67,7 +67,10 @@ __device__ __forceinline__ void ff_stage_atom(const FFConst& c, float x, float y
 // column passes the atom laterally at or beyond the core radius the floor max(r^2, floor^2) is r^2
 // for all its nodes; the warp votes once per atom and then skips the two scalar max per node pair
 // (the same bits; the floor binds only for columns within the core radius of an atom, a few % of
-// the warp-atom pairs).
+// the warp-atom pairs).  Likewise with kCutoff: where every lane's column passes the atom at or
+// beyond coul_rc, every node's r^2 >= rc^2 and the cut terms are the zeros the in-range tests would
+// select (the same expressions with those tests known false: the same bits), so the point-charge
+// (and quadrupole) arithmetic drops out; on a laterally periodic slab most atoms are that far.
 template <int ZP, bool kMinImage, bool kCutoff, bool kQuad, bool kSplit, bool kFloorVote = false>
 __device__ __forceinline__ void ff_accumulate_impl(const float4* s0, const float4* s1, const float4* s2,
                                                    const float4* s3, int cnt, const FFConst& c, float gx, float gy,
@@ -91,8 +94,10 @@ __device__ __forceinline__ void ff_accumulate_impl(const float4* s0, const float
         const float2 LB = make_float2(A2.x, A2.y), KQ = make_float2(A2.z, A2.w);
         const float2 EC = make_float2(A3.x, A3.y), ED = make_float2(A3.z, A3.w);
         const float2 KQQ = make_float2(A0.w, A0.w);
-        auto body = [&](auto floor_t) {
+        auto body = [&](auto floor_t, auto far_t) {
             constexpr bool kFloor = decltype(floor_t)::value;
+            constexpr bool kFar = decltype(far_t)::value;  // every node of every lane beyond coul_rc
+            auto in_rc = [&](float r2v) { return !kFar && r2v < c.rc2; };
 #pragma unroll
             for (int t = 0; t < ZP; ++t) {
                 const float2 rz = f2add(gz[t], NZ);
@@ -111,8 +116,8 @@ __device__ __forceinline__ void ff_accumulate_impl(const float4* s0, const float
                 float2 fe;   // kSplit: radial factor of the point-charge term
                 if (kCutoff) {
                     eel = f2mul(KQ, rs);
-                    eel.x = (r2.x < c.rc2) ? eel.x : 0.f;
-                    eel.y = (r2.y < c.rc2) ? eel.y : 0.f;
+                    eel.x = in_rc(r2.x) ? eel.x : 0.f;
+                    eel.y = in_rc(r2.y) ? eel.y : 0.f;
                     if (kSplit) {
                         fe = f2fma(eel, make_float2(-c.irc2, -c.irc2), f2mul(eel, ir2));  // kq (1/r^3 - 1/(r rc^2))
                         f = f2mul(lj, ir2);
@@ -122,8 +127,8 @@ __device__ __forceinline__ void ff_accumulate_impl(const float4* s0, const float
                     }
                     // shifted-force energy kq (1/r + r/rc^2 - 2/rc)
                     float2 ee = f2fma(eel, f2mul(r2, make_float2(c.irc2, c.irc2)), eel);
-                    ee.x -= (r2.x < c.rc2) ? KQ.x * c.two_irc : 0.f;
-                    ee.y -= (r2.y < c.rc2) ? KQ.y * c.two_irc : 0.f;
+                    ee.x -= in_rc(r2.x) ? KQ.x * c.two_irc : 0.f;
+                    ee.y -= in_rc(r2.y) ? KQ.y * c.two_irc : 0.f;
                     eel = ee;
                 } else if (kSplit) {
                     eel = f2mul(KQ, rs);
@@ -138,8 +143,8 @@ __device__ __forceinline__ void ff_accumulate_impl(const float4* s0, const float
                 if (kQuad) {
                     float2 c5 = f2mul(KQQ, f2mul(ir4, rs));  // kqq / r^5
                     if (kCutoff) {
-                        c5.x = (r2.x < c.rc2) ? c5.x : 0.f;
-                        c5.y = (r2.y < c.rc2) ? c5.y : 0.f;
+                        c5.x = in_rc(r2.x) ? c5.x : 0.f;
+                        c5.y = in_rc(r2.y) ? c5.y : 0.f;
                     }
                     const float2 rz2 = f2mul(rz, rz);
                     f = f2fma(c5, f2fma(f2mul(rz2, ir2), fifteen, minus3), f);  // + kqq (15 dz^2/r^2 - 3) / r^5
@@ -164,8 +169,15 @@ __device__ __forceinline__ void ff_accumulate_impl(const float4* s0, const float
                 }
             }
         };
-        if (kFloorVote && __all_sync(0xffffffffu, rxy2 >= A0.z)) body(std::false_type{});
-        else body(std::true_type{});
+        const bool clear = kFloorVote && __all_sync(0xffffffffu, rxy2 >= A0.z);
+        const bool far = kFloorVote && kCutoff && __all_sync(0xffffffffu, rxy2 >= c.rc2);
+        if (clear) {
+            if (far) body(std::false_type{}, std::true_type{});
+            else body(std::false_type{}, std::false_type{});
+        } else {
+            if (far) body(std::true_type{}, std::true_type{});
+            else body(std::true_type{}, std::false_type{});
+        }
     }
 }
 
