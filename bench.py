@@ -45,13 +45,13 @@ TRAFFIC = {
                    "files": ["relax_scan.cu", "relax_core.cuh", "interp.cuh"]},
     "relax_scan_tricubic": {"bytes": 24.60e6, "sha": "65e56d7ba4e85d47",
                             "files": ["relax_scan.cu", "relax_core.cuh", "interp.cuh"]},
-    "ff_assemble": {"bytes": 148.15e6, "sha": "4990a86aadbba153",
+    "ff_assemble": {"bytes": 148.24e6, "sha": "99618f336fa803b5",
                     "files": ["ff_assemble.cu", "ff_core.cuh", "interp.cuh"]},
-    "ff_assemble_quad": {"bytes": 148.23e6, "sha": "4990a86aadbba153",
+    "ff_assemble_quad": {"bytes": 148.63e6, "sha": "99618f336fa803b5",
                          "files": ["ff_assemble.cu", "ff_core.cuh", "interp.cuh"]},
-    "ff_assemble_split": {"bytes": 356.97e6, "sha": "4990a86aadbba153",
+    "ff_assemble_split": {"bytes": 357.02e6, "sha": "99618f336fa803b5",
                           "files": ["ff_assemble.cu", "ff_core.cuh", "interp.cuh"]},
-    "ff_combine": {"bytes": 601.38e6, "sha": "4990a86aadbba153",
+    "ff_combine": {"bytes": 600.94e6, "sha": "99618f336fa803b5",
                    "files": ["ff_assemble.cu", "ff_core.cuh", "interp.cuh"]},
 }
 
@@ -66,7 +66,7 @@ FP32_LANES_PER_SM = 128
 # (sm__sass_thread_inst_executed_op_{fadd,fmul,ffma}_pred_on, FFMA counted twice, over the pairs of
 # the launch) and the issue-active fraction of K2 (smsp__issue_active.avg.pct_of_peak_sustained_active).
 EXECUTED = {
-    "ff_forces": {"value": 18.69, "sha": "4990a86aadbba153", "files": ["ff_assemble.cu", "ff_core.cuh", "interp.cuh"]},
+    "ff_forces": {"value": 18.69, "sha": "99618f336fa803b5", "files": ["ff_assemble.cu", "ff_core.cuh", "interp.cuh"]},
     "ff_energy": {"value": None, "sha": None, "files": ["ff_assemble.cu", "ff_core.cuh", "interp.cuh"]},
 }
 ISSUE = {
