@@ -318,6 +318,7 @@ __global__ void __launch_bounds__(kFFBThreads) ff_backward_kernel(const BwdLaunc
     float qC = 0.f, qCq = 0.f;  // this thread's q_i C_i and q_i Cq_i (tip quadrupole only)
     for (int a0 = 0; a0 < P.n; a0 += kFFBThreads) {
         const int ia = a0 + threadIdx.x;
+        const unsigned live = __ballot_sync(0xffffffffu, ia < P.n);  // this warp's lanes with an atom
         if (ia >= P.n) break;
         const float ax = P.ax[ia], ay = P.ay[ia], azz = P.az[ia];
         const float Rij = P.aR[ia] + P.R_pp;
@@ -343,59 +344,68 @@ __global__ void __launch_bounds__(kFFBThreads) ff_backward_kernel(const BwdLaunc
             const float2 R2raw = f2fma(DX, DX, f2fma(DY, DY, f2mul(DZ, DZ)));
             const bool c0 = R2raw.x < rmin2, c1 = R2raw.y < rmin2;  // core floor per node
             const float2 R2v = make_float2(c0 ? rmin2 : R2raw.x, c1 ? rmin2 : R2raw.y);
-            const float2 RS = make_float2(rsqrtf(R2v.x), rsqrtf(R2v.y));
-            const float2 IR2 = f2mul(RS, RS);
-            const float2 U = f2mul(RR2, IR2);
-            const float2 S6 = f2mul(f2mul(U, U), U);
-            const float2 S12 = f2mul(S6, S6);
-            const float2 SLJ = f2mul(f2mul(TWELVE, f2sub(S12, S6)), IR2);                 // LJ S per unit e_iPP
-            const float2 DSLJDR = f2mul(f2mul(E12, f2fma(EIGHT, S6, f2mul(M14, S12))), f2mul(IR2, RS));
-            const float2 DSLJDRR = f2mul(f2mul(E12R, f2fma(TWELVE, S12, f2mul(M6, S6))), IR2);
-            float2 Cv, DC;
-            if (kCutoff) {
-                const bool i0 = R2v.x < rc2, i1 = R2v.y < rc2;
-                const float2 z = make_float2(0.f, 0.f);
-                Cv = sel2(i0, i1, f2mul(RS, f2sub(IR2, make_float2(irc2, irc2))), z);     // 1/r^3 - 1/(r rc^2)
-                DC = sel2(i0, i1, f2mul(IR2, f2fma(M3, IR2, make_float2(irc2, irc2))), z);  // -3/r^4 + 1/(r^2 rc^2)
-            } else {
-                Cv = f2mul(RS, IR2);
-                DC = f2mul(M3, f2mul(IR2, IR2));
-            }
-            const float2 S = f2fma(EIJ, SLJ, f2mul(QQ, Cv));
-            const float2 DSDR = f2fma(QQ, DC, DSLJDR);
-            const float2 AD = f2fma(GX, DX, f2fma(GY, DY, f2mul(GZ, DZ)));
-            const float2 RAD = sel2(c0, c1, make_float2(0.f, 0.f), f2mul(f2mul(DSDR, AD), RS));  // dS/dr (a.delta)/r
-            GPX = f2sub(GPX, f2fma(S, GX, f2mul(RAD, DX)));
-            GPY = f2sub(GPY, f2fma(S, GY, f2mul(RAD, DY)));
-            GPZ = f2sub(GPZ, f2fma(S, GZ, f2mul(RAD, DZ)));
-            GR = f2fma(AD, sel2(c0, c1, f2fma(DSDR, CF, DSLJDRR), DSLJDRR), GR);
-            GE = f2fma(AD, SLJ, GE);
-            CC = f2fma(AD, Cv, CC);
-            if (kQuad) {
-                // Phi = A delta - 6 dz r^-5 z_hat, A = 15 dz^2 r^-7 - 3 r^-5 (cut off at rc)
-                const bool q0 = !kCutoff || R2v.x < rc2, q1 = !kCutoff || R2v.y < rc2;
-                const float2 z = make_float2(0.f, 0.f);
-                const float2 IR5 = f2mul(f2mul(IR2, IR2), RS), IR7 = f2mul(IR5, IR2), DZ2 = f2mul(DZ, DZ);
-                const float2 Aq = sel2(q0, q1, f2fma(f2mul(make_float2(15.f, 15.f), DZ2), IR7, f2mul(M3, IR5)), z);
-                const float2 A6 = sel2(q0, q1, f2mul(make_float2(6.f, 6.f), f2mul(DZ, IR5)), z);
-                CQ = f2fma(Aq, AD, f2fma(f2mul(make_float2(-1.f, -1.f), A6), GZ, CQ));  // a . Phi
-                // a . dPhi/dr at fixed delta, and the z row of a^T dPhi/d delta at fixed r
-                const float2 W = sel2(q0, q1,
-                                      f2mul(RS, f2fma(f2fma(f2mul(make_float2(-105.f, -105.f), DZ2), IR7,
-                                                            f2mul(make_float2(15.f, 15.f), IR5)),
-                                                      AD, f2mul(f2mul(make_float2(30.f, 30.f), DZ), f2mul(IR5, GZ)))),
-                                      z);
-                const float2 ZROW = sel2(q0, q1,
-                                         f2fma(f2mul(make_float2(30.f, 30.f), f2mul(DZ, IR7)), AD,
-                                               f2mul(f2mul(M6, IR5), GZ)),
-                                         z);
-                const float2 WR = sel2(c0, c1, z, f2mul(W, RS));  // r follows delta unless floored
-                const float2 MK = make_float2(-kqq, -kqq);
-                GPX = f2fma(MK, f2fma(Aq, GX, f2mul(WR, DX)), GPX);
-                GPY = f2fma(MK, f2fma(Aq, GY, f2mul(WR, DY)), GPY);
-                GPZ = f2fma(MK, f2fma(Aq, GZ, f2fma(WR, DZ, ZROW)), GPZ);
-                GR = sel2(c0, c1, f2fma(make_float2(kqq * P.core_frac, kqq * P.core_frac), W, GR), GR);
-            }
+            // kFar: both nodes lie at or beyond coul_rc from every live lane's atom (a warp vote), so
+            // each in-range test below is false and is taken as such: the cut point-charge and
+            // quadrupole terms become the zeros they select, and their arithmetic drops out
+            auto pair = [&](auto far_t) {
+                constexpr bool kFar = decltype(far_t)::value;
+                auto in_rc = [&](float r2v) { return !kFar && r2v < rc2; };
+                const float2 RS = make_float2(rsqrtf(R2v.x), rsqrtf(R2v.y));
+                const float2 IR2 = f2mul(RS, RS);
+                const float2 U = f2mul(RR2, IR2);
+                const float2 S6 = f2mul(f2mul(U, U), U);
+                const float2 S12 = f2mul(S6, S6);
+                const float2 SLJ = f2mul(f2mul(TWELVE, f2sub(S12, S6)), IR2);                 // LJ S per unit e_iPP
+                const float2 DSLJDR = f2mul(f2mul(E12, f2fma(EIGHT, S6, f2mul(M14, S12))), f2mul(IR2, RS));
+                const float2 DSLJDRR = f2mul(f2mul(E12R, f2fma(TWELVE, S12, f2mul(M6, S6))), IR2);
+                float2 Cv, DC;
+                if (kCutoff) {
+                    const bool i0 = in_rc(R2v.x), i1 = in_rc(R2v.y);
+                    const float2 z = make_float2(0.f, 0.f);
+                    Cv = sel2(i0, i1, f2mul(RS, f2sub(IR2, make_float2(irc2, irc2))), z);     // 1/r^3 - 1/(r rc^2)
+                    DC = sel2(i0, i1, f2mul(IR2, f2fma(M3, IR2, make_float2(irc2, irc2))), z);  // -3/r^4 + 1/(r^2 rc^2)
+                } else {
+                    Cv = f2mul(RS, IR2);
+                    DC = f2mul(M3, f2mul(IR2, IR2));
+                }
+                const float2 S = f2fma(EIJ, SLJ, f2mul(QQ, Cv));
+                const float2 DSDR = f2fma(QQ, DC, DSLJDR);
+                const float2 AD = f2fma(GX, DX, f2fma(GY, DY, f2mul(GZ, DZ)));
+                const float2 RAD = sel2(c0, c1, make_float2(0.f, 0.f), f2mul(f2mul(DSDR, AD), RS));  // dS/dr (a.delta)/r
+                GPX = f2sub(GPX, f2fma(S, GX, f2mul(RAD, DX)));
+                GPY = f2sub(GPY, f2fma(S, GY, f2mul(RAD, DY)));
+                GPZ = f2sub(GPZ, f2fma(S, GZ, f2mul(RAD, DZ)));
+                GR = f2fma(AD, sel2(c0, c1, f2fma(DSDR, CF, DSLJDRR), DSLJDRR), GR);
+                GE = f2fma(AD, SLJ, GE);
+                CC = f2fma(AD, Cv, CC);
+                if (kQuad) {
+                    // Phi = A delta - 6 dz r^-5 z_hat, A = 15 dz^2 r^-7 - 3 r^-5 (cut off at rc)
+                    const bool q0 = !kCutoff || in_rc(R2v.x), q1 = !kCutoff || in_rc(R2v.y);
+                    const float2 z = make_float2(0.f, 0.f);
+                    const float2 IR5 = f2mul(f2mul(IR2, IR2), RS), IR7 = f2mul(IR5, IR2), DZ2 = f2mul(DZ, DZ);
+                    const float2 Aq = sel2(q0, q1, f2fma(f2mul(make_float2(15.f, 15.f), DZ2), IR7, f2mul(M3, IR5)), z);
+                    const float2 A6 = sel2(q0, q1, f2mul(make_float2(6.f, 6.f), f2mul(DZ, IR5)), z);
+                    CQ = f2fma(Aq, AD, f2fma(f2mul(make_float2(-1.f, -1.f), A6), GZ, CQ));  // a . Phi
+                    // a . dPhi/dr at fixed delta, and the z row of a^T dPhi/d delta at fixed r
+                    const float2 W = sel2(q0, q1,
+                                          f2mul(RS, f2fma(f2fma(f2mul(make_float2(-105.f, -105.f), DZ2), IR7,
+                                                                f2mul(make_float2(15.f, 15.f), IR5)),
+                                                          AD, f2mul(f2mul(make_float2(30.f, 30.f), DZ), f2mul(IR5, GZ)))),
+                                          z);
+                    const float2 ZROW = sel2(q0, q1,
+                                             f2fma(f2mul(make_float2(30.f, 30.f), f2mul(DZ, IR7)), AD,
+                                                   f2mul(f2mul(M6, IR5), GZ)),
+                                             z);
+                    const float2 WR = sel2(c0, c1, z, f2mul(W, RS));  // r follows delta unless floored
+                    const float2 MK = make_float2(-kqq, -kqq);
+                    GPX = f2fma(MK, f2fma(Aq, GX, f2mul(WR, DX)), GPX);
+                    GPY = f2fma(MK, f2fma(Aq, GY, f2mul(WR, DY)), GPY);
+                    GPZ = f2fma(MK, f2fma(Aq, GZ, f2fma(WR, DZ, ZROW)), GPZ);
+                    GR = sel2(c0, c1, f2fma(make_float2(kqq * P.core_frac, kqq * P.core_frac), W, GR), GR);
+                }
+            };
+            if (kCutoff && __all_sync(live, R2v.x >= rc2 && R2v.y >= rc2)) pair(std::true_type{});
+            else pair(std::false_type{});
         }
         const float gpx = GPX.x + GPX.y, gpy = GPY.x + GPY.y, gpz = GPZ.x + GPZ.y;
         const float gRr = GR.x + GR.y, ge = GE.x + GE.y, C = CC.x + CC.y, Cq = CQ.x + CQ.y;
