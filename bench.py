@@ -65,8 +65,9 @@ FP32_LANES_PER_SM = 128
 # taken on (same hash rule as TRAFFIC): the FP32 operations K1 executes per node-atom pair
 # (sm__sass_thread_inst_executed_op_{fadd,fmul,ffma}_pred_on, FFMA counted twice, over the pairs of
 # the launch) and the issue-active fraction of K2 (smsp__issue_active.avg.pct_of_peak_sustained_active).
-EXECUTED = {
-    "ff_forces": {"value": 18.69, "sha": "99618f336fa803b5", "files": ["ff_assemble.cu", "ff_core.cuh", "interp.cuh"]},
+EXECUTED = {  # per z-nodes-per-thread launch shape (16 computes the 200-node columns as 13 x 16 = 208)
+    "ff_forces": {"value": {8: 18.69, 16: 19.10}, "sha": "99618f336fa803b5",
+                  "files": ["ff_assemble.cu", "ff_core.cuh", "interp.cuh"]},
     "ff_energy": {"value": None, "sha": None, "files": ["ff_assemble.cu", "ff_core.cuh", "interp.cuh"]},
 }
 ISSUE = {
@@ -84,9 +85,11 @@ def _src_hash(files):
     return h.hexdigest()[:16]
 
 
-def executed_ff_flops(energy):
+def executed_ff_flops(energy, zpt=8):
     t = EXECUTED["ff_energy" if energy else "ff_forces"]
-    return t["value"] if t["sha"] == _src_hash(t["files"]) else None
+    if t["value"] is None or t["sha"] != _src_hash(t["files"]):
+        return None
+    return t["value"].get(int(zpt))
 
 
 def measured_issue(kernel):
@@ -1140,13 +1143,14 @@ def main():
     alu_peak = fp32_peak_tflops(sm_max, sms)
     alu_src = f"{sms} SMs (read from the device) x 128 FP32 lanes x 2 x {sm_max:.0f} MHz ({src} max SM clock)"
     rx_gbs = it_total * BYTES_PER_FIRE_ITER / (rx_ms * 1e-3) / 1e9
-    executed = executed_ff_flops(args.ff_energy)
+    ff_zpt = int(tuning["ff_zpt"]) if tuning is not None else 8
+    executed = executed_ff_flops(args.ff_energy, ff_zpt)
     kernels = {
         "ff_assemble": {"ms": ff_ms, "share": ff_ms / (ff_ms + rx_ms), "pair_evals_per_s": pairs / (ff_ms * 1e-3),
                         "flops_per_pair": flops_pair, "energy": bool(args.ff_energy),
                         "traffic": measured_traffic("ff_assemble") if not args.ff_energy else None,
                         "achieved_tflops": ff_tflops, "peak_tflops": alu_peak, "frac": ff_tflops / alu_peak,
-                        "executed_flops_per_pair": executed,
+                        "executed_flops_per_pair": executed, "ff_zpt": ff_zpt,
                         "executed_frac": (pairs * executed / (ff_ms * 1e-3) / 1e12 / alu_peak) if executed else None,
                         "note": "frac counts the algorithmic flops per pair (the number the >= 50 % target is stated "
                                 "in); executed_frac counts the FP32 operations the kernel executes, from ncu's "
