@@ -178,9 +178,20 @@ cudaError_t launch_ff_assemble(const FFLaunch& L, cudaStream_t s) {
         });
         return cudaGetLastError();
     }
-    if (L.zpt == 4) return launch_zpt<4>(L, s);
-    if (L.zpt == 16) return launch_zpt<16>(L, s);
-    return launch_zpt<8>(L, s);
+    // A column's last z-block would compute zpt - r nodes past the range when the layer count is not a
+    // multiple of zpt (nz = 200 at 16: 13 x 16 = 208, 4 % of the arithmetic); those r layers go to a
+    // second launch of a narrower shape instead (each node's sums are the same in every shape).
+    const int zpt = (L.zpt == 4 || L.zpt == 16) ? L.zpt : 8;
+    const int n = L.kend - L.kbeg, bulk = n - n % zpt, r = n - bulk;
+    FFLaunch head = L, tail = L;
+    head.kend = L.kbeg + bulk;
+    tail.kbeg = L.kbeg + bulk;
+    if (bulk > 0) {
+        const cudaError_t e = zpt == 4 ? launch_zpt<4>(head, s) : zpt == 16 ? launch_zpt<16>(head, s) : launch_zpt<8>(head, s);
+        if (e != cudaSuccess) return e;
+    }
+    if (r > 0) return r > 4 ? launch_zpt<8>(tail, s) : launch_zpt<4>(tail, s);
+    return cudaSuccess;
 }
 
 PP_CHECK_READER(check_flags_ff_assemble)
