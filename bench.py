@@ -45,28 +45,30 @@ TRAFFIC = {
                    "files": ["relax_scan.cu", "relax_core.cuh", "interp.cuh"]},
     "relax_scan_tricubic": {"bytes": 24.60e6, "sha": "65e56d7ba4e85d47",
                             "files": ["relax_scan.cu", "relax_core.cuh", "interp.cuh"]},
-    "ff_assemble": {"bytes": 148.24e6, "sha": "99618f336fa803b5",
+    "ff_assemble": {"bytes": 148.45e6, "bytes_zpt16": 139.83e6, "sha": "82384c014f2b4572",
                     "files": ["ff_assemble.cu", "ff_core.cuh", "interp.cuh"]},
-    "ff_assemble_quad": {"bytes": 148.63e6, "sha": "99618f336fa803b5",
+    "ff_assemble_quad": {"bytes": 148.68e6, "sha": "82384c014f2b4572",
                          "files": ["ff_assemble.cu", "ff_core.cuh", "interp.cuh"]},
-    "ff_assemble_split": {"bytes": 357.02e6, "sha": "99618f336fa803b5",
+    "ff_assemble_split": {"bytes": 357.10e6, "sha": "82384c014f2b4572",
                           "files": ["ff_assemble.cu", "ff_core.cuh", "interp.cuh"]},
-    "ff_combine": {"bytes": 600.94e6, "sha": "99618f336fa803b5",
+    "ff_combine": {"bytes": 600.65e6, "sha": "82384c014f2b4572",
                    "files": ["ff_assemble.cu", "ff_core.cuh", "interp.cuh"]},
 }
 
 
-def measured_traffic(kernel):
+def measured_traffic(kernel, zpt=8):
     t = TRAFFIC[kernel]
-    return t["bytes"] if _src_hash(t["files"]) == t["sha"] else None
+    if _src_hash(t["files"]) != t["sha"]:
+        return None
+    return t.get("bytes_zpt16") if int(zpt) == 16 and kernel == "ff_assemble" else t["bytes"]
 FP32_LANES_PER_SM = 128
 
 # Figures from single-kernel ncu captures summarised in profiles/, valid for the sources they were
 # taken on (same hash rule as TRAFFIC): the FP32 operations K1 executes per node-atom pair
 # (sm__sass_thread_inst_executed_op_{fadd,fmul,ffma}_pred_on, FFMA counted twice, over the pairs of
 # the launch) and the issue-active fraction of K2 (smsp__issue_active.avg.pct_of_peak_sustained_active).
-EXECUTED = {  # per z-nodes-per-thread launch shape (16 computes the 200-node columns as 13 x 16 = 208)
-    "ff_forces": {"value": {8: 18.69, 16: 19.10}, "sha": "99618f336fa803b5",
+EXECUTED = {  # per z-nodes-per-thread launch shape (16: a bulk launch of 12 x 16 layers and a tail of 8)
+    "ff_forces": {"value": {8: 18.69, 16: 18.37}, "sha": "82384c014f2b4572",
                   "files": ["ff_assemble.cu", "ff_core.cuh", "interp.cuh"]},
     "ff_energy": {"value": None, "sha": None, "files": ["ff_assemble.cu", "ff_core.cuh", "interp.cuh"]},
 }
@@ -1148,7 +1150,7 @@ def main():
     kernels = {
         "ff_assemble": {"ms": ff_ms, "share": ff_ms / (ff_ms + rx_ms), "pair_evals_per_s": pairs / (ff_ms * 1e-3),
                         "flops_per_pair": flops_pair, "energy": bool(args.ff_energy),
-                        "traffic": measured_traffic("ff_assemble") if not args.ff_energy else None,
+                        "traffic": measured_traffic("ff_assemble", ff_zpt) if not args.ff_energy else None,
                         "achieved_tflops": ff_tflops, "peak_tflops": alu_peak, "frac": ff_tflops / alu_peak,
                         "executed_flops_per_pair": executed, "ff_zpt": ff_zpt,
                         "executed_frac": (pairs * executed / (ff_ms * 1e-3) / 1e12 / alu_peak) if executed else None,
@@ -1177,7 +1179,7 @@ def main():
     dom = "ff_assemble" if ff_ms >= rx_ms else "relax_scan"
     if dom == "ff_assemble":
         roof = {"kernel": "ff_assemble", "bound": "alu", "achieved": ff_tflops, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": ff_tflops / alu_peak, "traffic": measured_traffic("ff_assemble"), "peak_source": alu_src}
+                "frac": ff_tflops / alu_peak, "traffic": measured_traffic("ff_assemble", ff_zpt), "peak_source": alu_src}
     else:
         roof = {"kernel": "relax_scan", "bound": "l2", "achieved": rx_gbs, "peak": l2["peak_gbs"], "unit": "GB/s",
                 "frac": rx_gbs / l2["peak_gbs"], "traffic": measured_traffic("relax_scan"),
