@@ -1221,7 +1221,7 @@ def main():
                     "per_step_synchronised_note": "Simulator.run_host, one image at a time, host-timed, on the "
                                                   "schedule its first calls picked (run_host_schedule)",
                     "run_host_schedule": sim._mode},
-            "gpu_launches": 2 * args.steps, "clocks": clk, "wall_s_timed": t_wall,
+            "gpu_launches": (2 + (case["grid"]["nz"] % ff_zpt != 0)) * args.steps, "clocks": clk, "wall_s_timed": t_wall,
             "device": {"sm_count": sms, "l2": l2}}
     if tuning is not None:
         line["autotune"] = tuning
