@@ -168,3 +168,28 @@ def test_forces_only_on_a_bricked_grid():
     a, b = full.view(-1, 4), forces.view(-1, 4)
     assert torch.isfinite(b).all()
     assert torch.equal(a[:, :3], b[:, :3]) and torch.count_nonzero(b[:, 3]).item() == 0
+
+
+@pytest.mark.parametrize("variant", ["plain", "min_image_cutoff"])
+def test_every_launch_shape_writes_the_same_grid(variant):
+    # 4, 8 or 16 z-nodes per thread, the last z-block of a column ragged for all three (29 layers; at
+    # 16 the last 13 go to a tail launch), the whole grid or a layer range: the same bits
+    c = case32(synth.small_case(seed=16, n_atoms=13, nxy=34, nz=29))
+    if variant == "min_image_cutoff":
+        c["probe"] = dict(synth.default_probe(coul_rc=3.0, min_image=1), Q=c["probe"]["Q"])
+        c = case32(c)
+    grid = pp.make_grid(c["grid"], 0)
+    atoms, probe = pp.make_atoms(afm.atoms_to_device(c["atoms"])), pp.make_probe(c["probe"])
+    grids = {}
+    for zpt in (4, 8, 16):
+        g = torch.full((pp.pp_ff_floats(grid),), float("nan"), dtype=torch.float32, device="cuda")
+        pp.pp_make_ff_tuned(atoms, probe, grid, g, pp.Tuning(zpt, 1))
+        grids[zpt] = g
+        part = torch.full_like(g, float("nan"))
+        pp.pp_make_ff_layers(atoms, probe, grid, part, 3, 26, pp.Tuning(zpt, 1))
+        torch.cuda.synchronize()
+        n = c["grid"]["nx"] * c["grid"]["ny"] * 4
+        assert torch.equal(part[3 * n:26 * n], g[3 * n:26 * n]), zpt
+        assert torch.isnan(part[:3 * n]).all() and torch.isnan(part[26 * n:]).all()
+    assert torch.isfinite(grids[8]).all()
+    assert torch.equal(grids[4], grids[8]) and torch.equal(grids[16], grids[8])
