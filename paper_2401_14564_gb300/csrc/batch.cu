@@ -173,10 +173,11 @@ __device__ __forceinline__ void add_release(int* p, int v) {
     asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-template <int kZPT, bool kMinImage, bool kCutoff, bool kQuad, bool kForcesOnly>
+// kZC: z-nodes computed (kZPT, or kZPT / 2 for a column's last tile when that many remain)
+template <int kZPT, bool kMinImage, bool kCutoff, bool kQuad, bool kForcesOnly, int kZC = kZPT>
 __device__ __forceinline__ void ff_tile(const BatchLaunch& B, const pp_mol_desc& D, long long tile, float4* s0,
                                         float4* s1, float4* s2, float4* s3, int lane) {
-    constexpr int ZP = kZPT / 2;
+    constexpr int ZP = kZC / 2;
     const int fw = 1 << B.fw_sh;
     const long long tx_n = cdiv(D.nx, fw), ty_n = cdiv(D.ny, 32 >> B.fw_sh);
     const int tz = (int)(tile / (tx_n * ty_n));
@@ -240,8 +241,14 @@ __global__ void __launch_bounds__(kThreads, kMinCtas) batch_kernel(const BatchLa
         const long long tile = t - B.seg_start[lo];
         const pp_mol_desc D = B.descs[mol];
         if (ff) {
-            ff_tile<kZPT, kMinImage, kCutoff, kQuad, kForcesOnly>(B, D, tile, st[warp][0], st[warp][1], st[warp][2],
-                                                                   st[warp][3], lane);
+            const long long per_z = cdiv(D.nx, 1 << B.fw_sh) * cdiv(D.ny, 32 >> B.fw_sh);
+            const int k0 = (int)(tile / per_z) * kZPT;
+            if (kZPT == 8 && D.nz - k0 <= 4)
+                ff_tile<kZPT, kMinImage, kCutoff, kQuad, kForcesOnly, 4>(B, D, tile, st[warp][0], st[warp][1],
+                                                                          st[warp][2], st[warp][3], lane);
+            else
+                ff_tile<kZPT, kMinImage, kCutoff, kQuad, kForcesOnly>(B, D, tile, st[warp][0], st[warp][1],
+                                                                       st[warp][2], st[warp][3], lane);
             __syncwarp();
             if (lane == 0) {
                 __threadfence();
